@@ -1,0 +1,320 @@
+"""FilterReg CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, single-threaded C restatement of the registration hot path
+(exact Gaussian E step, reference permutohedral lattice, twist Gauss-Newton M
+step, SE(3) exponential), written from the paper and kept independent of the
+CUDA library: the two share no code, header, constant or helper and neither
+imports the other.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's ``cpu_baseline`` / ``--impl reference`` legs may import this
+package.  The product path never calls it.
+
+This module is argument marshalling only (numpy <-> ctypes); every number is
+computed by the C sources beside it, compiled with ``-ffp-contract=off`` so
+that the float lattice embedding is evaluated exactly as written.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["estep.c", "lattice.c", "se3.c", "rigid.c", "articulated.c"]
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-Wall", "-Wno-unused-function"]
+
+PT2PT, PT2PL = 0, 1
+EXACT, LATTICE = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` with gcc (idempotent)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    deps = srcs + [os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(_LIB_PATH):
+        if os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(d) for d in deps):
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *_CFLAGS, "-o", tmp, *srcs, "-lm"], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_f32p = ctypes.POINTER(ctypes.c_float)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("backend", ctypes.c_int), ("residual", ctypes.c_int), ("blur", ctypes.c_int),
+                ("iters", ctypes.c_int), ("sigma_start", ctypes.c_double),
+                ("sigma_end", ctypes.c_double), ("w", ctypes.c_double),
+                ("renormalize_normals", ctypes.c_int), ("stop_twist", ctypes.c_double)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("iters_run", ctypes.c_int), ("degenerate_iters", ctypes.c_int),
+                ("last_inliers", ctypes.c_int64), ("last_sum_w", ctypes.c_double),
+                ("last_cost", ctypes.c_double), ("last_twist_norm", ctypes.c_double)]
+
+
+def _declare(L):
+    L.or_estep_exact.argtypes = [_f32p, ctypes.c_int64, _f32p, _f32p, ctypes.c_int64,
+                                 ctypes.c_double, _f64p, _f64p, _f64p]
+    L.or_lattice_feature_scale.argtypes = [ctypes.c_float, _f32p]
+    L.or_lattice_embed.argtypes = [_f32p, ctypes.c_int64, ctypes.c_float, _i32p, _f32p, _f32p, _i32p]
+    L.or_lattice_embed.restype = ctypes.c_int
+    L.or_lattice_build.argtypes = [_f32p, _f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_float,
+                                   ctypes.POINTER(ctypes.c_int)]
+    L.or_lattice_build.restype = ctypes.c_void_p
+    L.or_lattice_blur.argtypes = [ctypes.c_void_p]
+    L.or_lattice_slice.argtypes = [ctypes.c_void_p, _f32p, ctypes.c_int64, _f64p]
+    L.or_lattice_slice.restype = ctypes.c_int
+    L.or_lattice_size.argtypes = [ctypes.c_void_p]
+    L.or_lattice_size.restype = ctypes.c_int64
+    L.or_lattice_vdim.argtypes = [ctypes.c_void_p]
+    L.or_lattice_vertices.argtypes = [ctypes.c_void_p, _i32p, _f64p]
+    L.or_lattice_free.argtypes = [ctypes.c_void_p]
+    L.or_kernel_mass.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.or_kernel_mass.restype = ctypes.c_double
+    L.or_sigma_schedule.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, _f32p]
+    L.or_se3_exp.argtypes = [_f64p, _f64p]
+    L.or_se3_log.argtypes = [_f64p, _f64p]
+    L.or_cholesky_solve.argtypes = [ctypes.c_int, _f64p, _f64p, _f64p]
+    L.or_cholesky_solve.restype = ctypes.c_int
+    L.or_point_terms.argtypes = [_f64p, ctypes.c_double, _f64p, _f64p, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p]
+    L.or_point_terms.restype = ctypes.c_int
+    L.or_outlier_constant.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    L.or_outlier_constant.restype = ctypes.c_double
+    L.or_register_rigid.argtypes = [_f32p, ctypes.c_int64, _f32p, _f32p, ctypes.c_int64,
+                                    ctypes.POINTER(_Options), _f64p, ctypes.POINTER(_Report)]
+    L.or_register_rigid.restype = ctypes.c_int
+    L.or_estep.argtypes = [_f32p, ctypes.c_int64, _f32p, _f32p, ctypes.c_int64, ctypes.c_int,
+                           ctypes.c_int, ctypes.c_double, _f64p, _f64p]
+    L.or_estep.restype = ctypes.c_int
+    L.or_align_error.argtypes = [_f32p, ctypes.c_int64, _f64p, _f64p]
+    L.or_align_error.restype = ctypes.c_double
+    if hasattr(L, "or_register_articulated"):
+        _declare_articulated(L)
+
+
+def _pts(a) -> np.ndarray:
+    """Points as a C-contiguous float32 (n, 4) array (a 4th column of zeros is added to (n, 3))."""
+    a = np.asarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] not in (3, 4):
+        raise ValueError("points must have shape (n, 3) or (n, 4)")
+    if a.shape[1] == 3:
+        a = np.concatenate([a, np.zeros((a.shape[0], 1), np.float32)], axis=1)
+    return np.ascontiguousarray(a)
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(status, what):
+    if status != 0:
+        raise OracleError(f"{what}: oracle status {status}")
+
+
+# ---- E step -----------------------------------------------------------------
+
+def estep_exact(X, Y, Yn=None, sigma=0.02):
+    """Exact unnormalised Gaussian sums (Eq. 6, Eq. 9 numerator): M0 (M,), M1 (M,3), Ns (M,3)."""
+    X, Y = _pts(X), _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    M = X.shape[0]
+    M0 = np.zeros(M, np.float64)
+    M1 = np.zeros((M, 3), np.float64)
+    Ns = np.zeros((M, 3), np.float64)
+    _L().or_estep_exact(_p(X, _f32p), M, _p(Y, _f32p), _p(Yn, _f32p), Y.shape[0], float(sigma),
+                        _p(M0, _f64p), _p(M1, _f64p), _p(Ns, _f64p))
+    return M0, M1, (Ns if Yn is not None else None)
+
+
+def estep(X, Y, Yn=None, sigma=0.02, T=None, backend=LATTICE, blur=False):
+    """E-step sums at T*X: (M, 4) [M0, M1] or (M, 7) [M0, M1, Ns] when normals are given."""
+    X, Y = _pts(X), _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    T = np.ascontiguousarray(np.eye(4) if T is None else T, dtype=np.float64)
+    vdim = 7 if Yn is not None else 4
+    out = np.zeros((X.shape[0], vdim), np.float64)
+    _check(_L().or_estep(_p(X, _f32p), X.shape[0], _p(Y, _f32p), _p(Yn, _f32p), Y.shape[0],
+                         backend, int(blur), float(sigma), _p(T, _f64p), _p(out, _f64p)), "estep")
+    return out
+
+
+# ---- lattice ----------------------------------------------------------------
+
+def feature_scale(sigma: float) -> np.ndarray:
+    s = np.zeros(3, np.float32)
+    _L().or_lattice_feature_scale(ctypes.c_float(sigma), _p(s, _f32p))
+    return s
+
+
+def lattice_embed(P, sigma):
+    """Per point: keys (n,4,4) int32 [vertex k][coordinate j], bary (n,4), z (n,4), rank (n,4)."""
+    P = _pts(P)
+    n = P.shape[0]
+    keys = np.zeros((n, 4, 4), np.int32)
+    bary = np.zeros((n, 4), np.float32)
+    z = np.zeros((n, 4), np.float32)
+    rank = np.zeros((n, 4), np.int32)
+    st = _L().or_lattice_embed(_p(P, _f32p), n, ctypes.c_float(sigma), _p(keys, _i32p),
+                               _p(bary, _f32p), _p(z, _f32p), _p(rank, _i32p))
+    return keys, bary, z, rank, st
+
+
+class Lattice:
+    """The reference lattice: a key-sorted vertex array with double values."""
+
+    def __init__(self, P, V, sigma, blur=False):
+        P = _pts(P)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        if V.ndim == 1:
+            V = V[:, None].copy()
+        st = ctypes.c_int(0)
+        self._h = _L().or_lattice_build(_p(P, _f32p), _p(V, _f64p), P.shape[0], V.shape[1],
+                                        ctypes.c_float(sigma), ctypes.byref(st))
+        if not self._h:
+            raise OracleError(f"lattice build failed ({st.value})")
+        self.status = st.value
+        self.vdim = V.shape[1]
+        self.sigma = sigma
+        if blur:
+            _L().or_lattice_blur(self._h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_lattice_free(h)
+            self._h = None
+
+    def __len__(self):
+        return int(_L().or_lattice_size(self._h))
+
+    def slice(self, Q):
+        Q = _pts(Q)
+        out = np.zeros((Q.shape[0], self.vdim), np.float64)
+        st = _L().or_lattice_slice(self._h, _p(Q, _f32p), Q.shape[0], _p(out, _f64p))
+        return out, st
+
+    def vertices(self):
+        nv = len(self)
+        keys = np.zeros((nv, 4), np.int32)
+        vals = np.zeros((nv, self.vdim), np.float64)
+        _L().or_lattice_vertices(self._h, _p(keys, _i32p), _p(vals, _f64p))
+        return keys, vals
+
+
+def kernel_mass(backend=LATTICE, blur=False) -> float:
+    return float(_L().or_kernel_mass(backend, int(blur)))
+
+
+def sigma_schedule(s0, s1, iters) -> np.ndarray:
+    out = np.zeros(max(iters, 1), np.float32)
+    _L().or_sigma_schedule(float(s0), float(s1), int(iters), _p(out, _f32p))
+    return out[:iters]
+
+
+# ---- M step -----------------------------------------------------------------
+
+def se3_exp(zeta) -> np.ndarray:
+    z = np.ascontiguousarray(zeta, dtype=np.float64)
+    T = np.zeros((4, 4), np.float64)
+    _L().or_se3_exp(_p(z, _f64p), _p(T, _f64p))
+    return T
+
+
+def se3_log(T) -> np.ndarray:
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    z = np.zeros(6, np.float64)
+    _L().or_se3_log(_p(T, _f64p), _p(z, _f64p))
+    return z
+
+
+def cholesky_solve(A, b):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    st = _L().or_cholesky_solve(A.shape[0], _p(A, _f64p), _p(b, _f64p), _p(x, _f64p))
+    return (x if st == 0 else None)
+
+
+def point_terms(x, M0, M1, Ns=None, c_eff=0.0, sigma=1.0, residual=PT2PT, renormalize=False):
+    """(W, r (rows,), J (rows, 6)) for one model point; rows = 3 (pt2pt), 1 (pt2pl) or 0."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    M1 = np.ascontiguousarray(M1, dtype=np.float64)
+    Ns = np.ascontiguousarray(np.zeros(3) if Ns is None else Ns, dtype=np.float64)
+    W = np.zeros(1)
+    r = np.zeros(3)
+    J = np.zeros(18)
+    rows = _L().or_point_terms(_p(x, _f64p), float(M0), _p(M1, _f64p), _p(Ns, _f64p),
+                               float(c_eff), float(sigma), int(residual), int(renormalize),
+                               _p(W, _f64p), _p(r, _f64p), _p(J, _f64p))
+    return float(W[0]), r[:rows].copy(), J[:6 * rows].reshape(rows, 6).copy()
+
+
+def outlier_constant(w, N, M, sigma, backend=LATTICE, blur=False) -> float:
+    return float(_L().or_outlier_constant(float(w), int(N), int(M), float(sigma), backend, int(blur)))
+
+
+@dataclass
+class Report:
+    iters_run: int
+    degenerate_iters: int
+    last_inliers: int
+    last_sum_w: float
+    last_cost: float
+    last_twist_norm: float
+
+
+def register_rigid(X, Y, Yn=None, *, sigma=0.02, sigma_end=None, w=0.1, iters=30,
+                   residual=PT2PT, backend=LATTICE, blur=False, renormalize_normals=False,
+                   stop_twist=0.0, T0=None):
+    """Rigid EM registration; returns (T (4,4) float64, Report)."""
+    X, Y = _pts(X), _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    T = np.ascontiguousarray(np.eye(4) if T0 is None else T0, dtype=np.float64).copy()
+    o = _Options(backend, residual, int(blur), int(iters), float(sigma),
+                 float(sigma if sigma_end is None else sigma_end), float(w),
+                 int(renormalize_normals), float(stop_twist))
+    rep = _Report()
+    st = _L().or_register_rigid(_p(X, _f32p), X.shape[0], _p(Y, _f32p), _p(Yn, _f32p), Y.shape[0],
+                                ctypes.byref(o), _p(T, _f64p), ctypes.byref(rep))
+    _check(st, "register_rigid")
+    return T, Report(rep.iters_run, rep.degenerate_iters, rep.last_inliers, rep.last_sum_w,
+                     rep.last_cost, rep.last_twist_norm)
+
+
+def align_error(X, T, Tgt) -> float:
+    """Eq. 22: mean |(T - T_gt) x_ref|."""
+    X = _pts(X)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    Tgt = np.ascontiguousarray(Tgt, dtype=np.float64)
+    return float(_L().or_align_error(_p(X, _f32p), X.shape[0], _p(T, _f64p), _p(Tgt, _f64p)))
+
+
+def _declare_articulated(L):  # filled in by the articulated model
+    pass

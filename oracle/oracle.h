@@ -1,0 +1,137 @@
+/*
+ * FilterReg CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded restatement of what the registration hot path
+ * computes, written from the paper (Gao & Tedrake, "FilterReg", CVPR 2019) and
+ * from the permutohedral-lattice construction it cites (Adams et al. 2010).
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load it.  It shares no code, header, constant or helper with the CUDA
+ * library; the product path never calls it.
+ *
+ * Conventions
+ *   - Point clouds are float[n][4] (x, y, z, unused), the same host layout the
+ *     CUDA library takes, so one seeded array feeds both sides.
+ *   - Poses are double[16], row-major 4x4 homogeneous transforms.
+ *   - Twists are zeta = (omega; v) = (alpha, beta, gamma, a, b, c), rotation
+ *     first, as in the twist linearisation of Section 5 (Eq. 16).
+ *   - Sums of the E and M steps are in double.  The permutohedral embedding
+ *     (elevation, rounding, rank sort, barycentric weights) is evaluated in
+ *     float with no fused multiply-add, in a fixed operation order, because
+ *     those float results decide integer lattice keys.
+ *
+ * Parity status of each function is stated beside it; every function is
+ * pinned by the CPU tests (tests/test_oracle_*.py) against closed forms,
+ * invariants, library routines or brute force, except where marked
+ * "parity unpinned".
+ */
+#ifndef FILTERREG_ORACLE_H
+#define FILTERREG_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_EDEGENERATE = 7 };
+enum { OR_PT2PT = 0, OR_PT2PL = 1 };
+enum { OR_EXACT = 0, OR_LATTICE = 1 };
+
+typedef struct {
+    int backend;             /* OR_EXACT (Eq. 6 summed directly) or OR_LATTICE (Section 4.2) */
+    int residual;            /* OR_PT2PT (Eq. 7) or OR_PT2PL (Eq. 10) */
+    int blur;                /* lattice only: 1 = blur along the 4 lattice axes */
+    int iters;               /* EM iterations, one Gauss-Newton step each */
+    double sigma_start;      /* isotropic kernel std-dev of the first iteration */
+    double sigma_end;        /* of the last; geometric schedule in between */
+    double w;                /* outlier ratio, 0 <= w < 1 (Section 3.1) */
+    int renormalize_normals; /* pt2pl: 1 = unit-normalise N_x (Eq. 9 as written: 0) */
+    double stop_twist;       /* stop once |delta zeta| < stop_twist (0 = never) */
+} or_options;
+
+typedef struct {
+    int iters_run;
+    int degenerate_iters;    /* iterations whose normal matrix was not positive definite */
+    int64_t last_inliers;    /* model points with M0 > 0 in the last iteration */
+    double last_sum_w;       /* sum of outlier weights in the last iteration */
+    double last_cost;        /* sum of squared weighted residuals in the last iteration */
+    double last_twist_norm;  /* |delta zeta| of the last applied update */
+} or_report;
+
+/* ---- exact E step (Eq. 6, Eq. 9 numerator), unnormalised kernel ---------- */
+/* M0[i] = sum_k exp(-|x_i - y_k|^2 / (2 sigma^2)), M1[i] = sum_k (..) y_k,
+ * Ns[i] = sum_k (..) n_k.  Yn may be NULL (then Ns is not written).          */
+void or_estep_exact(const float *X, int64_t M, const float *Y, const float *Yn,
+                    int64_t N, double sigma, double *M0, double *M1, double *Ns);
+/* The same sums at one double-precision position x. */
+void or_exact_sums_at(const double x[3], const float *Y, const float *Yn, int64_t N,
+                      double sigma, double *M0, double M1[3], double Ns[3]);
+
+/* ---- permutohedral lattice, d = 3 (Section 4.2) -------------------------- */
+/* Per-axis float feature scale alpha / sqrt(i (i+1)) / sigma, i = 1..3.       */
+void or_lattice_feature_scale(float sigma, float scale[3]);
+
+/* Embed n points: for each, the 4 vertices of its enclosing simplex as full
+ * 4-coordinate integer keys (keys[i][k][j]), barycentric weights bary[i][k],
+ * elevated coordinates z[i][j] and ranks rank[i][j] (each output nullable).
+ * Returns OR_EINVAL if any coordinate is non-finite or beyond the key range.  */
+int or_lattice_embed(const float *P, int64_t n, float sigma, int32_t *keys,
+                     float *bary, float *z, int32_t *rank);
+
+typedef struct or_lattice or_lattice;
+/* Splat values V (n x vdim, double) of points P at scale sigma. */
+or_lattice *or_lattice_build(const float *P, const double *V, int64_t n, int vdim,
+                             float sigma, int *status);
+void or_lattice_blur(or_lattice *lat);
+/* Slice at m query points: out[i][c] = sum_k b_k table[key_k][c] (0 if absent). */
+int or_lattice_slice(const or_lattice *lat, const float *Q, int64_t m, double *out);
+int64_t or_lattice_size(const or_lattice *lat);
+int or_lattice_vdim(const or_lattice *lat);
+/* Vertex keys (nv x 4, all four coordinates) and values (nv x vdim), key-sorted. */
+void or_lattice_vertices(const or_lattice *lat, int32_t *keys, double *vals);
+void or_lattice_free(or_lattice *lat);
+
+/* Integral of the unnormalised E-step kernel over feature space (unit sigma):
+ * exact Gaussian (2 pi)^{3/2}; lattice splat+slice: volume per lattice vertex
+ * in feature units; times the blur gain 2^4 when blurred.                    */
+double or_kernel_mass(int backend, int blur);
+
+/* Geometric sigma schedule: sigma_k = s0 (s1/s0)^{k/(iters-1)}, rounded to float. */
+void or_sigma_schedule(double s0, double s1, int iters, float *out);
+
+/* ---- M step pieces (Section 5) ------------------------------------------- */
+void or_se3_exp(const double zeta[6], double T[16]);
+void or_se3_log(const double T[16], double zeta[6]);
+/* Solve A x = b for symmetric positive definite A (n x n, row-major) by
+ * Cholesky.  Returns 0 on success, 1 if A is not positive definite.          */
+int or_cholesky_solve(int n, const double *A, const double *b, double *x);
+
+/* One model point's outlier weight, residual and twist Jacobian.
+ * x: current position; M0, M1, Ns: its E-step sums; c_eff: outlier constant in
+ * the kernel's own normalisation.  Returns the number of residual rows (3 for
+ * pt2pt, 1 for pt2pl, 0 if M0 <= 0).  r[rows], J[rows][6] are sqrt(W)/sigma
+ * weighted, so that A = sum J^T J and b = sum J^T r (Eq. 17-18).             */
+int or_point_terms(const double x[3], double M0, const double M1[3], const double Ns[3],
+                   double c_eff, double sigma, int residual, int renormalize,
+                   double *W, double *r, double *J);
+
+/* Outlier constant c = w/(1-w) N/M of Eq. 7, in the unnormalised kernel's
+ * units: c * sigma^3 * G with G = or_kernel_mass(backend, blur).            */
+double or_outlier_constant(double w, int64_t N, int64_t M, double sigma, int backend, int blur);
+
+/* ---- rigid registration driver (EM of Section 3.1, M step of Section 5) --- */
+int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn,
+                      int64_t N, const or_options *opt, double T[16], or_report *rep);
+
+/* E-step sums at the model points moved by T (lattice or exact back end), for
+ * parity of a single E step: out is M x (1 + 3 [+ 3]) = [M0, M1, Ns].        */
+int or_estep(const float *X, int64_t M, const float *Y, const float *Yn, int64_t N,
+             int backend, int blur, double sigma, const double T[16], double *out);
+
+/* Alignment error of Eq. 22: mean |(T - T_gt) x_ref|. */
+double or_align_error(const float *X, int64_t M, const double T[16], const double Tgt[16]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

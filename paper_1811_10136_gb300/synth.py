@@ -1,0 +1,236 @@
+"""Seeded synthetic workloads shaped like the paper's experiments.
+
+The paper's datasets (Stanford Bunny and Lounge, the robot and RGBD sequences)
+are not available, so every input is generated here from a seed.  This module
+holds no arithmetic of the registration method itself (no lattice, no E or M
+step): it only draws point clouds, ground-truth transforms and normals, and it
+imports nothing but numpy.  Both the CUDA path's tests and benchmark and the
+CPU oracle's tests take their inputs from here.
+
+All clouds are float32 arrays of shape (n, 4) (x, y, z, 0): the layout the
+C-ABI takes.  Transforms are float64 (4, 4) row-major with y = T x.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def _pad4(p: np.ndarray) -> np.ndarray:
+    out = np.zeros((p.shape[0], 4), np.float32)
+    out[:, :3] = p
+    return out
+
+
+def random_rotation(rng: np.random.Generator, max_angle_rad: float, exact: bool = False) -> np.ndarray:
+    """Rotation about a uniform axis by an angle U[0, max] (or exactly max)."""
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    ang = max_angle_rad if exact else rng.uniform(0.0, max_angle_rad)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * (K @ K)
+
+
+def make_T(R: np.ndarray, t) -> np.ndarray:
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = t
+    return T
+
+
+def apply_T(T: np.ndarray, P: np.ndarray) -> np.ndarray:
+    return (P[:, :3].astype(np.float64) @ T[:3, :3].T + T[:3, 3])
+
+
+# ---------------------------------------------------------------------------
+# Rigid point-to-point: bumpy sphere (2,000 + 2,000 points)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class RigidPair:
+    X: np.ndarray            # model (M, 4)
+    Y: np.ndarray            # observation (N, 4)
+    T_gt: np.ndarray         # (4, 4): Y ~ T_gt X
+    Yn: np.ndarray | None = None
+    meta: dict = field(default_factory=dict)
+
+
+def _bumpy_sphere_points(rng, n, centres, amp, width):
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    d2 = ((u[:, None, :] - centres[None, :, :]) ** 2).sum(-1)
+    r = 1.0 + amp * np.exp(-d2 / (2 * width * width)).sum(1)
+    return u * r[:, None]
+
+
+def sphere_bumps_pair(seed: int, n_model: int = 2000, n_obs: int = 2000, n_bumps: int = 8,
+                      amp: float = 0.1, width: float = 0.2, max_angle_deg: float = 30.0,
+                      max_trans: float = 0.1, noise: float = 0.005,
+                      outlier_frac: float = 0.1) -> RigidPair:
+    """Unit sphere with Gaussian bumps; the observation is an independent sample
+    of the same surface under a random rigid motion, with isotropic noise and
+    uniform outliers (outlier_frac * n_obs extra points) in its bounding box."""
+    rng = np.random.default_rng(seed)
+    c = rng.normal(size=(n_bumps, 3))
+    c /= np.linalg.norm(c, axis=1, keepdims=True)
+    X = _bumpy_sphere_points(rng, n_model, c, amp, width)
+    Ys = _bumpy_sphere_points(rng, n_obs, c, amp, width)
+    R = random_rotation(rng, math.radians(max_angle_deg))
+    t = rng.uniform(-max_trans, max_trans, size=3)
+    T = make_T(R, t)
+    Y = Ys @ R.T + t + rng.normal(scale=noise, size=Ys.shape)
+    n_out = int(round(outlier_frac * n_obs))
+    if n_out:
+        lo, hi = Y.min(0), Y.max(0)
+        Y = np.concatenate([Y, rng.uniform(lo, hi, size=(n_out, 3))])
+    Y = Y[rng.permutation(Y.shape[0])]
+    return RigidPair(_pad4(X), _pad4(Y), T, None,
+                     {"workload": "sphere_bumps", "seed": seed, "M": n_model, "N": Y.shape[0]})
+
+
+# ---------------------------------------------------------------------------
+# Rigid point-to-plane: ray-cast depth frames of a box/sphere room
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Scene:
+    box_lo: np.ndarray       # (B, 3)
+    box_hi: np.ndarray
+    sph_c: np.ndarray        # (S, 3)
+    sph_r: np.ndarray        # (S,)
+    room: float              # half-size of the room cube
+
+
+def random_scene(rng: np.random.Generator, n_objects: int = 20, room: float = 1.0,
+                 keep_clear: np.ndarray | None = None, clear_radius: float = 0.35) -> Scene:
+    """n_objects random axis-aligned boxes and spheres inside a 2*room cube,
+    none closer than clear_radius to the point keep_clear (the camera)."""
+    keep = np.zeros(3) if keep_clear is None else keep_clear
+    lo, hi, sc, sr = [], [], [], []
+    while len(lo) + len(sc) < n_objects:
+        centre = rng.uniform(-0.8 * room, 0.8 * room, size=3)
+        if rng.uniform() < 0.5:
+            half = rng.uniform(0.05, 0.3, size=3)
+            d = np.maximum(np.abs(keep - centre) - half, 0.0)
+            if np.linalg.norm(d) < clear_radius:
+                continue
+            lo.append(centre - half)
+            hi.append(centre + half)
+        else:
+            r = rng.uniform(0.05, 0.3)
+            if np.linalg.norm(keep - centre) - r < clear_radius:
+                continue
+            sc.append(centre)
+            sr.append(r)
+    return Scene(np.array(lo).reshape(-1, 3), np.array(hi).reshape(-1, 3),
+                 np.array(sc).reshape(-1, 3), np.array(sr), room)
+
+
+def look_at_rotation(rng: np.random.Generator, forward: np.ndarray, jitter_rad: float) -> np.ndarray:
+    """Camera-to-world rotation whose optical (z) axis is `forward` tilted by
+    up to jitter_rad, with a random roll."""
+    z = random_rotation(rng, jitter_rad) @ (forward / np.linalg.norm(forward))
+    a = rng.normal(size=3)
+    x = a - (a @ z) * z
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    return np.stack([x, y, z], 1)
+
+
+def render_depth(scene: Scene, C: np.ndarray, W: int, H: int, fx: float, fy: float,
+                 cx: float, cy: float) -> np.ndarray:
+    """Analytic ray cast from the camera pose C (camera-to-world); returns the
+    depth map (H, W) along the optical axis.  Every ray hits the room."""
+    u, v = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
+    dc = np.stack([(u - cx) / fx, (v - cy) / fy, np.ones_like(u)], -1).reshape(-1, 3)
+    d = dc @ C[:3, :3].T
+    o = C[:3, 3]
+    inv = 1.0 / np.where(np.abs(d) < 1e-12, 1e-12, d)
+    # The room: distance to the far wall of the cube (camera inside).
+    t1 = (-scene.room - o) * inv
+    t2 = (scene.room - o) * inv
+    best = np.maximum(t1, t2).min(1)
+    for lo, hi in zip(scene.box_lo, scene.box_hi):
+        a = (lo - o) * inv
+        b = (hi - o) * inv
+        tn = np.minimum(a, b).max(1)
+        tf = np.maximum(a, b).min(1)
+        hit = (tn <= tf) & (tn > 1e-6)
+        best = np.where(hit & (tn < best), tn, best)
+    for c, r in zip(scene.sph_c, scene.sph_r):
+        oc = o - c
+        bq = d @ oc
+        cq = oc @ oc - r * r
+        aq = (d * d).sum(1)
+        disc = bq * bq - aq * cq
+        ok = disc >= 0
+        tn = (-bq - np.sqrt(np.where(ok, disc, 0.0))) / aq
+        hit = ok & (tn > 1e-6)
+        best = np.where(hit & (tn < best), tn, best)
+    return best.reshape(H, W)  # t along dc, whose z is 1: the depth
+
+
+def backproject(depth: np.ndarray, fx, fy, cx, cy) -> np.ndarray:
+    H, W = depth.shape
+    u, v = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
+    return np.stack([(u - cx) / fx * depth, (v - cy) / fy * depth, depth], -1)
+
+
+def depth_normals(P: np.ndarray) -> np.ndarray:
+    """Per-pixel normals from the cross product of +-1 pixel central differences
+    of the back-projected points (one-sided at the border), facing the camera."""
+    Pp = np.pad(P, ((1, 1), (1, 1), (0, 0)), mode="edge")
+    du = Pp[1:-1, 2:] - Pp[1:-1, :-2]
+    dv = Pp[2:, 1:-1] - Pp[:-2, 1:-1]
+    n = np.cross(du, dv)
+    nn = np.linalg.norm(n, axis=-1, keepdims=True)
+    n = n / np.where(nn > 0, nn, 1.0)
+    flip = (n * P).sum(-1, keepdims=True) > 0
+    return np.where(flip, -n, n)
+
+
+def depth_frame_pair(seed: int, W: int = 320, H: int = 240, fx: float = 300.0, fy: float = 300.0,
+                     n_objects: int = 20, max_angle_deg: float = 2.0, trans: float = 0.02,
+                     depth_noise: float = 0.001, dropout: float = 0.05,
+                     noise_on_model: bool = True) -> RigidPair:
+    """Frame-to-frame tracking pair: X = reference frame (all W*H pixels), Y =
+    the next frame after a random motion (rotation of max_angle_deg about a
+    uniform axis, translation of length trans), both with N(0, depth_noise^2)
+    depth noise; Y loses a random `dropout` fraction of its pixels and carries
+    per-pixel normals.  Points are in each frame's camera coordinates."""
+    rng = np.random.default_rng(seed)
+    cx, cy = (W - 1) / 2.0, (H - 1) / 2.0
+    # Camera 0.75 m from the room's centre, looking at the centre to within
+    # 15 degrees, so that every view holds objects as well as walls.
+    back = rng.normal(size=3)
+    back /= np.linalg.norm(back)
+    cam0 = 0.75 * back
+    scene = random_scene(rng, n_objects, keep_clear=cam0)
+    C0 = make_T(look_at_rotation(rng, -back, math.radians(15.0)), cam0)
+    dR = random_rotation(rng, math.radians(max_angle_deg), exact=True)
+    dt = rng.normal(size=3)
+    dt *= trans / np.linalg.norm(dt)
+    C1 = C0 @ make_T(dR, dt)                      # motion in the camera's own frame
+    T_gt = np.linalg.inv(C1) @ C0                 # camera-0 coordinates -> camera-1
+    d0 = render_depth(scene, C0, W, H, fx, fy, cx, cy)
+    d1 = render_depth(scene, C1, W, H, fx, fy, cx, cy)
+    if noise_on_model:
+        d0 = d0 + rng.normal(scale=depth_noise, size=d0.shape)
+    d1 = d1 + rng.normal(scale=depth_noise, size=d1.shape)
+    P0 = backproject(d0, fx, fy, cx, cy)
+    P1 = backproject(d1, fx, fy, cx, cy)
+    N1 = depth_normals(P1)
+    keep = rng.uniform(size=H * W) >= dropout
+    X = _pad4(P0.reshape(-1, 3))
+    Y = _pad4(P1.reshape(-1, 3)[keep])
+    Yn = _pad4(N1.reshape(-1, 3)[keep])
+    return RigidPair(X, Y, T_gt, Yn, {"workload": "depth_frames", "seed": seed, "W": W, "H": H,
+                                      "M": X.shape[0], "N": Y.shape[0]})
+
+
+def rotation_angle_deg(Ra: np.ndarray, Rb: np.ndarray) -> float:
+    """Angle of Ra Rb^T in degrees (pose comparison helper)."""
+    c = (np.trace(Ra[:3, :3] @ Rb[:3, :3].T) - 1.0) / 2.0
+    return math.degrees(math.acos(max(-1.0, min(1.0, c))))
