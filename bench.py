@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""FilterReg hot-path benchmark: EM iterations per second of rigid
+point-to-plane registration on 320x240 synthetic depth frames (76,800 model
+points, ~72,960 observation points after 5% dropout, sigma annealed
+0.04 -> 0.01 over 20 EM iterations, outlier ratio 0.1).
+
+One step = registering a batch of B frame pairs (B = --frames, default 16),
+i.e. B x 20 EM iterations.  The L2 cache is flushed (256 MiB write) between
+steps; per-step device time is taken with CUDA events on the library's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank registers its own frames (replicas, no
+collective on the data path); the job's value is the frames of all ranks over
+the slowest rank's time.  --impl reference times the CPU oracle (the paper's
+method restated plainly in C, single-threaded) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EM iters/s at 76.8k pts; batched regs/s + p99 latency vs plain, <=0.1 deg err"
+UNIT = "EM iters/s"
+ITERS = 20
+SIGMA0, SIGMA1, W_OUT = 0.04, 0.01, 0.1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=16, help="frame pairs registered per step")
+    ap.add_argument("--seed", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(frames, pairs):
+    Ns = [p.Y.shape[0] for p in pairs]
+    return {
+        "workload": "depth_frames_320x240_pt2pl",
+        "model": "rigid FilterReg, point-to-plane, permutohedral E step (splat+slice)",
+        "points_per_frame": 76800,
+        "M": int(pairs[0].X.shape[0]),
+        "N_mean": int(round(sum(Ns) / len(Ns))),
+        "frames_per_step": frames,
+        "em_iters": ITERS,
+        "sigma": f"{SIGMA0}->{SIGMA1} geometric",
+        "w": W_OUT,
+        "blur": False,
+        "l2": "flushed between steps (256 MiB write)",
+        "global_batch": frames,
+        "parallelism": "replicas",
+    }
+
+
+def make_pairs(seed, n):
+    from paper_1811_10136_gb300 import synth
+    return [synth.depth_frame_pair(seed + i) for i in range(n)]
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.rows = []
+        self.proc = None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "lattice.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1811_10136_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was captured from the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic_depth320.txt")
+    try:
+        rows = dict(line.split(":", 1) for line in open(path) if ":" in line and not line.startswith("#"))
+    except OSError:
+        return None
+    rows = {k.strip(): v.strip() for k, v in rows.items()}
+    if rows.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    v = rows.get(f"{kernel}_dram_bytes_per_launch")
+    return float(v) if v else None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1811_10136_gb300 as fr
+    from paper_1811_10136_gb300 import synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    pairs = make_pairs(args.seed + 7919 * rank, args.frames)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    dX = [dev(p.X) for p in pairs]
+    dY = [dev(p.Y) for p in pairs]
+    dN = [dev(p.Yn) for p in pairs]
+    ctx = fr.Context(local)
+    opts = dict(residual=fr.FR_PT2PL, iters=ITERS, sigma_start=SIGMA0, sigma_end=SIGMA1, w=W_OUT)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(record=None):
+        poses = []
+        for j in range(args.frames):
+            T, rep = ctx.register_rigid(dX[j], dY[j], dN[j], **opts)
+            poses.append((T, rep))
+        return poses
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+
+    # ---- timed region: K steps, device time per step by CUDA events -------
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ctx.kernel_launches
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        last = None
+        for k in range(args.steps):
+            flush.fill_(1.0)
+            starts[k].record(stream)
+            last = step()
+            ends[k].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    launches = ctx.kernel_launches - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1000.0
+    if dist:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    em_iters_all = ITERS * args.frames * args.steps * ws
+    value = em_iters_all / total_s
+
+    # accuracy of the timed results against the planted motion
+    rot_err = max(synth.rotation_angle_deg(T, p.T_gt) for (T, _), p in zip(last, pairs))
+    trans_err = max(float(np.linalg.norm(T[:3, 3] - p.T_gt[:3, 3])) for (T, _), p in zip(last, pairs))
+    reps = [r for _, r in last]
+    v_mean = sum(r.lattice_vertices_sum for r in reps) / max(1, sum(r.lattice_builds for r in reps))
+
+    # ---- per-kernel durations (event pairs inside the graph), K steps -----
+    ctx.set_profiling(True)
+    step()                              # capture the profiled graph
+    ctx.profile(reset=True)
+    for k in range(args.steps):
+        flush.fill_(1.0)
+        step()
+    prof = ctx.profile(reset=True)
+    ctx.set_profiling(False)
+    M = pairs[0].X.shape[0]
+    N_mean = sum(p.Y.shape[0] for p in pairs) / len(pairs)
+    algo = {  # algorithmic bytes per launch (each array touched once, float32)
+        "rigid_step": 12.0 * M + 36.0 * v_mean,
+        "build_splat": 24.0 * N_mean + 36.0 * v_mean,
+    }
+    per_launch_ms = {k: (ms / n if n else 0.0) for k, (n, ms) in prof.items()}
+    dominant = max(("rigid_step", "build_splat"), key=lambda k: prof[k][1])
+    peak, peak_kind = measured_peaks()
+    achieved = algo[dominant] / (per_launch_ms[dominant] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": f"{peak_kind} HBM copy GB/s", "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": recorded_traffic(dominant),
+                "algorithmic_bytes_per_launch": round(algo[dominant]),
+                "launch_us": round(per_launch_ms[dominant] * 1e3, 2),
+                "per_kernel_us": {k: round(v * 1e3, 2) for k, v in per_launch_ms.items() if prof[k][0]},
+                "lattice_vertices_mean": round(v_mean)}
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    e2e = None
+    if not args.no_e2e:
+        hX = [torch.from_numpy(p.X).pin_memory() for p in pairs]
+        hY = [torch.from_numpy(p.Y).pin_memory() for p in pairs]
+        hN = [torch.from_numpy(p.Yn).pin_memory() for p in pairs]
+        for j in range(args.frames):
+            ctx.register_rigid_host(hX[j], hY[j], hN[j], **opts)
+        b0 = ctx.transfer_bytes()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            for j in range(args.frames):
+                ctx.register_rigid_host(hX[j], hY[j], hN[j], **opts)
+        barrier()
+        te = time.perf_counter() - t0
+        b1 = ctx.transfer_bytes()
+        if dist:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": round(em_iters_all / te, 1), "unit": UNIT,
+               "h2d_bytes_per_step": (b1[0] - b0[0]) // args.steps,
+               "d2h_bytes_per_step": (b1[1] - b0[1]) // args.steps,
+               "timing": "host wall clock around fr_register_rigid_host calls (pinned inputs)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pairs[0])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ray-cast depth frames)",
+            "config": workload_config(args.frames, pairs),
+            "registrations_per_s": round(args.frames * args.steps * ws / total_s, 1),
+            "accuracy": {"max_rot_err_deg_vs_truth": round(rot_err, 4),
+                         "max_trans_err_vs_truth": round(trans_err, 6)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "wall_s_timed_region": round(t_wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(pair, budget_s=15.0):
+    """The oracle as it stands, single-threaded, on full registrations of one
+    frame pair until about budget_s of CPU work."""
+    import oracle
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.register_rigid(pair.X, pair.Y, pair.Yn, sigma=SIGMA0, sigma_end=SIGMA1, w=W_OUT, iters=ITERS,
+                              residual=oracle.PT2PL, backend=oracle.LATTICE)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s * 0.6 or n >= 20:
+            break
+    return {"value": round(n * ITERS / el, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full {ITERS}-iteration registrations of one 320x240 frame pair ({el:.1f} s)"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    pair = make_pairs(args.seed, 1)[0]
+    # One step = one registration (20 EM iterations); shortened when K is large
+    # so that the whole run stays within a few minutes.
+    est = 1.8
+    iters = ITERS if (args.steps + args.warmup) * est <= 150 else max(2, int(ITERS * 150 / ((args.steps + args.warmup) * est)))
+
+    def step():
+        oracle.register_rigid(pair.X, pair.Y, pair.Yn, sigma=SIGMA0, sigma_end=SIGMA1 if iters == ITERS else
+                              SIGMA0 * (SIGMA1 / SIGMA0) ** ((iters - 1) / (ITERS - 1)), w=W_OUT, iters=iters,
+                              residual=oracle.PT2PL, backend=oracle.LATTICE)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = iters * args.steps / el
+    cfg = workload_config(1, [pair])
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded ray-cast depth frames)", "config": cfg,
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {iters} EM iterations of one 320x240 pair"},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * filterreg.h -- C ABI of the GB300 (sm_103a) FilterReg hot path.
+ *
+ * FilterReg (Gao & Tedrake, CVPR 2019) registers a model cloud X (M points,
+ * moved by the motion parameters) to an observation cloud Y (N points, fixed)
+ * by EM on a Gaussian mixture induced by Y (Section 3.1).  The E step is
+ * computed as Gaussian filtering on a permutohedral lattice built over Y
+ * (Section 4), the M step as Gauss-Newton over twists (Section 5).
+ *
+ * Conventions shared by every entry point
+ *   - Point clouds are float32 arrays of n rows of 4 floats (x, y, z, unused),
+ *     16-byte aligned, row-major ("n x 4").  Normals use the same layout.
+ *   - Pointers named d_* are DEVICE pointers on the context's device; h_*
+ *     are host pointers (pinned host memory makes their copies asynchronous).
+ *     The caller owns every buffer it passes; the library never frees them
+ *     and keeps no reference after the call returns.
+ *   - Poses are host double[16], row-major 4x4 homogeneous transforms with
+ *     x_moved = T x; T_inout carries the initial guess in and the result out.
+ *   - Twists are zeta = (omega; v) = (alpha, beta, gamma, a, b, c), rotation
+ *     first, as in the twist matrix of Eq. 16.
+ *   - Every call returns an fr_status, never aborts and never traps; a
+ *     human-readable reason for the last failure is in fr_ctx_last_error().
+ *     Device-side failures (hash overflow, out-of-range coordinates) are
+ *     recorded in device flags and mapped to a status when the call returns.
+ *   - Work is issued on the context's CUDA stream; every call that launches
+ *     work synchronises that stream before it returns (so that device-side
+ *     error flags are reported by the call that raised them).
+ *   - Handles (fr_ctx, fr_lattice) are owned by the library and released by
+ *     the matching *_destroy call.  A context must be used by one host thread
+ *     at a time.
+ */
+#ifndef FILTERREG_H
+#define FILTERREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FR_API __attribute__((visibility("default")))
+#else
+#define FR_API
+#endif
+
+typedef enum {
+    FR_OK = 0,
+    FR_EINVAL = 1,         /* bad argument: null pointer, size < 1, sigma <= 0, w outside [0,1),
+                              non-finite input, coordinate beyond the lattice key range */
+    FR_ENOMEM = 2,         /* device or pinned-host allocation failed */
+    FR_ECUDA = 3,          /* a CUDA runtime call failed (message in fr_ctx_last_error) */
+    FR_ECAPACITY = 4,      /* lattice hash table full (capacity_hint too small) */
+    FR_ETIMEOUT = 5,       /* a bounded device-side wait expired */
+    FR_ENOTSUPPORTED = 6   /* option combination not implemented */
+} fr_status;
+
+typedef enum { FR_PT2PT = 0, FR_PT2PL = 1 } fr_residual;
+typedef enum { FR_FP32 = 0, FR_BF16 = 1, FR_FP16 = 2 } fr_storage;
+
+typedef struct fr_ctx fr_ctx;
+typedef struct fr_lattice fr_lattice;
+
+/* Options of one registration.  fr_options_default() fills the defaults in
+ * brackets. */
+typedef struct {
+    int32_t residual;           /* FR_PT2PT: Eq. 7; FR_PT2PL: Eq. 9-10            [PT2PT] */
+    int32_t blur;               /* 1 = blur the lattice along its 4 axes before
+                                   slicing (Section 4.2 "Blur"); 0 = splat+slice [0]   */
+    int32_t iters;              /* EM iterations, one Gauss-Newton step each     [30]  */
+    float sigma_start;          /* kernel std-dev of the first iteration          [0.02]*/
+    float sigma_end;            /* of the last; geometric schedule in between;
+                                   equal to sigma_start = fixed sigma, lattice built
+                                   once (Section 3.2)                              [0.02]*/
+    float w;                    /* outlier ratio of Section 3.1, 0 <= w < 1       [0.1] */
+    int32_t storage;            /* lattice value storage: FR_FP32, FR_BF16, FR_FP16 [FP32]*/
+    int32_t kahan;              /* 1 = Kahan-compensated float partial sums       [0]   */
+    int32_t renormalize_normals;/* pt2pl: unit-normalise N_x of Eq. 9             [0]   */
+    float stop_twist;           /* stop once |delta zeta| < stop_twist (Section 6.1's
+                                   termination); 0 = run all iterations           [0]   */
+    int32_t use_graph;          /* replay the EM loop as one CUDA graph           [1]   */
+} fr_options;
+
+/* Per-call diagnostics (all nullable where passed). */
+typedef struct {
+    int32_t iters_run;          /* EM iterations executed */
+    int32_t degenerate_iters;   /* iterations whose 6x6 normal matrix was not positive
+                                   definite (pose left unchanged that iteration) */
+    int64_t last_inliers;       /* model points with M0 > 0 in the last iteration */
+    double last_sum_w;          /* sum of outlier weights M0/(M0+c), last iteration */
+    double last_cost;           /* sum of squared weighted residuals, last iteration */
+    double last_twist_norm;     /* |delta zeta| of the last applied update */
+    int64_t lattice_vertices;   /* vertices of the last lattice built */
+    int32_t lattice_builds;     /* lattices built during the call (1, or one per sigma) */
+    int64_t lattice_vertices_sum; /* vertices summed over those builds */
+} fr_report;
+
+/* Kernel classes of the per-kernel profile. */
+enum { FR_K_CLEAR = 0, FR_K_BUILD = 1, FR_K_BLUR = 2, FR_K_STEP = 3, FR_K_CLASSES = 4 };
+typedef struct {
+    int64_t launches[FR_K_CLASSES]; /* kernels of each class timed since the last reset */
+    double total_ms[FR_K_CLASSES];  /* their summed durations (CUDA events) */
+} fr_profile;
+
+FR_API void fr_options_default(fr_options *opt);
+FR_API const char *fr_status_string(fr_status s);
+
+/* ---- context ---------------------------------------------------------------
+ * fr_ctx_create: bind a context to CUDA device `device` and the stream
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * context owns a growable device workspace (lattice hash tables, reduction
+ * partials) and small pinned host buffers.  FR_ECUDA if the device cannot be
+ * used.  fr_ctx_destroy frees everything the context allocated. */
+FR_API fr_status fr_ctx_create(int device, void *cuda_stream, fr_ctx **out);
+FR_API fr_status fr_ctx_destroy(fr_ctx *ctx);
+FR_API fr_status fr_ctx_set_stream(fr_ctx *ctx, void *cuda_stream);
+FR_API const char *fr_ctx_last_error(const fr_ctx *ctx);
+/* Number of kernels this context has launched (graph replays count each node). */
+FR_API int64_t fr_ctx_kernel_launches(const fr_ctx *ctx);
+/* fr_ctx_set_profiling: when on, registrations record a CUDA event pair on
+ * the context's stream around every kernel they launch (inside the replayed
+ * graph as event nodes) and accumulate each kernel class's launch count and
+ * duration; fr_ctx_profile copies the totals to *out and, if reset, zeroes
+ * them.  Off by default. */
+FR_API fr_status fr_ctx_set_profiling(fr_ctx *ctx, int on);
+/* Bytes this context has copied host->device and device->host (all calls). */
+FR_API fr_status fr_ctx_transfer_bytes(const fr_ctx *ctx, int64_t *h2d, int64_t *d2h);
+FR_API fr_status fr_ctx_profile(fr_ctx *ctx, fr_profile *out, int reset);
+
+/* ---- permutohedral lattice primitives (Section 4.2) -------------------------
+ * The lattice lives in the (d+1) = 4 dimensional hyperplane sum(z) = 0.  A
+ * position p is scaled to the feature f = p / sigma (identity covariance,
+ * Section 4.1), elevated, and assigned the 4 vertices of its enclosing simplex
+ * with barycentric weights.  Keys are the vertices' integer coordinates.
+ */
+
+/* fr_lattice_embed: for n points d_pos (n x 4), write the 4 vertex keys of each
+ * point's enclosing simplex, all four integer coordinates, to d_keys
+ * (int32, n x 4 x 4: [point][vertex k][coordinate j]; vertex k has every
+ * coordinate congruent to k mod 4) and the barycentric weights to d_bary
+ * (float, n x 4).  Either output may be NULL.  FR_EINVAL if a coordinate is
+ * non-finite or |elevated coordinate| >= 1e6 (that point's outputs are 0). */
+FR_API fr_status fr_lattice_embed(fr_ctx *ctx, const float *d_pos, int64_t n, float sigma,
+                                  int32_t *d_keys, float *d_bary);
+
+/* fr_lattice_build: create a lattice over n points d_pos (n x 4) at scale
+ * sigma: the hash table of their simplex vertices (no values yet).  The table
+ * holds max(capacity_hint, 8 n) slots rounded up to a power of two.  The
+ * lattice keeps each point's vertex slots and weights for fr_lattice_splat.
+ * FR_ECAPACITY if the table fills; FR_EINVAL as for fr_lattice_embed. */
+FR_API fr_status fr_lattice_build(fr_ctx *ctx, const float *d_pos, int64_t n, float sigma,
+                                  int64_t capacity_hint, fr_lattice **out);
+
+/* fr_lattice_splat: zero the lattice values and splat the n x val_dim float
+ * values d_vals (row stride val_dim, 1 <= val_dim <= 8) of the build points
+ * onto their vertices with the barycentric weights ("Splat" of Section 4.2;
+ * the observation's values [1, y, n_y] of Eq. 11). */
+FR_API fr_status fr_lattice_splat(fr_ctx *ctx, fr_lattice *lat, const float *d_vals, int val_dim);
+
+/* fr_lattice_blur: one (1/2, 1, 1/2) pass along each of the 4 lattice axes
+ * ("Blur" of Section 4.2); vertices absent from the table contribute 0 and
+ * are not created. */
+FR_API fr_status fr_lattice_blur(fr_ctx *ctx, fr_lattice *lat);
+
+/* fr_lattice_slice: for m query points d_query (m x 4), write
+ * out[i][c] = sum_k b_k value[key_k][c] (absent vertices contribute 0) to
+ * d_out (float, m x val_dim) ("Slice" of Section 4.2; with the augmentation of
+ * Eq. 13-14 the queries are never inserted). */
+FR_API fr_status fr_lattice_slice(fr_ctx *ctx, const fr_lattice *lat, const float *d_query,
+                                  int64_t m, float *d_out);
+
+/* fr_lattice_vertices: write the lattice's vertices, in unspecified order, as
+ * int32 keys d_keys (capacity x 4, all four coordinates) and float values
+ * d_vals (capacity x val_dim; nullable), and their count to *n_vertices
+ * (host).  Synchronises the stream. */
+FR_API fr_status fr_lattice_vertices(fr_ctx *ctx, const fr_lattice *lat, int32_t *d_keys,
+                                     float *d_vals, int64_t *n_vertices);
+/* Vertex count, table capacity and value width (host outputs, nullable). */
+FR_API fr_status fr_lattice_info(fr_ctx *ctx, const fr_lattice *lat, int64_t *n_vertices,
+                                 int64_t *capacity, int32_t *val_dim);
+FR_API fr_status fr_lattice_destroy(fr_ctx *ctx, fr_lattice *lat);
+
+/* ---- E step (Eq. 6 and Eq. 9 via Section 4) ---------------------------------
+ * fr_estep: build the lattice over the observation d_Y (N x 4) at sigma with
+ * values [1, y] (d_Yn == NULL) or [1, y, n_y] (d_Yn, N x 4), blur it if
+ * `blur`, and slice it at the model points moved by T (host double[16]):
+ * d_out (float, M x 4 or M x 7) = [M0, M1 (3) (, Nsum (3))] of Eq. 6 / Eq. 9's
+ * numerator, with the Gaussian's normalisation omitted as in Eq. 11.  This is
+ * the same build and slice the registration runs, exposed for checking. */
+FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                          const float *d_Yn, int64_t N, float sigma, int blur,
+                          const double T[16], float *d_out);
+
+/* ---- rigid registration (Sections 3.1, 3.3, 4, 5) ---------------------------
+ * fr_register_rigid: run opt->iters EM iterations aligning the model d_X
+ * (M x 4) to the observation d_Y (N x 4).  Each iteration: (re)build the
+ * lattice over Y when sigma changed (values [1, y] or [1, y, n_y]), slice it
+ * at x_i = T x_i (E step), weight each point by M0/(M0 + c) with
+ * c = w/(1-w) N/M (Eq. 7), form point-to-point (Eq. 7) or point-to-plane
+ * (Eq. 10, d_Yn required, N x 4 normals) residuals, reduce A = sum J^T J and
+ * b = sum J^T r over twists (Eq. 17-18, rigid: d zeta / d theta = I), solve
+ * delta zeta = -A^{-1} b in float64 on the device and update
+ * T <- exp(delta zeta^) T.  T_inout (host) carries the initial pose in and
+ * the result out; report (nullable) receives diagnostics.  Synchronises the
+ * stream.  FR_EINVAL for bad arguments or out-of-range inputs; FR_ECAPACITY
+ * if the lattice table fills (it is sized 8 N slots, so this indicates a bug). */
+FR_API fr_status fr_register_rigid(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                   const float *d_Yn, int64_t N, const fr_options *opt,
+                                   double T_inout[16], fr_report *report);
+
+/* fr_register_rigid_host: the same registration from HOST buffers h_X
+ * (M x 4), h_Y (N x 4), h_Yn (N x 4, nullable): the inputs are copied to a
+ * context-owned device staging area on the context's stream (asynchronously
+ * when the host buffers are pinned), then registered as above. */
+FR_API fr_status fr_register_rigid_host(fr_ctx *ctx, const float *h_X, int64_t M,
+                                        const float *h_Y, const float *h_Yn, int64_t N,
+                                        const fr_options *opt, double T_inout[16],
+                                        fr_report *report);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FILTERREG_H */

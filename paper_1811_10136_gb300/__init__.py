@@ -1,1 +1,341 @@
-"""GB300-native FilterReg hot path (placeholder; the binding is added with the C-ABI)."""
+"""GB300-native FilterReg hot path: Python binding of libfilterreg.so.
+
+This module is argument marshalling only.  Every step of the registration
+(lattice build, splat, blur, slice, residuals, Gauss-Newton reduction,
+float64 solve and SE(3) update) runs in the sm_103a kernels of
+``libfilterreg.so``, reached through the C ABI of ``include/filterreg.h``.
+There is no CPU fallback: if the library is missing or cannot be loaded, every
+call raises.  PyTorch is used only to hold device memory and to supply the
+current CUDA stream.
+
+The low-level functions keep the C names (``fr_ctx_create``,
+``fr_register_rigid``, ...); ``Context`` and ``Lattice`` wrap them for torch
+tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfilterreg.so")
+
+FR_OK, FR_EINVAL, FR_ENOMEM, FR_ECUDA, FR_ECAPACITY, FR_ETIMEOUT, FR_ENOTSUPPORTED = range(7)
+FR_PT2PT, FR_PT2PL = 0, 1
+FR_FP32, FR_BF16, FR_FP16 = 0, 1, 2
+
+# Every symbol include/filterreg.h declares (checked by the ABI tests).
+EXPORTED = [
+    "fr_options_default", "fr_status_string", "fr_ctx_create", "fr_ctx_destroy",
+    "fr_ctx_set_stream", "fr_ctx_last_error", "fr_ctx_kernel_launches", "fr_lattice_embed",
+    "fr_lattice_build", "fr_lattice_splat", "fr_lattice_blur", "fr_lattice_slice",
+    "fr_lattice_vertices", "fr_lattice_info", "fr_lattice_destroy", "fr_estep",
+    "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
+    "fr_ctx_transfer_bytes",
+]
+KERNEL_CLASSES = ("clear", "build_splat", "blur", "rigid_step")
+
+
+class FilterRegError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class fr_options(ctypes.Structure):
+    _fields_ = [("residual", ctypes.c_int32), ("blur", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("sigma_start", ctypes.c_float), ("sigma_end", ctypes.c_float), ("w", ctypes.c_float),
+                ("storage", ctypes.c_int32), ("kahan", ctypes.c_int32),
+                ("renormalize_normals", ctypes.c_int32), ("stop_twist", ctypes.c_float),
+                ("use_graph", ctypes.c_int32)]
+
+
+class fr_report(ctypes.Structure):
+    _fields_ = [("iters_run", ctypes.c_int32), ("degenerate_iters", ctypes.c_int32),
+                ("last_inliers", ctypes.c_int64), ("last_sum_w", ctypes.c_double),
+                ("last_cost", ctypes.c_double), ("last_twist_norm", ctypes.c_double),
+                ("lattice_vertices", ctypes.c_int64), ("lattice_builds", ctypes.c_int32),
+                ("lattice_vertices_sum", ctypes.c_int64)]
+
+
+class fr_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 4), ("total_ms", ctypes.c_double * 4)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_f64p = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libfilterreg.so (building it with nvcc first if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH) and build_if_missing:
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise FilterRegError(FR_ECUDA, f"{LIB_PATH} is missing: run paper_1811_10136_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    L.fr_options_default.argtypes = [ctypes.POINTER(fr_options)]
+    L.fr_options_default.restype = None
+    L.fr_status_string.argtypes = [ctypes.c_int]
+    L.fr_status_string.restype = ctypes.c_char_p
+    L.fr_ctx_create.argtypes = [ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+    L.fr_ctx_destroy.argtypes = [_vp]
+    L.fr_ctx_set_stream.argtypes = [_vp, _vp]
+    L.fr_ctx_last_error.argtypes = [_vp]
+    L.fr_ctx_last_error.restype = ctypes.c_char_p
+    L.fr_ctx_kernel_launches.argtypes = [_vp]
+    L.fr_ctx_kernel_launches.restype = _i64
+    L.fr_lattice_embed.argtypes = [_vp, _vp, _i64, ctypes.c_float, _vp, _vp]
+    L.fr_lattice_build.argtypes = [_vp, _vp, _i64, ctypes.c_float, _i64, ctypes.POINTER(_vp)]
+    L.fr_lattice_splat.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+    L.fr_lattice_blur.argtypes = [_vp, _vp]
+    L.fr_lattice_slice.argtypes = [_vp, _vp, _vp, _i64, _vp]
+    L.fr_lattice_vertices.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(_i64)]
+    L.fr_lattice_info.argtypes = [_vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                  ctypes.POINTER(ctypes.c_int32)]
+    L.fr_lattice_destroy.argtypes = [_vp, _vp]
+    L.fr_estep.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_float, ctypes.c_int, _f64p, _vp]
+    L.fr_register_rigid.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.POINTER(fr_options),
+                                    _f64p, ctypes.POINTER(fr_report)]
+    L.fr_register_rigid_host.argtypes = L.fr_register_rigid.argtypes
+    L.fr_ctx_set_profiling.argtypes = [_vp, ctypes.c_int]
+    L.fr_ctx_profile.argtypes = [_vp, ctypes.POINTER(fr_profile), ctypes.c_int]
+    L.fr_ctx_transfer_bytes.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    for name in EXPORTED:  # every entry point must resolve (ctypes restype defaults to int)
+        getattr(L, name)
+    _lib = L
+    return L
+
+
+def options(**kw) -> fr_options:
+    """fr_options with the library defaults, overridden by keyword."""
+    o = fr_options()
+    load().fr_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Report:
+    iters_run: int
+    degenerate_iters: int
+    last_inliers: int
+    last_sum_w: float
+    last_cost: float
+    last_twist_norm: float
+    lattice_vertices: int
+    lattice_builds: int
+    lattice_vertices_sum: int
+
+
+def _report(r: fr_report) -> Report:
+    return Report(r.iters_run, r.degenerate_iters, r.last_inliers, r.last_sum_w, r.last_cost,
+                  r.last_twist_norm, r.lattice_vertices, r.lattice_builds, r.lattice_vertices_sum)
+
+
+def _dev_ptr(t, name, rows=None, cols=4):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != cols or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 ({'n' if rows is None else rows}, {cols}) tensor")
+    if rows is not None and t.shape[0] != rows:
+        raise ValueError(f"{name} must have {rows} rows")
+    return t.data_ptr()
+
+
+def _pose(T) -> np.ndarray:
+    T = np.ascontiguousarray(np.eye(4) if T is None else T, dtype=np.float64).reshape(4, 4).copy()
+    return T
+
+
+class Context:
+    """An fr_ctx bound to a CUDA device and (by default) torch's current stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._stream = stream
+        h = _vp()
+        st = L.fr_ctx_create(int(device), _vp(stream.cuda_stream), ctypes.byref(h))
+        if st != FR_OK:
+            raise FilterRegError(st, f"fr_ctx_create(device={device}) failed")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fr_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != FR_OK:
+            L = load()
+            raise FilterRegError(st, f"{what}: {L.fr_status_string(st).decode()}: "
+                                     f"{L.fr_ctx_last_error(self._h).decode()}")
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(load().fr_ctx_kernel_launches(self._h))
+
+    def transfer_bytes(self):
+        """(host->device, device->host) bytes this context has copied."""
+        a, b = _i64(), _i64()
+        self._check(load().fr_ctx_transfer_bytes(self._h, ctypes.byref(a), ctypes.byref(b)),
+                    "fr_ctx_transfer_bytes")
+        return a.value, b.value
+
+    def set_profiling(self, on: bool):
+        self._check(load().fr_ctx_set_profiling(self._h, int(bool(on))), "fr_ctx_set_profiling")
+
+    def profile(self, reset: bool = False) -> dict:
+        """{kernel class: (launches, total ms)} accumulated while profiling was on."""
+        p = fr_profile()
+        self._check(load().fr_ctx_profile(self._h, ctypes.byref(p), int(bool(reset))), "fr_ctx_profile")
+        return {name: (int(p.launches[i]), float(p.total_ms[i])) for i, name in enumerate(KERNEL_CLASSES)}
+
+    # ---- registration ------------------------------------------------------
+    def register_rigid(self, X, Y, Yn=None, T0=None, **opts):
+        """Rigid FilterReg registration of X (M,4) to Y (N,4) (+ normals Yn for
+        point-to-plane).  Returns (T (4,4) float64 numpy, Report)."""
+        L = load()
+        o = options(**opts)
+        T = _pose(T0)
+        rep = fr_report()
+        pX = _dev_ptr(X, "X")
+        pY = _dev_ptr(Y, "Y")
+        pN = _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None
+        st = L.fr_register_rigid(self._h, pX, X.shape[0], pY, pN, Y.shape[0], ctypes.byref(o),
+                                 T.ctypes.data_as(_f64p), ctypes.byref(rep))
+        self._check(st, "fr_register_rigid")
+        return T, _report(rep)
+
+    def register_rigid_host(self, X, Y, Yn=None, T0=None, **opts):
+        """The same from host numpy arrays (pinned torch CPU tensors also work)."""
+        L = load()
+        o = options(**opts)
+        T = _pose(T0)
+        rep = fr_report()
+
+        def hp(a, name):
+            if a is None:
+                return None, 0
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or a.dtype.itemsize != 4 or a.dim() != 2 or a.shape[1] != 4 or not a.is_contiguous():
+                    raise TypeError(f"{name} must be a contiguous float32 (n, 4) host tensor")
+                return a.data_ptr(), a.shape[0]
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            if a.ndim != 2 or a.shape[1] != 4:
+                raise TypeError(f"{name} must be a float32 (n, 4) array")
+            return a.ctypes.data, a.shape[0]
+
+        keep = [X, Y, Yn]
+        pX, M = hp(X, "X")
+        pY, N = hp(Y, "Y")
+        pN, _ = hp(Yn, "Yn")
+        st = L.fr_register_rigid_host(self._h, pX, M, pY, pN, N, ctypes.byref(o),
+                                      T.ctypes.data_as(_f64p), ctypes.byref(rep))
+        del keep
+        self._check(st, "fr_register_rigid_host")
+        return T, _report(rep)
+
+    def estep(self, X, Y, Yn=None, sigma=0.02, blur=False, T=None):
+        """E-step sums at T X: (M, 4) [M0, M1] or (M, 7) [M0, M1, Nsum] float32 CUDA tensor."""
+        import torch
+        L = load()
+        vd = 7 if Yn is not None else 4
+        out = torch.empty((X.shape[0], vd), dtype=torch.float32, device=X.device)
+        Tm = _pose(T)
+        st = L.fr_estep(self._h, _dev_ptr(X, "X"), X.shape[0], _dev_ptr(Y, "Y"),
+                        _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None, Y.shape[0],
+                        float(sigma), int(bool(blur)), Tm.ctypes.data_as(_f64p), out.data_ptr())
+        self._check(st, "fr_estep")
+        return out
+
+    # ---- lattice primitives ----------------------------------------------
+    def lattice_embed(self, P, sigma):
+        import torch
+        n = P.shape[0]
+        keys = torch.empty((n, 4, 4), dtype=torch.int32, device=P.device)
+        bary = torch.empty((n, 4), dtype=torch.float32, device=P.device)
+        st = load().fr_lattice_embed(self._h, _dev_ptr(P, "P"), n, float(sigma), keys.data_ptr(),
+                                     bary.data_ptr())
+        self._check(st, "fr_lattice_embed")
+        return keys, bary
+
+    def lattice_build(self, P, sigma, capacity_hint=0) -> "Lattice":
+        h = _vp()
+        st = load().fr_lattice_build(self._h, _dev_ptr(P, "P"), P.shape[0], float(sigma),
+                                     int(capacity_hint), ctypes.byref(h))
+        self._check(st, "fr_lattice_build")
+        return Lattice(self, h, P.shape[0])
+
+
+class Lattice:
+    def __init__(self, ctx: Context, h, n):
+        self._ctx, self._h, self.n = ctx, h, n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fr_lattice_destroy(self._ctx._h, self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        nv, cap, vd = _i64(), _i64(), ctypes.c_int32()
+        self._ctx._check(load().fr_lattice_info(self._ctx._h, self._h, ctypes.byref(nv), ctypes.byref(cap),
+                                                ctypes.byref(vd)), "fr_lattice_info")
+        return nv.value, cap.value, vd.value
+
+    def splat(self, V):
+        import torch
+        if not (isinstance(V, torch.Tensor) and V.is_cuda and V.dtype == torch.float32 and V.is_contiguous()
+                and V.dim() == 2 and V.shape[0] == self.n):
+            raise TypeError("values must be a contiguous float32 (n, val_dim) CUDA tensor")
+        self._ctx._check(load().fr_lattice_splat(self._ctx._h, self._h, V.data_ptr(), V.shape[1]),
+                         "fr_lattice_splat")
+
+    def blur(self):
+        self._ctx._check(load().fr_lattice_blur(self._ctx._h, self._h), "fr_lattice_blur")
+
+    def slice(self, Q):
+        import torch
+        _, _, vd = self.info()
+        out = torch.empty((Q.shape[0], vd), dtype=torch.float32, device=Q.device)
+        self._ctx._check(load().fr_lattice_slice(self._ctx._h, self._h, _dev_ptr(Q, "Q"), Q.shape[0],
+                                                 out.data_ptr()), "fr_lattice_slice")
+        return out
+
+    def vertices(self):
+        import torch
+        _, cap, vd = self.info()
+        keys = torch.empty((cap, 4), dtype=torch.int32, device="cuda")
+        vals = torch.empty((cap, max(vd, 1)), dtype=torch.float32, device="cuda")
+        nv = _i64()
+        self._ctx._check(load().fr_lattice_vertices(self._ctx._h, self._h, keys.data_ptr(), vals.data_ptr(),
+                                                    ctypes.byref(nv)), "fr_lattice_vertices")
+        return keys[: nv.value], vals[: nv.value, :vd]

@@ -1,0 +1,889 @@
+// Host implementation of the C ABI declared in include/filterreg.h.
+//
+// A context owns a growable device workspace (one lattice hash table and its
+// blur ping-pong planes, reduction partials, the device-resident pose state,
+// the per-call job descriptor and per-iteration constants) plus pinned host
+// mirrors of the small structures.  A registration copies its job descriptor
+// to the device and replays a CUDA graph of the whole EM loop; graphs are
+// cached per loop shape, so calls on new buffers of the same shape reuse them.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "filterreg.h"
+#include "internal.h"
+
+using namespace fr;
+
+namespace {
+
+// Lattice scale alpha = sqrt(2/3) (d+1): splat-blur-slice then approximates a
+// unit-std Gaussian in feature units (Section 4.2 / Adams et al. 2010).
+const double kAlpha = std::sqrt(2.0 / 3.0) * 4.0;
+
+// Integral of the unnormalised splat+slice kernel over feature space: the
+// volume per lattice point of the remainder-class union in the hyperplane,
+// (d+1)^(d - 1/2), divided by alpha^d; each blur pass doubles it.
+double lattice_kernel_mass(int blur) {
+    double g = std::pow(4.0, 2.5) / std::pow(kAlpha, 3.0);
+    return blur ? g * 16.0 : g;
+}
+
+void feature_scales(float sigma, float s[3]) {
+    for (int i = 1; i <= 3; ++i)
+        s[i - 1] = (float)(kAlpha / std::sqrt((double)(i * (i + 1))) / (double)sigma);
+}
+
+uint32_t pow2_at_least(long long n) {
+    uint32_t c = 1024;
+    while ((long long)c < n && c < (1u << 30)) c <<= 1;
+    return c;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+struct GraphKey {
+    int iters, residual, blur, kahan, grid_build, grid_step, grid_clear, grid_blur, profile;
+    uint32_t mask;
+    uint64_t ws_gen;
+    std::vector<char> rebuild;
+    bool operator==(const GraphKey &o) const {
+        return iters == o.iters && residual == o.residual && blur == o.blur && kahan == o.kahan &&
+               grid_build == o.grid_build && grid_step == o.grid_step &&
+               grid_clear == o.grid_clear && grid_blur == o.grid_blur && profile == o.profile &&
+               mask == o.mask &&
+               ws_gen == o.ws_gen && rebuild == o.rebuild;
+    }
+};
+
+struct CachedGraph {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+    uint64_t last_use = 0;
+};
+
+template <typename T>
+cudaError_t dev_alloc(T **p, size_t count) {
+    return cudaMalloc((void **)p, count * sizeof(T) + 16);
+}
+
+}  // namespace
+
+struct fr_lattice {
+    uint32_t cap = 0;
+    int n = 0;
+    int vdim = 0;
+    float scale[3] = {0, 0, 0};
+    unsigned long long *keys = nullptr;
+    float4 *v0 = nullptr, *v1 = nullptr, *t0 = nullptr, *t1 = nullptr;
+    int *rec_slot = nullptr;
+    float *rec_w = nullptr;
+    int *counters = nullptr;  // [0] vertices, [1] flags, [2] scratch count
+    int64_t nvert = 0;
+};
+
+struct fr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int num_sms = 0;
+    int64_t launches = 0;
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
+
+    // workspace
+    uint64_t ws_gen = 1;
+    uint32_t table_cap = 0;
+    Table table{};
+    float4 *blur0 = nullptr, *blur1 = nullptr;
+    double *partials = nullptr;
+    int partial_rows = 0;
+    DeviceState *d_state = nullptr;
+    RigidJob *d_job = nullptr;
+    IterParams *d_ip = nullptr;
+    int ip_cap = 0;
+    float4 *stage = nullptr;  // host-call staging of X, Y, Yn
+    size_t stage_cap = 0;     // in float4
+
+    // pinned host mirrors
+    RigidJob *h_job = nullptr;
+    IterParams *h_ip = nullptr;
+    int h_ip_cap = 0;
+    DeviceState *h_state = nullptr;
+
+    std::vector<CachedGraph> graphs;
+    uint64_t use_clock = 0;
+
+    // per-kernel profiling: event pairs around each launch of a plan
+    int profiling = 0;
+    std::vector<cudaEvent_t> events;  // 2 per kernel, grown on demand, kept for the graphs
+    std::vector<int> event_class;     // kernel class of each event pair of the last plan
+    int64_t prof_launches[FR_K_CLASSES] = {0, 0, 0, 0};
+    double prof_ms[FR_K_CLASSES] = {0, 0, 0, 0};
+
+    fr_status fail(fr_status s, const char *fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return s;
+    }
+    fr_status cuda(cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return FR_OK;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA, "%s: %s", what,
+                    cudaGetErrorString(e));
+    }
+};
+
+#define FR_TRY(expr)                         \
+    do {                                     \
+        fr_status _s = (expr);               \
+        if (_s != FR_OK) return _s;          \
+    } while (0)
+#define FR_CUDA(ctx, call) FR_TRY((ctx)->cuda((call), #call))
+
+// cudaMemcpyAsync on the context's stream, counting the bytes moved.
+static cudaError_t copy_async(fr_ctx *ctx, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+    if (kind == cudaMemcpyHostToDevice) ctx->h2d_bytes += (int64_t)bytes;
+    if (kind == cudaMemcpyDeviceToHost) ctx->d2h_bytes += (int64_t)bytes;
+    return cudaMemcpyAsync(dst, src, bytes, kind, ctx->stream);
+}
+
+namespace {
+
+void drop_graphs(fr_ctx *ctx) {
+    for (auto &g : ctx->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
+fr_status ensure_table(fr_ctx *ctx, uint32_t cap, bool blur) {
+    if (cap > ctx->table_cap) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->table.keys);
+        cudaFree(ctx->table.v0);
+        cudaFree(ctx->table.v1);
+        cudaFree(ctx->blur0);
+        cudaFree(ctx->blur1);
+        ctx->table = Table{};
+        ctx->blur0 = ctx->blur1 = nullptr;
+        ctx->table_cap = 0;
+        FR_CUDA(ctx, dev_alloc(&ctx->table.keys, cap));
+        FR_CUDA(ctx, dev_alloc(&ctx->table.v0, cap));
+        FR_CUDA(ctx, dev_alloc(&ctx->table.v1, cap));
+        FR_CUDA(ctx, cudaMemsetAsync(ctx->table.keys, 0xFF, cap * sizeof(unsigned long long), ctx->stream));
+        FR_CUDA(ctx, cudaMemsetAsync(ctx->table.v0, 0, cap * sizeof(float4), ctx->stream));
+        FR_CUDA(ctx, cudaMemsetAsync(ctx->table.v1, 0, cap * sizeof(float4), ctx->stream));
+        ctx->table_cap = cap;
+        ctx->ws_gen++;
+        drop_graphs(ctx);
+    }
+    if (blur && !ctx->blur0) {
+        FR_CUDA(ctx, dev_alloc(&ctx->blur0, ctx->table_cap));
+        FR_CUDA(ctx, dev_alloc(&ctx->blur1, ctx->table_cap));
+        ctx->ws_gen++;
+        drop_graphs(ctx);
+    }
+    return FR_OK;
+}
+
+fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows) {
+    if (!ctx->d_state) {
+        FR_CUDA(ctx, dev_alloc(&ctx->d_state, 1));
+        FR_CUDA(ctx, dev_alloc(&ctx->d_job, 1));
+        FR_CUDA(ctx, cudaMallocHost((void **)&ctx->h_job, sizeof(RigidJob)));
+        FR_CUDA(ctx, cudaMallocHost((void **)&ctx->h_state, sizeof(DeviceState)));
+        FR_CUDA(ctx, cudaMemsetAsync(ctx->d_state, 0, sizeof(DeviceState), ctx->stream));
+    }
+    int need = iters > 1 ? iters : 1;
+    if (need > ctx->ip_cap) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->d_ip);
+        cudaFreeHost(ctx->h_ip);
+        ctx->d_ip = nullptr;
+        ctx->h_ip = nullptr;
+        ctx->ip_cap = 0;
+        int cap = 64;
+        while (cap < need) cap <<= 1;
+        FR_CUDA(ctx, dev_alloc(&ctx->d_ip, cap));
+        FR_CUDA(ctx, cudaMallocHost((void **)&ctx->h_ip, cap * sizeof(IterParams)));
+        ctx->ip_cap = cap;
+        ctx->ws_gen++;
+        drop_graphs(ctx);
+    }
+    if (grid_rows > ctx->partial_rows) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->partials);
+        ctx->partials = nullptr;
+        ctx->partial_rows = 0;
+        FR_CUDA(ctx, dev_alloc(&ctx->partials, (size_t)grid_rows * kRigidVals));
+        ctx->partial_rows = grid_rows;
+        ctx->ws_gen++;
+        drop_graphs(ctx);
+    }
+    return FR_OK;
+}
+
+int blocks_for(const fr_ctx *ctx, long long n, int per_sm) {
+    long long g = (n + kBlock - 1) / kBlock;
+    long long cap = (long long)ctx->num_sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+fr_status check_flags(fr_ctx *ctx, int flags) {
+    if (flags & kFlagCapacity)
+        return ctx->fail(FR_ECAPACITY, "lattice hash table full");
+    if (flags & kFlagRange)
+        return ctx->fail(FR_EINVAL, "non-finite coordinate or elevated coordinate beyond +-1e6 "
+                                    "(position / sigma too large)");
+    return FR_OK;
+}
+
+// Everything a registration launches, in stream order (captured into a graph
+// or issued directly).
+struct Plan {
+    int iters, residual, blur, kahan, profile;
+    int grid_build, grid_step, grid_clear, grid_blur;
+    std::vector<char> rebuild;
+};
+
+// Kernel launch wrapper: with profiling on, an event pair brackets each launch.
+struct Issuer {
+    fr_ctx *ctx;
+    cudaStream_t s;
+    int profile;
+    int kernels = 0;
+    template <typename F>
+    void operator()(int cls, F &&launch) {
+        if (profile) {
+            const size_t need = 2 * (size_t)(kernels + 1);
+            while (ctx->events.size() < need) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                ctx->events.push_back(e);
+            }
+            if (ctx->event_class.size() < (size_t)(kernels + 1)) ctx->event_class.resize(kernels + 1);
+            ctx->event_class[kernels] = cls;
+            cudaEventRecord(ctx->events[2 * kernels], s);
+        }
+        launch();
+        if (profile) cudaEventRecord(ctx->events[2 * kernels + 1], s);
+        ++kernels;
+    }
+};
+
+int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
+    Issuer k{ctx, s, p.profile};
+    Table t = ctx->table;
+    launch_init_state(ctx->d_job, ctx->d_state, s);
+    for (int it = 0; it < p.iters; ++it) {
+        if (p.rebuild[it]) {
+            Table full = t;
+            full.mask = ctx->table_cap - 1;  // clear the whole allocation
+            k(FR_K_CLEAR, [&] { launch_clear_table(full, ctx->d_state, 0, p.grid_clear, s); });
+            k(FR_K_BUILD, [&] {
+                launch_build_splat(p.residual, ctx->d_job, ctx->d_ip, it, t, ctx->d_state, p.grid_build, s);
+            });
+            if (p.blur) {
+                Table a = t, b = t;
+                b.v0 = ctx->blur0;
+                b.v1 = ctx->blur1;
+                for (int dir = 0; dir < 4; ++dir)
+                    k(FR_K_BLUR, [&] {
+                        if (dir % 2 == 0)
+                            launch_blur_pass(a, b, dir, p.grid_blur, ctx->d_state, s);
+                        else
+                            launch_blur_pass(b, a, dir, p.grid_blur, ctx->d_state, s);
+                    });
+            }
+        }
+        k(FR_K_STEP, [&] {
+            launch_rigid_step(p.residual, p.kahan, ctx->d_job, ctx->d_ip, it, t, ctx->partials,
+                              ctx->d_state, p.grid_step, s);
+        });
+    }
+    return k.kernels + 1;  // + the state initialisation
+}
+
+// After the stream is synchronised: add the event-pair durations of the last
+// plan to the per-class totals.
+void collect_profile(fr_ctx *ctx, int kernels) {
+    for (int i = 0; i < kernels; ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]) == cudaSuccess) {
+            ctx->prof_ms[ctx->event_class[i]] += ms;
+            ctx->prof_launches[ctx->event_class[i]] += 1;
+        }
+    }
+    cudaGetLastError();
+}
+
+// Kernels of a plan excluding the state initialisation (the profiled ones).
+int plan_kernels(const Plan &p) {
+    int n = 0;
+    for (int it = 0; it < p.iters; ++it) n += 1 + (p.rebuild[it] ? 2 + (p.blur ? 4 : 0) : 0);
+    return n;
+}
+
+fr_status run_plan(fr_ctx *ctx, const Plan &p, bool use_graph) {
+    if (!use_graph) {
+        ctx->launches += issue_plan(ctx, p, ctx->stream);
+        return ctx->cuda(cudaGetLastError(), "kernel launch");
+    }
+    GraphKey key{p.iters, p.residual, p.blur, p.kahan, p.grid_build, p.grid_step, p.grid_clear,
+                 p.grid_blur, p.profile, ctx->table.mask, ctx->ws_gen, p.rebuild};
+    CachedGraph *hit = nullptr;
+    for (auto &g : ctx->graphs)
+        if (g.key == key) hit = &g;
+    if (!hit) {
+        cudaStream_t cs;
+        FR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int kernels = 0;
+        if (e == cudaSuccess) {
+            kernels = issue_plan(ctx, p, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        cudaStreamDestroy(cs);
+        FR_CUDA(ctx, e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        FR_CUDA(ctx, e);
+        if (ctx->graphs.size() >= 8) {
+            size_t old = 0;
+            for (size_t i = 1; i < ctx->graphs.size(); ++i)
+                if (ctx->graphs[i].last_use < ctx->graphs[old].last_use) old = i;
+            cudaGraphExecDestroy(ctx->graphs[old].exec);
+            ctx->graphs.erase(ctx->graphs.begin() + old);
+        }
+        ctx->graphs.push_back(CachedGraph{key, exec, kernels, 0});
+        hit = &ctx->graphs.back();
+    }
+    hit->last_use = ++ctx->use_clock;
+    FR_CUDA(ctx, cudaGraphLaunch(hit->exec, ctx->stream));
+    ctx->launches += hit->kernels;
+    return FR_OK;
+}
+
+fr_status validate_cloud(fr_ctx *ctx, const void *p, int64_t n, const char *name) {
+    if (!p) return ctx->fail(FR_EINVAL, "%s is NULL", name);
+    if (n < 1 || n > (1ll << 30)) return ctx->fail(FR_EINVAL, "%s: size %lld out of range", name, (long long)n);
+    if (!aligned16(p)) return ctx->fail(FR_EINVAL, "%s must be 16-byte aligned (n x 4 floats)", name);
+    return FR_OK;
+}
+
+fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
+    if (!o) return ctx->fail(FR_EINVAL, "options are NULL");
+    if (o->residual != FR_PT2PT && o->residual != FR_PT2PL)
+        return ctx->fail(FR_EINVAL, "residual must be FR_PT2PT or FR_PT2PL");
+    if (o->iters < 0 || o->iters > 100000) return ctx->fail(FR_EINVAL, "iters out of range");
+    if (!(o->sigma_start > 0.0f) || !(o->sigma_end > 0.0f) || !std::isfinite(o->sigma_start) ||
+        !std::isfinite(o->sigma_end))
+        return ctx->fail(FR_EINVAL, "sigma must be finite and > 0");
+    if (!(o->w >= 0.0f && o->w < 1.0f)) return ctx->fail(FR_EINVAL, "w must lie in [0, 1)");
+    if (o->storage != FR_FP32)
+        return ctx->fail(FR_ENOTSUPPORTED, "only FP32 lattice storage is implemented");
+    return FR_OK;
+}
+
+// Host-side constants of every iteration: the sigma schedule (geometric
+// between sigma_start and sigma_end), feature scales and outlier constant
+// c = w/(1-w) N/M (Eq. 7) in the lattice kernel's units (times sigma^3 G).
+void fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip,
+                      std::vector<char> &rebuild) {
+    const double s0 = o->sigma_start, s1 = o->sigma_end;
+    const double c = (double)o->w / (1.0 - (double)o->w) * ((double)N / (double)M);
+    const double G = lattice_kernel_mass(o->blur);
+    rebuild.assign(o->iters, 0);
+    float prev = 0.0f;
+    for (int k = 0; k < o->iters; ++k) {
+        float sig;
+        if (o->iters == 1 || s0 == s1)
+            sig = (float)s0;
+        else
+            sig = (float)(s0 * std::pow(s1 / s0, (double)k / (double)(o->iters - 1)));
+        IterParams &p = ip[k];
+        p.sigma = sig;
+        float s[3];
+        feature_scales(sig, s);
+        p.s1 = s[0];
+        p.s2 = s[1];
+        p.s3 = s[2];
+        const double sd = (double)sig;
+        p.c_eff = (float)(c * sd * sd * sd * G);
+        p.inv_sigma2 = (float)(1.0 / (sd * sd));
+        p.rebuild = (k == 0 || sig != prev) ? 1 : 0;
+        p.pad = 0;
+        rebuild[k] = (char)p.rebuild;
+        prev = sig;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+FR_API void fr_options_default(fr_options *o) {
+    if (!o) return;
+    o->residual = FR_PT2PT;
+    o->blur = 0;
+    o->iters = 30;
+    o->sigma_start = 0.02f;
+    o->sigma_end = 0.02f;
+    o->w = 0.1f;
+    o->storage = FR_FP32;
+    o->kahan = 0;
+    o->renormalize_normals = 0;
+    o->stop_twist = 0.0f;
+    o->use_graph = 1;
+}
+
+FR_API const char *fr_status_string(fr_status s) {
+    switch (s) {
+    case FR_OK: return "ok";
+    case FR_EINVAL: return "invalid argument";
+    case FR_ENOMEM: return "out of memory";
+    case FR_ECUDA: return "CUDA error";
+    case FR_ECAPACITY: return "lattice capacity exceeded";
+    case FR_ETIMEOUT: return "device wait timed out";
+    case FR_ENOTSUPPORTED: return "not supported";
+    }
+    return "unknown status";
+}
+
+FR_API fr_status fr_ctx_create(int device, void *cuda_stream, fr_ctx **out) {
+    if (!out) return FR_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return FR_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return FR_ECUDA;
+    fr_ctx *ctx = new fr_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (ctx->num_sms < 1) ctx->num_sms = 1;
+    *out = ctx;
+    return FR_OK;
+}
+
+FR_API fr_status fr_ctx_destroy(fr_ctx *ctx) {
+    if (!ctx) return FR_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    cudaFree(ctx->table.keys);
+    cudaFree(ctx->table.v0);
+    cudaFree(ctx->table.v1);
+    cudaFree(ctx->blur0);
+    cudaFree(ctx->blur1);
+    cudaFree(ctx->partials);
+    cudaFree(ctx->d_state);
+    cudaFree(ctx->d_job);
+    cudaFree(ctx->d_ip);
+    cudaFree(ctx->stage);
+    cudaFreeHost(ctx->h_job);
+    cudaFreeHost(ctx->h_ip);
+    cudaFreeHost(ctx->h_state);
+    delete ctx;
+    return FR_OK;
+}
+
+FR_API fr_status fr_ctx_set_stream(fr_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return FR_EINVAL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return FR_OK;
+}
+
+FR_API const char *fr_ctx_last_error(const fr_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+FR_API int64_t fr_ctx_kernel_launches(const fr_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+FR_API fr_status fr_ctx_transfer_bytes(const fr_ctx *ctx, int64_t *h2d, int64_t *d2h) {
+    if (!ctx) return FR_EINVAL;
+    if (h2d) *h2d = ctx->h2d_bytes;
+    if (d2h) *d2h = ctx->d2h_bytes;
+    return FR_OK;
+}
+
+FR_API fr_status fr_ctx_set_profiling(fr_ctx *ctx, int on) {
+    if (!ctx) return FR_EINVAL;
+    ctx->profiling = on ? 1 : 0;
+    return FR_OK;
+}
+
+FR_API fr_status fr_ctx_profile(fr_ctx *ctx, fr_profile *out, int reset) {
+    if (!ctx) return FR_EINVAL;
+    if (out)
+        for (int c = 0; c < FR_K_CLASSES; ++c) {
+            out->launches[c] = ctx->prof_launches[c];
+            out->total_ms[c] = ctx->prof_ms[c];
+        }
+    if (reset)
+        for (int c = 0; c < FR_K_CLASSES; ++c) {
+            ctx->prof_launches[c] = 0;
+            ctx->prof_ms[c] = 0.0;
+        }
+    return FR_OK;
+}
+
+// ---- lattice primitives -----------------------------------------------------
+
+FR_API fr_status fr_lattice_embed(fr_ctx *ctx, const float *d_pos, int64_t n, float sigma,
+                                  int32_t *d_keys, float *d_bary) {
+    if (!ctx) return FR_EINVAL;
+    FR_TRY(validate_cloud(ctx, d_pos, n, "d_pos"));
+    if (!(sigma > 0.0f)) return ctx->fail(FR_EINVAL, "sigma must be > 0");
+    if (d_keys && !aligned16(d_keys)) return ctx->fail(FR_EINVAL, "d_keys must be 16-byte aligned");
+    cudaSetDevice(ctx->device);
+    FR_TRY(ensure_small(ctx, 1, 1));
+    float s[3];
+    feature_scales(sigma, s);
+    int *flags = &ctx->d_state->flags;
+    FR_CUDA(ctx, cudaMemsetAsync(flags, 0, sizeof(int), ctx->stream));
+    launch_embed((const float4 *)d_pos, (int)n, s[0], s[1], s[2], d_keys, d_bary, flags, ctx->stream);
+    ctx->launches += 1;
+    FR_CUDA(ctx, cudaGetLastError());
+    int h = 0;
+    FR_CUDA(ctx, copy_async(ctx, &h, flags, sizeof(int), cudaMemcpyDeviceToHost));
+    FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_flags(ctx, h);
+}
+
+FR_API fr_status fr_lattice_build(fr_ctx *ctx, const float *d_pos, int64_t n, float sigma,
+                                  int64_t capacity_hint, fr_lattice **out) {
+    if (!ctx || !out) return FR_EINVAL;
+    *out = nullptr;
+    FR_TRY(validate_cloud(ctx, d_pos, n, "d_pos"));
+    if (!(sigma > 0.0f) || !std::isfinite(sigma)) return ctx->fail(FR_EINVAL, "sigma must be > 0");
+    cudaSetDevice(ctx->device);
+    fr_lattice *lat = new fr_lattice();
+    long long want = capacity_hint > 8 * n ? capacity_hint : 8 * n;
+    lat->cap = pow2_at_least(want);
+    lat->n = (int)n;
+    feature_scales(sigma, lat->scale);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dev_alloc(&lat->keys, lat->cap);
+    if (e == cudaSuccess) e = dev_alloc(&lat->v0, lat->cap);
+    if (e == cudaSuccess) e = dev_alloc(&lat->v1, lat->cap);
+    if (e == cudaSuccess) e = dev_alloc(&lat->rec_slot, (size_t)n * 4);
+    if (e == cudaSuccess) e = dev_alloc(&lat->rec_w, (size_t)n * 4);
+    if (e == cudaSuccess) e = dev_alloc(&lat->counters, 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lat->keys, 0xFF, lat->cap * sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lat->v0, 0, lat->cap * sizeof(float4), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lat->v1, 0, lat->cap * sizeof(float4), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lat->counters, 0, 4 * sizeof(int), ctx->stream);
+    if (e != cudaSuccess) {
+        fr_lattice_destroy(ctx, lat);
+        return ctx->cuda(e, "fr_lattice_build allocation");
+    }
+    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    launch_build_records((const float4 *)d_pos, (int)n, lat->scale[0], lat->scale[1], lat->scale[2], t,
+                         lat->rec_slot, lat->rec_w, lat->counters, ctx->stream);
+    ctx->launches += 1;
+    int h[2] = {0, 0};
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = copy_async(ctx, h, lat->counters, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        fr_lattice_destroy(ctx, lat);
+        return ctx->cuda(e, "fr_lattice_build");
+    }
+    lat->nvert = h[0];
+    fr_status st = check_flags(ctx, h[1]);
+    if (st != FR_OK) {
+        fr_lattice_destroy(ctx, lat);
+        return st;
+    }
+    *out = lat;
+    return FR_OK;
+}
+
+FR_API fr_status fr_lattice_splat(fr_ctx *ctx, fr_lattice *lat, const float *d_vals, int val_dim) {
+    if (!ctx || !lat) return FR_EINVAL;
+    if (!d_vals) return ctx->fail(FR_EINVAL, "d_vals is NULL");
+    if (val_dim < 1 || val_dim > 8) return ctx->fail(FR_EINVAL, "val_dim must be 1..8");
+    cudaSetDevice(ctx->device);
+    lat->vdim = val_dim;
+    FR_CUDA(ctx, cudaMemsetAsync(lat->v0, 0, lat->cap * sizeof(float4), ctx->stream));
+    FR_CUDA(ctx, cudaMemsetAsync(lat->v1, 0, lat->cap * sizeof(float4), ctx->stream));
+    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    launch_splat_records(d_vals, val_dim, lat->n, lat->rec_slot, lat->rec_w, t, ctx->stream);
+    ctx->launches += 1;
+    FR_CUDA(ctx, cudaGetLastError());
+    FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FR_OK;
+}
+
+FR_API fr_status fr_lattice_blur(fr_ctx *ctx, fr_lattice *lat) {
+    if (!ctx || !lat) return FR_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (!lat->t0) {
+        FR_CUDA(ctx, dev_alloc(&lat->t0, lat->cap));
+        FR_CUDA(ctx, dev_alloc(&lat->t1, lat->cap));
+    }
+    Table a{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    Table b{lat->keys, lat->t0, lat->t1, lat->cap - 1};
+    int grid = blocks_for(ctx, lat->cap, 16);
+    for (int dir = 0; dir < 4; ++dir) {
+        if (dir % 2 == 0)
+            launch_blur_pass(a, b, dir, grid, nullptr, ctx->stream);
+        else
+            launch_blur_pass(b, a, dir, grid, nullptr, ctx->stream);
+    }
+    ctx->launches += 4;
+    FR_CUDA(ctx, cudaGetLastError());
+    FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FR_OK;
+}
+
+FR_API fr_status fr_lattice_slice(fr_ctx *ctx, const fr_lattice *lat, const float *d_query,
+                                  int64_t m, float *d_out) {
+    if (!ctx || !lat) return FR_EINVAL;
+    FR_TRY(validate_cloud(ctx, d_query, m, "d_query"));
+    if (!d_out) return ctx->fail(FR_EINVAL, "d_out is NULL");
+    if (lat->vdim < 1) return ctx->fail(FR_EINVAL, "lattice has no values (call fr_lattice_splat)");
+    cudaSetDevice(ctx->device);
+    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    FR_CUDA(ctx, cudaMemsetAsync(lat->counters + 1, 0, sizeof(int), ctx->stream));
+    launch_slice_out((const float4 *)d_query, (int)m, lat->scale[0], lat->scale[1], lat->scale[2], t,
+                     lat->vdim, d_out, lat->counters + 1, ctx->stream);
+    ctx->launches += 1;
+    FR_CUDA(ctx, cudaGetLastError());
+    int h = 0;
+    FR_CUDA(ctx, copy_async(ctx, &h, lat->counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_flags(ctx, h);
+}
+
+FR_API fr_status fr_lattice_vertices(fr_ctx *ctx, const fr_lattice *lat, int32_t *d_keys,
+                                     float *d_vals, int64_t *n_vertices) {
+    if (!ctx || !lat) return FR_EINVAL;
+    if (!d_keys || !aligned16(d_keys)) return ctx->fail(FR_EINVAL, "d_keys must be a 16-byte aligned buffer");
+    cudaSetDevice(ctx->device);
+    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    FR_CUDA(ctx, cudaMemsetAsync(lat->counters + 2, 0, sizeof(int), ctx->stream));
+    launch_vertices(t, lat->vdim > 0 ? lat->vdim : 1, d_keys, lat->vdim > 0 ? d_vals : nullptr,
+                    lat->counters + 2, ctx->stream);
+    ctx->launches += 1;
+    FR_CUDA(ctx, cudaGetLastError());
+    int h = 0;
+    FR_CUDA(ctx, copy_async(ctx, &h, lat->counters + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (n_vertices) *n_vertices = h;
+    return FR_OK;
+}
+
+FR_API fr_status fr_lattice_info(fr_ctx *ctx, const fr_lattice *lat, int64_t *n_vertices,
+                                 int64_t *capacity, int32_t *val_dim) {
+    if (!ctx || !lat) return FR_EINVAL;
+    if (n_vertices) *n_vertices = lat->nvert;
+    if (capacity) *capacity = lat->cap;
+    if (val_dim) *val_dim = lat->vdim;
+    return FR_OK;
+}
+
+FR_API fr_status fr_lattice_destroy(fr_ctx *ctx, fr_lattice *lat) {
+    if (!lat) return FR_OK;
+    if (ctx) {
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(lat->keys);
+    cudaFree(lat->v0);
+    cudaFree(lat->v1);
+    cudaFree(lat->t0);
+    cudaFree(lat->t1);
+    cudaFree(lat->rec_slot);
+    cudaFree(lat->rec_w);
+    cudaFree(lat->counters);
+    delete lat;
+    return FR_OK;
+}
+
+// ---- E step -----------------------------------------------------------------
+
+FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                          const float *d_Yn, int64_t N, float sigma, int blur, const double T[16],
+                          float *d_out) {
+    if (!ctx) return FR_EINVAL;
+    FR_TRY(validate_cloud(ctx, d_X, M, "d_X"));
+    FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));
+    if (d_Yn) FR_TRY(validate_cloud(ctx, d_Yn, N, "d_Yn"));
+    if (!d_out || !T) return ctx->fail(FR_EINVAL, "d_out and T must not be NULL");
+    if (!(sigma > 0.0f) || !std::isfinite(sigma)) return ctx->fail(FR_EINVAL, "sigma must be > 0");
+    cudaSetDevice(ctx->device);
+    const int pt2pl = d_Yn ? 1 : 0;
+    int grid_build = blocks_for(ctx, N, 8), grid_step = blocks_for(ctx, M, 8);
+    FR_TRY(ensure_small(ctx, 1, grid_step));
+    FR_TRY(ensure_table(ctx, pow2_at_least(6 * N), blur != 0));
+    Table t = ctx->table;
+    t.mask = pow2_at_least(6 * N) - 1;
+    fr_options o;
+    fr_options_default(&o);
+    o.iters = 1;
+    o.sigma_start = o.sigma_end = sigma;
+    o.blur = blur;
+    std::vector<char> rb;
+    fill_iter_params(&o, M, N, ctx->h_ip, rb);
+    RigidJob *j = ctx->h_job;
+    *j = RigidJob{};
+    j->X = (const float4 *)d_X;
+    j->Y = (const float4 *)d_Y;
+    j->Yn = (const float4 *)d_Yn;
+    j->M = (int)M;
+    j->N = (int)N;
+    for (int i = 0; i < 16; ++i) j->T0[i] = T[i];
+    FR_CUDA(ctx, copy_async(ctx, ctx->d_job, j, sizeof(RigidJob), cudaMemcpyHostToDevice));
+    FR_CUDA(ctx, copy_async(ctx, ctx->d_ip, ctx->h_ip, sizeof(IterParams), cudaMemcpyHostToDevice));
+    launch_init_state(ctx->d_job, ctx->d_state, ctx->stream);
+    Table full = t;
+    full.mask = ctx->table_cap - 1;
+    launch_clear_table(full, ctx->d_state, 0, blocks_for(ctx, ctx->table_cap, 8), ctx->stream);
+    launch_build_splat(pt2pl, ctx->d_job, ctx->d_ip, 0, t, ctx->d_state, grid_build, ctx->stream);
+    ctx->launches += 3;
+    if (blur) {
+        Table a = t, b = t;
+        b.v0 = ctx->blur0;
+        b.v1 = ctx->blur1;
+        int gb = blocks_for(ctx, (long long)t.mask + 1, 8);
+        for (int dir = 0; dir < 4; ++dir) {
+            if (dir % 2 == 0)
+                launch_blur_pass(a, b, dir, gb, ctx->d_state, ctx->stream);
+            else
+                launch_blur_pass(b, a, dir, gb, ctx->d_state, ctx->stream);
+        }
+        ctx->launches += 4;
+    }
+    launch_estep_out(pt2pl, ctx->d_job, ctx->d_ip, t, d_out, ctx->d_state, grid_step, ctx->stream);
+    ctx->launches += 1;
+    FR_CUDA(ctx, cudaGetLastError());
+    FR_CUDA(ctx, copy_async(ctx, ctx->h_state, ctx->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost));
+    FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_flags(ctx, ctx->h_state->flags);
+}
+
+// ---- rigid registration -----------------------------------------------------
+
+static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                     const float *d_Yn, int64_t N, const fr_options *opt,
+                                     double T_inout[16], fr_report *rep) {
+    const int pt2pl = opt->residual == FR_PT2PL;
+    const uint32_t cap = pow2_at_least(6 * N);
+    Plan p;
+    p.iters = opt->iters;
+    p.residual = pt2pl;
+    p.blur = opt->blur ? 1 : 0;
+    p.kahan = opt->kahan ? 1 : 0;
+    p.profile = ctx->profiling;
+    p.grid_build = blocks_for(ctx, N, 8);
+    p.grid_step = blocks_for(ctx, M, 8);
+    FR_TRY(ensure_small(ctx, opt->iters, p.grid_step));
+    FR_TRY(ensure_table(ctx, cap, p.blur != 0));
+    ctx->table.mask = cap - 1;
+    p.grid_clear = blocks_for(ctx, ctx->table_cap, 8);
+    p.grid_blur = blocks_for(ctx, cap, 8);
+    fill_iter_params(opt, M, N, ctx->h_ip, p.rebuild);
+
+    RigidJob *j = ctx->h_job;
+    *j = RigidJob{};
+    j->X = (const float4 *)d_X;
+    j->Y = (const float4 *)d_Y;
+    j->Yn = (const float4 *)d_Yn;
+    j->M = (int)M;
+    j->N = (int)N;
+    j->renormalize = opt->renormalize_normals ? 1 : 0;
+    j->stop_twist = opt->stop_twist;
+    for (int i = 0; i < 16; ++i) j->T0[i] = T_inout[i];
+    FR_CUDA(ctx, copy_async(ctx, ctx->d_job, j, sizeof(RigidJob), cudaMemcpyHostToDevice));
+    if (opt->iters > 0)
+        FR_CUDA(ctx, copy_async(ctx, ctx->d_ip, ctx->h_ip, opt->iters * sizeof(IterParams),
+                                cudaMemcpyHostToDevice));
+    FR_TRY(run_plan(ctx, p, opt->use_graph != 0));
+    FR_CUDA(ctx, copy_async(ctx, ctx->h_state, ctx->d_state, sizeof(DeviceState),
+                            cudaMemcpyDeviceToHost));
+    FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (p.profile) collect_profile(ctx, plan_kernels(p));
+    const DeviceState &s = *ctx->h_state;
+    FR_TRY(check_flags(ctx, s.flags));
+    for (int i = 0; i < 16; ++i) T_inout[i] = s.T[i];
+    if (rep) {
+        rep->iters_run = s.iters_run;
+        rep->degenerate_iters = s.degenerate;
+        rep->last_inliers = s.inliers;
+        rep->last_sum_w = s.sum_w;
+        rep->last_cost = s.cost;
+        rep->last_twist_norm = s.twist_norm;
+        rep->lattice_vertices = s.nvert;
+        rep->lattice_builds = s.builds;
+        rep->lattice_vertices_sum = s.nvert_total;
+    }
+    return FR_OK;
+}
+
+FR_API fr_status fr_register_rigid(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                   const float *d_Yn, int64_t N, const fr_options *opt,
+                                   double T_inout[16], fr_report *report) {
+    if (!ctx) return FR_EINVAL;
+    FR_TRY(validate_options(ctx, opt));
+    FR_TRY(validate_cloud(ctx, d_X, M, "d_X"));
+    FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));
+    if (opt->residual == FR_PT2PL) FR_TRY(validate_cloud(ctx, d_Yn, N, "d_Yn (normals, required for FR_PT2PL)"));
+    if (!T_inout) return ctx->fail(FR_EINVAL, "T_inout is NULL");
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(T_inout[i])) return ctx->fail(FR_EINVAL, "T_inout is not finite");
+    cudaSetDevice(ctx->device);
+    return register_rigid_impl(ctx, d_X, M, d_Y, opt->residual == FR_PT2PL ? d_Yn : nullptr, N, opt,
+                               T_inout, report);
+}
+
+FR_API fr_status fr_register_rigid_host(fr_ctx *ctx, const float *h_X, int64_t M,
+                                        const float *h_Y, const float *h_Yn, int64_t N,
+                                        const fr_options *opt, double T_inout[16],
+                                        fr_report *report) {
+    if (!ctx) return FR_EINVAL;
+    FR_TRY(validate_options(ctx, opt));
+    if (!h_X || !h_Y || M < 1 || N < 1 || M > (1ll << 30) || N > (1ll << 30))
+        return ctx->fail(FR_EINVAL, "host clouds must be non-NULL with 1 <= size <= 2^30");
+    const int pt2pl = opt->residual == FR_PT2PL;
+    if (pt2pl && !h_Yn) return ctx->fail(FR_EINVAL, "h_Yn (normals) is required for FR_PT2PL");
+    if (!T_inout) return ctx->fail(FR_EINVAL, "T_inout is NULL");
+    cudaSetDevice(ctx->device);
+    const size_t need = (size_t)M + (size_t)N * (pt2pl ? 2 : 1);
+    if (need > ctx->stage_cap) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_cap = 0;
+        FR_CUDA(ctx, dev_alloc(&ctx->stage, need));
+        ctx->stage_cap = need;
+    }
+    float4 *dX = ctx->stage, *dY = dX + M, *dN = pt2pl ? dY + N : nullptr;
+    FR_CUDA(ctx, copy_async(ctx, dX, h_X, M * sizeof(float4), cudaMemcpyHostToDevice));
+    FR_CUDA(ctx, copy_async(ctx, dY, h_Y, N * sizeof(float4), cudaMemcpyHostToDevice));
+    if (pt2pl)
+        FR_CUDA(ctx, copy_async(ctx, dN, h_Yn, N * sizeof(float4), cudaMemcpyHostToDevice));
+    return register_rigid_impl(ctx, (const float *)dX, M, (const float *)dY, (const float *)dN, N,
+                               opt, T_inout, report);
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Internal interfaces between the C-ABI host code (api.cu) and the kernels
+// (kernels.cu).  Not installed, not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fr {
+
+// Number of values each rigid reduction carries: the 21 upper-triangular
+// entries of A = sum J^T J, the 6 of b = sum J^T r (Eq. 18), then
+// sum of outlier weights, sum of squared residuals and the inlier count.
+constexpr int kRigidVals = 30;
+constexpr int kBlock = 256;
+
+// Device flags (DeviceState::flags).
+constexpr int kFlagRange = 1;     // non-finite or out-of-range coordinate
+constexpr int kFlagCapacity = 2;  // hash table full
+
+// Per-EM-iteration constants, computed on the host from the sigma schedule.
+struct IterParams {
+    float sigma;
+    float s1, s2, s3;      // feature scales alpha / (sqrt(i (i+1)) sigma)
+    float c_eff;           // outlier constant in the lattice kernel's units
+    float inv_sigma2;      // Sigma^{-1} of Eq. 7
+    int rebuild;           // lattice rebuilt at this iteration
+    int pad;
+};
+
+// The per-call job: user buffers and sizes (copied to the device each call so
+// that a captured graph can be replayed on new buffers).
+struct RigidJob {
+    const float4 *X;
+    const float4 *Y;
+    const float4 *Yn;
+    int M, N;
+    int renormalize;
+    float stop_twist;
+    double T0[16];         // initial pose
+};
+
+// Device-resident state of one registration.
+struct DeviceState {
+    double T[16];          // current pose, row-major
+    double sum_w, cost, twist_norm;
+    long long inliers;
+    int iters_run, degenerate;
+    int done;              // stop_twist reached: later kernels return at once
+    int ticket;            // last-block-done counter of the grid reduction
+    int flags;
+    int nvert;             // vertices created by the last build
+    int builds;            // lattices built during this call
+    long long nvert_total; // vertices summed over this call's builds
+};
+
+// A lattice hash table: keys plus up to 8 float values per slot, stored as
+// two float4 planes (channels 0..3 and 4..7).
+struct Table {
+    unsigned long long *keys;
+    float4 *v0;
+    float4 *v1;
+    uint32_t mask;         // capacity - 1 (capacity a power of two)
+};
+
+// ---- launchers (kernels.cu) -------------------------------------------------
+void launch_init_state(const RigidJob *job, DeviceState *st, cudaStream_t s);
+void launch_clear_table(Table t, DeviceState *st, int full, int grid, cudaStream_t s);
+void launch_build_splat(int pt2pl, const RigidJob *job, const IterParams *ip, int it, Table t,
+                        DeviceState *st, int grid, cudaStream_t s);
+void launch_blur_pass(Table in, Table out, int dir, int grid, const DeviceState *st, cudaStream_t s);
+void launch_rigid_step(int pt2pl, int kahan, const RigidJob *job, const IterParams *ip, int it,
+                       Table t, double *partials, DeviceState *st, int grid, cudaStream_t s);
+void launch_estep_out(int pt2pl, const RigidJob *job, const IterParams *ip, Table t, float *out,
+                      DeviceState *st, int grid, cudaStream_t s);
+
+// Lattice primitives.
+void launch_embed(const float4 *P, int n, float s1, float s2, float s3, int *keys, float *bary,
+                  int *flags, cudaStream_t s);
+void launch_build_records(const float4 *P, int n, float s1, float s2, float s3, Table t,
+                          int *rec_slot, float *rec_w, int *counters, cudaStream_t s);
+void launch_splat_records(const float *vals, int vdim, int n, const int *rec_slot,
+                          const float *rec_w, Table t, cudaStream_t s);
+void launch_slice_out(const float4 *Q, int m, float s1, float s2, float s3, Table t, int vdim,
+                      float *out, int *flags, cudaStream_t s);
+void launch_vertices(Table t, int vdim, int *keys_out, float *vals_out, int *count,
+                     cudaStream_t s);
+
+int max_resident_blocks(const void *kernel_tag);
+
+}  // namespace fr

@@ -1,0 +1,179 @@
+"""GPU parity of rigid registration (fused E+M step kernels, float64 device
+solve, SE(3) update, CUDA-graph EM loop) against the CPU oracle.
+
+Bar (from the method's stated accuracy target): final poses within 1e-3 rad
+of rotation and 1e-4 scene units of translation of the oracle's; a single
+Gauss-Newton step much tighter.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1811_10136_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ROT_TOL = 1e-3      # rad
+TRANS_TOL = 1e-4    # scene units
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    import paper_1811_10136_gb300 as fr
+    assert torch.cuda.is_available()
+    return fr.Context(0)
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def pose_diff(A, B):
+    return math.radians(synth.rotation_angle_deg(A, B)), float(np.linalg.norm(A[:3, 3] - B[:3, 3]))
+
+
+def run_both(ctx, orc, p, pt2pl, iters, s0, s1=None, w=0.1, blur=False, T0=None, **kw):
+    s1 = s0 if s1 is None else s1
+    Yn = p.Yn if pt2pl else None
+    Tg, rg = ctx.register_rigid(dev(p.X), dev(p.Y), dev(Yn) if pt2pl else None, T0=T0,
+                                residual=int(pt2pl), iters=iters, sigma_start=f32(s0),
+                                sigma_end=f32(s1), w=f32(w), blur=int(blur), **kw)
+    To, ro = orc.register_rigid(p.X, p.Y, Yn, sigma=f32(s0), sigma_end=f32(s1), w=f32(w), iters=iters,
+                                residual=int(pt2pl), backend=orc.LATTICE, blur=blur, T0=T0)
+    return Tg, rg, To, ro
+
+
+@pytest.mark.parametrize("pt2pl", [False, True])
+def test_single_step_matches_oracle(ctx, orc, pt2pl):
+    p = synth.depth_frame_pair(2, W=160, H=120)
+    Tg, rg, To, ro = run_both(ctx, orc, p, pt2pl, iters=1, s0=0.03)
+    dr, dt = pose_diff(Tg, To)
+    assert dr < 2e-6 and dt < 2e-6, (dr, dt)
+    assert rg.last_inliers == ro.last_inliers
+    assert rg.last_sum_w == pytest.approx(ro.last_sum_w, rel=1e-5)
+    assert rg.last_cost == pytest.approx(ro.last_cost, rel=1e-3)
+
+
+def test_depth_frames_full_workload(ctx, orc):
+    # 320 x 240 point-to-plane tracking, sigma 0.04 -> 0.01 over 20 iterations:
+    # the configuration the benchmark times.
+    p = synth.depth_frame_pair(0)
+    Tg, rg, To, ro = run_both(ctx, orc, p, True, iters=20, s0=0.04, s1=0.01)
+    dr, dt = pose_diff(Tg, To)
+    assert dr < ROT_TOL and dt < TRANS_TOL, (dr, dt)
+    gr, gt = pose_diff(Tg, p.T_gt)
+    assert math.degrees(gr) < 0.1 and gt < 1e-3
+    assert rg.iters_run == 20 and rg.degenerate_iters == 0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_sphere_pt2pt_matches_oracle(ctx, orc, seed):
+    # Bumpy sphere, 2,000 + 2,200 points, sigma 0.02, 30 iterations.
+    p = synth.sphere_bumps_pair(seed)
+    Tg, rg, To, ro = run_both(ctx, orc, p, False, iters=30, s0=0.02)
+    dr, dt = pose_diff(Tg, To)
+    assert dr < ROT_TOL and dt < TRANS_TOL, (dr, dt)
+
+
+def test_blur_registration_matches_oracle(ctx, orc):
+    p = synth.depth_frame_pair(4, W=128, H=96)
+    Tg, rg, To, ro = run_both(ctx, orc, p, True, iters=8, s0=0.03, s1=0.015, blur=True)
+    dr, dt = pose_diff(Tg, To)
+    assert dr < ROT_TOL and dt < TRANS_TOL, (dr, dt)
+
+
+@pytest.mark.parametrize("M,N", [(1, 1), (37, 29), (1000, 257), (2999, 5003)])
+def test_ragged_sizes(ctx, orc, M, N):
+    rng = np.random.default_rng(M * 7 + N)
+    src = synth.sphere_bumps_pair(M + N, n_model=max(M, 8), n_obs=max(N, 8), outlier_frac=0.0,
+                                  max_angle_deg=1.0, max_trans=0.005)
+    p = synth.RigidPair(src.X[:M], src.Y[:N], src.T_gt)
+    Tg, rg, To, ro = run_both(ctx, orc, p, False, iters=5, s0=0.1)
+    dr, dt = pose_diff(Tg, To)
+    assert dr < ROT_TOL and dt < TRANS_TOL, (dr, dt)
+    assert rg.degenerate_iters == ro.degenerate_iters
+
+
+def test_graph_and_direct_launch_agree(ctx):
+    p = synth.depth_frame_pair(6, W=160, H=120)
+    X, Y, Yn = dev(p.X), dev(p.Y), dev(p.Yn)
+    a, _ = ctx.register_rigid(X, Y, Yn, residual=1, iters=10, sigma_start=0.04, sigma_end=0.01, use_graph=1)
+    b, _ = ctx.register_rigid(X, Y, Yn, residual=1, iters=10, sigma_start=0.04, sigma_end=0.01, use_graph=0)
+    c, _ = ctx.register_rigid(X, Y, Yn, residual=1, iters=10, sigma_start=0.04, sigma_end=0.01, use_graph=1)
+    for T in (b, c):
+        dr, dt = pose_diff(a, T)
+        assert dr < 1e-5 and dt < 1e-6
+
+
+def test_host_buffers_equal_device_buffers(ctx):
+    p = synth.depth_frame_pair(7, W=160, H=120)
+    a, ra = ctx.register_rigid(dev(p.X), dev(p.Y), dev(p.Yn), residual=1, iters=10, sigma_start=0.04,
+                               sigma_end=0.01)
+    b, rb = ctx.register_rigid_host(p.X, p.Y, p.Yn, residual=1, iters=10, sigma_start=0.04, sigma_end=0.01)
+    dr, dt = pose_diff(a, b)
+    assert dr < 1e-5 and dt < 1e-6
+    assert ra.last_inliers == rb.last_inliers
+
+
+def test_kahan_sums_agree(ctx, orc):
+    p = synth.depth_frame_pair(8, W=160, H=120)
+    Tg, _, To, _ = run_both(ctx, orc, p, True, iters=10, s0=0.04, s1=0.01, kahan=1)
+    dr, dt = pose_diff(Tg, To)
+    assert dr < ROT_TOL and dt < TRANS_TOL
+
+
+def test_no_overlap_is_degenerate(ctx):
+    p = synth.sphere_bumps_pair(0, n_model=300, n_obs=300)
+    Y = p.Y.copy()
+    Y[:, :3] += 50.0
+    T, rep = ctx.register_rigid(dev(p.X), dev(Y), iters=4, sigma_start=0.02, sigma_end=0.02)
+    np.testing.assert_array_equal(T, np.eye(4))
+    assert rep.degenerate_iters == 4 and rep.last_inliers == 0
+
+
+def test_planar_scene_pt2pl_rank_deficient(ctx, orc):
+    # A plane constrains only 3 of the 6 twist directions under point-to-plane:
+    # the normal matrix is singular and both sides leave the pose unchanged.
+    g = np.linspace(-0.5, 0.5, 60)
+    xx, yy = np.meshgrid(g, g)
+    P = np.zeros((xx.size, 4), np.float32)
+    P[:, 0], P[:, 1] = xx.ravel(), yy.ravel()
+    Nn = np.zeros_like(P)
+    Nn[:, 2] = 1.0
+    Tg, rg = ctx.register_rigid(dev(P), dev(P), dev(Nn), residual=1, iters=2, sigma_start=0.05,
+                                sigma_end=0.05)
+    To, ro = orc.register_rigid(P, P, Nn, sigma=0.05, iters=2, residual=1)
+    assert rg.degenerate_iters == ro.degenerate_iters == 2
+    np.testing.assert_array_equal(Tg, np.eye(4))
+
+
+def test_stop_twist_terminates(ctx):
+    p = synth.depth_frame_pair(9, W=160, H=120)
+    T, rep = ctx.register_rigid(dev(p.X), dev(p.Y), dev(p.Yn), residual=1, iters=60, sigma_start=0.02,
+                                sigma_end=0.02, stop_twist=1e-6)
+    assert 1 <= rep.iters_run < 60
+    assert rep.last_twist_norm < 1e-6
+
+
+def test_invalid_arguments(ctx):
+    import paper_1811_10136_gb300 as fr
+    X = dev(np.zeros((10, 4)))
+    with pytest.raises(fr.FilterRegError) as e:
+        ctx.register_rigid(X, X, sigma_start=-1.0)
+    assert e.value.status == fr.FR_EINVAL
+    with pytest.raises(fr.FilterRegError):
+        ctx.register_rigid(X, X, w=1.0)
+    with pytest.raises(fr.FilterRegError):
+        ctx.register_rigid(X, X, residual=1)          # normals missing
+    Xn = X.clone()
+    Xn[3, 1] = float("nan")
+    with pytest.raises(fr.FilterRegError) as e:
+        ctx.register_rigid(Xn, X, iters=1)
+    assert e.value.status == fr.FR_EINVAL
