@@ -47,17 +47,12 @@ uint32_t pow2_at_least(long long n) {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Everything a captured graph bakes in besides the job descriptor.
 struct GraphKey {
-    int iters, residual, blur, kahan, grid_build, grid_step, grid_clear, grid_blur, profile;
-    uint32_t mask;
+    int v[14];
     uint64_t ws_gen;
-    std::vector<char> rebuild;
     bool operator==(const GraphKey &o) const {
-        return iters == o.iters && residual == o.residual && blur == o.blur && kahan == o.kahan &&
-               grid_build == o.grid_build && grid_step == o.grid_step &&
-               grid_clear == o.grid_clear && grid_blur == o.grid_blur && profile == o.profile &&
-               mask == o.mask &&
-               ws_gen == o.ws_gen && rebuild == o.rebuild;
+        return ws_gen == o.ws_gen && std::memcmp(v, o.v, sizeof v) == 0;
     }
 };
 
@@ -96,12 +91,15 @@ struct fr_ctx {
     int64_t launches = 0;
     int64_t h2d_bytes = 0, d2h_bytes = 0;
 
-    // workspace
+    // workspace: three rotating lattice tables (the build of the next sigma
+    // overlaps the slice of the current one), blur scratch planes, reduction
+    // partials, device state, job descriptor and per-iteration constants.
     uint64_t ws_gen = 1;
     uint32_t table_cap = 0;
-    Table table{};
+    Table tables[3] = {};
+    int *lists[3] = {nullptr, nullptr, nullptr};  // slots claimed by each table's last build
     float4 *blur0 = nullptr, *blur1 = nullptr;
-    double *partials = nullptr;
+    float2 *partials = nullptr;
     int partial_rows = 0;
     DeviceState *d_state = nullptr;
     RigidJob *d_job = nullptr;
@@ -113,11 +111,11 @@ struct fr_ctx {
     // pinned host mirrors
     RigidJob *h_job = nullptr;
     IterParams *h_ip = nullptr;
-    int h_ip_cap = 0;
     DeviceState *h_state = nullptr;
 
     std::vector<CachedGraph> graphs;
     uint64_t use_clock = 0;
+    int bpsm[2][2] = {{0, 0}, {0, 0}};  // resident fused-kernel blocks per SM
 
     // per-kernel profiling: event pairs around each launch of a plan
     int profiling = 0;
@@ -165,23 +163,38 @@ void drop_graphs(fr_ctx *ctx) {
     ctx->graphs.clear();
 }
 
-fr_status ensure_table(fr_ctx *ctx, uint32_t cap, bool blur) {
+void free_tables(fr_ctx *ctx) {
+    for (int i = 0; i < 3; ++i) {
+        Table &t = ctx->tables[i];
+        cudaFree(t.keys);
+        cudaFree(t.v0);
+        cudaFree(t.v1);
+        cudaFree(ctx->lists[i]);
+        ctx->lists[i] = nullptr;
+        t = Table{};
+    }
+    cudaFree(ctx->blur0);
+    cudaFree(ctx->blur1);
+    ctx->blur0 = ctx->blur1 = nullptr;
+    ctx->table_cap = 0;
+}
+
+// Three tables of at least `cap` slots, all empty; blur scratch if asked.
+fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur) {
     if (cap > ctx->table_cap) {
         cudaStreamSynchronize(ctx->stream);
-        cudaFree(ctx->table.keys);
-        cudaFree(ctx->table.v0);
-        cudaFree(ctx->table.v1);
-        cudaFree(ctx->blur0);
-        cudaFree(ctx->blur1);
-        ctx->table = Table{};
-        ctx->blur0 = ctx->blur1 = nullptr;
-        ctx->table_cap = 0;
-        FR_CUDA(ctx, dev_alloc(&ctx->table.keys, cap));
-        FR_CUDA(ctx, dev_alloc(&ctx->table.v0, cap));
-        FR_CUDA(ctx, dev_alloc(&ctx->table.v1, cap));
-        FR_CUDA(ctx, cudaMemsetAsync(ctx->table.keys, 0xFF, cap * sizeof(unsigned long long), ctx->stream));
-        FR_CUDA(ctx, cudaMemsetAsync(ctx->table.v0, 0, cap * sizeof(float4), ctx->stream));
-        FR_CUDA(ctx, cudaMemsetAsync(ctx->table.v1, 0, cap * sizeof(float4), ctx->stream));
+        free_tables(ctx);
+        for (int i = 0; i < 3; ++i) {
+            Table &t = ctx->tables[i];
+            FR_CUDA(ctx, dev_alloc(&ctx->lists[i], cap));
+            FR_CUDA(ctx, dev_alloc(&t.keys, cap));
+            FR_CUDA(ctx, dev_alloc(&t.v0, cap));
+            FR_CUDA(ctx, dev_alloc(&t.v1, cap));
+            FR_CUDA(ctx, cudaMemsetAsync(t.keys, 0xFF, cap * sizeof(unsigned long long), ctx->stream));
+            FR_CUDA(ctx, cudaMemsetAsync(t.v0, 0, cap * sizeof(float4), ctx->stream));
+            FR_CUDA(ctx, cudaMemsetAsync(t.v1, 0, cap * sizeof(float4), ctx->stream));
+            t.mask = cap - 1;
+        }
         ctx->table_cap = cap;
         ctx->ws_gen++;
         drop_graphs(ctx);
@@ -249,12 +262,15 @@ fr_status check_flags(fr_ctx *ctx, int flags) {
     return FR_OK;
 }
 
-// Everything a registration launches, in stream order (captured into a graph
-// or issued directly).
+// The registration as a sequence of launches (captured into a graph or
+// issued directly).
+//   fixed sigma:  build(0) -> step(0) .. step(iters-1) -> clear
+//   annealed:     build(0) -> [step(k) | build(k+1) | clear(k-1)] for each k
+//                 -> clear all three tables
+// with 4 blur passes after every build when blur is on.
 struct Plan {
-    int iters, residual, blur, kahan, profile;
-    int grid_build, grid_step, grid_clear, grid_blur;
-    std::vector<char> rebuild;
+    int iters, residual, blur, kahan, profile, annealed;
+    int gs, gb, gc, g_blur, g_final;  // block counts of the roles
 };
 
 // Kernel launch wrapper: with profiling on, an event pair brackets each launch.
@@ -263,6 +279,16 @@ struct Issuer {
     cudaStream_t s;
     int profile;
     int kernels = 0;
+    // Inside stream capture an event record must be marked external to become
+    // an event node of the graph; outside capture it is a plain record.
+    void record(cudaEvent_t e) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cs);
+        if (cs == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else
+            cudaEventRecord(e, s);
+    }
     template <typename F>
     void operator()(int cls, F &&launch) {
         if (profile) {
@@ -274,45 +300,93 @@ struct Issuer {
             }
             if (ctx->event_class.size() < (size_t)(kernels + 1)) ctx->event_class.resize(kernels + 1);
             ctx->event_class[kernels] = cls;
-            cudaEventRecord(ctx->events[2 * kernels], s);
+            record(ctx->events[2 * kernels]);
         }
         launch();
-        if (profile) cudaEventRecord(ctx->events[2 * kernels + 1], s);
+        if (profile) record(ctx->events[2 * kernels + 1]);
         ++kernels;
     }
 };
 
+void issue_blur(fr_ctx *ctx, Issuer &k, const Plan &p, const Table &t) {
+    Table a = t, b = t;
+    b.v0 = ctx->blur0;
+    b.v1 = ctx->blur1;
+    for (int dir = 0; dir < 4; ++dir)
+        k(FR_K_BLUR, [&] {
+            if (dir % 2 == 0)
+                launch_blur_pass(a, b, dir, p.g_blur, ctx->d_state, k.s);
+            else
+                launch_blur_pass(b, a, dir, p.g_blur, ctx->d_state, k.s);
+        });
+}
+
 int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
     Issuer k{ctx, s, p.profile};
-    Table t = ctx->table;
-    launch_init_state(ctx->d_job, ctx->d_state, s);
-    for (int it = 0; it < p.iters; ++it) {
-        if (p.rebuild[it]) {
-            Table full = t;
-            full.mask = ctx->table_cap - 1;  // clear the whole allocation
-            k(FR_K_CLEAR, [&] { launch_clear_table(full, ctx->d_state, 0, p.grid_clear, s); });
-            k(FR_K_BUILD, [&] {
-                launch_build_splat(p.residual, ctx->d_job, ctx->d_ip, it, t, ctx->d_state, p.grid_build, s);
-            });
-            if (p.blur) {
-                Table a = t, b = t;
-                b.v0 = ctx->blur0;
-                b.v1 = ctx->blur1;
-                for (int dir = 0; dir < 4; ++dir)
-                    k(FR_K_BLUR, [&] {
-                        if (dir % 2 == 0)
-                            launch_blur_pass(a, b, dir, p.grid_blur, ctx->d_state, s);
-                        else
-                            launch_blur_pass(b, a, dir, p.grid_blur, ctx->d_state, s);
-                    });
-            }
-        }
-        k(FR_K_STEP, [&] {
-            launch_rigid_step(p.residual, p.kahan, ctx->d_job, ctx->d_ip, it, t, ctx->partials,
-                              ctx->d_state, p.grid_step, s);
-        });
+    Table *tab = ctx->tables;
+    IterLaunch base{};
+    base.job = ctx->d_job;
+    base.ip = ctx->d_ip;
+    base.partials = ctx->partials;
+    base.st = ctx->d_state;
+    base.check_done = 1;
+    auto which = [&](int build) { return p.annealed ? build % 3 : 0; };
+    if (p.iters > 0) {
+        IterLaunch b0 = base;
+        b0.build = tab[0];
+        b0.build_list = ctx->lists[0];
+        b0.build_it = 0;
+        b0.gb = p.gb + p.gs;  // nothing else runs: use the step blocks too
+        b0.check_done = 0;
+        k(FR_K_BUILD, [&] { launch_em_iter(p.residual, p.kahan, b0, s); });
+        if (p.blur) issue_blur(ctx, k, p, tab[0]);
     }
-    return k.kernels + 1;  // + the state initialisation
+    for (int it = 0; it < p.iters; ++it) {
+        IterLaunch L = base;
+        L.it = it;
+        L.gs = p.gs;
+        L.step = tab[which(it)];
+        if (p.annealed && it + 1 < p.iters) {
+            L.build = tab[which(it + 1)];
+            L.build_list = ctx->lists[which(it + 1)];
+            L.build_it = it + 1;
+            L.gb = p.gb;
+        }
+        if (p.annealed && it >= 1) {  // the table of build it-1, last read by step it-1
+            L.clear = tab[which(it - 1)];
+            L.clear_list = ctx->lists[which(it - 1)];
+            L.clear_it = it - 1;
+            L.gc = p.gc;
+        }
+        k(FR_K_STEP, [&] { launch_em_iter(p.residual, p.kahan, L, s); });
+        if (p.blur && L.gb) issue_blur(ctx, k, p, L.build);
+    }
+    if (p.iters > 0) {
+        // Free what is left: the last build's table (and, annealed, the one
+        // before it, in case the loop stopped early).
+        Table t[2];
+        int *lists[2];
+        const int *counts[2];
+        int n = 0;
+        const int last = p.annealed ? p.iters - 1 : 0;
+        for (int b = (p.annealed && last > 0) ? last - 1 : last; b <= last; ++b) {
+            t[n] = tab[which(b)];
+            lists[n] = ctx->lists[which(b)];
+            counts[n] = &ctx->d_ip[b].nvert;
+            ++n;
+        }
+        k(FR_K_CLEAR, [&] { launch_clear_lists(t, lists, counts, n, p.g_final, s); });
+    }
+    return k.kernels;
+}
+
+// Kernels of a plan (all are profiled).
+int plan_kernels(const Plan &p) {
+    int n = 0;
+    if (p.iters > 0) n += 2 + (p.blur ? 4 : 0);  // first build (+ blur), final clear
+    n += p.iters;
+    if (p.annealed && p.blur && p.iters > 1) n += 4 * (p.iters - 1);
+    return n;
 }
 
 // After the stream is synchronised: add the event-pair durations of the last
@@ -328,20 +402,14 @@ void collect_profile(fr_ctx *ctx, int kernels) {
     cudaGetLastError();
 }
 
-// Kernels of a plan excluding the state initialisation (the profiled ones).
-int plan_kernels(const Plan &p) {
-    int n = 0;
-    for (int it = 0; it < p.iters; ++it) n += 1 + (p.rebuild[it] ? 2 + (p.blur ? 4 : 0) : 0);
-    return n;
-}
-
 fr_status run_plan(fr_ctx *ctx, const Plan &p, bool use_graph) {
     if (!use_graph) {
         ctx->launches += issue_plan(ctx, p, ctx->stream);
         return ctx->cuda(cudaGetLastError(), "kernel launch");
     }
-    GraphKey key{p.iters, p.residual, p.blur, p.kahan, p.grid_build, p.grid_step, p.grid_clear,
-                 p.grid_blur, p.profile, ctx->table.mask, ctx->ws_gen, p.rebuild};
+    GraphKey key{{p.iters, p.residual, p.blur, p.kahan, p.profile, p.annealed, p.gs, p.gb, p.gc,
+                  p.g_blur, p.g_final, (int)ctx->tables[0].mask, 0, 0},
+                 ctx->ws_gen};
     CachedGraph *hit = nullptr;
     for (auto &g : ctx->graphs)
         if (g.key == key) hit = &g;
@@ -401,13 +469,12 @@ fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
 // Host-side constants of every iteration: the sigma schedule (geometric
 // between sigma_start and sigma_end), feature scales and outlier constant
 // c = w/(1-w) N/M (Eq. 7) in the lattice kernel's units (times sigma^3 G).
-void fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip,
-                      std::vector<char> &rebuild) {
+// Returns true when sigma changes during the schedule (annealing).
+bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip) {
     const double s0 = o->sigma_start, s1 = o->sigma_end;
     const double c = (double)o->w / (1.0 - (double)o->w) * ((double)N / (double)M);
     const double G = lattice_kernel_mass(o->blur);
-    rebuild.assign(o->iters, 0);
-    float prev = 0.0f;
+    bool changes = false;
     for (int k = 0; k < o->iters; ++k) {
         float sig;
         if (o->iters == 1 || s0 == s1)
@@ -424,11 +491,33 @@ void fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip,
         const double sd = (double)sig;
         p.c_eff = (float)(c * sd * sd * sd * G);
         p.inv_sigma2 = (float)(1.0 / (sd * sd));
-        p.rebuild = (k == 0 || sig != prev) ? 1 : 0;
-        p.pad = 0;
-        rebuild[k] = (char)p.rebuild;
-        prev = sig;
+        p.rebuild = (k == 0 || sig != ip[k - 1].sigma) ? 1 : 0;
+        p.nvert = 0;
+        if (k > 0 && p.rebuild) changes = true;
     }
+    return changes;
+}
+
+// Splits the resident blocks of the fused kernel between its roles.
+void plan_grids(fr_ctx *ctx, Plan &p, int64_t M, int64_t N, uint32_t cap) {
+    int &bpsm = ctx->bpsm[p.residual][p.kahan];
+    if (!bpsm) bpsm = em_iter_blocks_per_sm(p.residual, p.kahan);
+    const long long resident = (long long)bpsm * ctx->num_sms;
+    long long gs = (M + kBlock - 1) / kBlock, gb = (N + kBlock - 1) / kBlock;
+    long long gc = p.annealed ? std::max<long long>(8, std::min<long long>(64, cap / 16384)) : 0;
+    if (!p.annealed) gb = std::max<long long>(1, std::min(gb, resident));
+    const long long room = resident - gc;
+    const long long want = gs + (p.annealed ? gb : 0);
+    if (want > room) {
+        const double f = (double)room / (double)want;
+        gs = std::max<long long>(1, (long long)(gs * f));
+        if (p.annealed) gb = std::max<long long>(1, (long long)(gb * f));
+    }
+    p.gs = (int)gs;
+    p.gb = (int)gb;
+    p.gc = (int)gc;
+    p.g_blur = blocks_for(ctx, cap, 8);
+    p.g_final = (int)std::max<long long>(8, std::min<long long>(resident / 2, (N + kBlock - 1) / kBlock));
 }
 
 }  // namespace
@@ -491,11 +580,7 @@ FR_API fr_status fr_ctx_destroy(fr_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
-    cudaFree(ctx->table.keys);
-    cudaFree(ctx->table.v0);
-    cudaFree(ctx->table.v1);
-    cudaFree(ctx->blur0);
-    cudaFree(ctx->blur1);
+    free_tables(ctx);
     cudaFree(ctx->partials);
     cudaFree(ctx->d_state);
     cudaFree(ctx->d_job);
@@ -733,18 +818,17 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
     if (!(sigma > 0.0f) || !std::isfinite(sigma)) return ctx->fail(FR_EINVAL, "sigma must be > 0");
     cudaSetDevice(ctx->device);
     const int pt2pl = d_Yn ? 1 : 0;
-    int grid_build = blocks_for(ctx, N, 8), grid_step = blocks_for(ctx, M, 8);
-    FR_TRY(ensure_small(ctx, 1, grid_step));
-    FR_TRY(ensure_table(ctx, pow2_at_least(6 * N), blur != 0));
-    Table t = ctx->table;
-    t.mask = pow2_at_least(6 * N) - 1;
+    const uint32_t cap = pow2_at_least(6 * N);
+    FR_TRY(ensure_small(ctx, 1, 1));
+    FR_TRY(ensure_tables(ctx, cap, blur != 0));
+    Table t = ctx->tables[0];
+    t.mask = cap - 1;
     fr_options o;
     fr_options_default(&o);
     o.iters = 1;
     o.sigma_start = o.sigma_end = sigma;
     o.blur = blur;
-    std::vector<char> rb;
-    fill_iter_params(&o, M, N, ctx->h_ip, rb);
+    fill_iter_params(&o, M, N, ctx->h_ip);
     RigidJob *j = ctx->h_job;
     *j = RigidJob{};
     j->X = (const float4 *)d_X;
@@ -752,34 +836,45 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
     j->Yn = (const float4 *)d_Yn;
     j->M = (int)M;
     j->N = (int)N;
-    for (int i = 0; i < 16; ++i) j->T0[i] = T[i];
+    DeviceState *hs = ctx->h_state;
+    *hs = DeviceState{};
+    for (int i = 0; i < 16; ++i) hs->T[i] = T[i];
     FR_CUDA(ctx, copy_async(ctx, ctx->d_job, j, sizeof(RigidJob), cudaMemcpyHostToDevice));
     FR_CUDA(ctx, copy_async(ctx, ctx->d_ip, ctx->h_ip, sizeof(IterParams), cudaMemcpyHostToDevice));
-    launch_init_state(ctx->d_job, ctx->d_state, ctx->stream);
-    Table full = t;
-    full.mask = ctx->table_cap - 1;
-    launch_clear_table(full, ctx->d_state, 0, blocks_for(ctx, ctx->table_cap, 8), ctx->stream);
-    launch_build_splat(pt2pl, ctx->d_job, ctx->d_ip, 0, t, ctx->d_state, grid_build, ctx->stream);
-    ctx->launches += 3;
+    FR_CUDA(ctx, copy_async(ctx, ctx->d_state, hs, sizeof(DeviceState), cudaMemcpyHostToDevice));
+    IterLaunch b{};
+    b.job = ctx->d_job;
+    b.ip = ctx->d_ip;
+    b.st = ctx->d_state;
+    b.build = t;
+    b.build_list = ctx->lists[0];
+    b.build_it = 0;
+    b.gb = blocks_for(ctx, N, 8);
+    launch_em_iter(pt2pl, 0, b, ctx->stream);
+    ctx->launches += 1;
     if (blur) {
-        Table a = t, b = t;
-        b.v0 = ctx->blur0;
-        b.v1 = ctx->blur1;
-        int gb = blocks_for(ctx, (long long)t.mask + 1, 8);
+        Table a = t, c = t;
+        c.v0 = ctx->blur0;
+        c.v1 = ctx->blur1;
+        const int gb = blocks_for(ctx, cap, 8);
         for (int dir = 0; dir < 4; ++dir) {
             if (dir % 2 == 0)
-                launch_blur_pass(a, b, dir, gb, ctx->d_state, ctx->stream);
+                launch_blur_pass(a, c, dir, gb, ctx->d_state, ctx->stream);
             else
-                launch_blur_pass(b, a, dir, gb, ctx->d_state, ctx->stream);
+                launch_blur_pass(c, a, dir, gb, ctx->d_state, ctx->stream);
         }
         ctx->launches += 4;
     }
-    launch_estep_out(pt2pl, ctx->d_job, ctx->d_ip, t, d_out, ctx->d_state, grid_step, ctx->stream);
-    ctx->launches += 1;
+    launch_estep_out(pt2pl, ctx->d_job, ctx->d_ip, t, d_out, ctx->d_state, blocks_for(ctx, M, 8),
+                     ctx->stream);
+    int *l0 = ctx->lists[0];
+    const int *c0 = &ctx->d_ip[0].nvert;
+    launch_clear_lists(&t, &l0, &c0, 1, blocks_for(ctx, N, 4), ctx->stream);
+    ctx->launches += 2;
     FR_CUDA(ctx, cudaGetLastError());
-    FR_CUDA(ctx, copy_async(ctx, ctx->h_state, ctx->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost));
+    FR_CUDA(ctx, copy_async(ctx, hs, ctx->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost));
     FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return check_flags(ctx, ctx->h_state->flags);
+    return check_flags(ctx, hs->flags);
 }
 
 // ---- rigid registration -----------------------------------------------------
@@ -789,20 +884,18 @@ static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, c
                                      double T_inout[16], fr_report *rep) {
     const int pt2pl = opt->residual == FR_PT2PL;
     const uint32_t cap = pow2_at_least(6 * N);
-    Plan p;
+    FR_TRY(ensure_small(ctx, opt->iters, 1));
+    Plan p{};
     p.iters = opt->iters;
     p.residual = pt2pl;
     p.blur = opt->blur ? 1 : 0;
     p.kahan = opt->kahan ? 1 : 0;
     p.profile = ctx->profiling;
-    p.grid_build = blocks_for(ctx, N, 8);
-    p.grid_step = blocks_for(ctx, M, 8);
-    FR_TRY(ensure_small(ctx, opt->iters, p.grid_step));
-    FR_TRY(ensure_table(ctx, cap, p.blur != 0));
-    ctx->table.mask = cap - 1;
-    p.grid_clear = blocks_for(ctx, ctx->table_cap, 8);
-    p.grid_blur = blocks_for(ctx, cap, 8);
-    fill_iter_params(opt, M, N, ctx->h_ip, p.rebuild);
+    p.annealed = fill_iter_params(opt, M, N, ctx->h_ip) ? 1 : 0;
+    plan_grids(ctx, p, M, N, cap);
+    FR_TRY(ensure_small(ctx, opt->iters, p.gs));
+    FR_TRY(ensure_tables(ctx, cap, p.blur != 0));
+    for (Table &t : ctx->tables) t.mask = cap - 1;
 
     RigidJob *j = ctx->h_job;
     *j = RigidJob{};
@@ -814,16 +907,22 @@ static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, c
     j->renormalize = opt->renormalize_normals ? 1 : 0;
     j->stop_twist = opt->stop_twist;
     for (int i = 0; i < 16; ++i) j->T0[i] = T_inout[i];
+    DeviceState *hs = ctx->h_state;
+    *hs = DeviceState{};
+    for (int i = 0; i < 16; ++i) hs->T[i] = T_inout[i];
     FR_CUDA(ctx, copy_async(ctx, ctx->d_job, j, sizeof(RigidJob), cudaMemcpyHostToDevice));
+    FR_CUDA(ctx, copy_async(ctx, ctx->d_state, hs, sizeof(DeviceState), cudaMemcpyHostToDevice));
     if (opt->iters > 0)
         FR_CUDA(ctx, copy_async(ctx, ctx->d_ip, ctx->h_ip, opt->iters * sizeof(IterParams),
                                 cudaMemcpyHostToDevice));
     FR_TRY(run_plan(ctx, p, opt->use_graph != 0));
-    FR_CUDA(ctx, copy_async(ctx, ctx->h_state, ctx->d_state, sizeof(DeviceState),
-                            cudaMemcpyDeviceToHost));
+    FR_CUDA(ctx, copy_async(ctx, hs, ctx->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost));
+    if (opt->iters > 0)
+        FR_CUDA(ctx, copy_async(ctx, ctx->h_ip, ctx->d_ip, opt->iters * sizeof(IterParams),
+                                cudaMemcpyDeviceToHost));
     FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (p.profile) collect_profile(ctx, plan_kernels(p));
-    const DeviceState &s = *ctx->h_state;
+    const DeviceState &s = *hs;
     FR_TRY(check_flags(ctx, s.flags));
     for (int i = 0; i < 16; ++i) T_inout[i] = s.T[i];
     if (rep) {
@@ -833,7 +932,8 @@ static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, c
         rep->last_sum_w = s.sum_w;
         rep->last_cost = s.cost;
         rep->last_twist_norm = s.twist_norm;
-        rep->lattice_vertices = s.nvert;
+        const int last_build = (p.annealed && s.iters_run > 0) ? s.iters_run - 1 : 0;
+        rep->lattice_vertices = opt->iters > 0 ? ctx->h_ip[last_build].nvert : 0;
         rep->lattice_builds = s.builds;
         rep->lattice_vertices_sum = s.nvert_total;
     }

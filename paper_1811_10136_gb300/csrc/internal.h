@@ -24,7 +24,7 @@ struct IterParams {
     float c_eff;           // outlier constant in the lattice kernel's units
     float inv_sigma2;      // Sigma^{-1} of Eq. 7
     int rebuild;           // lattice rebuilt at this iteration
-    int pad;
+    int nvert;             // vertices created by this iteration's build (device counter)
 };
 
 // The per-call job: user buffers and sizes (copied to the device each call so
@@ -62,14 +62,31 @@ struct Table {
     uint32_t mask;         // capacity - 1 (capacity a power of two)
 };
 
+// One fused EM-iteration launch: blocks [0, gs) run the step of iteration
+// `it` on table `step` (slice, residuals, reduction, last-block solve);
+// blocks [gs, gs + gb) build the lattice of iteration `build_it` into table
+// `build` (gb = 0: no build); blocks [gs + gb, gs + gb + gc) clear table
+// `clear` (gc = 0: none).  Any role may be empty.
+struct IterLaunch {
+    const RigidJob *job;
+    IterParams *ip;
+    int it, build_it, clear_it;  // clear_it: the build whose table is cleared
+    Table step, build, clear;
+    int *build_list;       // slots claimed by the build (count: ip[build_it].nvert)
+    const int *clear_list; // slots to free (count: ip[clear_it].nvert)
+    float2 *partials;      // gs rows of kRigidVals (hi, lo) float pairs
+    DeviceState *st;
+    int gs, gb, gc;
+    int check_done;        // roles return at once once st->done is set
+};
+
 // ---- launchers (kernels.cu) -------------------------------------------------
-void launch_init_state(const RigidJob *job, DeviceState *st, cudaStream_t s);
-void launch_clear_table(Table t, DeviceState *st, int full, int grid, cudaStream_t s);
-void launch_build_splat(int pt2pl, const RigidJob *job, const IterParams *ip, int it, Table t,
-                        DeviceState *st, int grid, cudaStream_t s);
+void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s);
+int em_iter_blocks_per_sm(int pt2pl, int kahan);
+// Frees the slots listed by builds (list lists[i], count *counts[i]).
+void launch_clear_lists(const Table *tabs, int *const *lists, const int *const *counts, int n,
+                        int grid, cudaStream_t s);
 void launch_blur_pass(Table in, Table out, int dir, int grid, const DeviceState *st, cudaStream_t s);
-void launch_rigid_step(int pt2pl, int kahan, const RigidJob *job, const IterParams *ip, int it,
-                       Table t, double *partials, DeviceState *st, int grid, cudaStream_t s);
 void launch_estep_out(int pt2pl, const RigidJob *job, const IterParams *ip, Table t, float *out,
                       DeviceState *st, int grid, cudaStream_t s);
 

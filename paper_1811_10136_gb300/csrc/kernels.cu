@@ -30,107 +30,26 @@ __device__ __forceinline__ int grid_stride() { return gridDim.x * blockDim.x; }
 __device__ __forceinline__ int gtid() { return blockIdx.x * blockDim.x + threadIdx.x; }
 
 // ---------------------------------------------------------------------------
-// Small float64 linear algebra of the M step (one thread).
+// Reductions: float accumulation per thread, double-float across blocks.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int tri_index(int p, int q) {  // p <= q, row-major upper
+__device__ __forceinline__ int tri_index(int p, int q) {  // p <= q, row-major upper, 6 x 6
     return p * 6 - p * (p - 1) / 2 + (q - p);
 }
 
-// Cholesky solve of the 6x6 normal equations A x = rhs.  A pivot below
-// 1e-12 * max(diag A) means "not positive definite": returns false.
-__device__ bool cholesky6(const double *tri, const double *rhs, double *x) {
-    double L[6][6];
-    double maxdiag = 0.0;
-    for (int i = 0; i < 6; ++i) maxdiag = fmax(maxdiag, tri[tri_index(i, i)]);
-    if (!(maxdiag > 0.0)) return false;
-    const double floor_ = maxdiag * 1e-12;
-    for (int i = 0; i < 6; ++i) {
-        for (int j = 0; j <= i; ++j) {
-            double s = tri[tri_index(j, i)];
-            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-            if (i == j) {
-                if (!(s > floor_)) return false;
-                L[i][i] = sqrt(s);
-            } else {
-                L[i][j] = s / L[j][j];
-            }
-        }
-    }
-    double y[6];
-    for (int i = 0; i < 6; ++i) {
-        double s = rhs[i];
-        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-        y[i] = s / L[i][i];
-    }
-    for (int i = 5; i >= 0; --i) {
-        double s = y[i];
-        for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
-        x[i] = s / L[i][i];
-    }
-    return true;
-}
+// Unevaluated sum hi + lo of two floats (about 48 significant bits), added
+// with error-free transformations (Knuth's two-sum), all at float32 rate.
+struct DF {
+    float hi, lo;
+};
 
-// exp of the twist matrix of Eq. 16: R = I + A W + B W^2, t = (I + B W + C W^2) v.
-__device__ void se3_exp(const double *z, double *T) {
-    const double w0 = z[0], w1 = z[1], w2 = z[2];
-    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-    const double th = sqrt(th2);
-    double A, B, C;
-    if (th < 1e-3) {
-        A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-        B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-        C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
-    } else {
-        double s, c;
-        sincos(th, &s, &c);
-        A = s / th;
-        B = (1.0 - c) / th2;
-        C = (th - s) / (th2 * th);
-    }
-    const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
-    double W2[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            W2[3 * i + j] = W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j];
-    for (int i = 0; i < 3; ++i) {
-        double tv = 0.0;
-        for (int j = 0; j < 3; ++j) {
-            const double I = (i == j) ? 1.0 : 0.0;
-            T[4 * i + j] = I + A * W[3 * i + j] + B * W2[3 * i + j];
-            tv += (I + B * W[3 * i + j] + C * W2[3 * i + j]) * z[3 + j];
-        }
-        T[4 * i + 3] = tv;
-    }
-    T[12] = T[13] = T[14] = 0.0;
-    T[15] = 1.0;
-}
-
-// Gauss-Newton step from the reduced sums; updates the pose in st.
-__device__ void solve_update(const double *tot, DeviceState *st, float stop_twist) {
-    st->iters_run += 1;
-    st->sum_w = tot[27];
-    st->cost = tot[28];
-    st->inliers = (long long)(tot[29] + 0.5);
-    double rhs[6], dz[6];
-    for (int p = 0; p < 6; ++p) rhs[p] = -tot[21 + p];
-    if (!cholesky6(tot, rhs, dz)) {
-        st->degenerate += 1;
-        return;
-    }
-    double E[16], Tn[16];
-    se3_exp(dz, E);
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < 4; ++k) s += E[4 * i + k] * st->T[4 * k + j];
-            Tn[4 * i + j] = s;
-        }
-    for (int i = 0; i < 16; ++i) st->T[i] = Tn[i];
-    double n2 = 0.0;
-    for (int p = 0; p < 6; ++p) n2 += dz[p] * dz[p];
-    st->twist_norm = sqrt(n2);
-    if (stop_twist > 0.0f && st->twist_norm < (double)stop_twist) st->done = 1;
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float lo = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, lo);
+    return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
 }
 
 // Float accumulator with optional Kahan compensation.
@@ -141,179 +60,340 @@ struct Acc {
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int v = 0; v < kRigidVals; ++v) s[v] = 0.0f;
-        if (KAHAN) {
 #pragma unroll
-            for (int v = 0; v < (KAHAN ? kRigidVals : 1); ++v) c[v] = 0.0f;
-        }
+        for (int v = 0; v < (KAHAN ? kRigidVals : 1); ++v) c[v] = 0.0f;
     }
     __device__ __forceinline__ void add(int v, float x) {
         if (KAHAN) {
-            const float y = __fsub_rn(x, c[v]);
+            const float y = __fsub_rn(x, c[KAHAN ? v : 0]);
             const float t = __fadd_rn(s[v], y);
-            c[v] = __fsub_rn(__fsub_rn(t, s[v]), y);
+            c[KAHAN ? v : 0] = __fsub_rn(__fsub_rn(t, s[v]), y);
             s[v] = t;
         } else {
             s[v] += x;
         }
     }
+    __device__ __forceinline__ float total(int v) const {
+        return KAHAN ? __fsub_rn(s[v], c[KAHAN ? v : 0]) : s[v];
+    }
 };
 
-// Block reduction of kRigidVals floats: warp shuffles, then shared memory;
-// writes one float64 row per block.
+// Block reduction of kRigidVals floats -- warp shuffles, then the 8 warp sums
+// combined as double-float -- written value-major: value v of block blk at
+// partials[v * rows + blk].
 template <bool KAHAN>
-__device__ __forceinline__ void block_partial(Acc<KAHAN> &acc, double *partials) {
+__device__ __forceinline__ void block_partial(const Acc<KAHAN> &acc, float2 *partials, int blk,
+                                              int rows) {
     __shared__ float sm[kBlock / 32][kRigidVals];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < kRigidVals; ++v) {
-        float x = acc.s[v];
-        if (KAHAN) x -= acc.c[KAHAN ? v : 0];
+        float x = acc.total(v);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
         if (lane == 0) sm[warp][v] = x;
     }
     __syncthreads();
     if (threadIdx.x < kRigidVals) {
-        double s = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) s += (double)sm[w][threadIdx.x];
-        partials[(size_t)blockIdx.x * kRigidVals + threadIdx.x] = s;
-    }
-}
-
-// The last block to arrive sums all partials in float64 and runs the solve.
-__device__ __forceinline__ void grid_finish(double *partials, DeviceState *st, float stop_twist) {
-    __shared__ int last;
-    __shared__ double tot[kRigidVals];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(&st->ticket, 1) == (int)gridDim.x - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (threadIdx.x < kRigidVals) {
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b)
-            s += __ldcg(partials + (size_t)b * kRigidVals + threadIdx.x);
-        tot[threadIdx.x] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        solve_update(tot, st, stop_twist);
-        st->ticket = 0;
+        DF a{0.0f, 0.0f};
+        for (int w = 0; w < kBlock / 32; ++w) a = df_add(a, DF{sm[w][threadIdx.x], 0.0f});
+        partials[(size_t)threadIdx.x * rows + blk] = make_float2(a.hi, a.lo);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Registration kernels
+// The M-step solve in float64, spread over the lanes of one warp.
+//
+// GB300's float64 pipe is narrow, so the cost of float64 work is the number
+// of warp instructions on its critical path; each lane therefore owns one
+// matrix entry.  LDL^T of the 6 x 6 normal matrix (Eq. 18): lane
+// tri_index(p, q) (p <= q) holds A[p][q], then D[p] (p == q) or L[q][p].
 // ---------------------------------------------------------------------------
 
-__global__ void k_init_state(const RigidJob *job, DeviceState *st) {
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 16; ++i) st->T[i] = job->T0[i];
-        st->sum_w = st->cost = st->twist_norm = 0.0;
-        st->inliers = 0;
-        st->iters_run = st->degenerate = 0;
-        st->done = 0;
-        st->ticket = 0;
-        st->flags = 0;
-        st->nvert = 0;
-        st->builds = 0;
-        st->nvert_total = 0;
-    }
+// 1/d in float64 from the float reciprocal refined by two Newton steps
+// (error squared at each step: ~1e-7 -> 1e-14 -> below float64 rounding),
+// a handful of float64 operations instead of a full division sequence.
+__device__ __forceinline__ double rcp64(double d) {
+    double r = (double)(1.0f / (float)d);
+    r = fma(r, fma(-d, r, 1.0), r);
+    r = fma(r, fma(-d, r, 1.0), r);
+    return r;
 }
 
-__global__ void k_clear_table(Table t, DeviceState *st, int full) {
-    if (st && gtid() == 0) {
-        st->nvert = 0;
-        st->builds += 1;
-    }
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t s = gtid(); s <= t.mask; s += grid_stride()) {
-        if (full || __ldcg(t.keys + s) != kEmpty) {
-            t.keys[s] = kEmpty;
-            t.v0[s] = z;
-            if (t.v1) t.v1[s] = z;
+struct Solved {
+    bool ok;
+    double dz;     // lane i < 6: delta zeta_i = -(A^{-1} b)_i
+};
+
+__device__ Solved warp_solve6(double t /* lane v: reduced value v */) {
+    const int lane = threadIdx.x & 31;
+    int p = 0, q = 0;
+    {
+        int l = lane;
+        for (int r = 0; r < 6; ++r) {
+            if (l < 6 - r) { p = r; q = r + l; break; }
+            l -= 6 - r;
         }
     }
+    const bool mine = lane < 21;
+    double a = mine ? t : 0.0;
+    // pivot floor relative to the largest diagonal entry
+    double md = (mine && p == q) ? a : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(kFull, md, o));
+    bool ok = md > 0.0;
+    const double floor_ = md * 1e-12;
+    for (int k = 0; k < 6 && ok; ++k) {
+        const double dk = __shfl_sync(kFull, a, tri_index(k, k));
+        const double akp = __shfl_sync(kFull, a, tri_index(k, p < k ? k : p));
+        const double akq = __shfl_sync(kFull, a, tri_index(k, q < k ? k : q));
+        ok = dk > floor_;
+        if (!ok) break;
+        const double inv = rcp64(dk);
+        if (mine) {
+            if (p == k && q > k) a = a * inv;            // L[q][k]
+            else if (p > k) a = a - akp * akq * inv;      // Schur complement
+        }
+    }
+    Solved r{ok, 0.0};
+    if (!ok) return r;
+    // rhs = -b: lane i < 6 takes reduced value 21 + i
+    double y = -__shfl_sync(kFull, t, 21 + (lane < 6 ? lane : 0));
+    for (int k = 0; k < 6; ++k) {          // L y = rhs (unit lower)
+        const double yk = __shfl_sync(kFull, y, k);
+        const double lik = __shfl_sync(kFull, a, tri_index(k, lane > k && lane < 6 ? lane : k));
+        if (lane < 6 && lane > k) y -= lik * yk;
+    }
+    const int li = lane < 6 ? lane : 0;
+    y = y * rcp64(__shfl_sync(kFull, a, tri_index(li, li)));   // D z = y
+    for (int k = 5; k >= 0; --k) {         // L^T x = z
+        const double xk = __shfl_sync(kFull, y, k);
+        const double lki = __shfl_sync(kFull, a, tri_index(lane < k ? lane : k, k));
+        if (lane < k) y -= lki * xk;
+    }
+    r.dz = y;
+    return r;
 }
 
+// T <- exp(dzeta^) T (Eq. 16 applied as the SE(3) exponential), lanes of one
+// warp: R = I + A W + B W^2 and V = I + B W + C W^2 with W = [omega]_x,
+// W^2 = omega omega^T - th^2 I; A, B, C by their series for th < 0.25 (each
+// term below 2e-17 at the cut-off), else from sin and cos.
+__device__ void warp_se3_update(double dz, double *T /* row-major 4x4, global */,
+                                double *smem /* 24 doubles */) {
+    const int lane = threadIdx.x & 31;
+    double w[3], v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        w[i] = __shfl_sync(kFull, dz, i);
+        v[i] = __shfl_sync(kFull, dz, 3 + i);
+    }
+    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double coef;  // lane 0: A, lane 1: B, lane 2: C
+    if (th2 < 0.0625) {
+        // A = sum_n (-1)^n th^{2n} / (2n+1)!, B: / (2n+2)!, C: / (2n+3)!, n = 0..5
+        const bool la = lane == 0, lb = lane == 1;
+#define FR_SERIES(n, a, b, c) (la ? (a) : (lb ? (b) : (c)))
+        coef = FR_SERIES(5, -1.0 / 39916800.0, -1.0 / 479001600.0, -1.0 / 6227020800.0);
+        coef = coef * th2 + FR_SERIES(4, 1.0 / 362880.0, 1.0 / 3628800.0, 1.0 / 39916800.0);
+        coef = coef * th2 + FR_SERIES(3, -1.0 / 5040.0, -1.0 / 40320.0, -1.0 / 362880.0);
+        coef = coef * th2 + FR_SERIES(2, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0);
+        coef = coef * th2 + FR_SERIES(1, -1.0 / 6.0, -1.0 / 24.0, -1.0 / 120.0);
+        coef = coef * th2 + FR_SERIES(0, 1.0, 0.5, 1.0 / 6.0);
+#undef FR_SERIES
+    } else {
+        const double th = sqrt(th2);
+        double s, cth;
+        sincos(th, &s, &cth);
+        coef = lane == 0 ? s / th : (lane == 1 ? (1.0 - cth) / th2 : (th - s) / (th2 * th));
+    }
+    const double A = __shfl_sync(kFull, coef, 0), B = __shfl_sync(kFull, coef, 1),
+                 C = __shfl_sync(kFull, coef, 2);
+    // lanes 0..8: R_ij ; lanes 9..17: V_ij v_j
+    if (lane < 18) {
+        const int r = lane < 9 ? lane : lane - 9;
+        const int i = r / 3, j = r % 3;
+        const double Wij = (i == j) ? 0.0 : ((j == (i + 1) % 3) ? -w[(i + 2) % 3] : w[(i + 1) % 3]);
+        const double W2ij = w[i] * w[j] - (i == j ? th2 : 0.0);
+        const double I = (i == j) ? 1.0 : 0.0;
+        if (lane < 9) smem[lane] = I + A * Wij + B * W2ij;
+        else smem[lane] = (I + B * Wij + C * W2ij) * v[j];
+    }
+    __syncwarp();
+    if (lane < 3) smem[18 + lane] = smem[9 + 3 * lane] + smem[10 + 3 * lane] + smem[11 + 3 * lane];
+    __syncwarp();
+    double tn = 0.0;
+    if (lane < 12) {
+        const int i = lane / 4, j = lane % 4;
+        tn = smem[3 * i] * T[j] + smem[3 * i + 1] * T[4 + j] + smem[3 * i + 2] * T[8 + j];
+        if (j == 3) tn += smem[18 + i];
+    }
+    __syncwarp();
+    if (lane < 12) T[lane] = tn;
+}
+
+// The last step block: double-float sum of all block partials (warp w sums
+// values w, w + 8, ...; each lane keeps 4 independent loads in flight), then
+// the solve and the pose update in warp 0.
+__device__ void finish_iteration(const float2 *partials, int rows, DeviceState *st,
+                                 float stop_twist) {
+    __shared__ DF tot_s[32];
+    __shared__ double sm_e[24];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Warp w reduces values w, w + 8, w + 16, w + 24: all of its loads are
+    // issued before any of them is consumed.
+    constexpr int kPer = 4;      // values per warp
+    constexpr int kBatch = 4;    // rows per lane per batch
+    DF acc[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) acc[j] = DF{0.0f, 0.0f};
+    for (int b0 = lane; b0 < rows; b0 += 32 * kBatch) {
+        float2 r[kPer][kBatch];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int v = warp + 8 * j;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int b = b0 + 32 * u;
+                r[j][u] = (v < kRigidVals && b < rows) ? __ldcg(partials + (size_t)v * rows + b)
+                                                       : make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) acc[j] = df_add(acc[j], DF{r[j][u].x, r[j][u].y});
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        DF a = acc[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const DF b{__shfl_xor_sync(kFull, a.hi, o), __shfl_xor_sync(kFull, a.lo, o)};
+            a = df_add(a, b);
+        }
+        const int v = warp + 8 * j;
+        if (lane == 0 && v < kRigidVals) tot_s[v] = a;
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    const double t = (lane < kRigidVals) ? (double)tot_s[lane].hi + (double)tot_s[lane].lo : 0.0;
+    if (lane == 27) st->sum_w = t;
+    if (lane == 28) st->cost = t;
+    if (lane == 29) st->inliers = (long long)(t + 0.5);
+    const Solved r = warp_solve6(t);
+    if (lane == 0) st->iters_run += 1;
+    if (!r.ok) {
+        if (lane == 0) st->degenerate += 1;
+        return;
+    }
+    warp_se3_update(r.dz, st->T, sm_e);
+    // |delta zeta| (a diagnostic and the stop test) in float
+    float n2 = lane < 6 ? (float)r.dz * (float)r.dz : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(kFull, n2, o);
+    if (lane == 0) {
+        const float nrm = sqrtf(n2);
+        st->twist_norm = nrm;
+        if (stop_twist > 0.0f && nrm < stop_twist) st->done = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Roles of the fused EM-iteration kernel
+// ---------------------------------------------------------------------------
+
+// Build: Section 4.2 "Splat" of the observation with values [1, y] or
+// [1, y, n_y] (Eq. 11), fused with the lattice build (elevate, simplex, hash
+// insert, float4 atomic accumulation).  One thread per point per round; the
+// slots a round claims are appended to `list` (one atomic per block and
+// round on the build's vertex counter) so that the table can later be freed
+// without scanning it.
 template <bool PT2PL>
-__global__ void __launch_bounds__(kBlock) k_build_splat(const RigidJob *__restrict__ job,
-                                                         const IterParams *__restrict__ ipa, int it,
-                                                         Table t, DeviceState *st) {
-    if (st->done) return;
-    const IterParams ip = ipa[it];
+__device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, IterParams *ipp,
+                                           Table t, int *list, DeviceState *st, int blk, int nblk) {
+    __shared__ int s_warp[kBlock / 32];
+    __shared__ int s_base;
+    const IterParams ip = *ipp;
     const int N = job->N;
     const float4 *__restrict__ Y = job->Y;
     const float4 *__restrict__ Yn = job->Yn;
-    int claimed_here = 0, bad = 0;
-    for (int i = gtid(); i < N; i += grid_stride()) {
-        const float4 y = __ldg(Y + i);
-        Simplex sx;
-        if (!embed(y.x, y.y, y.z, ip.s1, ip.s2, ip.s3, sx)) {
-            bad |= kFlagRange;
-            continue;
-        }
-        float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (PT2PL) n = __ldg(Yn + i);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per_round = nblk * kBlock;
+    const int rounds = (N + per_round - 1) / per_round;
+    int bad = 0;
+    unsigned long long claimed_total = 0;
+    for (int r = 0; r < rounds; ++r) {
+        const int i = r * per_round + blk * kBlock + threadIdx.x;
+        int sl[kD];
+        int mask = 0;
+        if (i < N) {
+            const float4 y = __ldg(Y + i);
+            Simplex sx;
+            if (!embed(y.x, y.y, y.z, ip.s1, ip.s2, ip.s3, sx)) {
+                bad |= kFlagRange;
+            } else {
+                float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (PT2PL) n = __ldg(Yn + i);
 #pragma unroll
-        for (int k = 0; k < kD; ++k) {
-            bool claimed;
-            const int s = insert_key(t.keys, t.mask, sx.key[k], t.mask + 1, claimed);
-            if (s < 0) {
-                bad |= kFlagCapacity;
-                continue;
+                for (int k = 0; k < kD; ++k) {
+                    bool claimed;
+                    sl[k] = insert_key(t.keys, t.mask, sx.key[k], t.mask + 1, claimed);
+                    if (sl[k] < 0) {
+                        bad |= kFlagCapacity;
+                        continue;
+                    }
+                    mask |= claimed ? (1 << k) : 0;
+                    const float b = sx.b[k];
+                    atomicAdd(t.v0 + sl[k], make_float4(b, b * y.x, b * y.y, b * y.z));
+                    if (PT2PL) atomicAdd(t.v1 + sl[k], make_float4(b * n.x, b * n.y, b * n.z, 0.f));
+                }
             }
-            claimed_here += claimed;
-            const float b = sx.b[k];
-            atomicAdd(t.v0 + s, make_float4(b, b * y.x, b * y.y, b * y.z));
-            if (PT2PL) atomicAdd(t.v1 + s, make_float4(b * n.x, b * n.y, b * n.z, 0.f));
         }
-    }
-    // One counter update per warp.
+        // Block-wide exclusive prefix of the claimed counts.
+        const int cnt = __popc(mask);
+        int pre = cnt;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        claimed_here += __shfl_xor_sync(kFull, claimed_here, o);
-        bad |= __shfl_xor_sync(kFull, bad, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (claimed_here) {
-            atomicAdd(&st->nvert, claimed_here);
-            atomicAdd((unsigned long long *)&st->nvert_total, (unsigned long long)claimed_here);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, pre, o);
+            if (lane >= o) pre += v;
         }
-        if (bad) atomicOr(&st->flags, bad);
+        if (lane == 31) s_warp[warp] = pre;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < kBlock / 32; ++w) {
+                const int c = s_warp[w];
+                s_warp[w] = tot;
+                tot += c;
+            }
+            s_base = tot ? atomicAdd(&ipp->nvert, tot) : 0;
+            claimed_total += tot;
+        }
+        __syncthreads();
+        int o = s_base + s_warp[warp] + pre - cnt;
+#pragma unroll
+        for (int k = 0; k < kD; ++k)
+            if (mask & (1 << k)) list[o++] = sl[k];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(kFull, bad, o);
+    if (lane == 0 && bad) atomicOr(&st->flags, bad);
+    if (threadIdx.x == 0) {
+        if (claimed_total) atomicAdd((unsigned long long *)&st->nvert_total, claimed_total);
+        if (blk == 0) atomicAdd(&st->builds, 1);
     }
 }
 
-__global__ void k_blur_pass(Table in, Table out, int dir, const DeviceState *st) {
-    if (st && st->done) return;
-    for (uint32_t s = gtid(); s <= in.mask; s += grid_stride()) {
-        const unsigned long long key = __ldg(in.keys + s);
-        if (key == kEmpty) continue;
-        const int sm = find_key(in.keys, in.mask, neighbour_key(key, dir, -1));
-        const int sp = find_key(in.keys, in.mask, neighbour_key(key, dir, +1));
-        float4 a = __ldg(in.v0 + s);
-        if (sm >= 0) {
-            const float4 u = __ldg(in.v0 + sm);
-            a.x += 0.5f * u.x; a.y += 0.5f * u.y; a.z += 0.5f * u.z; a.w += 0.5f * u.w;
-        }
-        if (sp >= 0) {
-            const float4 u = __ldg(in.v0 + sp);
-            a.x += 0.5f * u.x; a.y += 0.5f * u.y; a.z += 0.5f * u.z; a.w += 0.5f * u.w;
-        }
-        out.v0[s] = a;
-        if (in.v1) {
-            float4 c = __ldg(in.v1 + s);
-            if (sm >= 0) {
-                const float4 u = __ldg(in.v1 + sm);
-                c.x += 0.5f * u.x; c.y += 0.5f * u.y; c.z += 0.5f * u.z; c.w += 0.5f * u.w;
-            }
-            if (sp >= 0) {
-                const float4 u = __ldg(in.v1 + sp);
-                c.x += 0.5f * u.x; c.y += 0.5f * u.y; c.z += 0.5f * u.z; c.w += 0.5f * u.w;
-            }
-            out.v1[s] = c;
-        }
+// Clear: free the slots a build listed (keys to empty, values to zero).
+__device__ __forceinline__ void clear_role(Table t, const int *list, int n, int blk, int nblk) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = blk * kBlock + threadIdx.x; e < n; e += nblk * kBlock) {
+        const int s = __ldcg(list + e);
+        t.keys[s] = kEmpty;
+        t.v0[s] = z;
+        if (t.v1) t.v1[s] = z;
     }
 }
 
@@ -355,32 +435,42 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
     return true;
 }
 
+// Row j of x = T x_ref in float, as ((P_j0 x + P_j1 y) + P_j2 z) + P_j3 with
+// every operation rounded (no FMA), so that the moved positions -- which
+// decide lattice keys -- are reproducible outside the kernel.
+__device__ __forceinline__ float apply_row(const float *P, int j, float4 r) {
+    const float a = __fadd_rn(__fmul_rn(P[4 * j], r.x), __fmul_rn(P[4 * j + 1], r.y));
+    return __fadd_rn(__fadd_rn(a, __fmul_rn(P[4 * j + 2], r.z)), P[4 * j + 3]);
+}
+
 __device__ __forceinline__ void load_pose(const double *T, float *P) {
     // P: row-major 3x4 float copy of the pose, staged in shared memory.
     if (threadIdx.x < 12) P[threadIdx.x] = (float)T[(threadIdx.x / 4) * 4 + (threadIdx.x % 4)];
     __syncthreads();
 }
 
+// Step: one EM iteration minus the build.  Slice at x = T x_ref (E step,
+// Eq. 6 / Eq. 9), outlier weight M0/(M0+c) and residuals (Eq. 7 / Eq. 10),
+// twist Jacobian, reduction of A and b (Eq. 17-18); the last block to finish
+// solves and updates the pose.
 template <bool PT2PL, bool KAHAN>
-__global__ void __launch_bounds__(kBlock) k_rigid_step(const RigidJob *__restrict__ job,
-                                                        const IterParams *__restrict__ ipa, int it,
-                                                        Table t, double *partials,
-                                                        DeviceState *st) {
-    if (st->done) return;
+__device__ __forceinline__ void step_role(const IterLaunch &L, int blk, int nblk) {
     __shared__ float P[12];
+    __shared__ int last;
+    DeviceState *st = L.st;
     load_pose(st->T, P);
-    const IterParams ip = ipa[it];
+    const IterParams ip = L.ip[L.it];
+    const RigidJob *job = L.job;
     const int M = job->M;
     const int renorm = job->renormalize;
     const float4 *__restrict__ X = job->X;
+    const Table t = L.step;
     Acc<KAHAN> acc;
     acc.zero();
     int bad = 0;
-    for (int i = gtid(); i < M; i += grid_stride()) {
+    for (int i = blk * kBlock + threadIdx.x; i < M; i += nblk * kBlock) {
         const float4 r = __ldg(X + i);
-        const float x0 = P[0] * r.x + P[1] * r.y + P[2] * r.z + P[3];
-        const float x1 = P[4] * r.x + P[5] * r.y + P[6] * r.z + P[7];
-        const float x2 = P[8] * r.x + P[9] * r.y + P[10] * r.z + P[11];
+        const float x0 = apply_row(P, 0, r), x1 = apply_row(P, 1, r), x2 = apply_row(P, 2, r);
         Sums e;
         if (!slice_point<PT2PL>(t, x0, x1, x2, ip, e, bad)) continue;
         if (!(e.m0 > 0.0f)) continue;
@@ -438,8 +528,83 @@ __global__ void __launch_bounds__(kBlock) k_rigid_step(const RigidJob *__restric
         acc.add(29, 1.0f);
     }
     if (bad) atomicOr(&st->flags, bad);
-    block_partial<KAHAN>(acc, partials);
-    grid_finish(partials, st, job->stop_twist);
+    block_partial<KAHAN>(acc, L.partials, blk, nblk);
+    // The block's partial row is published by one thread: the barrier orders
+    // the row's stores before thread 0's fence, whose release covers them.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int done_blocks = atomicAdd(&st->ticket, 1);
+        last = done_blocks == nblk - 1;
+        if (last) __threadfence();
+    }
+    __syncthreads();
+    if (!last) return;
+    finish_iteration(L.partials, nblk, st, job->stop_twist);
+    if (threadIdx.x == 0) st->ticket = 0;
+}
+
+template <bool PT2PL, bool KAHAN>
+__global__ void __launch_bounds__(kBlock, 3) k_em_iter(IterLaunch L) {
+    int b = blockIdx.x;
+    if (b < L.gs) {
+        if (L.check_done && L.st->done) return;
+        step_role<PT2PL, KAHAN>(L, b, L.gs);
+        return;
+    }
+    b -= L.gs;
+    if (b < L.gb) {
+        if (L.check_done && L.st->done) return;
+        build_role<PT2PL>(L.job, L.ip + L.build_it, L.build, L.build_list, L.st, b, L.gb);
+        return;
+    }
+    b -= L.gb;
+    if (b < L.gc) clear_role(L.clear, L.clear_list, __ldcg(&L.ip[L.clear_it].nvert), b, L.gc);
+}
+
+struct ClearSet {
+    Table t[3];
+    const int *list[3];
+    const int *count[3];
+};
+
+__global__ void k_clear_lists(ClearSet c, int n) {
+    const int per = gridDim.x / n;
+    const int which = blockIdx.x / per;
+    if (which >= n) return;
+    clear_role(c.t[which], c.list[which], __ldcg(c.count[which]), blockIdx.x % per, per);
+}
+
+__global__ void k_blur_pass(Table in, Table out, int dir, const DeviceState *st) {
+    if (st && st->done) return;
+    for (uint32_t s = gtid(); s <= in.mask; s += grid_stride()) {
+        const unsigned long long key = __ldg(in.keys + s);
+        if (key == kEmpty) continue;
+        const int sm = find_key(in.keys, in.mask, neighbour_key(key, dir, -1));
+        const int sp = find_key(in.keys, in.mask, neighbour_key(key, dir, +1));
+        float4 a = __ldg(in.v0 + s);
+        if (sm >= 0) {
+            const float4 u = __ldg(in.v0 + sm);
+            a.x += 0.5f * u.x; a.y += 0.5f * u.y; a.z += 0.5f * u.z; a.w += 0.5f * u.w;
+        }
+        if (sp >= 0) {
+            const float4 u = __ldg(in.v0 + sp);
+            a.x += 0.5f * u.x; a.y += 0.5f * u.y; a.z += 0.5f * u.z; a.w += 0.5f * u.w;
+        }
+        out.v0[s] = a;
+        if (in.v1) {
+            float4 c = __ldg(in.v1 + s);
+            if (sm >= 0) {
+                const float4 u = __ldg(in.v1 + sm);
+                c.x += 0.5f * u.x; c.y += 0.5f * u.y; c.z += 0.5f * u.z; c.w += 0.5f * u.w;
+            }
+            if (sp >= 0) {
+                const float4 u = __ldg(in.v1 + sp);
+                c.x += 0.5f * u.x; c.y += 0.5f * u.y; c.z += 0.5f * u.z; c.w += 0.5f * u.w;
+            }
+            out.v1[s] = c;
+        }
+    }
 }
 
 // E-step sums at T x for every model point (the fr_estep entry point).
@@ -455,9 +620,7 @@ __global__ void __launch_bounds__(kBlock) k_estep_out(const RigidJob *__restrict
     int bad = 0;
     for (int i = gtid(); i < M; i += grid_stride()) {
         const float4 r = __ldg(job->X + i);
-        const float x0 = P[0] * r.x + P[1] * r.y + P[2] * r.z + P[3];
-        const float x1 = P[4] * r.x + P[5] * r.y + P[6] * r.z + P[7];
-        const float x2 = P[8] * r.x + P[9] * r.y + P[10] * r.z + P[11];
+        const float x0 = apply_row(P, 0, r), x1 = apply_row(P, 1, r), x2 = apply_row(P, 2, r);
         Sums e;
         slice_point<PT2PL>(t, x0, x1, x2, ip, e, bad);
         float *o = out + (size_t)i * vd;
@@ -607,39 +770,41 @@ int grid_for(long long n, int cap_blocks) {
 // Launchers
 // ---------------------------------------------------------------------------
 
-void launch_init_state(const RigidJob *job, DeviceState *st, cudaStream_t s) {
-    k_init_state<<<1, 32, 0, s>>>(job, st);
+void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s) {
+    const int grid = a.gs + a.gb + a.gc;
+    if (grid <= 0) return;
+    if (pt2pl) {
+        if (kahan) k_em_iter<true, true><<<grid, kBlock, 0, s>>>(a);
+        else k_em_iter<true, false><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        if (kahan) k_em_iter<false, true><<<grid, kBlock, 0, s>>>(a);
+        else k_em_iter<false, false><<<grid, kBlock, 0, s>>>(a);
+    }
 }
 
-void launch_clear_table(Table t, DeviceState *st, int full, int grid, cudaStream_t s) {
-    k_clear_table<<<grid, kBlock, 0, s>>>(t, st, full);
+int em_iter_blocks_per_sm(int pt2pl, int kahan) {
+    int n = 0;
+    const void *f = pt2pl ? (kahan ? (const void *)k_em_iter<true, true> : (const void *)k_em_iter<true, false>)
+                          : (kahan ? (const void *)k_em_iter<false, true> : (const void *)k_em_iter<false, false>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kBlock, 0);
+    return n > 0 ? n : 1;
 }
 
-void launch_build_splat(int pt2pl, const RigidJob *job, const IterParams *ip, int it, Table t,
-                        DeviceState *st, int grid, cudaStream_t s) {
-    if (pt2pl)
-        k_build_splat<true><<<grid, kBlock, 0, s>>>(job, ip, it, t, st);
-    else
-        k_build_splat<false><<<grid, kBlock, 0, s>>>(job, ip, it, t, st);
+void launch_clear_lists(const Table *tabs, int *const *lists, const int *const *counts, int n,
+                        int grid, cudaStream_t s) {
+    if (n <= 0) return;
+    ClearSet c{};
+    for (int i = 0; i < n && i < 3; ++i) {
+        c.t[i] = tabs[i];
+        c.list[i] = lists[i];
+        c.count[i] = counts[i];
+    }
+    const int per = (grid + n - 1) / n;
+    k_clear_lists<<<per * n, kBlock, 0, s>>>(c, n);
 }
 
 void launch_blur_pass(Table in, Table out, int dir, int grid, const DeviceState *st, cudaStream_t s) {
     k_blur_pass<<<grid, kBlock, 0, s>>>(in, out, dir, st);
-}
-
-void launch_rigid_step(int pt2pl, int kahan, const RigidJob *job, const IterParams *ip, int it,
-                       Table t, double *partials, DeviceState *st, int grid, cudaStream_t s) {
-    if (pt2pl) {
-        if (kahan)
-            k_rigid_step<true, true><<<grid, kBlock, 0, s>>>(job, ip, it, t, partials, st);
-        else
-            k_rigid_step<true, false><<<grid, kBlock, 0, s>>>(job, ip, it, t, partials, st);
-    } else {
-        if (kahan)
-            k_rigid_step<false, true><<<grid, kBlock, 0, s>>>(job, ip, it, t, partials, st);
-        else
-            k_rigid_step<false, false><<<grid, kBlock, 0, s>>>(job, ip, it, t, partials, st);
-    }
 }
 
 void launch_estep_out(int pt2pl, const RigidJob *job, const IterParams *ip, Table t, float *out,
