@@ -218,6 +218,32 @@ FR_API fr_status fr_register_rigid_host(fr_ctx *ctx, const float *h_X, int64_t M
                                         const fr_options *opt, double T_inout[16],
                                         fr_report *report);
 
+/* ---- E step without allocation ---------------------------------------------
+ * The paper has no counterpart to this entry point: it serves callers that
+ * cannot call cudaMalloc -- a host framework whose allocator has reserved
+ * the device's memory and forbids other allocations, or a real-time loop that
+ * must not take the device-wide synchronisation cudaMalloc / cudaFree can
+ * cause.
+ *
+ * fr_estep_noalloc: the E step of fr_estep without blur -- lattice over the
+ * observation d_Y (N x 4) with values [1, y] (d_Yn == NULL) or [1, y, n_y]
+ * (d_Yn, N x 4), sliced at the model points d_X (M x 4) moved by T (host
+ * double[16]) -- written to d_out (float, M x 4 or M x 7) on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default) of the current device.  It needs no
+ * context and allocates nothing: the hash table lives in a fixed scratch
+ * array compiled into the library (about 2.8 MB on every device that loads
+ * it, held until the process exits).  The first call on a device finds that
+ * array's device address and empties it (synchronising the stream once); it
+ * should come before any stream capture.  Every call shares the array and
+ * leaves it empty; calls that overlap on the GPU race and give wrong results.
+ * Synchronises the stream.  FR_EINVAL for null or misaligned pointers,
+ * M < 1, N < 1, N > FR_NOALLOC_MAX_OBS, sigma <= 0, a non-finite pose or
+ * input; FR_ECAPACITY if the table fills; FR_ECUDA if a CUDA call fails. */
+#define FR_NOALLOC_MAX_OBS 8192
+FR_API fr_status fr_estep_noalloc(const float *d_X, int64_t M, const float *d_Y,
+                                  const float *d_Yn, int64_t N, float sigma, const double T[16],
+                                  float *d_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,8 +34,9 @@ EXPORTED = [
     "fr_lattice_build", "fr_lattice_splat", "fr_lattice_blur", "fr_lattice_slice",
     "fr_lattice_vertices", "fr_lattice_info", "fr_lattice_destroy", "fr_estep",
     "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
-    "fr_ctx_transfer_bytes",
+    "fr_ctx_transfer_bytes", "fr_estep_noalloc",
 ]
+FR_NOALLOC_MAX_OBS = 8192
 KERNEL_CLASSES = ("clear", "build_splat", "blur", "rigid_step")
 
 
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = True):
     L.fr_ctx_set_profiling.argtypes = [_vp, ctypes.c_int]
     L.fr_ctx_profile.argtypes = [_vp, ctypes.POINTER(fr_profile), ctypes.c_int]
     L.fr_ctx_transfer_bytes.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    L.fr_estep_noalloc.argtypes = [_vp, _i64, _vp, _vp, _i64, ctypes.c_float, _f64p, _vp, _vp]
     for name in EXPORTED:  # every entry point must resolve (ctypes restype defaults to int)
         getattr(L, name)
     _lib = L
@@ -158,6 +160,30 @@ def _dev_ptr(t, name, rows=None, cols=4):
 def _pose(T) -> np.ndarray:
     T = np.ascontiguousarray(np.eye(4) if T is None else T, dtype=np.float64).reshape(4, 4).copy()
     return T
+
+
+def estep_noalloc(X, Y, Yn=None, sigma=0.02, T=None, out=None, stream=None):
+    """fr_estep_noalloc: the E step on the library's fixed scratch array (no
+    device allocation by the library; at most FR_NOALLOC_MAX_OBS observation
+    points).  X (M,4), Y (N,4), Yn (N,4) and `out` ((M,4) or (M,7) float32)
+    are CUDA tensors owned by the caller; `out` is created here if omitted.
+    Returns `out`."""
+    import torch
+    L = load()
+    vd = 7 if Yn is not None else 4
+    if out is None:
+        out = torch.empty((X.shape[0], vd), dtype=torch.float32, device=X.device)
+    _dev_ptr(out, "out", rows=X.shape[0], cols=vd)
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device)
+    Tm = _pose(T)
+    st = L.fr_estep_noalloc(_dev_ptr(X, "X"), X.shape[0], _dev_ptr(Y, "Y"),
+                            _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None,
+                            Y.shape[0], float(sigma), Tm.ctypes.data_as(_f64p), out.data_ptr(),
+                            _vp(stream.cuda_stream))
+    if st != FR_OK:
+        raise FilterRegError(st, f"fr_estep_noalloc: {L.fr_status_string(st).decode()}")
+    return out
 
 
 class Context:
