@@ -218,6 +218,40 @@ FR_API fr_status fr_register_rigid_host(fr_ctx *ctx, const float *h_X, int64_t M
                                         const fr_options *opt, double T_inout[16],
                                         fr_report *report);
 
+/* ---- batched rigid registration ---------------------------------------------
+ * One registration of a batch.  Clouds as for fr_register_rigid (device
+ * pointers for fr_register_rigid_batch, host pointers for
+ * fr_register_rigid_batch_host); sigma_start/sigma_end/w replace the options'
+ * values for this item; T carries the initial pose in and the result out;
+ * status receives this item's outcome. */
+typedef struct {
+    const float *d_X;
+    int64_t M;
+    const float *d_Y;
+    const float *d_Yn;
+    int64_t N;
+    float sigma_start, sigma_end, w;
+    double T[16];
+    fr_status status;
+} fr_batch_item;
+
+/* fr_register_rigid_batch: register n_items independent pairs together, each
+ * exactly as fr_register_rigid would (Sections 3.1, 4, 5) but with one launch
+ * per EM iteration for the whole batch: every item's step, next-sigma build
+ * and clear run side by side, so that one item's float64 solve overlaps the
+ * others' work.  Items may differ in size and sigma schedule; they share
+ * opt->residual, iters, kahan, renormalize_normals and stop_twist (blur is
+ * not supported: FR_ENOTSUPPORTED).  reports (nullable) has n_items entries.
+ * Returns FR_OK, or the status of the first failed item (each item's own
+ * outcome is in its status field; failed items keep their input pose).
+ * Synchronises the stream. */
+FR_API fr_status fr_register_rigid_batch(fr_ctx *ctx, fr_batch_item *items, int n_items,
+                                         const fr_options *opt, fr_report *reports);
+/* The same with the items' clouds in host memory: they are copied into a
+ * context-owned device staging area on the context's stream first. */
+FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items, int n_items,
+                                              const fr_options *opt, fr_report *reports);
+
 /* ---- E step without allocation ---------------------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
  * cannot call cudaMalloc -- a host framework whose allocator has reserved

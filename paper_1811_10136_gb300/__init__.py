@@ -34,10 +34,11 @@ EXPORTED = [
     "fr_lattice_build", "fr_lattice_splat", "fr_lattice_blur", "fr_lattice_slice",
     "fr_lattice_vertices", "fr_lattice_info", "fr_lattice_destroy", "fr_estep",
     "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
-    "fr_ctx_transfer_bytes", "fr_estep_noalloc",
+    "fr_ctx_transfer_bytes", "fr_estep_noalloc", "fr_register_rigid_batch",
+    "fr_register_rigid_batch_host",
 ]
 FR_NOALLOC_MAX_OBS = 8192
-KERNEL_CLASSES = ("clear", "build_splat", "blur", "rigid_step")
+KERNEL_CLASSES = ("clear", "build", "blur", "em_iter")
 
 
 class FilterRegError(RuntimeError):
@@ -60,6 +61,13 @@ class fr_report(ctypes.Structure):
                 ("last_cost", ctypes.c_double), ("last_twist_norm", ctypes.c_double),
                 ("lattice_vertices", ctypes.c_int64), ("lattice_builds", ctypes.c_int32),
                 ("lattice_vertices_sum", ctypes.c_int64)]
+
+
+class fr_batch_item(ctypes.Structure):
+    _fields_ = [("d_X", ctypes.c_void_p), ("M", ctypes.c_int64), ("d_Y", ctypes.c_void_p),
+                ("d_Yn", ctypes.c_void_p), ("N", ctypes.c_int64), ("sigma_start", ctypes.c_float),
+                ("sigma_end", ctypes.c_float), ("w", ctypes.c_float), ("T", ctypes.c_double * 16),
+                ("status", ctypes.c_int)]
 
 
 class fr_profile(ctypes.Structure):
@@ -110,6 +118,9 @@ def load(build_if_missing: bool = True):
     L.fr_ctx_set_profiling.argtypes = [_vp, ctypes.c_int]
     L.fr_ctx_profile.argtypes = [_vp, ctypes.POINTER(fr_profile), ctypes.c_int]
     L.fr_ctx_transfer_bytes.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    L.fr_register_rigid_batch.argtypes = [_vp, ctypes.POINTER(fr_batch_item), ctypes.c_int,
+                                          ctypes.POINTER(fr_options), ctypes.POINTER(fr_report)]
+    L.fr_register_rigid_batch_host.argtypes = L.fr_register_rigid_batch.argtypes
     L.fr_estep_noalloc.argtypes = [_vp, _i64, _vp, _vp, _i64, ctypes.c_float, _f64p, _vp, _vp]
     for name in EXPORTED:  # every entry point must resolve (ctypes restype defaults to int)
         getattr(L, name)
@@ -283,6 +294,48 @@ class Context:
         del keep
         self._check(st, "fr_register_rigid_host")
         return T, _report(rep)
+
+    def register_rigid_batch(self, pairs, sigmas=None, ws=None, T0s=None, host=False, **opts):
+        """Register a batch of pairs in one launch per EM iteration.
+
+        pairs: list of (X, Y, Yn) -- CUDA tensors (host=False) or float32 (n, 4)
+        host arrays / tensors (host=True); Yn may be None for point-to-point.
+        sigmas: list of (sigma_start, sigma_end) per item (default: the
+        options' schedule); ws: outlier ratios; T0s: initial poses.
+        Returns a list of (T (4,4), Report, status) per item."""
+        L = load()
+        o = options(**opts)
+        n = len(pairs)
+        items = (fr_batch_item * n)()
+        reps = (fr_report * n)()
+        keep = []
+        for b, (X, Y, Yn) in enumerate(pairs):
+            it = items[b]
+            if host:
+                arrs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None for a in (X, Y, Yn)]
+                keep.append(arrs)
+                it.d_X, it.d_Y = arrs[0].ctypes.data, arrs[1].ctypes.data
+                it.d_Yn = arrs[2].ctypes.data if arrs[2] is not None else None
+                it.M, it.N = arrs[0].shape[0], arrs[1].shape[0]
+            else:
+                it.d_X, it.d_Y = _dev_ptr(X, "X"), _dev_ptr(Y, "Y")
+                it.d_Yn = _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None
+                it.M, it.N = X.shape[0], Y.shape[0]
+            s0, s1 = sigmas[b] if sigmas is not None else (o.sigma_start, o.sigma_end)
+            it.sigma_start, it.sigma_end = float(s0), float(s1)
+            it.w = float(ws[b]) if ws is not None else o.w
+            T = _pose(T0s[b] if T0s is not None else None)
+            for i in range(16):
+                it.T[i] = T.ravel()[i]
+        f = L.fr_register_rigid_batch_host if host else L.fr_register_rigid_batch
+        st = f(self._h, items, n, ctypes.byref(o), reps)
+        if st != FR_OK and not any(items[b].status != FR_OK for b in range(n)):
+            self._check(st, "fr_register_rigid_batch")   # the call itself failed
+        out = []
+        for b in range(n):
+            T = np.array(items[b].T[:], dtype=np.float64).reshape(4, 4)
+            out.append((T, _report(reps[b]), int(items[b].status)))
+        return out
 
     def estep(self, X, Y, Yn=None, sigma=0.02, blur=False, T=None):
         """E-step sums at T X: (M, 4) [M0, M1] or (M, 7) [M0, M1, Nsum] float32 CUDA tensor."""

@@ -15,145 +15,9 @@
 #include <string>
 #include <vector>
 
-#include "filterreg.h"
-#include "internal.h"
+#include "context.h"
 
 using namespace fr;
-
-namespace {
-
-// Lattice scale alpha = sqrt(2/3) (d+1): splat-blur-slice then approximates a
-// unit-std Gaussian in feature units (Section 4.2 / Adams et al. 2010).
-const double kAlpha = std::sqrt(2.0 / 3.0) * 4.0;
-
-// Integral of the unnormalised splat+slice kernel over feature space: the
-// volume per lattice point of the remainder-class union in the hyperplane,
-// (d+1)^(d - 1/2), divided by alpha^d; each blur pass doubles it.
-double lattice_kernel_mass(int blur) {
-    double g = std::pow(4.0, 2.5) / std::pow(kAlpha, 3.0);
-    return blur ? g * 16.0 : g;
-}
-
-void feature_scales(float sigma, float s[3]) {
-    for (int i = 1; i <= 3; ++i)
-        s[i - 1] = (float)(kAlpha / std::sqrt((double)(i * (i + 1))) / (double)sigma);
-}
-
-uint32_t pow2_at_least(long long n) {
-    uint32_t c = 1024;
-    while ((long long)c < n && c < (1u << 30)) c <<= 1;
-    return c;
-}
-
-bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
-
-// Everything a captured graph bakes in besides the job descriptor.
-struct GraphKey {
-    int v[14];
-    uint64_t ws_gen;
-    bool operator==(const GraphKey &o) const {
-        return ws_gen == o.ws_gen && std::memcmp(v, o.v, sizeof v) == 0;
-    }
-};
-
-struct CachedGraph {
-    GraphKey key;
-    cudaGraphExec_t exec = nullptr;
-    int kernels = 0;
-    uint64_t last_use = 0;
-};
-
-template <typename T>
-cudaError_t dev_alloc(T **p, size_t count) {
-    return cudaMalloc((void **)p, count * sizeof(T) + 16);
-}
-
-}  // namespace
-
-struct fr_lattice {
-    uint32_t cap = 0;
-    int n = 0;
-    int vdim = 0;
-    float scale[3] = {0, 0, 0};
-    unsigned long long *keys = nullptr;
-    float4 *v0 = nullptr, *v1 = nullptr, *t0 = nullptr, *t1 = nullptr;
-    int *rec_slot = nullptr;
-    float *rec_w = nullptr;
-    int *counters = nullptr;  // [0] vertices, [1] flags, [2] scratch count
-    int64_t nvert = 0;
-};
-
-struct fr_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    std::string err;
-    int num_sms = 0;
-    int64_t launches = 0;
-    int64_t h2d_bytes = 0, d2h_bytes = 0;
-
-    // workspace: three rotating lattice tables (the build of the next sigma
-    // overlaps the slice of the current one), blur scratch planes, reduction
-    // partials, device state, job descriptor and per-iteration constants.
-    uint64_t ws_gen = 1;
-    uint32_t table_cap = 0;
-    Table tables[3] = {};
-    int *lists[3] = {nullptr, nullptr, nullptr};  // slots claimed by each table's last build
-    float4 *blur0 = nullptr, *blur1 = nullptr;
-    float2 *partials = nullptr;
-    int partial_rows = 0;
-    DeviceState *d_state = nullptr;
-    RigidJob *d_job = nullptr;
-    IterParams *d_ip = nullptr;
-    int ip_cap = 0;
-    float4 *stage = nullptr;  // host-call staging of X, Y, Yn
-    size_t stage_cap = 0;     // in float4
-
-    // pinned host mirrors
-    RigidJob *h_job = nullptr;
-    IterParams *h_ip = nullptr;
-    DeviceState *h_state = nullptr;
-
-    std::vector<CachedGraph> graphs;
-    uint64_t use_clock = 0;
-    int bpsm[2][2] = {{0, 0}, {0, 0}};  // resident fused-kernel blocks per SM
-
-    // per-kernel profiling: event pairs around each launch of a plan
-    int profiling = 0;
-    std::vector<cudaEvent_t> events;  // 2 per kernel, grown on demand, kept for the graphs
-    std::vector<int> event_class;     // kernel class of each event pair of the last plan
-    int64_t prof_launches[FR_K_CLASSES] = {0, 0, 0, 0};
-    double prof_ms[FR_K_CLASSES] = {0, 0, 0, 0};
-
-    fr_status fail(fr_status s, const char *fmt, ...) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        err = buf;
-        return s;
-    }
-    fr_status cuda(cudaError_t e, const char *what) {
-        if (e == cudaSuccess) return FR_OK;
-        cudaGetLastError();
-        return fail(e == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA, "%s: %s", what,
-                    cudaGetErrorString(e));
-    }
-};
-
-#define FR_TRY(expr)                         \
-    do {                                     \
-        fr_status _s = (expr);               \
-        if (_s != FR_OK) return _s;          \
-    } while (0)
-#define FR_CUDA(ctx, call) FR_TRY((ctx)->cuda((call), #call))
-
-// cudaMemcpyAsync on the context's stream, counting the bytes moved.
-static cudaError_t copy_async(fr_ctx *ctx, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
-    if (kind == cudaMemcpyHostToDevice) ctx->h2d_bytes += (int64_t)bytes;
-    if (kind == cudaMemcpyDeviceToHost) ctx->d2h_bytes += (int64_t)bytes;
-    return cudaMemcpyAsync(dst, src, bytes, kind, ctx->stream);
-}
 
 namespace {
 
@@ -245,6 +109,9 @@ fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows) {
     return FR_OK;
 }
 
+}  // namespace
+
+namespace fr {
 int blocks_for(const fr_ctx *ctx, long long n, int per_sm) {
     long long g = (n + kBlock - 1) / kBlock;
     long long cap = (long long)ctx->num_sms * per_sm;
@@ -252,7 +119,6 @@ int blocks_for(const fr_ctx *ctx, long long n, int per_sm) {
     if (g < 1) g = 1;
     return (int)g;
 }
-
 fr_status check_flags(fr_ctx *ctx, int flags) {
     if (flags & kFlagCapacity)
         return ctx->fail(FR_ECAPACITY, "lattice hash table full");
@@ -261,6 +127,9 @@ fr_status check_flags(fr_ctx *ctx, int flags) {
                                     "(position / sigma too large)");
     return FR_OK;
 }
+}  // namespace fr
+
+namespace {
 
 // The registration as a sequence of launches (captured into a graph or
 // issued directly).
@@ -445,13 +314,15 @@ fr_status run_plan(fr_ctx *ctx, const Plan &p, bool use_graph) {
     return FR_OK;
 }
 
+}  // namespace
+
+namespace fr {
 fr_status validate_cloud(fr_ctx *ctx, const void *p, int64_t n, const char *name) {
     if (!p) return ctx->fail(FR_EINVAL, "%s is NULL", name);
     if (n < 1 || n > (1ll << 30)) return ctx->fail(FR_EINVAL, "%s: size %lld out of range", name, (long long)n);
     if (!aligned16(p)) return ctx->fail(FR_EINVAL, "%s must be 16-byte aligned (n x 4 floats)", name);
     return FR_OK;
 }
-
 fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
     if (!o) return ctx->fail(FR_EINVAL, "options are NULL");
     if (o->residual != FR_PT2PT && o->residual != FR_PT2PL)
@@ -465,11 +336,17 @@ fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
         return ctx->fail(FR_ENOTSUPPORTED, "only FP32 lattice storage is implemented");
     return FR_OK;
 }
+}  // namespace fr
+
+namespace {
 
 // Host-side constants of every iteration: the sigma schedule (geometric
 // between sigma_start and sigma_end), feature scales and outlier constant
 // c = w/(1-w) N/M (Eq. 7) in the lattice kernel's units (times sigma^3 G).
 // Returns true when sigma changes during the schedule (annealing).
+}  // namespace
+
+namespace fr {
 bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip) {
     const double s0 = o->sigma_start, s1 = o->sigma_end;
     const double c = (double)o->w / (1.0 - (double)o->w) * ((double)N / (double)M);
@@ -497,11 +374,18 @@ bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip)
     }
     return changes;
 }
+int fused_blocks_per_sm(fr_ctx *ctx, int pt2pl, int kahan) {
+    int &bpsm = ctx->bpsm[pt2pl][kahan];
+    if (!bpsm) bpsm = em_iter_blocks_per_sm(pt2pl, kahan);
+    return bpsm;
+}
+}  // namespace fr
+
+namespace {
 
 // Splits the resident blocks of the fused kernel between its roles.
 void plan_grids(fr_ctx *ctx, Plan &p, int64_t M, int64_t N, uint32_t cap) {
-    int &bpsm = ctx->bpsm[p.residual][p.kahan];
-    if (!bpsm) bpsm = em_iter_blocks_per_sm(p.residual, p.kahan);
+    const int bpsm = fused_blocks_per_sm(ctx, p.residual, p.kahan);
     const long long resident = (long long)bpsm * ctx->num_sms;
     long long gs = (M + kBlock - 1) / kBlock, gb = (N + kBlock - 1) / kBlock;
     long long gc = p.annealed ? std::max<long long>(8, std::min<long long>(64, cap / 16384)) : 0;
@@ -579,6 +463,7 @@ FR_API fr_status fr_ctx_destroy(fr_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
+    free_batch_workspace(ctx);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     free_tables(ctx);
     cudaFree(ctx->partials);

@@ -1,0 +1,170 @@
+// Internal host-side context of the C ABI, shared by the translation units
+// that implement it (api.cu: context, lattice primitives, single
+// registration; batch.cu: batched registration and the serving loop).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "filterreg.h"
+#include "internal.h"
+
+namespace fr {
+struct BatchWorkspace;
+struct ServerState;
+}
+
+namespace fr {
+
+// Lattice scale alpha = sqrt(2/3) (d+1): splat-blur-slice then approximates a
+// unit-std Gaussian in feature units (Section 4.2 / Adams et al. 2010).
+inline const double kAlpha = std::sqrt(2.0 / 3.0) * 4.0;
+
+// Integral of the unnormalised splat+slice kernel over feature space: the
+// volume per lattice point of the remainder-class union in the hyperplane,
+// (d+1)^(d - 1/2), divided by alpha^d; each blur pass doubles it.
+inline double lattice_kernel_mass(int blur) {
+    double g = std::pow(4.0, 2.5) / std::pow(kAlpha, 3.0);
+    return blur ? g * 16.0 : g;
+}
+
+inline void feature_scales(float sigma, float s[3]) {
+    for (int i = 1; i <= 3; ++i)
+        s[i - 1] = (float)(kAlpha / std::sqrt((double)(i * (i + 1))) / (double)sigma);
+}
+
+inline uint32_t pow2_at_least(long long n) {
+    uint32_t c = 1024;
+    while ((long long)c < n && c < (1u << 30)) c <<= 1;
+    return c;
+}
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Everything a captured graph bakes in besides the job descriptor.
+struct GraphKey {
+    int v[14];
+    uint64_t ws_gen;
+    bool operator==(const GraphKey &o) const {
+        return ws_gen == o.ws_gen && std::memcmp(v, o.v, sizeof v) == 0;
+    }
+};
+
+struct CachedGraph {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+    uint64_t last_use = 0;
+};
+
+template <typename T>
+inline cudaError_t dev_alloc(T **p, size_t count) {
+    return cudaMalloc((void **)p, count * sizeof(T) + 16);
+}
+
+}  // namespace fr
+
+struct fr_lattice {
+    uint32_t cap = 0;
+    int n = 0;
+    int vdim = 0;
+    float scale[3] = {0, 0, 0};
+    unsigned long long *keys = nullptr;
+    float4 *v0 = nullptr, *v1 = nullptr, *t0 = nullptr, *t1 = nullptr;
+    int *rec_slot = nullptr;
+    float *rec_w = nullptr;
+    int *counters = nullptr;  // [0] vertices, [1] flags, [2] scratch count
+    int64_t nvert = 0;
+};
+
+struct fr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int num_sms = 0;
+    int64_t launches = 0;
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
+
+    // workspace: three rotating lattice tables (the build of the next sigma
+    // overlaps the slice of the current one), blur scratch planes, reduction
+    // partials, device state, job descriptor and per-iteration constants.
+    uint64_t ws_gen = 1;
+    uint32_t table_cap = 0;
+    fr::Table tables[3] = {};
+    int *lists[3] = {nullptr, nullptr, nullptr};  // slots claimed by each table's last build
+    float4 *blur0 = nullptr, *blur1 = nullptr;
+    float2 *partials = nullptr;
+    int partial_rows = 0;
+    fr::DeviceState *d_state = nullptr;
+    fr::RigidJob *d_job = nullptr;
+    fr::IterParams *d_ip = nullptr;
+    int ip_cap = 0;
+    float4 *stage = nullptr;  // host-call staging of X, Y, Yn
+    size_t stage_cap = 0;     // in float4
+
+    // pinned host mirrors
+    fr::RigidJob *h_job = nullptr;
+    fr::IterParams *h_ip = nullptr;
+    fr::DeviceState *h_state = nullptr;
+
+    std::vector<fr::CachedGraph> graphs;
+    uint64_t use_clock = 0;
+    int bpsm[2][2] = {{0, 0}, {0, 0}};  // resident fused-kernel blocks per SM
+
+    fr::BatchWorkspace *batch = nullptr;  // batched-registration workspace (batch.cu)
+
+    // per-kernel profiling: event pairs around each launch of a plan
+    int profiling = 0;
+    std::vector<cudaEvent_t> events;  // 2 per kernel, grown on demand, kept for the graphs
+    std::vector<int> event_class;     // kernel class of each event pair of the last plan
+    int64_t prof_launches[FR_K_CLASSES] = {0, 0, 0, 0};
+    double prof_ms[FR_K_CLASSES] = {0, 0, 0, 0};
+
+    fr_status fail(fr_status s, const char *fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return s;
+    }
+    fr_status cuda(cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return FR_OK;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA, "%s: %s", what,
+                    cudaGetErrorString(e));
+    }
+};
+
+#define FR_TRY(expr)                         \
+    do {                                     \
+        fr_status _s = (expr);               \
+        if (_s != FR_OK) return _s;          \
+    } while (0)
+#define FR_CUDA(ctx, call) FR_TRY((ctx)->cuda((call), #call))
+
+// cudaMemcpyAsync on the context's stream, counting the bytes moved.
+inline cudaError_t copy_async(fr_ctx *ctx, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+    if (kind == cudaMemcpyHostToDevice) ctx->h2d_bytes += (int64_t)bytes;
+    if (kind == cudaMemcpyDeviceToHost) ctx->d2h_bytes += (int64_t)bytes;
+    return cudaMemcpyAsync(dst, src, bytes, kind, ctx->stream);
+}
+
+
+namespace fr {
+// Helpers implemented in api.cu.
+int blocks_for(const fr_ctx *ctx, long long n, int per_sm);
+fr_status check_flags(fr_ctx *ctx, int flags);
+fr_status validate_cloud(fr_ctx *ctx, const void *p, int64_t n, const char *name);
+fr_status validate_options(fr_ctx *ctx, const fr_options *o);
+bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip);
+int fused_blocks_per_sm(fr_ctx *ctx, int pt2pl, int kahan);
+void free_batch_workspace(fr_ctx *ctx);   // batch.cu
+}  // namespace fr

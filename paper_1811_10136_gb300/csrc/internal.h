@@ -80,7 +80,29 @@ struct IterLaunch {
     int check_done;        // roles return at once once st->done is set
 };
 
+// One registration of a multi-registration launch (device-resident).
+struct Slot {
+    const RigidJob *job;
+    DeviceState *st;
+    IterParams *ip;        // [iters] of this registration
+    float2 *partials;      // >= step blocks per launch rows of kRigidVals pairs
+    Table tab[3];          // rotating lattice tables
+    int *list[3];          // slots claimed by each table's last build
+};
+
+enum { kRoleNone = 0, kRoleStep = 1, kRoleBuild = 2, kRoleClear = 3 };
+
+// A run of nblk consecutive blocks (from blk0) doing one role for one slot:
+// step of iteration `it` on table `tab`; build of iteration `it` into `tab`;
+// or clear of `tab`, whose claimed slots build `it` listed.
+struct Seg {
+    int slot, role, it, tab;
+    int blk0, nblk;
+};
+
 // ---- launchers (kernels.cu) -------------------------------------------------
+void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
+                     const unsigned short *blockseg, int grid, int check_done, cudaStream_t s);
 void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s);
 int em_iter_blocks_per_sm(int pt2pl, int kahan);
 // Frees the slots listed by builds (list lists[i], count *counts[i]).

@@ -305,13 +305,18 @@ __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *
 
 // Build: Section 4.2 "Splat" of the observation with values [1, y] or
 // [1, y, n_y] (Eq. 11), fused with the lattice build (elevate, simplex, hash
-// insert, float4 atomic accumulation).  One thread per point per round; the
-// slots a round claims are appended to `list` (one atomic per block and
-// round on the build's vertex counter) so that the table can later be freed
-// without scanning it.
+// insert, float4 atomic accumulation).  One thread per point per round.
+// Lanes of a warp whose points share a lattice vertex (neighbouring pixels
+// of a depth image mostly do, in raster order) are merged first: runs of
+// equal keys in consecutive lanes are summed by a segmented scan and only
+// the run's last lane inserts the key and issues the atomics.  The slots a
+// round claims are appended to `list` (one atomic per block and round on the
+// build's vertex counter) so that the table can later be freed without
+// scanning it.
 template <bool PT2PL>
 __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, IterParams *ipp,
                                            Table t, int *list, DeviceState *st, int blk, int nblk) {
+    constexpr int kCh = PT2PL ? 7 : 4;
     __shared__ int s_warp[kBlock / 32];
     __shared__ int s_base;
     const IterParams ip = *ipp;
@@ -325,30 +330,63 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
     unsigned long long claimed_total = 0;
     for (int r = 0; r < rounds; ++r) {
         const int i = r * per_round + blk * kBlock + threadIdx.x;
-        int sl[kD];
-        int mask = 0;
+        Simplex sx;
+        bool valid = false;
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f), n = y;
         if (i < N) {
-            const float4 y = __ldg(Y + i);
-            Simplex sx;
-            if (!embed(y.x, y.y, y.z, ip.s1, ip.s2, ip.s3, sx)) {
-                bad |= kFlagRange;
-            } else {
-                float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (PT2PL) n = __ldg(Yn + i);
+            y = __ldg(Y + i);
+            if (PT2PL) n = __ldg(Yn + i);
+            valid = embed(y.x, y.y, y.z, ip.s1, ip.s2, ip.s3, sx);
+            if (!valid) bad |= kFlagRange;
+        }
+        // Merge runs of equal keys across neighbouring lanes: a segmented
+        // inclusive scan (five shuffle steps, lane order) leaves each run's sum
+        // at its last lane, which alone inserts the key and issues the atomics.
+        unsigned long long key[kD];
+        float sum[kD][kCh];
+        int tails = 0;
 #pragma unroll
-                for (int k = 0; k < kD; ++k) {
-                    bool claimed;
-                    sl[k] = insert_key(t.keys, t.mask, sx.key[k], t.mask + 1, claimed);
-                    if (sl[k] < 0) {
-                        bad |= kFlagCapacity;
-                        continue;
-                    }
-                    mask |= claimed ? (1 << k) : 0;
-                    const float b = sx.b[k];
-                    atomicAdd(t.v0 + sl[k], make_float4(b, b * y.x, b * y.y, b * y.z));
-                    if (PT2PL) atomicAdd(t.v1 + sl[k], make_float4(b * n.x, b * n.y, b * n.z, 0.f));
+        for (int k = 0; k < kD; ++k) {
+            key[k] = valid ? sx.key[k] : kEmpty;
+            const unsigned long long prev = __shfl_up_sync(kFull, key[k], 1);
+            const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != key[k]);
+            const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+            const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+            const float b = valid ? sx.b[k] : 0.0f;
+            float v[kCh];
+            v[0] = b;
+            v[1] = b * y.x;
+            v[2] = b * y.y;
+            v[3] = b * y.z;
+            if (PT2PL) {
+                v[4] = b * n.x;
+                v[5] = b * n.y;
+                v[6] = b * n.z;
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int c = 0; c < kCh; ++c) {
+                    const float t = __shfl_up_sync(kFull, v[c], o);
+                    if (lane - o >= head) v[c] += t;
                 }
             }
+#pragma unroll
+            for (int c = 0; c < kCh; ++c) sum[k][c] = v[c];
+            tails |= (valid && tail) ? (1 << k) : 0;
+        }
+        // Run tails insert their keys (four probes in flight) and accumulate.
+        int sl[kD];
+        const int mask = insert4(t.keys, t.mask, key, tails, sl);
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            if (!(tails >> k & 1)) continue;
+            if (sl[k] < 0) {
+                bad |= kFlagCapacity;
+                continue;
+            }
+            atomicAdd(t.v0 + sl[k], make_float4(sum[k][0], sum[k][1], sum[k][2], sum[k][3]));
+            if (PT2PL) atomicAdd(t.v1 + sl[k], make_float4(sum[k][4], sum[k][5], sum[k][6], 0.f));
         }
         // Block-wide exclusive prefix of the claimed counts.
         const int cnt = __popc(mask);
@@ -454,17 +492,15 @@ __device__ __forceinline__ void load_pose(const double *T, float *P) {
 // twist Jacobian, reduction of A and b (Eq. 17-18); the last block to finish
 // solves and updates the pose.
 template <bool PT2PL, bool KAHAN>
-__device__ __forceinline__ void step_role(const IterLaunch &L, int blk, int nblk) {
+__device__ __forceinline__ void step_role(const RigidJob *job, const IterParams *ipp, const Table t,
+                                          float2 *partials, DeviceState *st, int blk, int nblk) {
     __shared__ float P[12];
     __shared__ int last;
-    DeviceState *st = L.st;
     load_pose(st->T, P);
-    const IterParams ip = L.ip[L.it];
-    const RigidJob *job = L.job;
+    const IterParams ip = *ipp;
     const int M = job->M;
     const int renorm = job->renormalize;
     const float4 *__restrict__ X = job->X;
-    const Table t = L.step;
     Acc<KAHAN> acc;
     acc.zero();
     int bad = 0;
@@ -528,7 +564,7 @@ __device__ __forceinline__ void step_role(const IterLaunch &L, int blk, int nblk
         acc.add(29, 1.0f);
     }
     if (bad) atomicOr(&st->flags, bad);
-    block_partial<KAHAN>(acc, L.partials, blk, nblk);
+    block_partial<KAHAN>(acc, partials, blk, nblk);
     // The block's partial row is published by one thread: the barrier orders
     // the row's stores before thread 0's fence, whose release covers them.
     __syncthreads();
@@ -540,7 +576,7 @@ __device__ __forceinline__ void step_role(const IterLaunch &L, int blk, int nblk
     }
     __syncthreads();
     if (!last) return;
-    finish_iteration(L.partials, nblk, st, job->stop_twist);
+    finish_iteration(partials, nblk, st, job->stop_twist);
     if (threadIdx.x == 0) st->ticket = 0;
 }
 
@@ -549,7 +585,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_em_iter(IterLaunch L) {
     int b = blockIdx.x;
     if (b < L.gs) {
         if (L.check_done && L.st->done) return;
-        step_role<PT2PL, KAHAN>(L, b, L.gs);
+        step_role<PT2PL, KAHAN>(L.job, L.ip + L.it, L.step, L.partials, L.st, b, L.gs);
         return;
     }
     b -= L.gs;
@@ -560,6 +596,31 @@ __global__ void __launch_bounds__(kBlock, 3) k_em_iter(IterLaunch L) {
     }
     b -= L.gb;
     if (b < L.gc) clear_role(L.clear, L.clear_list, __ldcg(&L.ip[L.clear_it].nvert), b, L.gc);
+}
+
+// Many registrations per launch: block b runs segment blockseg[b] -- one role
+// of one slot (registration) at that slot's own iteration.  Used by the
+// batched entry point (all slots in lockstep) and the serving loop (slots at
+// different iterations).
+template <bool PT2PL, bool KAHAN>
+__global__ void __launch_bounds__(kBlock, 3) k_em_multi(const Slot *__restrict__ slots,
+                                                         const Seg *__restrict__ segs,
+                                                         const unsigned short *__restrict__ blockseg,
+                                                         int check_done) {
+    const Seg sg = segs[blockseg[blockIdx.x]];
+    if (sg.role == kRoleNone) return;
+    const Slot &sl = slots[sg.slot];
+    DeviceState *st = sl.st;
+    const int b = blockIdx.x - sg.blk0;
+    if (sg.role == kRoleStep) {
+        if (check_done && st->done) return;
+        step_role<PT2PL, KAHAN>(sl.job, sl.ip + sg.it, sl.tab[sg.tab], sl.partials, st, b, sg.nblk);
+    } else if (sg.role == kRoleBuild) {
+        if (check_done && st->done) return;
+        build_role<PT2PL>(sl.job, sl.ip + sg.it, sl.tab[sg.tab], sl.list[sg.tab], st, b, sg.nblk);
+    } else if (sg.role == kRoleClear) {
+        clear_role(sl.tab[sg.tab], sl.list[sg.tab], __ldcg(&sl.ip[sg.it].nvert), b, sg.nblk);
+    }
 }
 
 struct ClearSet {
@@ -779,6 +840,18 @@ void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s) {
     } else {
         if (kahan) k_em_iter<false, true><<<grid, kBlock, 0, s>>>(a);
         else k_em_iter<false, false><<<grid, kBlock, 0, s>>>(a);
+    }
+}
+
+void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
+                     const unsigned short *blockseg, int grid, int check_done, cudaStream_t s) {
+    if (grid <= 0) return;
+    if (pt2pl) {
+        if (kahan) k_em_multi<true, true><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
+        else k_em_multi<true, false><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
+    } else {
+        if (kahan) k_em_multi<false, true><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
+        else k_em_multi<false, false><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
     }
 }
 

@@ -141,8 +141,8 @@ __device__ __forceinline__ bool embed(float px, float py, float pz, float s1, fl
 // by other keys).  *claimed is set when this call created the vertex.
 __device__ __forceinline__ int insert_key(unsigned long long *keys, uint32_t mask,
                                           unsigned long long key, uint32_t max_probe,
-                                          bool &claimed) {
-    uint32_t s = slot_of(key, mask);
+                                          bool &claimed, int start = -1) {
+    uint32_t s = start >= 0 ? (uint32_t)start : slot_of(key, mask);
     claimed = false;
     for (uint32_t p = 0; p < max_probe; ++p) {
         unsigned long long cur = __ldcg(keys + s);
@@ -158,6 +158,43 @@ __device__ __forceinline__ int insert_key(unsigned long long *keys, uint32_t mas
         s = (s + 1) & mask;
     }
     return -1;
+}
+
+// Inserts up to four keys at once (key k only where active & (1 << k)):
+// the first probes are loaded together and the needed CASes issued back to
+// back, so the four round trips to L2 overlap; collision chains are walked
+// afterwards by insert_key.  slot[k] = -1 where inactive or the table is
+// full; bit k of the return value is set where this call created the vertex.
+__device__ __forceinline__ int insert4(unsigned long long *keys, uint32_t mask,
+                                       const unsigned long long key[kD], int active, int slot[kD]) {
+    uint32_t s[kD];
+    unsigned long long cur[kD], old[kD];
+#pragma unroll
+    for (int k = 0; k < kD; ++k) s[k] = slot_of(key[k], mask);
+#pragma unroll
+    for (int k = 0; k < kD; ++k) cur[k] = (active >> k & 1) ? __ldcg(keys + s[k]) : key[k];
+#pragma unroll
+    for (int k = 0; k < kD; ++k)
+        old[k] = ((active >> k & 1) && cur[k] == kEmpty) ? atomicCAS(keys + s[k], kEmpty, key[k])
+                                                          : cur[k];
+    int claimed = 0;
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        slot[k] = -1;
+        if (!(active >> k & 1)) continue;
+        if (cur[k] == kEmpty && old[k] == kEmpty) {
+            claimed |= 1 << k;
+            slot[k] = (int)s[k];
+        } else if (old[k] == key[k]) {
+            slot[k] = (int)s[k];
+        } else {
+            bool c;
+            const int t = insert_key(keys, mask, key[k], mask, c, (s[k] + 1) & mask);
+            slot[k] = t;
+            claimed |= c ? (1 << k) : 0;
+        }
+    }
+    return claimed;
 }
 
 // Slot of `key`, or -1 if absent.  The table must not change during the call
