@@ -4,9 +4,12 @@ point-to-plane registration on 320x240 synthetic depth frames (76,800 model
 points, ~72,960 observation points after 5% dropout, sigma annealed
 0.04 -> 0.01 over 20 EM iterations, outlier ratio 0.1).
 
-One step = registering a batch of B frame pairs (B = --frames, default 16),
-i.e. B x 20 EM iterations.  The L2 cache is flushed (256 MiB write) between
-steps; per-step device time is taken with CUDA events on the library's stream.
+One step = registering a batch of B frame pairs (B = --frames, default 16)
+with fr_register_rigid_batch -- one launch per EM iteration for the whole
+batch -- i.e. B x 20 EM iterations.  The plain path (fr_register_rigid, one
+pair at a time) is timed on the same frames beside it.  The L2 cache is
+flushed (256 MiB write) between steps; per-step device time is taken with
+CUDA events on the library's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -61,7 +64,7 @@ def workload_config(frames, pairs):
     Ns = [p.Y.shape[0] for p in pairs]
     return {
         "workload": "depth_frames_320x240_pt2pl",
-        "model": "rigid FilterReg, point-to-plane, permutohedral E step (splat+slice)",
+        "model": "rigid FilterReg, point-to-plane, permutohedral E step (splat+slice), batched",
         "points_per_frame": 76800,
         "M": int(pairs[0].X.shape[0]),
         "N_mean": int(round(sum(Ns) / len(Ns))),
@@ -199,122 +202,137 @@ def run_ours(args):
 
     pairs = make_pairs(args.seed + 7919 * rank, args.frames)
     dev = lambda a: torch.from_numpy(a).cuda()
-    dX = [dev(p.X) for p in pairs]
-    dY = [dev(p.Y) for p in pairs]
-    dN = [dev(p.Yn) for p in pairs]
+    dpairs = [(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs]
     ctx = fr.Context(local)
     opts = dict(residual=fr.FR_PT2PL, iters=ITERS, sigma_start=SIGMA0, sigma_end=SIGMA1, w=W_OUT)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(record=None):
-        poses = []
-        for j in range(args.frames):
-            T, rep = ctx.register_rigid(dX[j], dY[j], dN[j], **opts)
-            poses.append((T, rep))
-        return poses
+    def batched_step():
+        return ctx.register_rigid_batch(dpairs, **opts)
+
+    def plain_step():
+        return [ctx.register_rigid(X, Y, Yn, **opts) for X, Y, Yn in dpairs]
 
     def barrier():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
 
+    def timed_steps(fn, k_steps):
+        """k_steps steps, L2 flushed before each; per-step CUDA-event times (ms)."""
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
+        last = None
+        for k in range(k_steps):
+            flush.fill_(1.0)
+            starts[k].record(stream)
+            last = fn()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in zip(starts, ends)], last
+
+    def slowest(total_s):
+        if dist:
+            t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return total_s
+
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        step()
+        batched_step()
+        plain_step()
 
-    # ---- timed region: K steps, device time per step by CUDA events -------
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # ---- timed region: K batched steps (the headline) ------------------------
     launches0 = ctx.kernel_launches
     barrier()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        last = None
-        for k in range(args.steps):
-            flush.fill_(1.0)
-            starts[k].record(stream)
-            last = step()
-            ends[k].record(stream)
+        step_ms, last = timed_steps(batched_step, args.steps)
         barrier()
         t_wall = time.perf_counter() - t_wall
     launches = ctx.kernel_launches - launches0
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(step_ms) / 1000.0
-    if dist:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = slowest(sum(step_ms) / 1000.0)
     em_iters_all = ITERS * args.frames * args.steps * ws
     value = em_iters_all / total_s
 
-    # accuracy of the timed results against the planted motion
-    rot_err = max(synth.rotation_angle_deg(T, p.T_gt) for (T, _), p in zip(last, pairs))
-    trans_err = max(float(np.linalg.norm(T[:3, 3] - p.T_gt[:3, 3])) for (T, _), p in zip(last, pairs))
-    reps = [r for _, r in last]
-    v_mean = sum(r.lattice_vertices_sum for r in reps) / max(1, sum(r.lattice_builds for r in reps))
+    # ---- the plain path (one registration at a time, float32) on the same frames
+    plain_ms, plain_last = timed_steps(plain_step, args.steps)
+    plain_s = slowest(sum(plain_ms) / 1000.0)
+    reg_lat_ms = []
+    for X, Y, Yn in dpairs[: min(8, len(dpairs))]:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.register_rigid(X, Y, Yn, **opts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        reg_lat_ms.append(a.elapsed_time(b))
 
-    # ---- per-kernel durations (event pairs inside the graph), K steps -----
+    # accuracy of the timed results: vs the planted motion, and batched vs plain
+    rot_err = max(synth.rotation_angle_deg(T, p.T_gt) for (T, _, _), p in zip(last, pairs))
+    trans_err = max(float(np.linalg.norm(T[:3, 3] - p.T_gt[:3, 3])) for (T, _, _), p in zip(last, pairs))
+    mix_rot = max(synth.rotation_angle_deg(T, Tp) for (T, _, _), (Tp, _) in zip(last, plain_last))
+    reps = [r for _, r, _ in last]
+
+    # ---- per-kernel durations of the batched launches (CUDA events), K steps --
     ctx.set_profiling(True)
-    step()                              # capture the profiled graph
     ctx.profile(reset=True)
-    for k in range(args.steps):
-        flush.fill_(1.0)
-        step()
+    timed_steps(batched_step, args.steps)
     prof = ctx.profile(reset=True)
     ctx.set_profiling(False)
-    M = pairs[0].X.shape[0]
-    N_mean = sum(p.Y.shape[0] for p in pairs) / len(pairs)
     # Algorithmic bytes per launch, each array touched once, float32 (pt2pl):
     # slice = 12 B per model point + 36 B per lattice vertex (8 B key + 28 B
-    # [1, y, n]); build = 24 B per observation point + 36 B per vertex.  The
-    # fused EM-iteration kernel slices iteration k and builds k+1 (all but
-    # the last of the ITERS launches build).
-    slice_b = 12.0 * M + 36.0 * v_mean
-    build_b = 24.0 * N_mean + 36.0 * v_mean
-    algo = {"em_iter": slice_b + build_b * (ITERS - 1) / ITERS, "build": build_b}
+    # [1, y, n]); build = 24 B per observation point + 36 B per vertex.  One
+    # batched EM-iteration launch slices iteration k of every item and builds
+    # k+1 (all but the last of the ITERS launches build).
+    algo_iter = algo_build = 0.0
+    v_means = []
+    for p, r in zip(pairs, reps):
+        v = r.lattice_vertices_sum / max(1, r.lattice_builds)
+        v_means.append(v)
+        algo_iter += 12.0 * p.X.shape[0] + 36.0 * v + (24.0 * p.Y.shape[0] + 36.0 * v) * (ITERS - 1) / ITERS
+        algo_build += 24.0 * p.Y.shape[0] + 36.0 * v
+    algo = {"em_iter": algo_iter, "build": algo_build}
     per_launch_ms = {k: (ms / n if n else 0.0) for k, (n, ms) in prof.items()}
     dominant = max(("em_iter", "build"), key=lambda k: prof[k][1])
     peak, peak_kind = measured_peaks()
     achieved = algo[dominant] / (per_launch_ms[dominant] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "k_em_multi (batched EM iteration)" if dominant == "em_iter"
+                else "k_em_multi (first build)", "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": f"{peak_kind} HBM copy GB/s", "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": recorded_traffic(dominant),
                 "algorithmic_bytes_per_launch": round(algo[dominant]),
                 "launch_us": round(per_launch_ms[dominant] * 1e3, 2),
                 "per_kernel_us": {k: round(v * 1e3, 2) for k, v in per_launch_ms.items() if prof[k][0]},
-                "lattice_vertices_mean": round(v_mean)}
+                "lattice_vertices_mean": round(sum(v_means) / len(v_means))}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
     if not args.no_e2e:
-        hX = [torch.from_numpy(p.X).pin_memory() for p in pairs]
-        hY = [torch.from_numpy(p.Y).pin_memory() for p in pairs]
-        hN = [torch.from_numpy(p.Yn).pin_memory() for p in pairs]
-        for j in range(args.frames):
-            ctx.register_rigid_host(hX[j], hY[j], hN[j], **opts)
+        hpairs = [(torch.from_numpy(p.X).pin_memory(), torch.from_numpy(p.Y).pin_memory(),
+                   torch.from_numpy(p.Yn).pin_memory()) for p in pairs]
+        hp = [(a.numpy(), b.numpy(), c.numpy()) for a, b, c in hpairs]
+        ctx.register_rigid_batch(hp, host=True, **opts)
         b0 = ctx.transfer_bytes()
         barrier()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            for j in range(args.frames):
-                ctx.register_rigid_host(hX[j], hY[j], hN[j], **opts)
+            ctx.register_rigid_batch(hp, host=True, **opts)
         barrier()
-        te = time.perf_counter() - t0
+        te = slowest(time.perf_counter() - t0)
         b1 = ctx.transfer_bytes()
-        if dist:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
         e2e = {"value": round(em_iters_all / te, 1), "unit": UNIT,
                "h2d_bytes_per_step": (b1[0] - b0[0]) // args.steps,
                "d2h_bytes_per_step": (b1[1] - b0[1]) // args.steps,
-               "timing": "host wall clock around fr_register_rigid_host calls (pinned inputs)"}
+               "timing": "host wall clock around fr_register_rigid_batch_host calls (pinned inputs)"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pairs[0])
+    lat = sorted(reg_lat_ms)
 
     if rank == 0:
         line = {
@@ -325,8 +343,15 @@ def run_ours(args):
             "data": "synthetic (seeded ray-cast depth frames)",
             "config": workload_config(args.frames, pairs),
             "registrations_per_s": round(args.frames * args.steps * ws / total_s, 1),
+            "plain": {"em_iters_per_s": round(em_iters_all / plain_s, 1),
+                      "registrations_per_s": round(args.frames * args.steps * ws / plain_s, 1),
+                      "ms_per_step": round(statistics.mean(plain_ms), 4),
+                      "latency_ms_p50": round(lat[len(lat) // 2], 4),
+                      "note": "fr_register_rigid one frame pair at a time, same frames, same flush"},
+            "batched_over_plain": round(plain_s / total_s, 3),
             "accuracy": {"max_rot_err_deg_vs_truth": round(rot_err, 4),
-                         "max_trans_err_vs_truth": round(trans_err, 6)},
+                         "max_trans_err_vs_truth": round(trans_err, 6),
+                         "max_rot_diff_deg_batched_vs_plain": round(mix_rot, 6)},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

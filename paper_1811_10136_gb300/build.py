@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError(f"nvcc failed ({p.returncode}): {' '.join(cmd)}")
     tmp = LIB + f".tmp{os.getpid()}"
     link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-            "-Xlinker", f"-rpath={_cuda_lib_dir(nvcc)}"]
+            "-Xlinker", f"-rpath={_cuda_lib_dir(nvcc)}", "-Xlinker", "--no-undefined"]
     subprocess.run(link, check=True)
     os.replace(tmp, LIB)
     return LIB

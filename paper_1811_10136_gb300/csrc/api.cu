@@ -58,6 +58,7 @@ fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur) {
             FR_CUDA(ctx, cudaMemsetAsync(t.v0, 0, cap * sizeof(float4), ctx->stream));
             FR_CUDA(ctx, cudaMemsetAsync(t.v1, 0, cap * sizeof(float4), ctx->stream));
             t.mask = cap - 1;
+            t.max_probe = cap;
         }
         ctx->table_cap = cap;
         ctx->ws_gen++;
@@ -258,18 +259,6 @@ int plan_kernels(const Plan &p) {
     return n;
 }
 
-// After the stream is synchronised: add the event-pair durations of the last
-// plan to the per-class totals.
-void collect_profile(fr_ctx *ctx, int kernels) {
-    for (int i = 0; i < kernels; ++i) {
-        float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]) == cudaSuccess) {
-            ctx->prof_ms[ctx->event_class[i]] += ms;
-            ctx->prof_launches[ctx->event_class[i]] += 1;
-        }
-    }
-    cudaGetLastError();
-}
 
 fr_status run_plan(fr_ctx *ctx, const Plan &p, bool use_graph) {
     if (!use_graph) {
@@ -338,15 +327,25 @@ fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
 }
 }  // namespace fr
 
-namespace {
+namespace fr {
+
+// After the stream is synchronised: add the event-pair durations of the last
+// launches to the per-class totals.
+void collect_profile(fr_ctx *ctx, int kernels) {
+    for (int i = 0; i < kernels; ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]) == cudaSuccess) {
+            ctx->prof_ms[ctx->event_class[i]] += ms;
+            ctx->prof_launches[ctx->event_class[i]] += 1;
+        }
+    }
+    cudaGetLastError();
+}
 
 // Host-side constants of every iteration: the sigma schedule (geometric
 // between sigma_start and sigma_end), feature scales and outlier constant
 // c = w/(1-w) N/M (Eq. 7) in the lattice kernel's units (times sigma^3 G).
 // Returns true when sigma changes during the schedule (annealing).
-}  // namespace
-
-namespace fr {
 bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip) {
     const double s0 = o->sigma_start, s1 = o->sigma_end;
     const double c = (double)o->w / (1.0 - (double)o->w) * ((double)N / (double)M);
@@ -566,7 +565,7 @@ FR_API fr_status fr_lattice_build(fr_ctx *ctx, const float *d_pos, int64_t n, fl
         fr_lattice_destroy(ctx, lat);
         return ctx->cuda(e, "fr_lattice_build allocation");
     }
-    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
     launch_build_records((const float4 *)d_pos, (int)n, lat->scale[0], lat->scale[1], lat->scale[2], t,
                          lat->rec_slot, lat->rec_w, lat->counters, ctx->stream);
     ctx->launches += 1;
@@ -596,7 +595,7 @@ FR_API fr_status fr_lattice_splat(fr_ctx *ctx, fr_lattice *lat, const float *d_v
     lat->vdim = val_dim;
     FR_CUDA(ctx, cudaMemsetAsync(lat->v0, 0, lat->cap * sizeof(float4), ctx->stream));
     FR_CUDA(ctx, cudaMemsetAsync(lat->v1, 0, lat->cap * sizeof(float4), ctx->stream));
-    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
     launch_splat_records(d_vals, val_dim, lat->n, lat->rec_slot, lat->rec_w, t, ctx->stream);
     ctx->launches += 1;
     FR_CUDA(ctx, cudaGetLastError());
@@ -611,8 +610,8 @@ FR_API fr_status fr_lattice_blur(fr_ctx *ctx, fr_lattice *lat) {
         FR_CUDA(ctx, dev_alloc(&lat->t0, lat->cap));
         FR_CUDA(ctx, dev_alloc(&lat->t1, lat->cap));
     }
-    Table a{lat->keys, lat->v0, lat->v1, lat->cap - 1};
-    Table b{lat->keys, lat->t0, lat->t1, lat->cap - 1};
+    Table a{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
+    Table b{lat->keys, lat->t0, lat->t1, lat->cap - 1, lat->cap};
     int grid = blocks_for(ctx, lat->cap, 16);
     for (int dir = 0; dir < 4; ++dir) {
         if (dir % 2 == 0)
@@ -633,7 +632,7 @@ FR_API fr_status fr_lattice_slice(fr_ctx *ctx, const fr_lattice *lat, const floa
     if (!d_out) return ctx->fail(FR_EINVAL, "d_out is NULL");
     if (lat->vdim < 1) return ctx->fail(FR_EINVAL, "lattice has no values (call fr_lattice_splat)");
     cudaSetDevice(ctx->device);
-    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
     FR_CUDA(ctx, cudaMemsetAsync(lat->counters + 1, 0, sizeof(int), ctx->stream));
     launch_slice_out((const float4 *)d_query, (int)m, lat->scale[0], lat->scale[1], lat->scale[2], t,
                      lat->vdim, d_out, lat->counters + 1, ctx->stream);
@@ -650,7 +649,7 @@ FR_API fr_status fr_lattice_vertices(fr_ctx *ctx, const fr_lattice *lat, int32_t
     if (!ctx || !lat) return FR_EINVAL;
     if (!d_keys || !aligned16(d_keys)) return ctx->fail(FR_EINVAL, "d_keys must be a 16-byte aligned buffer");
     cudaSetDevice(ctx->device);
-    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1};
+    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
     FR_CUDA(ctx, cudaMemsetAsync(lat->counters + 2, 0, sizeof(int), ctx->stream));
     launch_vertices(t, lat->vdim > 0 ? lat->vdim : 1, d_keys, lat->vdim > 0 ? d_vals : nullptr,
                     lat->counters + 2, ctx->stream);
@@ -703,11 +702,12 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
     if (!(sigma > 0.0f) || !std::isfinite(sigma)) return ctx->fail(FR_EINVAL, "sigma must be > 0");
     cudaSetDevice(ctx->device);
     const int pt2pl = d_Yn ? 1 : 0;
-    const uint32_t cap = pow2_at_least(6 * N);
+    const uint32_t cap = table_slots(N, true);
     FR_TRY(ensure_small(ctx, 1, 1));
     FR_TRY(ensure_tables(ctx, cap, blur != 0));
     Table t = ctx->tables[0];
     t.mask = cap - 1;
+    t.max_probe = table_probe_limit(cap, true);
     fr_options o;
     fr_options_default(&o);
     o.iters = 1;
@@ -764,11 +764,11 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
 
 // ---- rigid registration -----------------------------------------------------
 
-static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                                      const float *d_Yn, int64_t N, const fr_options *opt,
-                                     double T_inout[16], fr_report *rep) {
+                                     double T_inout[16], fr_report *rep, bool safe) {
     const int pt2pl = opt->residual == FR_PT2PL;
-    const uint32_t cap = pow2_at_least(6 * N);
+    const uint32_t cap = table_slots(N, safe);
     FR_TRY(ensure_small(ctx, opt->iters, 1));
     Plan p{};
     p.iters = opt->iters;
@@ -780,7 +780,10 @@ static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, c
     plan_grids(ctx, p, M, N, cap);
     FR_TRY(ensure_small(ctx, opt->iters, p.gs));
     FR_TRY(ensure_tables(ctx, cap, p.blur != 0));
-    for (Table &t : ctx->tables) t.mask = cap - 1;
+    for (Table &t : ctx->tables) {
+        t.mask = cap - 1;
+        t.max_probe = table_probe_limit(cap, safe);
+    }
 
     RigidJob *j = ctx->h_job;
     *j = RigidJob{};
@@ -823,6 +826,16 @@ static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, c
         rep->lattice_vertices_sum = s.nvert_total;
     }
     return FR_OK;
+}
+
+// Compact tables first; if one overflows, the registration is rerun from its
+// initial pose at the size that cannot overflow.
+static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                     const float *d_Yn, int64_t N, const fr_options *opt,
+                                     double T_inout[16], fr_report *rep) {
+    const fr_status s = register_rigid_once(ctx, d_X, M, d_Y, d_Yn, N, opt, T_inout, rep, false);
+    if (s != FR_ECAPACITY) return s;
+    return register_rigid_once(ctx, d_X, M, d_Y, d_Yn, N, opt, T_inout, rep, true);
 }
 
 FR_API fr_status fr_register_rigid(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,

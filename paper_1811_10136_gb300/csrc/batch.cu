@@ -117,7 +117,7 @@ struct ItemPlan {
 };
 
 fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *opt,
-                    fr_report *reports) {
+                    fr_report *reports, bool safe) {
     const int pt2pl = opt->residual == FR_PT2PL;
     const int kahan = opt->kahan ? 1 : 0;
     const int iters = opt->iters;
@@ -130,7 +130,7 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     for (int b = 0; b < n; ++b) {
         const fr_batch_item &it = items[b];
         ItemPlan &p = ip[b];
-        p.cap = pow2_at_least(6 * it.N);
+        p.cap = table_slots(it.N, safe);
         p.tab_off = slots;
         slots += 3 * (size_t)p.cap;
         p.gs = div_up(it.M, (long long)kBlock * kPointsPerThread);
@@ -201,7 +201,8 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
         s.partials = (float2 *)(D + ip[b].part_off);
         for (int t = 0; t < 3; ++t) {
             const size_t base = ip[b].tab_off + (size_t)t * ip[b].cap;
-            s.tab[t] = Table{w->keys + base, w->v0 + base, pt2pl ? w->v1 + base : nullptr, ip[b].cap - 1};
+            s.tab[t] = Table{w->keys + base, w->v0 + base, pt2pl ? w->v1 + base : nullptr, ip[b].cap - 1,
+                             table_probe_limit(ip[b].cap, safe)};
             s.list[t] = (int *)(D + ip[b].list_off) + (size_t)t * ip[b].cap;
         }
     }
@@ -268,14 +269,38 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     FR_CUDA(ctx, copy_async(ctx, D, U, up_bytes, cudaMemcpyHostToDevice));
     const Slot *dslots = (const Slot *)(D + o_slots);
     const Seg *dsegs = (const Seg *)(D + o_segs);
+    // With profiling on, an event pair brackets each launch (classes: first
+    // build, EM iteration, final clear).
+    int nprof = 0;
+    auto timed = [&](int cls, auto &&launch) {
+        if (ctx->profiling) {
+            while (ctx->events.size() < 2 * (size_t)(nprof + 1)) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                ctx->events.push_back(e);
+            }
+            if (ctx->event_class.size() < (size_t)(nprof + 1)) ctx->event_class.resize(nprof + 1);
+            ctx->event_class[nprof] = cls;
+            cudaEventRecord(ctx->events[2 * nprof], ctx->stream);
+        }
+        launch();
+        if (ctx->profiling) cudaEventRecord(ctx->events[2 * nprof + 1], ctx->stream);
+        ++nprof;
+    };
     if (iters > 0) {
-        launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter,
-                        (const unsigned short *)(D + o_bs_pro), grid_pro, 0, ctx->stream);
+        timed(FR_K_BUILD, [&] {
+            launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter,
+                            (const unsigned short *)(D + o_bs_pro), grid_pro, 0, ctx->stream);
+        });
         for (int k = 0; k < iters; ++k)
-            launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)k * seg_per_iter,
-                            (const unsigned short *)(D + o_bs_iter), grid_iter, 1, ctx->stream);
-        launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter + seg_pro,
-                        (const unsigned short *)(D + o_bs_epi), grid_epi, 0, ctx->stream);
+            timed(FR_K_STEP, [&] {
+                launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)k * seg_per_iter,
+                                (const unsigned short *)(D + o_bs_iter), grid_iter, 1, ctx->stream);
+            });
+        timed(FR_K_CLEAR, [&] {
+            launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter + seg_pro,
+                            (const unsigned short *)(D + o_bs_epi), grid_epi, 0, ctx->stream);
+        });
         ctx->launches += iters + 2;
     }
     FR_CUDA(ctx, cudaGetLastError());
@@ -284,6 +309,7 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     FR_CUDA(ctx, copy_async(ctx, H + align256(n * sizeof(DeviceState)), D + o_ips,
                             (size_t)n * iters1 * sizeof(IterParams), cudaMemcpyDeviceToHost));
     FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->profiling) collect_profile(ctx, nprof);
     const DeviceState *rs = (const DeviceState *)H;
     const IterParams *rip = (const IterParams *)(H + align256(n * sizeof(DeviceState)));
     fr_status first_bad = FR_OK;
@@ -315,6 +341,30 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
         }
     }
     return first_bad;
+}
+
+// Compact tables first; items whose table overflowed are rerun (from their
+// initial poses) at the size that cannot overflow.
+fr_status run_batch_sized(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *opt,
+                          fr_report *reports) {
+    std::vector<fr_batch_item> init(items, items + n);
+    fr_status st = run_batch(ctx, items, n, opt, reports, false);
+    std::vector<int> redo;
+    for (int b = 0; b < n; ++b)
+        if (items[b].status == FR_ECAPACITY) redo.push_back(b);
+    if (redo.empty()) return st;
+    std::vector<fr_batch_item> sub;
+    std::vector<fr_report> subrep(redo.size());
+    for (int b : redo) sub.push_back(init[b]);
+    run_batch(ctx, sub.data(), (int)sub.size(), opt, reports ? subrep.data() : nullptr, true);
+    st = FR_OK;
+    for (size_t q = 0; q < redo.size(); ++q) {
+        items[redo[q]] = sub[q];
+        if (reports) reports[redo[q]] = subrep[q];
+    }
+    for (int b = 0; b < n; ++b)
+        if (items[b].status != FR_OK && st == FR_OK) st = items[b].status;
+    return st;
 }
 
 fr_status validate_batch(fr_ctx *ctx, const fr_batch_item *items, int n, const fr_options *opt,
@@ -349,7 +399,7 @@ FR_API fr_status fr_register_rigid_batch(fr_ctx *ctx, fr_batch_item *items, int 
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_batch(ctx, items, n_items, opt, false));
     cudaSetDevice(ctx->device);
-    return run_batch(ctx, items, n_items, opt, reports);
+    return run_batch_sized(ctx, items, n_items, opt, reports);
 }
 
 FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items, int n_items,
@@ -388,7 +438,7 @@ FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items,
             dev[b].d_Yn = nullptr;
         }
     }
-    const fr_status st = run_batch(ctx, dev.data(), n_items, opt, reports);
+    const fr_status st = run_batch_sized(ctx, dev.data(), n_items, opt, reports);
     for (int b = 0; b < n_items; ++b) {
         items[b].status = dev[b].status;
         for (int i = 0; i < 16; ++i) items[b].T[i] = dev[b].T[i];

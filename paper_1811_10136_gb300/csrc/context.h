@@ -166,5 +166,6 @@ fr_status validate_cloud(fr_ctx *ctx, const void *p, int64_t n, const char *name
 fr_status validate_options(fr_ctx *ctx, const fr_options *o);
 bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip);
 int fused_blocks_per_sm(fr_ctx *ctx, int pt2pl, int kahan);
+void collect_profile(fr_ctx *ctx, int kernels);
 void free_batch_workspace(fr_ctx *ctx);   // batch.cu
 }  // namespace fr

@@ -60,7 +60,21 @@ struct Table {
     float4 *v0;
     float4 *v1;
     uint32_t mask;         // capacity - 1 (capacity a power of two)
+    uint32_t max_probe;    // an insert that probes this many taken slots reports overflow
 };
+
+// Table sizing.  A point creates at most 4 vertices, so 6 N slots can never
+// fill; but a lattice over a surface has far fewer vertices than 4 N (about
+// 0.05 N to 0.4 N for depth frames), and a table sized to match keeps its
+// working set in L2.  The compact size is tried first with a bounded probe
+// length; an overflow reruns the registration at the safe size.
+inline uint32_t table_slots(long long n_points, bool safe) {
+    const long long want = safe ? 6 * n_points : (3 * n_points) / 2;
+    uint32_t c = 1024;
+    while ((long long)c < want && c < (1u << 30)) c <<= 1;
+    return c;
+}
+inline uint32_t table_probe_limit(uint32_t cap, bool safe) { return safe ? cap : (cap < 512 ? cap : 512); }
 
 // One fused EM-iteration launch: blocks [0, gs) run the step of iteration
 // `it` on table `step` (slice, residuals, reduction, last-block solve);

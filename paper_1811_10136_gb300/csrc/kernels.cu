@@ -377,7 +377,7 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
         }
         // Run tails insert their keys (four probes in flight) and accumulate.
         int sl[kD];
-        const int mask = insert4(t.keys, t.mask, key, tails, sl);
+        const int mask = insert4(t.keys, t.mask, key, tails, sl, t.max_probe);
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
             if (!(tails >> k & 1)) continue;

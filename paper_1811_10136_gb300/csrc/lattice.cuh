@@ -163,10 +163,12 @@ __device__ __forceinline__ int insert_key(unsigned long long *keys, uint32_t mas
 // Inserts up to four keys at once (key k only where active & (1 << k)):
 // the first probes are loaded together and the needed CASes issued back to
 // back, so the four round trips to L2 overlap; collision chains are walked
-// afterwards by insert_key.  slot[k] = -1 where inactive or the table is
-// full; bit k of the return value is set where this call created the vertex.
+// afterwards by insert_key (at most max_probe more slots).  slot[k] = -1 where
+// inactive or no free slot was found; bit k of the return value is set where
+// this call created the vertex.
 __device__ __forceinline__ int insert4(unsigned long long *keys, uint32_t mask,
-                                       const unsigned long long key[kD], int active, int slot[kD]) {
+                                       const unsigned long long key[kD], int active, int slot[kD],
+                                       uint32_t max_probe) {
     uint32_t s[kD];
     unsigned long long cur[kD], old[kD];
 #pragma unroll
@@ -189,7 +191,7 @@ __device__ __forceinline__ int insert4(unsigned long long *keys, uint32_t mask,
             slot[k] = (int)s[k];
         } else {
             bool c;
-            const int t = insert_key(keys, mask, key[k], mask, c, (s[k] + 1) & mask);
+            const int t = insert_key(keys, mask, key[k], max_probe, c, (s[k] + 1) & mask);
             slot[k] = t;
             claimed |= c ? (1 << k) : 0;
         }

@@ -108,3 +108,21 @@ def test_batch_item_error_reported_per_item(ctx):
     assert out[0][2] == fr.FR_OK and out[1][2] == fr.FR_EINVAL
     with pytest.raises(fr.FilterRegError):
         ctx.register_rigid_batch([(dev(good.X), dev(good.Y), None)], residual=1, iters=3)
+
+
+def test_batch_overflowing_item_reruns(ctx):
+    rng = np.random.default_rng(78)
+    X = np.zeros((3000, 4), np.float32)
+    X[:, :3] = rng.uniform(-1, 1, size=(3000, 3))
+    Y = X.copy()
+    Y[:, 0] += 0.001
+    good = synth.depth_frame_pair(310, W=96, H=72)
+    pairs = [(dev(good.X), dev(good.Y), None), (dev(X), dev(Y), None)]
+    out = ctx.register_rigid_batch(pairs, residual=0, iters=3, sigma_start=0.01, sigma_end=0.01)
+    for (Xd, Yd, _), (T, rep, st) in zip(pairs, out):
+        assert st == 0
+        Ts, rs = ctx.register_rigid(Xd, Yd, residual=0, iters=3, sigma_start=0.01, sigma_end=0.01)
+        assert rep.lattice_vertices == rs.lattice_vertices
+        dr, dt = pose_diff(T, Ts)
+        assert dr < SAME_ROT and dt < SAME_TRANS
+    assert out[1][1].lattice_vertices > 1.5 * 3000

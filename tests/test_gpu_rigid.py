@@ -177,3 +177,20 @@ def test_invalid_arguments(ctx):
     with pytest.raises(fr.FilterRegError) as e:
         ctx.register_rigid(Xn, X, iters=1)
     assert e.value.status == fr.FR_EINVAL
+
+
+def test_compact_table_overflow_reruns_at_safe_size(ctx, orc):
+    # Scattered points at a small sigma create ~4 vertices each, more than the
+    # compact table (1.5 N slots) holds: the registration must transparently
+    # rerun with the safe size and still match the oracle.
+    rng = np.random.default_rng(77)
+    X = np.zeros((3000, 4), np.float32)
+    X[:, :3] = rng.uniform(-1, 1, size=(3000, 3))
+    T = synth.make_T(synth.random_rotation(rng, 0.002), [0.001, 0.0, -0.001])
+    Y = np.zeros_like(X)
+    Y[:, :3] = synth.apply_T(T, X)
+    p = synth.RigidPair(X, Y, T)
+    Tg, rg, To, ro = run_both(ctx, orc, p, False, iters=3, s0=0.01)
+    assert rg.lattice_vertices > 1.5 * 3000          # the compact table could not hold it
+    dr, dt = pose_diff(Tg, To)
+    assert dr < ROT_TOL and dt < TRANS_TOL
