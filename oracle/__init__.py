@@ -316,5 +316,107 @@ def align_error(X, T, Tgt) -> float:
     return float(_L().or_align_error(_p(X, _f32p), X.shape[0], _p(T, _f64p), _p(Tgt, _f64p)))
 
 
-def _declare_articulated(L):  # filled in by the articulated model
-    pass
+class _Kintree(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("nj", ctypes.c_int), ("parent", _i32p), ("offset", _f64p),
+                ("joint_body", _i32p), ("joint_axis", _f64p), ("q_min", _f64p), ("q_max", _f64p)]
+
+
+def _declare_articulated(L):
+    kp = ctypes.POINTER(_Kintree)
+    L.or_fk.argtypes = [kp, _f64p, _f64p, _f64p, _f64p, _f64p]
+    L.or_fk.restype = ctypes.c_int
+    L.or_spatial_jacobian.argtypes = [kp, _f64p, _f64p, ctypes.c_int, _f64p]
+    L.or_spatial_jacobian.restype = ctypes.c_int
+    L.or_articulated_normal_equations.argtypes = [_f32p, _i32p, ctypes.c_int64, kp, _f32p, _f32p,
+                                                  ctypes.c_int64, ctypes.POINTER(_Options),
+                                                  ctypes.c_double, _f64p, _f64p, _f64p, _f64p]
+    L.or_articulated_normal_equations.restype = ctypes.c_int
+    L.or_register_articulated.argtypes = [_f32p, _i32p, ctypes.c_int64, kp, _f32p, _f32p,
+                                          ctypes.c_int64, ctypes.POINTER(_Options), _f64p, _f64p,
+                                          ctypes.POINTER(_Report)]
+    L.or_register_articulated.restype = ctypes.c_int
+
+
+def _tree(tree):
+    """(struct, keep-alive arrays) from an object with parent, offset, joint_body,
+    joint_axis, q_min, q_max (numpy arrays, see paper_1811_10136_gb300.synth.KinTree)."""
+    arrs = dict(parent=np.ascontiguousarray(tree.parent, dtype=np.int32),
+                offset=np.ascontiguousarray(tree.offset, dtype=np.float64).reshape(-1, 16),
+                joint_body=np.ascontiguousarray(tree.joint_body, dtype=np.int32),
+                joint_axis=np.ascontiguousarray(tree.joint_axis, dtype=np.float64).reshape(-1, 3),
+                q_min=np.ascontiguousarray(tree.q_min, dtype=np.float64),
+                q_max=np.ascontiguousarray(tree.q_max, dtype=np.float64))
+    st = _Kintree(len(arrs["parent"]), len(arrs["joint_body"]), _p(arrs["parent"], _i32p),
+                  _p(arrs["offset"], _f64p), _p(arrs["joint_body"], _i32p),
+                  _p(arrs["joint_axis"], _f64p), _p(arrs["q_min"], _f64p), _p(arrs["q_max"], _f64p))
+    return st, arrs
+
+
+def fk(tree, root_T, q):
+    """Body transforms (nb, 4, 4), joint world axes (nj, 3) and points (nj, 3)."""
+    st, keep = _tree(tree)
+    root_T = np.ascontiguousarray(root_T, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    T = np.zeros((st.nb, 4, 4))
+    aw = np.zeros((max(st.nj, 1), 3))
+    pw = np.zeros((max(st.nj, 1), 3))
+    _check(_L().or_fk(ctypes.byref(st), _p(root_T, _f64p), _p(q, _f64p), _p(T, _f64p),
+                      _p(aw, _f64p), _p(pw, _f64p)), "fk")
+    return T, aw[: st.nj], pw[: st.nj]
+
+
+def spatial_jacobian(tree, aw, pw, b):
+    st, keep = _tree(tree)
+    aw = np.ascontiguousarray(aw, dtype=np.float64)
+    pw = np.ascontiguousarray(pw, dtype=np.float64)
+    J = np.zeros((6, 6 + st.nj))
+    _L().or_spatial_jacobian(ctypes.byref(st), _p(aw, _f64p), _p(pw, _f64p), int(b), _p(J, _f64p))
+    return J
+
+
+def _opts(sigma, sigma_end, w, iters, residual, backend, blur, renormalize_normals=False,
+          stop_twist=0.0):
+    return _Options(backend, residual, int(blur), int(iters), float(sigma),
+                    float(sigma if sigma_end is None else sigma_end), float(w),
+                    int(renormalize_normals), float(stop_twist))
+
+
+def articulated_normal_equations(Xref, body, tree, Y, Yn=None, *, sigma, w=0.1, residual=PT2PT,
+                                 backend=LATTICE, blur=False, root_T=None, q=None):
+    """(A, g) of Algorithm 1 for one E step at (root_T, q)."""
+    st, keep = _tree(tree)
+    Xref, Y = _pts(Xref), _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    body = np.ascontiguousarray(body, dtype=np.int32)
+    root_T = np.ascontiguousarray(np.eye(4) if root_T is None else root_T, dtype=np.float64)
+    q = np.ascontiguousarray(np.zeros(st.nj) if q is None else q, dtype=np.float64)
+    nd = 6 + st.nj
+    A = np.zeros((nd, nd))
+    g = np.zeros(nd)
+    o = _opts(sigma, sigma, w, 1, residual, backend, blur)
+    _check(_L().or_articulated_normal_equations(_p(Xref, _f32p), _p(body, _i32p), Xref.shape[0],
+                                                ctypes.byref(st), _p(Y, _f32p), _p(Yn, _f32p),
+                                                Y.shape[0], ctypes.byref(o), float(sigma),
+                                                _p(root_T, _f64p), _p(q, _f64p), _p(A, _f64p),
+                                                _p(g, _f64p)), "articulated_normal_equations")
+    return A, g
+
+
+def register_articulated(Xref, body, tree, Y, Yn=None, *, sigma=0.01, sigma_end=None, w=0.1,
+                         iters=15, residual=PT2PT, backend=LATTICE, blur=False, root_T0=None,
+                         q0=None, stop_twist=0.0):
+    """Articulated EM registration; returns (root_T (4,4), q (nj,), Report)."""
+    st, keep = _tree(tree)
+    Xref, Y = _pts(Xref), _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    body = np.ascontiguousarray(body, dtype=np.int32)
+    root_T = np.ascontiguousarray(np.eye(4) if root_T0 is None else root_T0, dtype=np.float64).copy()
+    q = np.ascontiguousarray(np.zeros(st.nj) if q0 is None else q0, dtype=np.float64).copy()
+    o = _opts(sigma, sigma_end, w, iters, residual, backend, blur, stop_twist=stop_twist)
+    rep = _Report()
+    _check(_L().or_register_articulated(_p(Xref, _f32p), _p(body, _i32p), Xref.shape[0],
+                                        ctypes.byref(st), _p(Y, _f32p), _p(Yn, _f32p), Y.shape[0],
+                                        ctypes.byref(o), _p(root_T, _f64p), _p(q, _f64p),
+                                        ctypes.byref(rep)), "register_articulated")
+    return root_T, q, Report(rep.iters_run, rep.degenerate_iters, rep.last_inliers, rep.last_sum_w,
+                             rep.last_cost, rep.last_twist_norm)

@@ -128,6 +128,39 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
 int or_estep(const float *X, int64_t M, const float *Y, const float *Yn, int64_t N,
              int backend, int blur, double sigma, const double T[16], double *out);
 
+/* ---- articulated model (Section 5.1, Eq. 20, Algorithm 1) -------------------
+ * Body 0 is the root; parent[b] < b for b > 0.  T_b = T_parent(b) * offset_b *
+ * R(a_j1, q_j1) * R(a_j2, q_j2) * ... over the joints of b (consecutive in the
+ * joint arrays, ordered by body); the root's parent transform is the root
+ * pose.  Joint axes are unit vectors in the frame each joint acts in.       */
+typedef struct {
+    int nb, nj;
+    const int32_t *parent;     /* nb */
+    const double *offset;      /* nb x 16, row-major */
+    const int32_t *joint_body; /* nj, non-decreasing */
+    const double *joint_axis;  /* nj x 3 */
+    const double *q_min, *q_max; /* nj joint limits */
+} or_kintree;
+
+/* Forward kinematics: body transforms T (nb x 16) and each joint's world axis
+ * and a world point on it (nj x 3 each; nullable). */
+int or_fk(const or_kintree *t, const double root_T[16], const double *q, double *T,
+          double *axis_w, double *point_w);
+/* Spatial velocity Jacobian of body b: 6 x (6 + nj), row-major. */
+int or_spatial_jacobian(const or_kintree *t, const double *axis_w, const double *point_w, int b,
+                        double *Jsp);
+/* One E step at (root_T, q) and the normal equations of Algorithm 1:
+ * A ((6+nj) x (6+nj)) and g (6+nj), with A dtheta = -g the Gauss-Newton step. */
+int or_articulated_normal_equations(const float *Xref, const int32_t *body, int64_t M,
+                                    const or_kintree *t, const float *Y, const float *Yn,
+                                    int64_t N, const or_options *opt, double sigma,
+                                    const double root_T[16], const double *q, double *A,
+                                    double *g);
+/* Articulated EM registration; Xref in body frames, body[i] its body. */
+int or_register_articulated(const float *Xref, const int32_t *body, int64_t M,
+                            const or_kintree *t, const float *Y, const float *Yn, int64_t N,
+                            const or_options *opt, double root_T[16], double *q, or_report *rep);
+
 /* Alignment error of Eq. 22: mean |(T - T_gt) x_ref|. */
 double or_align_error(const float *X, int64_t M, const double T[16], const double Tgt[16]);
 

@@ -234,3 +234,156 @@ def rotation_angle_deg(Ra: np.ndarray, Rb: np.ndarray) -> float:
     """Angle of Ra Rb^T in degrees (pose comparison helper)."""
     c = (np.trace(Ra[:3, :3] @ Rb[:3, :3].T) - 1.0) / 2.0
     return math.degrees(math.acos(max(-1.0, min(1.0, c))))
+
+
+# ---------------------------------------------------------------------------
+# Articulated: a kinematic tree of capsules
+# ---------------------------------------------------------------------------
+
+@dataclass
+class KinTree:
+    parent: np.ndarray       # (nb,) int32; -1 for the root (body 0)
+    offset: np.ndarray       # (nb, 4, 4) joint frame of each body in its parent's frame
+    joint_body: np.ndarray   # (nj,) int32, non-decreasing
+    joint_axis: np.ndarray   # (nj, 3) unit axes in the frame each joint acts in
+    q_min: np.ndarray        # (nj,)
+    q_max: np.ndarray        # (nj,)
+    radius: np.ndarray       # (nb,) capsule radius
+    length: np.ndarray       # (nb,) capsule length along the body's local z
+
+    @property
+    def nb(self):
+        return len(self.parent)
+
+    @property
+    def nj(self):
+        return len(self.joint_body)
+
+
+def _axis_rot(a, q):
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(q) * K + (1 - math.cos(q)) * (K @ K)
+
+
+def pose_bodies(tree: KinTree, root_T: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """World transform of every body for the root pose and joint angles
+    (used to place synthetic observations)."""
+    T = np.zeros((tree.nb, 4, 4))
+    j = 0
+    for b in range(tree.nb):
+        F = (root_T if b == 0 else T[tree.parent[b]]) @ tree.offset[b]
+        while j < tree.nj and tree.joint_body[j] == b:
+            R = np.eye(4)
+            R[:3, :3] = _axis_rot(tree.joint_axis[j], q[j])
+            F = F @ R
+            j += 1
+        T[b] = F
+    return T
+
+
+def random_kintree(seed: int, n_links: int = 16, n_double: int = 5, n_single: int = 10,
+                   limit_deg: float = 90.0) -> KinTree:
+    """A random tree of capsules (radius U[0.01, 0.03], length U[0.03, 0.1]):
+    body 0 is the root; each other link hangs at the tip of a random earlier
+    link, bent by up to 60 degrees; n_double links carry two orthogonal
+    revolute joints, n_single links one, the rest none (6 root DOF besides)."""
+    rng = np.random.default_rng(seed)
+    parent = np.full(n_links, -1, np.int32)
+    radius = rng.uniform(0.01, 0.03, n_links)
+    length = rng.uniform(0.03, 0.1, n_links)
+    offset = np.zeros((n_links, 4, 4))
+    offset[0] = np.eye(4)
+    for b in range(1, n_links):
+        parent[b] = rng.integers(0, b)
+        O = np.eye(4)
+        O[:3, :3] = random_rotation(rng, math.radians(60.0))
+        O[:3, 3] = [0.0, 0.0, length[parent[b]]]
+        offset[b] = O
+    kinds = np.array([2] * n_double + [1] * n_single + [0] * (n_links - 1 - n_double - n_single))
+    rng.shuffle(kinds)
+    jb, ax = [], []
+    for b in range(1, n_links):
+        k = kinds[b - 1]
+        if k == 0:
+            continue
+        u = rng.normal(size=3)
+        u[2] = 0.0
+        u /= np.linalg.norm(u)
+        jb.append(b)
+        ax.append(u)
+        if k == 2:
+            jb.append(b)
+            ax.append(np.cross([0.0, 0.0, 1.0], u))
+    lim = math.radians(limit_deg)
+    nj = len(jb)
+    return KinTree(parent, offset, np.array(jb, np.int32), np.array(ax), np.full(nj, -lim),
+                   np.full(nj, lim), radius, length)
+
+
+def sample_capsules(tree: KinTree, n: int, rng: np.random.Generator):
+    """n surface points of the capsules, area-proportional, in body frames:
+    (points (n, 4), normals (n, 4), body ids (n,)), sorted by body."""
+    area_cyl = 2 * math.pi * tree.radius * tree.length
+    area_cap = 4 * math.pi * tree.radius ** 2
+    area = area_cyl + area_cap
+    counts = rng.multinomial(n, area / area.sum())
+    P, Nn, B = [], [], []
+    for b in range(tree.nb):
+        c = counts[b]
+        on_cyl = rng.uniform(size=c) < area_cyl[b] / area[b]
+        th = rng.uniform(0, 2 * math.pi, c)
+        z = rng.uniform(0, tree.length[b], c)
+        u = rng.normal(size=(c, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        nrm = np.where(on_cyl[:, None], np.stack([np.cos(th), np.sin(th), np.zeros(c)], 1), u)
+        cap_base = np.where((u[:, 2] >= 0)[:, None], [0.0, 0.0, 1.0], 0.0) * tree.length[b]
+        pts = np.where(on_cyl[:, None], np.stack([tree.radius[b] * np.cos(th), tree.radius[b] * np.sin(th), z], 1),
+                       cap_base + tree.radius[b] * u)
+        P.append(pts)
+        Nn.append(nrm)
+        B.append(np.full(c, b, np.int32))
+    return _pad4(np.concatenate(P)), _pad4(np.concatenate(Nn)), np.concatenate(B)
+
+
+@dataclass
+class ArticulatedPair:
+    tree: KinTree
+    Xref: np.ndarray         # (M, 4) model points in body frames
+    body: np.ndarray         # (M,) int32
+    Y: np.ndarray            # (N, 4) observation (world)
+    Yn: np.ndarray           # (N, 4) observation normals
+    root_gt: np.ndarray      # (4, 4)
+    q_gt: np.ndarray         # (nj,)
+    meta: dict = field(default_factory=dict)
+
+
+def articulated_pair(seed: int, n_points: int = 30000, max_joint_deg: float = 20.0,
+                     root_deg: float = 5.0, root_trans: float = 0.01, noise: float = 0.002,
+                     outlier_frac: float = 0.1, tree: KinTree | None = None) -> ArticulatedPair:
+    """Model: n_points capsule surface samples (body frames) at the zero pose.
+    Observation: independent samples at a perturbed pose (joints U[-max, max]
+    clamped to the limits; root rotated up to root_deg and moved up to
+    root_trans), N(0, noise^2) noise, plus outlier_frac * n_points uniform
+    outliers in the bounding box."""
+    rng = np.random.default_rng(seed)
+    tree = random_kintree(seed) if tree is None else tree
+    Xref, _, body = sample_capsules(tree, n_points, rng)
+    q_gt = np.clip(rng.uniform(-1, 1, tree.nj) * math.radians(max_joint_deg), tree.q_min, tree.q_max)
+    t = rng.normal(size=3)
+    t *= rng.uniform(0, root_trans) / np.linalg.norm(t)
+    root_gt = make_T(random_rotation(rng, math.radians(root_deg)), t)
+    Tb = pose_bodies(tree, root_gt, q_gt)
+    P, Nn, B = sample_capsules(tree, n_points, rng)
+    Yw = np.einsum("nij,nj->ni", Tb[B][:, :3, :3], P[:, :3]) + Tb[B][:, :3, 3]
+    Nw = np.einsum("nij,nj->ni", Tb[B][:, :3, :3], Nn[:, :3])
+    Yw += rng.normal(scale=noise, size=Yw.shape)
+    n_out = int(round(outlier_frac * n_points))
+    if n_out:
+        lo, hi = Yw.min(0), Yw.max(0)
+        Yw = np.concatenate([Yw, rng.uniform(lo, hi, size=(n_out, 3))])
+        on = rng.normal(size=(n_out, 3))
+        Nw = np.concatenate([Nw, on / np.linalg.norm(on, axis=1, keepdims=True)])
+    perm = rng.permutation(Yw.shape[0])
+    return ArticulatedPair(tree, Xref, body, _pad4(Yw[perm]), _pad4(Nw[perm]), root_gt, q_gt,
+                           {"workload": "kintree_capsules", "seed": seed, "M": n_points,
+                            "N": Yw.shape[0], "dof": 6 + tree.nj})
