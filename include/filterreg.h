@@ -218,6 +218,46 @@ FR_API fr_status fr_register_rigid_host(fr_ctx *ctx, const float *h_X, int64_t M
                                         const fr_options *opt, double T_inout[16],
                                         fr_report *report);
 
+/* ---- articulated registration (Section 5.1, Eq. 20, Algorithm 1) -----------
+ * A kinematic tree: body 0 is the root; every other body b has a parent
+ * parent[b] < b.  Body b's frame is
+ *     T_b = T_parent(b) * offset_b * R(axis_j1, q_j1) * R(axis_j2, q_j2) ...
+ * over the revolute joints that move b (consecutive entries of joint_body,
+ * which is non-decreasing); the root's parent frame is the root pose.  The
+ * motion parameters are the root pose (6 DOF, updated by the exponential of
+ * its twist) and the joint angles (added, then clamped to [q_min, q_max]). */
+typedef struct {
+    int32_t n_bodies;           /* 1..32 */
+    int32_t n_joints;           /* 0..32 */
+    const int32_t *parent;      /* [n_bodies]; parent[0] is ignored */
+    const double *offset;       /* [n_bodies][16], row-major */
+    const int32_t *joint_body;  /* [n_joints], non-decreasing, each in [0, n_bodies) */
+    const double *joint_axis;   /* [n_joints][3], unit, in the frame the joint acts in */
+    const double *q_min;        /* [n_joints], radians */
+    const double *q_max;        /* [n_joints], radians */
+} fr_kintree;
+
+/* fr_register_articulated: EM registration of an articulated model.  The
+ * model points d_Xref (M x 4) are given in their bodies' frames, d_body
+ * (int32, M) names each point's body (points sorted by body run faster);
+ * the observation d_Y (N x 4, + normals d_Yn for FR_PT2PL).  Each iteration
+ * slices the lattice over Y at x_i = T_b(i) x_i_ref, sums J^T J and J^T r
+ * per body over the body twists (Algorithm 1, lines 1-4), assembles the
+ * (6 + n_joints)^2 normal equations with the spatial velocity Jacobians
+ * (lines 5-9: world-frame twists about the origin; identity for the root,
+ * (a; p x a) for a joint of world axis a through world point p, on every
+ * body under the joint), solves them in float64 and updates the root pose
+ * and the joint angles (clamped).  root_T_inout (host double[16]) and
+ * q_inout (host double[n_joints]) carry the initial and the final
+ * parameters.  FR_EINVAL for an invalid tree or arguments;
+ * FR_ENOTSUPPORTED for blur or Kahan sums (rigid path only).  Synchronises
+ * the stream. */
+FR_API fr_status fr_register_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_body,
+                                         int64_t M, const fr_kintree *tree, const float *d_Y,
+                                         const float *d_Yn, int64_t N, const fr_options *opt,
+                                         double root_T_inout[16], double *q_inout,
+                                         fr_report *report);
+
 /* ---- batched rigid registration ---------------------------------------------
  * One registration of a batch.  Clouds as for fr_register_rigid (device
  * pointers for fr_register_rigid_batch, host pointers for

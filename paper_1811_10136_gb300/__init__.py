@@ -35,7 +35,7 @@ EXPORTED = [
     "fr_lattice_vertices", "fr_lattice_info", "fr_lattice_destroy", "fr_estep",
     "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
     "fr_ctx_transfer_bytes", "fr_estep_noalloc", "fr_register_rigid_batch",
-    "fr_register_rigid_batch_host",
+    "fr_register_rigid_batch_host", "fr_register_articulated",
 ]
 FR_NOALLOC_MAX_OBS = 8192
 KERNEL_CLASSES = ("clear", "build", "blur", "em_iter")
@@ -61,6 +61,27 @@ class fr_report(ctypes.Structure):
                 ("last_cost", ctypes.c_double), ("last_twist_norm", ctypes.c_double),
                 ("lattice_vertices", ctypes.c_int64), ("lattice_builds", ctypes.c_int32),
                 ("lattice_vertices_sum", ctypes.c_int64)]
+
+
+class fr_kintree(ctypes.Structure):
+    _fields_ = [("n_bodies", ctypes.c_int32), ("n_joints", ctypes.c_int32), ("parent", ctypes.c_void_p),
+                ("offset", ctypes.c_void_p), ("joint_body", ctypes.c_void_p), ("joint_axis", ctypes.c_void_p),
+                ("q_min", ctypes.c_void_p), ("q_max", ctypes.c_void_p)]
+
+
+def kintree(tree):
+    """fr_kintree view of a tree object with parent, offset (nb,4,4), joint_body,
+    joint_axis (nj,3), q_min, q_max; returns (struct, keep-alive arrays)."""
+    a = dict(parent=np.ascontiguousarray(tree.parent, dtype=np.int32),
+             offset=np.ascontiguousarray(tree.offset, dtype=np.float64).reshape(-1, 16),
+             joint_body=np.ascontiguousarray(tree.joint_body, dtype=np.int32),
+             joint_axis=np.ascontiguousarray(tree.joint_axis, dtype=np.float64).reshape(-1, 3),
+             q_min=np.ascontiguousarray(tree.q_min, dtype=np.float64),
+             q_max=np.ascontiguousarray(tree.q_max, dtype=np.float64))
+    st = fr_kintree(len(a["parent"]), len(a["joint_body"]), a["parent"].ctypes.data, a["offset"].ctypes.data,
+                    a["joint_body"].ctypes.data, a["joint_axis"].ctypes.data, a["q_min"].ctypes.data,
+                    a["q_max"].ctypes.data)
+    return st, a
 
 
 class fr_batch_item(ctypes.Structure):
@@ -121,6 +142,8 @@ def load(build_if_missing: bool = True):
     L.fr_register_rigid_batch.argtypes = [_vp, ctypes.POINTER(fr_batch_item), ctypes.c_int,
                                           ctypes.POINTER(fr_options), ctypes.POINTER(fr_report)]
     L.fr_register_rigid_batch_host.argtypes = L.fr_register_rigid_batch.argtypes
+    L.fr_register_articulated.argtypes = [_vp, _vp, _vp, _i64, ctypes.POINTER(fr_kintree), _vp, _vp, _i64,
+                                          ctypes.POINTER(fr_options), _f64p, _f64p, ctypes.POINTER(fr_report)]
     L.fr_estep_noalloc.argtypes = [_vp, _i64, _vp, _vp, _i64, ctypes.c_float, _f64p, _vp, _vp]
     for name in EXPORTED:  # every entry point must resolve (ctypes restype defaults to int)
         getattr(L, name)
@@ -294,6 +317,30 @@ class Context:
         del keep
         self._check(st, "fr_register_rigid_host")
         return T, _report(rep)
+
+    def register_articulated(self, Xref, body, tree, Y, Yn=None, root_T0=None, q0=None, **opts):
+        """Articulated registration (Algorithm 1).  Xref (M,4) in body frames,
+        body (M,) int32 CUDA tensor, tree a synth.KinTree-like object.  Returns
+        (root_T (4,4), q (nj,), Report)."""
+        import torch
+        L = load()
+        o = options(**opts)
+        st, keep = kintree(tree)
+        R = _pose(root_T0)
+        q = np.ascontiguousarray(np.zeros(st.n_joints) if q0 is None else q0, dtype=np.float64).copy()
+        if not (isinstance(body, torch.Tensor) and body.is_cuda and body.dtype == torch.int32
+                and body.is_contiguous() and body.shape[0] == Xref.shape[0]):
+            raise TypeError("body must be a contiguous int32 CUDA tensor with one entry per model point")
+        rep = fr_report()
+        qp = q.ctypes.data_as(_f64p) if q.size else None
+        r = L.fr_register_articulated(self._h, _dev_ptr(Xref, "Xref"), body.data_ptr(), Xref.shape[0],
+                                      ctypes.byref(st), _dev_ptr(Y, "Y"),
+                                      _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None,
+                                      Y.shape[0], ctypes.byref(o), R.ctypes.data_as(_f64p), qp,
+                                      ctypes.byref(rep))
+        del keep
+        self._check(r, "fr_register_articulated")
+        return R, q, _report(rep)
 
     def register_rigid_batch(self, pairs, sigmas=None, ws=None, T0s=None, host=False, **opts):
         """Register a batch of pairs in one launch per EM iteration.

@@ -44,6 +44,9 @@ void free_tables(fr_ctx *ctx) {
 }
 
 // Three tables of at least `cap` slots, all empty; blur scratch if asked.
+}  // namespace
+
+namespace fr {
 fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur) {
     if (cap > ctx->table_cap) {
         cudaStreamSynchronize(ctx->stream);
@@ -72,7 +75,13 @@ fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur) {
     }
     return FR_OK;
 }
+}  // namespace fr
 
+namespace {
+
+}  // namespace
+
+namespace fr {
 fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows) {
     if (!ctx->d_state) {
         FR_CUDA(ctx, dev_alloc(&ctx->d_state, 1));
@@ -109,6 +118,9 @@ fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows) {
     }
     return FR_OK;
 }
+}  // namespace fr
+
+namespace {
 
 }  // namespace
 
@@ -463,6 +475,7 @@ FR_API fr_status fr_ctx_destroy(fr_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
     free_batch_workspace(ctx);
+    free_art_workspace(ctx);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     free_tables(ctx);
     cudaFree(ctx->partials);

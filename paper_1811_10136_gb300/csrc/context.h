@@ -17,6 +17,7 @@
 
 namespace fr {
 struct BatchWorkspace;
+struct ArtWorkspace;
 struct ServerState;
 }
 
@@ -118,6 +119,7 @@ struct fr_ctx {
     int bpsm[2][2] = {{0, 0}, {0, 0}};  // resident fused-kernel blocks per SM
 
     fr::BatchWorkspace *batch = nullptr;  // batched-registration workspace (batch.cu)
+    fr::ArtWorkspace *art = nullptr;      // articulated-registration workspace (articulated.cu)
 
     // per-kernel profiling: event pairs around each launch of a plan
     int profiling = 0;
@@ -168,4 +170,7 @@ bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip)
 int fused_blocks_per_sm(fr_ctx *ctx, int pt2pl, int kahan);
 void collect_profile(fr_ctx *ctx, int kernels);
 void free_batch_workspace(fr_ctx *ctx);   // batch.cu
+void free_art_workspace(fr_ctx *ctx);     // articulated.cu
+fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur);
+fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows);
 }  // namespace fr

@@ -94,6 +94,52 @@ struct IterLaunch {
     int check_done;        // roles return at once once st->done is set
 };
 
+// ---- articulated model -------------------------------------------------------
+constexpr int kMaxBodies = 32;
+constexpr int kMaxJoints = 32;
+constexpr int kMaxDof = 6 + kMaxJoints;
+constexpr int kArtVals = 30;  // per body: 21 of J^T J, 6 of J^T r, weight sum, cost, count
+
+// Kinematic tree (device copy).  Body 0 is the root; parent[b] < b.  Body b's
+// frame is T_parent * offset_b * R(axis_j, q_j) ... over its joints
+// [joint_begin[b], joint_begin[b+1]).
+struct ArtTree {
+    int nb, nj;
+    int parent[kMaxBodies];
+    int joint_begin[kMaxBodies + 1];
+    int joint_body[kMaxJoints];
+    float offset[kMaxBodies][12];   // row-major 3 x 4
+    float axis[kMaxJoints][3];      // unit, in the frame the joint acts in
+    double q_min[kMaxJoints], q_max[kMaxJoints];
+};
+
+struct ArtJob {
+    RigidJob base;      // X = model points in body frames, Y, Yn, M, N, flags
+    const int *body;    // body of each model point
+    ArtTree tree;
+};
+
+struct ArtState {
+    DeviceState ds;                         // ticket, flags, diagnostics, vertex counters
+    double root_T[16];
+    double q[kMaxJoints];
+    float body_T[kMaxBodies][12];           // every body's pose at the current parameters
+    float jaxis[kMaxJoints][3];             // world joint axes ...
+    float jpoint[kMaxJoints][3];            // ... and a world point on each
+    double acc[kMaxBodies][kArtVals];       // per-body sums of the running iteration
+};
+
+struct ArtLaunch {
+    const ArtJob *job;
+    IterParams *ip;
+    int it, build_it, clear_it;
+    Table step, build, clear;
+    int *build_list;
+    const int *clear_list;
+    ArtState *st;
+    int gs, gb, gc;
+};
+
 // One registration of a multi-registration launch (device-resident).
 struct Slot {
     const RigidJob *job;
@@ -117,6 +163,7 @@ struct Seg {
 // ---- launchers (kernels.cu) -------------------------------------------------
 void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
                      const unsigned short *blockseg, int grid, int check_done, cudaStream_t s);
+void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s);
 void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s);
 int em_iter_blocks_per_sm(int pt2pl, int kahan);
 // Frees the slots listed by builds (list lists[i], count *counts[i]).

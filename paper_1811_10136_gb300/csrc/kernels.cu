@@ -473,6 +473,72 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
     return true;
 }
 
+// One model point's terms of the M step, handed to add(value index, value):
+// outlier weight W = M0/(M0+c) (Eq. 7), the point-to-point (Eq. 7) or
+// point-to-plane (Eq. 10) residual with Sigma^{-1} weighting, its twist
+// Jacobian J = [-[x]_x, I] (Eq. 16) and the contributions to A = sum J^T J
+// (upper triangle, 21 values), b = sum J^T r (6), the weight sum, the cost
+// and the inlier count (Eq. 17-18).  Returns false for a point without
+// observations nearby (M0 = 0).
+template <bool PT2PL, typename Add>
+__device__ __forceinline__ bool point_terms(float x0, float x1, float x2, const Sums &e,
+                                            const IterParams &ip, int renorm, Add &&add) {
+    if (!(e.m0 > 0.0f)) return false;
+    const float W = e.m0 / (e.m0 + ip.c_eff);
+    const float ws = W * ip.inv_sigma2;
+    const float inv = 1.0f / e.m0;
+    const float e0 = x0 - e.m1x * inv, e1 = x1 - e.m1y * inv, e2 = x2 - e.m1z * inv;
+    if (!PT2PL) {
+        // J = [S, I], S = -[x]_x:  J^T J = [[|x|^2 I - x x^T, [x]_x], [-[x]_x, I]],
+        // J^T e = [x cross e; e].
+        const float xx = x0 * x0, yy = x1 * x1, zz = x2 * x2;
+        add(tri_index(0, 0), ws * (yy + zz));
+        add(tri_index(0, 1), -ws * x0 * x1);
+        add(tri_index(0, 2), -ws * x0 * x2);
+        add(tri_index(1, 1), ws * (xx + zz));
+        add(tri_index(1, 2), -ws * x1 * x2);
+        add(tri_index(2, 2), ws * (xx + yy));
+        // upper-right block [x]_x = [[0,-z,y],[z,0,-x],[-y,x,0]]
+        add(tri_index(0, 4), -ws * x2);
+        add(tri_index(0, 5), ws * x1);
+        add(tri_index(1, 3), ws * x2);
+        add(tri_index(1, 5), -ws * x0);
+        add(tri_index(2, 3), -ws * x1);
+        add(tri_index(2, 4), ws * x0);
+        add(tri_index(3, 3), ws);
+        add(tri_index(4, 4), ws);
+        add(tri_index(5, 5), ws);
+        add(21, ws * (x1 * e2 - x2 * e1));
+        add(22, ws * (x2 * e0 - x0 * e2));
+        add(23, ws * (x0 * e1 - x1 * e0));
+        add(24, ws * e0);
+        add(25, ws * e1);
+        add(26, ws * e2);
+        add(28, ws * (e0 * e0 + e1 * e1 + e2 * e2));
+    } else {
+        float n0 = e.nx * inv, n1 = e.ny * inv, n2 = e.nz * inv;
+        if (renorm) {
+            const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+            if (!(nn > 0.0f)) return false;
+            n0 /= nn; n1 /= nn; n2 /= nn;
+        }
+        const float res = n0 * e0 + n1 * e1 + n2 * e2;
+        // j = [x cross n, n]
+        const float j[6] = {x1 * n2 - x2 * n1, x2 * n0 - x0 * n2, x0 * n1 - x1 * n0, n0, n1, n2};
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            const float wj = ws * j[p];
+#pragma unroll
+            for (int q = p; q < 6; ++q) add(tri_index(p, q), wj * j[q]);
+            add(21 + p, wj * res);
+        }
+        add(28, ws * res * res);
+    }
+    add(27, W);
+    add(29, 1.0f);
+    return true;
+}
+
 // Row j of x = T x_ref in float, as ((P_j0 x + P_j1 y) + P_j2 z) + P_j3 with
 // every operation rounded (no FMA), so that the moved positions -- which
 // decide lattice keys -- are reproducible outside the kernel.
@@ -509,59 +575,7 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
         const float x0 = apply_row(P, 0, r), x1 = apply_row(P, 1, r), x2 = apply_row(P, 2, r);
         Sums e;
         if (!slice_point<PT2PL>(t, x0, x1, x2, ip, e, bad)) continue;
-        if (!(e.m0 > 0.0f)) continue;
-        const float W = e.m0 / (e.m0 + ip.c_eff);
-        const float ws = W * ip.inv_sigma2;
-        const float inv = 1.0f / e.m0;
-        const float e0 = x0 - e.m1x * inv, e1 = x1 - e.m1y * inv, e2 = x2 - e.m1z * inv;
-        if (!PT2PL) {
-            // J = [S, I], S = -[x]_x:  J^T J = [[|x|^2 I - x x^T, [x]_x], [-[x]_x, I]],
-            // J^T e = [x cross e; e].
-            const float xx = x0 * x0, yy = x1 * x1, zz = x2 * x2;
-            acc.add(tri_index(0, 0), ws * (yy + zz));
-            acc.add(tri_index(0, 1), -ws * x0 * x1);
-            acc.add(tri_index(0, 2), -ws * x0 * x2);
-            acc.add(tri_index(1, 1), ws * (xx + zz));
-            acc.add(tri_index(1, 2), -ws * x1 * x2);
-            acc.add(tri_index(2, 2), ws * (xx + yy));
-            // upper-right block [x]_x = [[0,-z,y],[z,0,-x],[-y,x,0]]
-            acc.add(tri_index(0, 4), -ws * x2);
-            acc.add(tri_index(0, 5), ws * x1);
-            acc.add(tri_index(1, 3), ws * x2);
-            acc.add(tri_index(1, 5), -ws * x0);
-            acc.add(tri_index(2, 3), -ws * x1);
-            acc.add(tri_index(2, 4), ws * x0);
-            acc.add(tri_index(3, 3), ws);
-            acc.add(tri_index(4, 4), ws);
-            acc.add(tri_index(5, 5), ws);
-            acc.add(21, ws * (x1 * e2 - x2 * e1));
-            acc.add(22, ws * (x2 * e0 - x0 * e2));
-            acc.add(23, ws * (x0 * e1 - x1 * e0));
-            acc.add(24, ws * e0);
-            acc.add(25, ws * e1);
-            acc.add(26, ws * e2);
-            acc.add(28, ws * (e0 * e0 + e1 * e1 + e2 * e2));
-        } else {
-            float n0 = e.nx * inv, n1 = e.ny * inv, n2 = e.nz * inv;
-            if (renorm) {
-                const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
-                if (!(nn > 0.0f)) continue;
-                n0 /= nn; n1 /= nn; n2 /= nn;
-            }
-            const float res = n0 * e0 + n1 * e1 + n2 * e2;
-            // j = [x cross n, n]
-            const float j[6] = {x1 * n2 - x2 * n1, x2 * n0 - x0 * n2, x0 * n1 - x1 * n0, n0, n1, n2};
-#pragma unroll
-            for (int p = 0; p < 6; ++p) {
-                const float wj = ws * j[p];
-#pragma unroll
-                for (int q = p; q < 6; ++q) acc.add(tri_index(p, q), wj * j[q]);
-                acc.add(21 + p, wj * res);
-            }
-            acc.add(28, ws * res * res);
-        }
-        acc.add(27, W);
-        acc.add(29, 1.0f);
+        point_terms<PT2PL>(x0, x1, x2, e, ip, renorm, [&](int v, float x) { acc.add(v, x); });
     }
     if (bad) atomicOr(&st->flags, bad);
     block_partial<KAHAN>(acc, partials, blk, nblk);
@@ -621,6 +635,326 @@ __global__ void __launch_bounds__(kBlock, 3) k_em_multi(const Slot *__restrict__
     } else if (sg.role == kRoleClear) {
         clear_role(sl.tab[sg.tab], sl.list[sg.tab], __ldcg(&sl.ip[sg.it].nvert), b, sg.nblk);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Articulated model (Section 5.1, Eq. 20, Algorithm 1)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool in_subtree(const ArtTree &t, int b, int a) {  // b under or = a
+    for (int x = b; x >= 0; x = (x == 0) ? -1 : t.parent[x])
+        if (x == a) return true;
+    return false;
+}
+
+// 3 x 4 row-major product C = A * B (float), B's implicit last row 0 0 0 1.
+__device__ __forceinline__ void mul34(const float *A, const float *B, float *C) {
+    float t[12];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            t[4 * i + j] = A[4 * i] * B[j] + A[4 * i + 1] * B[4 + j] + A[4 * i + 2] * B[8 + j] +
+                           (j == 3 ? A[4 * i + 3] : 0.0f);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) C[k] = t[k];
+}
+
+// Forward kinematics in float for body b: its pose, and the world axis and
+// point of each of its joints (thread-per-body; each walks its own chain).
+__device__ void art_fk_body(const ArtTree &t, const double *root_T, const double *q, int b,
+                            float *Tb, float (*jaxis)[3], float (*jpoint)[3]) {
+    int chain[kMaxBodies];
+    int n = 0;
+    for (int x = b; x >= 0; x = (x == 0) ? -1 : t.parent[x]) chain[n++] = x;
+    float F[12];
+    for (int k = 0; k < 12; ++k) F[k] = (float)root_T[k];
+    for (int c = n - 1; c >= 0; --c) {
+        const int a = chain[c];
+        mul34(F, t.offset[a], F);
+        for (int j = t.joint_begin[a]; j < t.joint_begin[a + 1]; ++j) {
+            const float *u = t.axis[j];
+            if (a == b) {
+                for (int r = 0; r < 3; ++r) {
+                    jaxis[j][r] = F[4 * r] * u[0] + F[4 * r + 1] * u[1] + F[4 * r + 2] * u[2];
+                    jpoint[j][r] = F[4 * r + 3];
+                }
+            }
+            float sn, cs;
+            sincosf((float)q[j], &sn, &cs);
+            const float v = 1.0f - cs;
+            const float R[12] = {cs + u[0] * u[0] * v, u[0] * u[1] * v - u[2] * sn, u[0] * u[2] * v + u[1] * sn, 0.f,
+                                 u[1] * u[0] * v + u[2] * sn, cs + u[1] * u[1] * v, u[1] * u[2] * v - u[0] * sn, 0.f,
+                                 u[2] * u[0] * v - u[1] * sn, u[2] * u[1] * v + u[0] * sn, cs + u[2] * u[2] * v, 0.f};
+            mul34(F, R, F);
+        }
+    }
+    for (int k = 0; k < 12; ++k) Tb[k] = F[k];
+}
+
+// Last block of an articulated step: the normal equations of Algorithm 1 from
+// the per-body sums, a float64 LDL^T solve, the parameter update and the
+// kinematics of the new pose.  With H_b, h_b the body sums and S_b, s_b their
+// sums over the subtree of b, and c_j = (a_j; p_j x a_j) the twist column of
+// joint j (shared by every body under the joint):
+//   A_rr = S_root,  A_r,j = S_{b(j)} c_j,  g_r = s_root,  g_j = c_j . s_{b(j)},
+//   A_jk = c_j^T S_d c_k  (d the deeper of b(j), b(k) when one is under the
+//   other, else 0) -- the sum of J_sp^T (J^T J)_b J_sp over bodies.
+__device__ void art_finish(const ArtJob *job, ArtState *st, float stop_twist) {
+    __shared__ double S[kMaxBodies][21];
+    __shared__ double sv[kMaxBodies][6];
+    __shared__ double H[kMaxBodies][21];
+    __shared__ double hv[kMaxBodies][6];
+    __shared__ double cj[kMaxJoints][6];
+    __shared__ double A[kMaxDof][kMaxDof + 1];
+    __shared__ double y[kMaxDof];
+    __shared__ double ext[kMaxBodies][3];  // per body: weight sum, cost, count
+    __shared__ double diag[3];
+    __shared__ double inv_d, floor_;
+    __shared__ int ok;
+    __shared__ double sm_e[24];
+    const ArtTree &t = job->tree;
+    const int nb = t.nb, nj = t.nj, nd = 6 + nj;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nb * kArtVals; e += kBlock) {
+        const int b = e / kArtVals, v = e % kArtVals;
+        const double x = __ldcg(&st->acc[b][v]);
+        st->acc[b][v] = 0.0;                       // ready for the next iteration
+        if (v < 21) H[b][v] = x;
+        else if (v < 27) hv[b][v - 21] = x;
+        else ext[b][v - 27] = x;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += ext[b][tid];
+        diag[tid] = s;
+    }
+    // subtree sums
+    for (int e = tid; e < nb * 27; e += kBlock) {
+        const int b = e / 27, v = e % 27;
+        double s = 0.0;
+        for (int c = 0; c < nb; ++c)
+            if (in_subtree(t, c, b)) s += (v < 21) ? H[c][v] : hv[c][v - 21];
+        if (v < 21) S[b][v] = s;
+        else sv[b][v - 21] = s;
+    }
+    for (int j = tid; j < nj; j += kBlock) {
+        const double a0 = st->jaxis[j][0], a1 = st->jaxis[j][1], a2 = st->jaxis[j][2];
+        const double p0 = st->jpoint[j][0], p1 = st->jpoint[j][1], p2 = st->jpoint[j][2];
+        cj[j][0] = a0; cj[j][1] = a1; cj[j][2] = a2;
+        cj[j][3] = p1 * a2 - p2 * a1;
+        cj[j][4] = p2 * a0 - p0 * a2;
+        cj[j][5] = p0 * a1 - p1 * a0;
+    }
+    __syncthreads();
+    auto Sx = [&](int b, int p, int q) { return p <= q ? S[b][tri_index(p, q)] : S[b][tri_index(q, p)]; };
+    // lower triangle of A (i >= j) and g
+    const int nlow = nd * (nd + 1) / 2;
+    for (int e = tid; e < nlow + nd; e += kBlock) {
+        if (e >= nlow) {
+            const int i = e - nlow;
+            double gi;
+            if (i < 6) {
+                gi = sv[0][i];
+            } else {
+                const int j = i - 6, b = t.joint_body[j];
+                gi = 0.0;
+                for (int p = 0; p < 6; ++p) gi += cj[j][p] * sv[b][p];
+            }
+            y[i] = -gi;
+            continue;
+        }
+        int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+        while (i * (i + 1) / 2 > e) --i;
+        while ((i + 1) * (i + 2) / 2 <= e) ++i;
+        const int j = e - i * (i + 1) / 2;
+        double a;
+        if (i < 6) {
+            a = Sx(0, i, j);
+        } else if (j < 6) {
+            const int k = i - 6, b = t.joint_body[k];
+            a = 0.0;
+            for (int q = 0; q < 6; ++q) a += Sx(b, j, q) * cj[k][q];
+        } else {
+            const int k1 = i - 6, k2 = j - 6, b1 = t.joint_body[k1], b2 = t.joint_body[k2];
+            const int d = in_subtree(t, b1, b2) ? b1 : (in_subtree(t, b2, b1) ? b2 : -1);
+            a = 0.0;
+            if (d >= 0)
+                for (int p = 0; p < 6; ++p) {
+                    double u = 0.0;
+                    for (int q = 0; q < 6; ++q) u += Sx(d, p, q) * cj[k2][q];
+                    a += cj[k1][p] * u;
+                }
+        }
+        A[i][j] = a;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double md = 0.0;
+        for (int i = 0; i < nd; ++i) md = fmax(md, A[i][i]);
+        floor_ = md * 1e-12;
+        ok = md > 0.0;
+    }
+    __syncthreads();
+    // LDL^T, right-looking: pivot, Schur update of the trailing triangle, scale.
+    for (int k = 0; k < nd && ok; ++k) {
+        if (tid == 0) {
+            const double d = A[k][k];
+            ok = d > floor_;
+            inv_d = ok ? rcp64(d) : 0.0;
+        }
+        __syncthreads();
+        if (!ok) break;
+        const int m = nd - k - 1;
+        for (int e = tid; e < m * (m + 1) / 2; e += kBlock) {
+            int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+            while (r * (r + 1) / 2 > e) --r;
+            while ((r + 1) * (r + 2) / 2 <= e) ++r;
+            const int i = k + 1 + r, j = k + 1 + (e - r * (r + 1) / 2);
+            A[i][j] -= A[i][k] * A[j][k] * inv_d;
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < nd; i += kBlock) A[i][k] *= inv_d;
+        __syncthreads();
+    }
+    if (ok) {
+        for (int k = 0; k < nd; ++k) {           // L z = rhs
+            for (int i = k + 1 + tid; i < nd; i += kBlock) y[i] -= A[i][k] * y[k];
+            __syncthreads();
+        }
+        for (int i = tid; i < nd; i += kBlock) y[i] *= rcp64(A[i][i]);   // D w = z
+        __syncthreads();
+        for (int k = nd - 1; k >= 0; --k) {      // L^T x = w
+            for (int i = tid; i < k; i += kBlock) y[i] -= A[k][i] * y[k];
+            __syncthreads();
+        }
+    }
+    // parameter update (warp 0 for the root exponential), diagnostics
+    if (tid < 32) {
+        const int lane = tid;
+        if (lane == 0) {
+            st->ds.iters_run += 1;
+            st->ds.sum_w = diag[0];
+            st->ds.cost = diag[1];
+            st->ds.inliers = (long long)(diag[2] + 0.5);
+            if (!ok) st->ds.degenerate += 1;
+        }
+        if (ok) {
+            warp_se3_update(lane < 6 ? y[lane] : 0.0, st->root_T, sm_e);
+            float n2 = 0.0f;
+            for (int i = 0; i < nd; ++i) n2 += (float)y[i] * (float)y[i];
+            if (lane == 0) {
+                st->ds.twist_norm = sqrtf(n2);
+                if (stop_twist > 0.0f && sqrtf(n2) < stop_twist) st->ds.done = 1;
+            }
+        }
+    }
+    if (ok)
+        for (int j = tid; j < nj; j += kBlock) {
+            double qj = st->q[j] + y[6 + j];
+            qj = fmin(fmax(qj, t.q_min[j]), t.q_max[j]);
+            st->q[j] = qj;
+        }
+    __syncthreads();
+    for (int b = tid; b < nb; b += kBlock) art_fk_body(t, st->root_T, st->q, b, st->body_T[b], st->jaxis, st->jpoint);
+}
+
+// Articulated step: slice at x = T_{b(i)} x_ref (body poses staged in shared
+// memory), the same point terms as the rigid step, summed per body (Algorithm
+// 1, lines 1-4): thread registers while the body is unchanged, then a warp
+// reduction into shared memory, then float64 atomics per touched body.  Each
+// block takes a contiguous range of points (points sorted by body keep the
+// flushes rare).
+template <bool PT2PL>
+__device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
+    __shared__ float Tb[kMaxBodies][12];
+    __shared__ float sacc[kMaxBodies][kArtVals];
+    __shared__ int last;
+    const ArtJob *job = L.job;
+    ArtState *st = L.st;
+    const int nb = job->tree.nb;
+    for (int e = threadIdx.x; e < nb * 12; e += kBlock) Tb[e / 12][e % 12] = st->body_T[e / 12][e % 12];
+    for (int e = threadIdx.x; e < nb * kArtVals; e += kBlock) sacc[e / kArtVals][e % kArtVals] = 0.0f;
+    __syncthreads();
+    const IterParams ip = L.ip[L.it];
+    const int M = job->base.M;
+    const int renorm = job->base.renormalize;
+    const int chunk = (M + nblk - 1) / nblk;
+    const int start = blk * chunk, end = min(M, start + chunk);
+    float acc[kArtVals];
+    int cur = -1, bad = 0;
+    auto flush_lane = [&](int b) {
+#pragma unroll
+        for (int v = 0; v < kArtVals; ++v) atomicAdd(&sacc[b][v], acc[v]);
+    };
+    for (int i = start + threadIdx.x; i < end; i += kBlock) {
+        const int b = __ldg(job->body + i);
+        if (b < 0 || b >= nb) {
+            bad |= kFlagRange;
+            continue;
+        }
+        if (b != cur) {
+            if (cur >= 0) flush_lane(cur);
+#pragma unroll
+            for (int v = 0; v < kArtVals; ++v) acc[v] = 0.0f;
+            cur = b;
+        }
+        const float4 r = __ldg(job->base.X + i);
+        const float x0 = apply_row(Tb[b], 0, r), x1 = apply_row(Tb[b], 1, r), x2 = apply_row(Tb[b], 2, r);
+        Sums e;
+        if (!slice_point<PT2PL>(L.step, x0, x1, x2, ip, e, bad)) continue;
+        point_terms<PT2PL>(x0, x1, x2, e, ip, renorm, [&](int v, float x) { acc[v] += x; });
+    }
+    const int lane = threadIdx.x & 31;
+    const int c0 = __shfl_sync(kFull, cur, 0);
+    if (__all_sync(kFull, cur == c0)) {
+        if (c0 >= 0) {
+#pragma unroll
+            for (int v = 0; v < kArtVals; ++v) {
+                float x = acc[v];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+                if (lane == 0) atomicAdd(&sacc[c0][v], x);
+            }
+        }
+    } else if (cur >= 0) {
+        flush_lane(cur);
+    }
+    if (bad) atomicOr(&st->ds.flags, bad);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * kArtVals; e += kBlock) {
+        const int b = e / kArtVals;
+        if (sacc[b][kArtVals - 1] > 0.0f) atomicAdd(&st->acc[b][e % kArtVals], (double)sacc[b][e % kArtVals]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st->ds.ticket, 1) == nblk - 1;
+        if (last) __threadfence();
+    }
+    __syncthreads();
+    if (!last) return;
+    art_finish(job, st, job->base.stop_twist);
+    if (threadIdx.x == 0) st->ds.ticket = 0;
+}
+
+template <bool PT2PL>
+__global__ void __launch_bounds__(kBlock) k_art_iter(ArtLaunch L) {
+    int b = blockIdx.x;
+    if (b < L.gs) {
+        if (L.st->ds.done) return;
+        art_step_role<PT2PL>(L, b, L.gs);
+        return;
+    }
+    b -= L.gs;
+    if (b < L.gb) {
+        if (L.st->ds.done) return;
+        build_role<PT2PL>(&L.job->base, L.ip + L.build_it, L.build, L.build_list, &L.st->ds, b, L.gb);
+        return;
+    }
+    b -= L.gb;
+    if (b < L.gc) clear_role(L.clear, L.clear_list, __ldcg(&L.ip[L.clear_it].nvert), b, L.gc);
 }
 
 struct ClearSet {
@@ -853,6 +1187,13 @@ void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
         if (kahan) k_em_multi<false, true><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
         else k_em_multi<false, false><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
     }
+}
+
+void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s) {
+    const int grid = a.gs + a.gb + a.gc;
+    if (grid <= 0) return;
+    if (pt2pl) k_art_iter<true><<<grid, kBlock, 0, s>>>(a);
+    else k_art_iter<false><<<grid, kBlock, 0, s>>>(a);
 }
 
 int em_iter_blocks_per_sm(int pt2pl, int kahan) {
