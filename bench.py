@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the 16-bit storage lines")
     return ap.parse_args()
 
 
@@ -309,6 +310,25 @@ def run_ours(args):
                 "per_kernel_us": {k: round(v * 1e3, 2) for k, v in per_launch_ms.items() if prof[k][0]},
                 "lattice_vertices_mean": round(sum(v_means) / len(v_means))}
 
+    # ---- 16-bit lattice storage: the same batched step, bfloat16 / half records
+    precision = None
+    if not args.no_precision:
+        precision = {}
+        for name, code in (("bf16", fr.FR_BF16), ("fp16", fr.FR_FP16)):
+            popts = dict(opts, storage=code)
+            for _ in range(max(1, args.warmup)):
+                ctx.register_rigid_batch(dpairs, **popts)
+            ms, res = timed_steps(lambda: ctx.register_rigid_batch(dpairs, **popts), args.steps)
+            ps = slowest(sum(ms) / 1000.0)
+            precision[name] = {
+                "value": round(em_iters_all / ps, 1), "unit": UNIT,
+                "max_rot_diff_deg_vs_f32": round(max(synth.rotation_angle_deg(T, Tf) for (T, _, _), (Tf, _, _)
+                                                     in zip(res, last)), 6),
+                "max_trans_diff_vs_f32": round(max(float(np.linalg.norm(T[:3, 3] - Tf[:3, 3]))
+                                                   for (T, _, _), (Tf, _, _) in zip(res, last)), 7),
+                "max_rot_err_deg_vs_truth": round(max(synth.rotation_angle_deg(T, p.T_gt)
+                                                      for (T, _, _), p in zip(res, pairs)), 4)}
+
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
     if not args.no_e2e:
@@ -353,6 +373,7 @@ def run_ours(args):
                          "max_trans_err_vs_truth": round(trans_err, 6),
                          "max_rot_diff_deg_batched_vs_plain": round(mix_rot, 6)},
             "roofline": roofline,
+            "precision": precision,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

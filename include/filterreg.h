@@ -74,7 +74,11 @@ typedef struct {
                                    equal to sigma_start = fixed sigma, lattice built
                                    once (Section 3.2)                              [0.02]*/
     float w;                    /* outlier ratio of Section 3.1, 0 <= w < 1       [0.1] */
-    int32_t storage;            /* lattice value storage: FR_FP32, FR_BF16, FR_FP16 [FP32]*/
+    int32_t storage;            /* lattice values read by the slice: FR_FP32, or
+                                   FR_BF16 / FR_FP16 16-byte records made from the
+                                   float32 sums (see fr_estep_storage); the 16-bit
+                                   modes take neither blur nor kahan
+                                   (FR_ENOTSUPPORTED)                              [FP32]*/
     int32_t kahan;              /* 1 = Kahan-compensated float partial sums       [0]   */
     int32_t renormalize_normals;/* pt2pl: unit-normalise N_x of Eq. 9             [0]   */
     float stop_twist;           /* stop once |delta zeta| < stop_twist (Section 6.1's
@@ -97,7 +101,9 @@ typedef struct {
 } fr_report;
 
 /* Kernel classes of the per-kernel profile. */
-enum { FR_K_CLEAR = 0, FR_K_BUILD = 1, FR_K_BLUR = 2, FR_K_STEP = 3, FR_K_CLASSES = 4 };
+/* FR_K_CONVERT: a launch that only converts (and builds) ahead of the first
+ * step under 16-bit storage; later conversions run inside FR_K_STEP launches. */
+enum { FR_K_CLEAR = 0, FR_K_BUILD = 1, FR_K_BLUR = 2, FR_K_STEP = 3, FR_K_CONVERT = 4, FR_K_CLASSES = 5 };
 typedef struct {
     int64_t launches[FR_K_CLASSES]; /* kernels of each class timed since the last reset */
     double total_ms[FR_K_CLASSES];  /* their summed durations (CUDA events) */
@@ -191,6 +197,18 @@ FR_API fr_status fr_lattice_destroy(fr_ctx *ctx, fr_lattice *lat);
 FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                           const float *d_Yn, int64_t N, float sigma, int blur,
                           const double T[16], float *d_out);
+/* fr_estep_storage: fr_estep without blur, with the lattice values read by
+ * the slice stored as `storage` (fr_storage).  FR_FP32 is fr_estep itself;
+ * FR_BF16 / FR_FP16 keep the splat's float32 sums and, once the build is
+ * complete, round each vertex's values to one 16-byte record
+ * [W, sum b (y - p_v) (3), sum b n (3), 0] re-centred on the vertex position
+ * p_v (FR_FP16 also scales by 2^-e, e >= 0 the least with N 2^-e <= 2^14);
+ * the slice restores W p_v in float32.  The paper stores the lattice in
+ * float32 (Section 4.2); this mode has no counterpart there.  FR_EINVAL for
+ * an unknown storage value, otherwise as fr_estep. */
+FR_API fr_status fr_estep_storage(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                  const float *d_Yn, int64_t N, float sigma, int32_t storage,
+                                  const double T[16], float *d_out);
 
 /* ---- rigid registration (Sections 3.1, 3.3, 4, 5) ---------------------------
  * fr_register_rigid: run opt->iters EM iterations aligning the model d_X

@@ -35,10 +35,10 @@ EXPORTED = [
     "fr_lattice_vertices", "fr_lattice_info", "fr_lattice_destroy", "fr_estep",
     "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
     "fr_ctx_transfer_bytes", "fr_estep_noalloc", "fr_register_rigid_batch",
-    "fr_register_rigid_batch_host", "fr_register_articulated",
+    "fr_register_rigid_batch_host", "fr_register_articulated", "fr_estep_storage",
 ]
 FR_NOALLOC_MAX_OBS = 8192
-KERNEL_CLASSES = ("clear", "build", "blur", "em_iter")
+KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert")
 
 
 class FilterRegError(RuntimeError):
@@ -92,7 +92,7 @@ class fr_batch_item(ctypes.Structure):
 
 
 class fr_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 4), ("total_ms", ctypes.c_double * 4)]
+    _fields_ = [("launches", ctypes.c_int64 * 5), ("total_ms", ctypes.c_double * 5)]
 
 
 _vp = ctypes.c_void_p
@@ -133,6 +133,8 @@ def load(build_if_missing: bool = True):
                                   ctypes.POINTER(ctypes.c_int32)]
     L.fr_lattice_destroy.argtypes = [_vp, _vp]
     L.fr_estep.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_float, ctypes.c_int, _f64p, _vp]
+    L.fr_estep_storage.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_float, ctypes.c_int32,
+                                   _f64p, _vp]
     L.fr_register_rigid.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.POINTER(fr_options),
                                     _f64p, ctypes.POINTER(fr_report)]
     L.fr_register_rigid_host.argtypes = L.fr_register_rigid.argtypes
@@ -384,17 +386,26 @@ class Context:
             out.append((T, _report(reps[b]), int(items[b].status)))
         return out
 
-    def estep(self, X, Y, Yn=None, sigma=0.02, blur=False, T=None):
-        """E-step sums at T X: (M, 4) [M0, M1] or (M, 7) [M0, M1, Nsum] float32 CUDA tensor."""
+    def estep(self, X, Y, Yn=None, sigma=0.02, blur=False, T=None, storage=FR_FP32):
+        """E-step sums at T X: (M, 4) [M0, M1] or (M, 7) [M0, M1, Nsum] float32
+        CUDA tensor.  storage != FR_FP32 calls fr_estep_storage (no blur)."""
         import torch
         L = load()
         vd = 7 if Yn is not None else 4
         out = torch.empty((X.shape[0], vd), dtype=torch.float32, device=X.device)
         Tm = _pose(T)
-        st = L.fr_estep(self._h, _dev_ptr(X, "X"), X.shape[0], _dev_ptr(Y, "Y"),
-                        _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None, Y.shape[0],
-                        float(sigma), int(bool(blur)), Tm.ctypes.data_as(_f64p), out.data_ptr())
-        self._check(st, "fr_estep")
+        args = (_dev_ptr(X, "X"), X.shape[0], _dev_ptr(Y, "Y"),
+                _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None, Y.shape[0],
+                float(sigma))
+        if storage == FR_FP32:
+            st = L.fr_estep(self._h, *args, int(bool(blur)), Tm.ctypes.data_as(_f64p), out.data_ptr())
+            self._check(st, "fr_estep")
+        else:
+            if blur:
+                raise ValueError("16-bit lattice storage has no blur")
+            st = L.fr_estep_storage(self._h, *args, int(storage), Tm.ctypes.data_as(_f64p),
+                                    out.data_ptr())
+            self._check(st, "fr_estep_storage")
         return out
 
     # ---- lattice primitives ----------------------------------------------

@@ -28,11 +28,12 @@ void drop_graphs(fr_ctx *ctx) {
 }
 
 void free_tables(fr_ctx *ctx) {
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < kMaxTables; ++i) {
         Table &t = ctx->tables[i];
         cudaFree(t.keys);
         cudaFree(t.v0);
         cudaFree(t.v1);
+        cudaFree(t.cv);
         cudaFree(ctx->lists[i]);
         ctx->lists[i] = nullptr;
         t = Table{};
@@ -43,27 +44,38 @@ void free_tables(fr_ctx *ctx) {
     ctx->table_cap = 0;
 }
 
-// Three tables of at least `cap` slots, all empty; blur scratch if asked.
+fr_status alloc_table(fr_ctx *ctx, int i, uint32_t cap) {
+    Table &t = ctx->tables[i];
+    FR_CUDA(ctx, dev_alloc(&ctx->lists[i], cap));
+    FR_CUDA(ctx, dev_alloc(&t.keys, cap));
+    FR_CUDA(ctx, dev_alloc(&t.v0, cap));
+    FR_CUDA(ctx, dev_alloc(&t.v1, cap));
+    FR_CUDA(ctx, cudaMemsetAsync(t.keys, 0xFF, cap * sizeof(unsigned long long), ctx->stream));
+    FR_CUDA(ctx, cudaMemsetAsync(t.v0, 0, cap * sizeof(float4), ctx->stream));
+    FR_CUDA(ctx, cudaMemsetAsync(t.v1, 0, cap * sizeof(float4), ctx->stream));
+    t.mask = cap - 1;
+    t.max_probe = cap;
+    return FR_OK;
+}
+
+// Three tables of at least `cap` slots, all empty; with `compact`, a fourth
+// and the 16-bit record planes of all four; blur scratch if asked.
 }  // namespace
 
 namespace fr {
-fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur) {
+fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur, bool compact) {
     if (cap > ctx->table_cap) {
         cudaStreamSynchronize(ctx->stream);
         free_tables(ctx);
-        for (int i = 0; i < 3; ++i) {
-            Table &t = ctx->tables[i];
-            FR_CUDA(ctx, dev_alloc(&ctx->lists[i], cap));
-            FR_CUDA(ctx, dev_alloc(&t.keys, cap));
-            FR_CUDA(ctx, dev_alloc(&t.v0, cap));
-            FR_CUDA(ctx, dev_alloc(&t.v1, cap));
-            FR_CUDA(ctx, cudaMemsetAsync(t.keys, 0xFF, cap * sizeof(unsigned long long), ctx->stream));
-            FR_CUDA(ctx, cudaMemsetAsync(t.v0, 0, cap * sizeof(float4), ctx->stream));
-            FR_CUDA(ctx, cudaMemsetAsync(t.v1, 0, cap * sizeof(float4), ctx->stream));
-            t.mask = cap - 1;
-            t.max_probe = cap;
-        }
+        for (int i = 0; i < 3; ++i) FR_TRY(alloc_table(ctx, i, cap));
         ctx->table_cap = cap;
+        ctx->ws_gen++;
+        drop_graphs(ctx);
+    }
+    if (compact && !ctx->tables[3].keys) {
+        FR_TRY(alloc_table(ctx, 3, ctx->table_cap));
+        // written for every listed vertex before any read: no clearing needed
+        for (int i = 0; i < kMaxTables; ++i) FR_CUDA(ctx, dev_alloc(&ctx->tables[i].cv, ctx->table_cap));
         ctx->ws_gen++;
         drop_graphs(ctx);
     }
@@ -151,8 +163,8 @@ namespace {
 //                 -> clear all three tables
 // with 4 blur passes after every build when blur is on.
 struct Plan {
-    int iters, residual, blur, kahan, profile, annealed;
-    int gs, gb, gc, g_blur, g_final;  // block counts of the roles
+    int iters, residual, blur, kahan, profile, annealed, storage;
+    int gs, gv, gb, gc, g_blur, g_final;  // block counts of the roles
 };
 
 // Kernel launch wrapper: with profiling on, an event pair brackets each launch.
@@ -203,44 +215,62 @@ void issue_blur(fr_ctx *ctx, Issuer &k, const Plan &p, const Table &t) {
         });
 }
 
+// Builds run `lead` iterations ahead of the step that reads them: 1 with
+// float32 storage; 2 with 16-bit storage, whose records are made by a
+// convert role one launch after the build completed.
+//   lead 1: build(0) -> [step k | build k+1 | clear k-1] ...
+//   lead 2: build(0) -> [convert 0 | build 1] -> [step k | convert k+1 | build k+2 | clear k-1] ...
+// A fixed sigma builds (and converts) table 0 only.  Then the tables left
+// are cleared.
 int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
     Issuer k{ctx, s, p.profile};
     Table *tab = ctx->tables;
+    const int lead = p.storage != FR_FP32 ? 2 : 1;
+    const int ntab = lead + 2;
     IterLaunch base{};
     base.job = ctx->d_job;
     base.ip = ctx->d_ip;
     base.partials = ctx->partials;
     base.st = ctx->d_state;
     base.check_done = 1;
-    auto which = [&](int build) { return p.annealed ? build % 3 : 0; };
-    if (p.iters > 0) {
-        IterLaunch b0 = base;
-        b0.build = tab[0];
-        b0.build_list = ctx->lists[0];
-        b0.build_it = 0;
-        b0.gb = p.gb + p.gs;  // nothing else runs: use the step blocks too
-        b0.check_done = 0;
-        k(FR_K_BUILD, [&] { launch_em_iter(p.residual, p.kahan, b0, s); });
-        if (p.blur) issue_blur(ctx, k, p, tab[0]);
+    auto which = [&](int build) { return p.annealed ? build % ntab : 0; };
+    auto builds = [&](int b) { return b < p.iters && (p.annealed || b == 0); };
+    auto add_build = [&](IterLaunch &L, int b, int blocks) {
+        L.build = tab[which(b)];
+        L.build_list = ctx->lists[which(b)];
+        L.build_it = b;
+        L.gb = blocks;
+    };
+    auto add_conv = [&](IterLaunch &L, int b) {
+        L.conv = tab[which(b)];
+        L.conv_list = ctx->lists[which(b)];
+        L.conv_it = b;
+        L.gv = p.gv;
+    };
+    // prologue: the first `lead` builds (and the conversion of build 0)
+    for (int j = 0; j < lead && p.iters > 0; ++j) {
+        IterLaunch L = base;
+        L.check_done = 0;
+        if (builds(j)) add_build(L, j, j == 0 ? p.gb + p.gs : p.gb);  // nothing else runs at first
+        if (j >= 1) add_conv(L, j - 1);
+        if (L.gb + L.gv == 0) continue;
+        k(j == 0 ? FR_K_BUILD : FR_K_CONVERT, [&] { launch_em_iter(p.residual, p.kahan, L, s, p.storage); });
+        if (p.blur && L.gb) issue_blur(ctx, k, p, L.build);
     }
     for (int it = 0; it < p.iters; ++it) {
         IterLaunch L = base;
         L.it = it;
         L.gs = p.gs;
         L.step = tab[which(it)];
-        if (p.annealed && it + 1 < p.iters) {
-            L.build = tab[which(it + 1)];
-            L.build_list = ctx->lists[which(it + 1)];
-            L.build_it = it + 1;
-            L.gb = p.gb;
-        }
+        if (p.annealed && builds(it + lead)) add_build(L, it + lead, p.gb);
+        if (lead == 2 && p.annealed && builds(it + 1)) add_conv(L, it + 1);
         if (p.annealed && it >= 1) {  // the table of build it-1, last read by step it-1
             L.clear = tab[which(it - 1)];
             L.clear_list = ctx->lists[which(it - 1)];
             L.clear_it = it - 1;
             L.gc = p.gc;
         }
-        k(FR_K_STEP, [&] { launch_em_iter(p.residual, p.kahan, L, s); });
+        k(FR_K_STEP, [&] { launch_em_iter(p.residual, p.kahan, L, s, p.storage); });
         if (p.blur && L.gb) issue_blur(ctx, k, p, L.build);
     }
     if (p.iters > 0) {
@@ -265,7 +295,8 @@ int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
 // Kernels of a plan (all are profiled).
 int plan_kernels(const Plan &p) {
     int n = 0;
-    if (p.iters > 0) n += 2 + (p.blur ? 4 : 0);  // first build (+ blur), final clear
+    const int lead = p.storage != FR_FP32 ? 2 : 1;
+    if (p.iters > 0) n += 2 + (p.blur ? 4 : 0) + (lead - 1);  // prologue (+ blur), final clear
     n += p.iters;
     if (p.annealed && p.blur && p.iters > 1) n += 4 * (p.iters - 1);
     return n;
@@ -278,7 +309,7 @@ fr_status run_plan(fr_ctx *ctx, const Plan &p, bool use_graph) {
         return ctx->cuda(cudaGetLastError(), "kernel launch");
     }
     GraphKey key{{p.iters, p.residual, p.blur, p.kahan, p.profile, p.annealed, p.gs, p.gb, p.gc,
-                  p.g_blur, p.g_final, (int)ctx->tables[0].mask, 0, 0},
+                  p.g_blur, p.g_final, (int)ctx->tables[0].mask, p.storage, 0},
                  ctx->ws_gen};
     CachedGraph *hit = nullptr;
     for (auto &g : ctx->graphs)
@@ -333,8 +364,10 @@ fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
         !std::isfinite(o->sigma_end))
         return ctx->fail(FR_EINVAL, "sigma must be finite and > 0");
     if (!(o->w >= 0.0f && o->w < 1.0f)) return ctx->fail(FR_EINVAL, "w must lie in [0, 1)");
-    if (o->storage != FR_FP32)
-        return ctx->fail(FR_ENOTSUPPORTED, "only FP32 lattice storage is implemented");
+    if (o->storage != FR_FP32 && o->storage != FR_BF16 && o->storage != FR_FP16)
+        return ctx->fail(FR_EINVAL, "storage must be FR_FP32, FR_BF16 or FR_FP16");
+    if (o->storage != FR_FP32 && (o->kahan || o->blur))
+        return ctx->fail(FR_ENOTSUPPORTED, "16-bit lattice storage is implemented without blur and Kahan sums");
     return FR_OK;
 }
 }  // namespace fr
@@ -381,6 +414,16 @@ bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip)
         p.inv_sigma2 = (float)(1.0 / (sd * sd));
         p.rebuild = (k == 0 || sig != ip[k - 1].sigma) ? 1 : 0;
         p.nvert = 0;
+        // A vertex's weight is at most N (every barycentric weight is <= 1):
+        // half-precision records are scaled by 2^-e so that N 2^-e <= 2^14.
+        int e = 0;
+        while (o->storage == FR_FP16 && (double)N > std::ldexp(1.0, 14 + e)) ++e;
+        p.vscale = (float)std::ldexp(1.0, -e);
+        p.inv_vscale = (float)std::ldexp(1.0, e);
+        p.ws1 = 1.0f / (2.0f * p.s1);
+        p.ws2 = 1.0f / (6.0f * p.s2);
+        p.ws3 = 1.0f / (12.0f * p.s3);
+        p.pad[0] = p.pad[1] = p.pad[2] = 0;
         if (k > 0 && p.rebuild) changes = true;
     }
     return changes;
@@ -400,8 +443,9 @@ void plan_grids(fr_ctx *ctx, Plan &p, int64_t M, int64_t N, uint32_t cap) {
     const long long resident = (long long)bpsm * ctx->num_sms;
     long long gs = (M + kBlock - 1) / kBlock, gb = (N + kBlock - 1) / kBlock;
     long long gc = p.annealed ? std::max<long long>(8, std::min<long long>(64, cap / 16384)) : 0;
+    const long long gv = p.storage != FR_FP32 ? std::max<long long>(8, std::min<long long>(128, cap / 4096)) : 0;
     if (!p.annealed) gb = std::max<long long>(1, std::min(gb, resident));
-    const long long room = resident - gc;
+    const long long room = resident - gc - (p.annealed ? gv : 0);
     const long long want = gs + (p.annealed ? gb : 0);
     if (want > room) {
         const double f = (double)room / (double)want;
@@ -409,6 +453,7 @@ void plan_grids(fr_ctx *ctx, Plan &p, int64_t M, int64_t N, uint32_t cap) {
         if (p.annealed) gb = std::max<long long>(1, (long long)(gb * f));
     }
     p.gs = (int)gs;
+    p.gv = (int)gv;
     p.gb = (int)gb;
     p.gc = (int)gc;
     p.g_blur = blocks_for(ctx, cap, 8);
@@ -704,9 +749,9 @@ FR_API fr_status fr_lattice_destroy(fr_ctx *ctx, fr_lattice *lat) {
 
 // ---- E step -----------------------------------------------------------------
 
-FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
-                          const float *d_Yn, int64_t N, float sigma, int blur, const double T[16],
-                          float *d_out) {
+static fr_status estep_impl(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                            const float *d_Yn, int64_t N, float sigma, int blur, int storage,
+                            const double T[16], float *d_out) {
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_cloud(ctx, d_X, M, "d_X"));
     FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));
@@ -716,8 +761,10 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
     cudaSetDevice(ctx->device);
     const int pt2pl = d_Yn ? 1 : 0;
     const uint32_t cap = table_slots(N, true);
+    if (storage != FR_FP32 && storage != FR_BF16 && storage != FR_FP16)
+        return ctx->fail(FR_EINVAL, "storage must be FR_FP32, FR_BF16 or FR_FP16");
     FR_TRY(ensure_small(ctx, 1, 1));
-    FR_TRY(ensure_tables(ctx, cap, blur != 0));
+    FR_TRY(ensure_tables(ctx, cap, blur != 0, storage != FR_FP32));
     Table t = ctx->tables[0];
     t.mask = cap - 1;
     t.max_probe = table_probe_limit(cap, true);
@@ -726,6 +773,7 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
     o.iters = 1;
     o.sigma_start = o.sigma_end = sigma;
     o.blur = blur;
+    o.storage = storage;
     fill_iter_params(&o, M, N, ctx->h_ip);
     RigidJob *j = ctx->h_job;
     *j = RigidJob{};
@@ -748,8 +796,20 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
     b.build_list = ctx->lists[0];
     b.build_it = 0;
     b.gb = blocks_for(ctx, N, 8);
-    launch_em_iter(pt2pl, 0, b, ctx->stream);
+    launch_em_iter(pt2pl, 0, b, ctx->stream, storage);
     ctx->launches += 1;
+    if (storage != FR_FP32) {  // 16-bit records of the completed build
+        IterLaunch c{};
+        c.job = ctx->d_job;
+        c.ip = ctx->d_ip;
+        c.st = ctx->d_state;
+        c.conv = t;
+        c.conv_list = ctx->lists[0];
+        c.conv_it = 0;
+        c.gv = blocks_for(ctx, cap, 4);
+        launch_em_iter(pt2pl, 0, c, ctx->stream, storage);
+        ctx->launches += 1;
+    }
     if (blur) {
         Table a = t, c = t;
         c.v0 = ctx->blur0;
@@ -764,7 +824,7 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
         ctx->launches += 4;
     }
     launch_estep_out(pt2pl, ctx->d_job, ctx->d_ip, t, d_out, ctx->d_state, blocks_for(ctx, M, 8),
-                     ctx->stream);
+                     ctx->stream, storage);
     int *l0 = ctx->lists[0];
     const int *c0 = &ctx->d_ip[0].nvert;
     launch_clear_lists(&t, &l0, &c0, 1, blocks_for(ctx, N, 4), ctx->stream);
@@ -773,6 +833,18 @@ FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float 
     FR_CUDA(ctx, copy_async(ctx, hs, ctx->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost));
     FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return check_flags(ctx, hs->flags);
+}
+
+FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                          const float *d_Yn, int64_t N, float sigma, int blur, const double T[16],
+                          float *d_out) {
+    return estep_impl(ctx, d_X, M, d_Y, d_Yn, N, sigma, blur, FR_FP32, T, d_out);
+}
+
+FR_API fr_status fr_estep_storage(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                  const float *d_Yn, int64_t N, float sigma, int32_t storage,
+                                  const double T[16], float *d_out) {
+    return estep_impl(ctx, d_X, M, d_Y, d_Yn, N, sigma, 0, storage, T, d_out);
 }
 
 // ---- rigid registration -----------------------------------------------------
@@ -788,11 +860,12 @@ static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, c
     p.residual = pt2pl;
     p.blur = opt->blur ? 1 : 0;
     p.kahan = opt->kahan ? 1 : 0;
+    p.storage = opt->storage;
     p.profile = ctx->profiling;
     p.annealed = fill_iter_params(opt, M, N, ctx->h_ip) ? 1 : 0;
     plan_grids(ctx, p, M, N, cap);
     FR_TRY(ensure_small(ctx, opt->iters, p.gs));
-    FR_TRY(ensure_tables(ctx, cap, p.blur != 0));
+    FR_TRY(ensure_tables(ctx, cap, p.blur != 0, p.storage != FR_FP32));
     for (Table &t : ctx->tables) {
         t.mask = cap - 1;
         t.max_probe = table_probe_limit(cap, safe);

@@ -115,9 +115,9 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
     }
     const uint32_t cap = table_slots(N, safe);
     FR_TRY(ensure_small(ctx, opt->iters, 1));
-    FR_TRY(ensure_tables(ctx, cap, false));
-    Table tab[3];
-    for (int i = 0; i < 3; ++i) {
+    FR_TRY(ensure_tables(ctx, cap, false, opt->storage != FR_FP32));
+    Table tab[kMaxTables];
+    for (int i = 0; i < kMaxTables; ++i) {
         tab[i] = ctx->tables[i];
         tab[i].mask = cap - 1;
         tab[i].max_probe = table_probe_limit(cap, safe);
@@ -168,17 +168,30 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
     // ---- launches ----------------------------------------------------------
     const int gs = blocks_for(ctx, M, 4), gb = blocks_for(ctx, N, 4);
     const int gc = annealed ? std::max(8, std::min(64, (int)(N / 4096) + 1)) : 0;
-    auto tab_of = [&](int build) { return annealed ? build % 3 : 0; };
-    if (opt->iters > 0) {
+    // Builds run `lead` iterations ahead of their step: 2 with 16-bit storage,
+    // whose records are converted in the launch after the build.
+    const int lead = opt->storage != FR_FP32 ? 2 : 1;
+    const int gv = lead == 2 ? blocks_for(ctx, cap, 1) : 0;
+    auto tab_of = [&](int build) { return annealed ? build % (lead + 2) : 0; };
+    auto builds = [&](int b) { return b < opt->iters && (annealed || b == 0); };
+    for (int j = 0; j < lead && opt->iters > 0; ++j) {  // prologue: builds 0..lead-1, convert 0
         IterLaunch b0{};
         b0.job = &w->d_job->base;
         b0.ip = ctx->d_ip;
         b0.st = &w->d_state->ds;
-        b0.build = tab[0];
-        b0.build_list = ctx->lists[0];
-        b0.build_it = 0;
-        b0.gb = blocks_for(ctx, N, 8);
-        launch_em_iter(pt2pl, 0, b0, ctx->stream);
+        if (builds(j)) {
+            b0.build = tab[tab_of(j)];
+            b0.build_list = ctx->lists[tab_of(j)];
+            b0.build_it = j;
+            b0.gb = blocks_for(ctx, N, 8);
+        }
+        if (j >= 1) {
+            b0.conv = tab[tab_of(j - 1)];
+            b0.conv_list = ctx->lists[tab_of(j - 1)];
+            b0.conv_it = j - 1;
+            b0.gv = gv;
+        }
+        launch_em_iter(pt2pl, 0, b0, ctx->stream, opt->storage);
         ctx->launches += 1;
     }
     for (int it = 0; it < opt->iters; ++it) {
@@ -189,11 +202,17 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
         L.it = it;
         L.step = tab[tab_of(it)];
         L.gs = gs;
-        if (annealed && it + 1 < opt->iters) {
-            L.build = tab[tab_of(it + 1)];
-            L.build_list = ctx->lists[tab_of(it + 1)];
-            L.build_it = it + 1;
+        if (annealed && builds(it + lead)) {
+            L.build = tab[tab_of(it + lead)];
+            L.build_list = ctx->lists[tab_of(it + lead)];
+            L.build_it = it + lead;
             L.gb = gb;
+        }
+        if (lead == 2 && annealed && builds(it + 1)) {
+            L.conv = tab[tab_of(it + 1)];
+            L.conv_list = ctx->lists[tab_of(it + 1)];
+            L.conv_it = it + 1;
+            L.gv = gv;
         }
         if (annealed && it >= 1) {
             L.clear = tab[tab_of(it - 1)];
@@ -201,7 +220,7 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
             L.clear_it = it - 1;
             L.gc = gc;
         }
-        launch_art_iter(pt2pl, L, ctx->stream);
+        launch_art_iter(pt2pl, L, ctx->stream, opt->storage);
         ctx->launches += 1;
     }
     if (opt->iters > 0) {

@@ -26,6 +26,7 @@ struct BatchWorkspace {
     unsigned long long *keys = nullptr;  // key arena, all empty between calls
     float4 *v0 = nullptr, *v1 = nullptr; // value arenas, zero between calls
     size_t slots_cap = 0;                // table slots in each arena
+    uint4 *cv = nullptr;                 // compact values (16-bit storage), slots_cap slots
     unsigned char *misc = nullptr;       // descriptors, lists, partials
     size_t misc_cap = 0;
     unsigned char *h_up = nullptr;       // pinned staging of the uploaded descriptors
@@ -42,6 +43,7 @@ void free_batch_workspace(fr_ctx *ctx) {
     cudaFree(w->keys);
     cudaFree(w->v0);
     cudaFree(w->v1);
+    cudaFree(w->cv);
     cudaFree(w->misc);
     cudaFree(w->stage);
     cudaFreeHost(w->h_up);
@@ -58,7 +60,8 @@ constexpr int kPointsPerThread = 2;  // step and build blocks cover 512 points
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-fr_status ensure_arenas(fr_ctx *ctx, size_t slots, size_t misc, size_t up, size_t down) {
+fr_status ensure_arenas(fr_ctx *ctx, size_t slots, size_t misc, size_t up, size_t down,
+                        bool compact) {
     if (!ctx->batch) ctx->batch = new BatchWorkspace();
     BatchWorkspace *w = ctx->batch;
     if (slots > w->slots_cap) {
@@ -67,8 +70,10 @@ fr_status ensure_arenas(fr_ctx *ctx, size_t slots, size_t misc, size_t up, size_
         cudaFree(w->keys);
         cudaFree(w->v0);
         cudaFree(w->v1);
+        cudaFree(w->cv);
         w->keys = nullptr;
         w->v0 = w->v1 = nullptr;
+        w->cv = nullptr;
         w->slots_cap = 0;
         FR_CUDA(ctx, dev_alloc(&w->keys, cap));
         FR_CUDA(ctx, dev_alloc(&w->v0, cap));
@@ -78,6 +83,7 @@ fr_status ensure_arenas(fr_ctx *ctx, size_t slots, size_t misc, size_t up, size_
         FR_CUDA(ctx, cudaMemsetAsync(w->v1, 0, cap * sizeof(float4), ctx->stream));
         w->slots_cap = cap;
     }
+    if (compact && !w->cv) FR_CUDA(ctx, dev_alloc(&w->cv, w->slots_cap));
     if (misc > w->misc_cap) {
         const size_t cap = std::max(misc, w->misc_cap * 3 / 2);
         cudaStreamSynchronize(ctx->stream);
@@ -111,8 +117,8 @@ int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 struct ItemPlan {
     uint32_t cap;
     int annealed;
-    int gs, gb, gc, gp;        // step, build, clear blocks per launch; first-build blocks
-    size_t tab_off;            // first slot of its three tables in the arenas
+    int gs, gb, gc, gp, gv;    // step, build, clear blocks per launch; first-build blocks; convert
+    size_t tab_off;            // first slot of its tables in the arenas
     size_t list_off, part_off; // in misc (bytes)
 };
 
@@ -122,42 +128,52 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     const int kahan = opt->kahan ? 1 : 0;
     const int iters = opt->iters;
     const int iters1 = iters > 0 ? iters : 1;
+    // Builds run `lead` iterations ahead of their step (2 with 16-bit storage:
+    // a build's records are converted in the launch after it), so
+    // lead + 2 tables rotate per item.
+    const int lead = opt->storage != FR_FP32 ? 2 : 1;
+    const int ntab = lead + 2;
 
     // ---- per-item plans and the arena layout --------------------------------
     std::vector<ItemPlan> ip(n);
     size_t slots = 0;
-    int seg_per_iter = 0, grid_iter = 0, grid_pro = 0, grid_epi = 0;
+    int seg_per_iter = 0, grid_iter = 0, grid_pro = 0, grid_pro2 = 0, grid_epi = 0;
     for (int b = 0; b < n; ++b) {
         const fr_batch_item &it = items[b];
         ItemPlan &p = ip[b];
         p.cap = table_slots(it.N, safe);
         p.tab_off = slots;
-        slots += 3 * (size_t)p.cap;
+        slots += ntab * (size_t)p.cap;
         p.gs = div_up(it.M, (long long)kBlock * kPointsPerThread);
         p.gp = div_up(it.N, (long long)kBlock * kPointsPerThread);
         p.annealed = (it.sigma_start != it.sigma_end && iters > 1) ? 1 : 0;
         p.gb = p.annealed ? p.gp : 0;
         p.gc = p.annealed ? std::max(1, div_up(it.N, 4096)) : 0;
-        seg_per_iter += 1 + (p.annealed ? 2 : 0);
-        grid_iter += p.gs + p.gb + p.gc;
+        p.gv = lead == 2 ? std::max(1, div_up(it.N, 2048)) : 0;
+        seg_per_iter += 1 + (p.annealed ? 2 + (lead - 1) : 0);
+        grid_iter += p.gs + p.gb + p.gc + (p.annealed ? p.gv : 0);
         grid_pro += p.gp;
+        grid_pro2 += p.gv + (p.annealed ? p.gb : 0);
         grid_epi += (p.annealed && iters > 1) ? 2 * p.gc : std::max(1, div_up(it.N, 4096));
     }
-    const int seg_pro = n, seg_epi_max = 2 * n;
+    if (lead == 1) grid_pro2 = 0;
+    const int seg_pro = n, seg_pro2 = 2 * n, seg_epi_max = 2 * n;
     // upload region (also the device layout of the misc arena's head)
     size_t off = 0;
     const size_t o_jobs = off; off = align256(off + n * sizeof(RigidJob));
     const size_t o_states = off; off = align256(off + n * sizeof(DeviceState));
     const size_t o_ips = off; off = align256(off + (size_t)n * iters1 * sizeof(IterParams));
     const size_t o_slots = off; off = align256(off + n * sizeof(Slot));
-    const size_t o_segs = off; off = align256(off + (size_t)(iters1 * seg_per_iter + seg_pro + seg_epi_max) * sizeof(Seg));
+    const size_t o_segs = off;
+    off = align256(off + (size_t)(iters1 * seg_per_iter + seg_pro + seg_pro2 + seg_epi_max) * sizeof(Seg));
     const size_t o_bs_iter = off; off = align256(off + grid_iter * sizeof(unsigned short));
     const size_t o_bs_pro = off; off = align256(off + grid_pro * sizeof(unsigned short));
+    const size_t o_bs_pro2 = off; off = align256(off + grid_pro2 * sizeof(unsigned short));
     const size_t o_bs_epi = off; off = align256(off + grid_epi * sizeof(unsigned short));
     const size_t up_bytes = off;
     for (int b = 0; b < n; ++b) {
         ip[b].list_off = off;
-        off = align256(off + 3 * (size_t)ip[b].cap * sizeof(int));
+        off = align256(off + ntab * (size_t)ip[b].cap * sizeof(int));
     }
     for (int b = 0; b < n; ++b) {
         ip[b].part_off = off;
@@ -165,7 +181,7 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     }
     const size_t misc_bytes = off;
     const size_t down_bytes = align256(n * sizeof(DeviceState)) + (size_t)n * iters1 * sizeof(IterParams);
-    FR_TRY(ensure_arenas(ctx, slots, misc_bytes, up_bytes, down_bytes));
+    FR_TRY(ensure_arenas(ctx, slots, misc_bytes, up_bytes, down_bytes, opt->storage != FR_FP32));
     BatchWorkspace *w = ctx->batch;
     unsigned char *U = w->h_up, *D = w->misc;
 
@@ -199,10 +215,10 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
         s.st = (DeviceState *)(D + o_states) + b;
         s.ip = (IterParams *)(D + o_ips) + (size_t)b * iters1;
         s.partials = (float2 *)(D + ip[b].part_off);
-        for (int t = 0; t < 3; ++t) {
+        for (int t = 0; t < ntab; ++t) {
             const size_t base = ip[b].tab_off + (size_t)t * ip[b].cap;
             s.tab[t] = Table{w->keys + base, w->v0 + base, pt2pl ? w->v1 + base : nullptr, ip[b].cap - 1,
-                             table_probe_limit(ip[b].cap, safe)};
+                             table_probe_limit(ip[b].cap, safe), w->cv ? w->cv + base : nullptr};
             s.list[t] = (int *)(D + ip[b].list_off) + (size_t)t * ip[b].cap;
         }
     }
@@ -210,8 +226,10 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     Seg *segs = (Seg *)(U + o_segs);
     unsigned short *bs_iter = (unsigned short *)(U + o_bs_iter);
     unsigned short *bs_pro = (unsigned short *)(U + o_bs_pro);
+    unsigned short *bs_pro2 = (unsigned short *)(U + o_bs_pro2);
     unsigned short *bs_epi = (unsigned short *)(U + o_bs_epi);
-    auto tab_of = [&](int b, int build) { return ip[b].annealed ? build % 3 : 0; };
+    auto tab_of = [&](int b, int build) { return ip[b].annealed ? build % ntab : 0; };
+    // iteration k: per item step k | [annealed] build k+lead | convert k+1 (lead 2) | clear k-1
     for (int k = 0; k < iters; ++k) {
         Seg *S = segs + (size_t)k * seg_per_iter;
         int si = 0, blk = 0;
@@ -219,10 +237,16 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
             S[si++] = Seg{b, kRoleStep, k, tab_of(b, k), blk, ip[b].gs};
             blk += ip[b].gs;
             if (ip[b].annealed) {
-                const bool build = k + 1 < iters, clear = k >= 1;
-                S[si++] = Seg{b, build ? kRoleBuild : kRoleNone, k + 1, tab_of(b, k + 1), blk, ip[b].gb};
+                const bool build = k + lead < iters, clear = k >= 1;
+                S[si++] = Seg{b, build ? kRoleBuild : kRoleNone, k + lead, tab_of(b, k + lead), blk, ip[b].gb};
                 blk += ip[b].gb;
-                S[si++] = Seg{b, clear ? kRoleClear : kRoleNone, k - 1, tab_of(b, k + 2), blk, ip[b].gc};
+                if (lead == 2) {
+                    const bool conv = k + 1 < iters;
+                    S[si++] = Seg{b, conv ? kRoleConvert : kRoleNone, k + 1, tab_of(b, k + 1), blk, ip[b].gv};
+                    blk += ip[b].gv;
+                }
+                S[si++] = Seg{b, clear ? kRoleClear : kRoleNone, k - 1, clear ? tab_of(b, k - 1) : 0, blk,
+                              ip[b].gc};
                 blk += ip[b].gc;
             }
         }
@@ -235,11 +259,16 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
             if (ip[b].annealed) {
                 for (int q = 0; q < ip[b].gb; ++q) bs_iter[blk++] = (unsigned short)si;
                 ++si;
+                if (lead == 2) {
+                    for (int q = 0; q < ip[b].gv; ++q) bs_iter[blk++] = (unsigned short)si;
+                    ++si;
+                }
                 for (int q = 0; q < ip[b].gc; ++q) bs_iter[blk++] = (unsigned short)si;
                 ++si;
             }
         }
     }
+    // prologue: build 0; with lead 2 a second launch converts 0 and builds 1
     Seg *Spro = segs + (size_t)iters1 * seg_per_iter;
     {
         int blk = 0;
@@ -248,7 +277,22 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
             for (int q = 0; q < ip[b].gp; ++q) bs_pro[blk++] = (unsigned short)b;
         }
     }
-    Seg *Sepi = Spro + seg_pro;
+    Seg *Spro2 = Spro + seg_pro;
+    if (lead == 2) {
+        int blk = 0, si = 0;
+        for (int b = 0; b < n; ++b) {
+            Spro2[si] = Seg{b, kRoleConvert, 0, 0, blk, ip[b].gv};
+            for (int q = 0; q < ip[b].gv; ++q) bs_pro2[blk++] = (unsigned short)si;
+            ++si;
+            if (ip[b].annealed) {
+                Spro2[si] = Seg{b, iters > 1 ? kRoleBuild : kRoleNone, 1, tab_of(b, 1), blk, ip[b].gb};
+                for (int q = 0; q < ip[b].gb; ++q) bs_pro2[blk++] = (unsigned short)si;
+                ++si;
+            }
+        }
+        grid_pro2 = blk;
+    }
+    Seg *Sepi = Spro2 + seg_pro2;
     int n_epi = 0;
     {
         int blk = 0;
@@ -290,18 +334,25 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     if (iters > 0) {
         timed(FR_K_BUILD, [&] {
             launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter,
-                            (const unsigned short *)(D + o_bs_pro), grid_pro, 0, ctx->stream);
+                            (const unsigned short *)(D + o_bs_pro), grid_pro, 0, ctx->stream, opt->storage);
         });
+        if (lead == 2)
+            timed(FR_K_CONVERT, [&] {
+                launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter + seg_pro,
+                                (const unsigned short *)(D + o_bs_pro2), grid_pro2, 0, ctx->stream,
+                                opt->storage);
+            });
         for (int k = 0; k < iters; ++k)
             timed(FR_K_STEP, [&] {
                 launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)k * seg_per_iter,
-                                (const unsigned short *)(D + o_bs_iter), grid_iter, 1, ctx->stream);
+                                (const unsigned short *)(D + o_bs_iter), grid_iter, 1, ctx->stream,
+                                opt->storage);
             });
         timed(FR_K_CLEAR, [&] {
-            launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter + seg_pro,
-                            (const unsigned short *)(D + o_bs_epi), grid_epi, 0, ctx->stream);
+            launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter + seg_pro + seg_pro2,
+                            (const unsigned short *)(D + o_bs_epi), grid_epi, 0, ctx->stream, opt->storage);
         });
-        ctx->launches += iters + 2;
+        ctx->launches += iters + 2 + (lead - 1);
     }
     FR_CUDA(ctx, cudaGetLastError());
     unsigned char *H = w->h_down;
@@ -371,7 +422,10 @@ fr_status validate_batch(fr_ctx *ctx, const fr_batch_item *items, int n, const f
                          bool on_host) {
     FR_TRY(validate_options(ctx, opt));
     if (opt->blur) return ctx->fail(FR_ENOTSUPPORTED, "batched registration does not blur");
-    if (!items || n < 1 || n > 16384) return ctx->fail(FR_EINVAL, "need 1..16384 batch items");
+    // block -> segment maps hold 16-bit segment indices: at most 65536
+    // segments per launch, 4 per item (5 with 16-bit storage)
+    const int max_items = opt->storage != FR_FP32 ? 65536 / 5 : 65536 / 4;
+    if (!items || n < 1 || n > max_items) return ctx->fail(FR_EINVAL, "need 1..%d batch items", max_items);
     for (int b = 0; b < n; ++b) {
         const fr_batch_item &it = items[b];
         if (!it.d_X || !it.d_Y || it.M < 1 || it.N < 1 || it.M > (1ll << 30) || it.N > (1ll << 30))

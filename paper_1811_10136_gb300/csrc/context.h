@@ -97,8 +97,8 @@ struct fr_ctx {
     // partials, device state, job descriptor and per-iteration constants.
     uint64_t ws_gen = 1;
     uint32_t table_cap = 0;
-    fr::Table tables[3] = {};
-    int *lists[3] = {nullptr, nullptr, nullptr};  // slots claimed by each table's last build
+    fr::Table tables[fr::kMaxTables] = {};  // 3 with float32 storage, 4 with 16-bit storage
+    int *lists[fr::kMaxTables] = {};        // slots claimed by each table's last build
     float4 *blur0 = nullptr, *blur1 = nullptr;
     float2 *partials = nullptr;
     int partial_rows = 0;
@@ -125,8 +125,8 @@ struct fr_ctx {
     int profiling = 0;
     std::vector<cudaEvent_t> events;  // 2 per kernel, grown on demand, kept for the graphs
     std::vector<int> event_class;     // kernel class of each event pair of the last plan
-    int64_t prof_launches[FR_K_CLASSES] = {0, 0, 0, 0};
-    double prof_ms[FR_K_CLASSES] = {0, 0, 0, 0};
+    int64_t prof_launches[FR_K_CLASSES] = {};
+    double prof_ms[FR_K_CLASSES] = {};
 
     fr_status fail(fr_status s, const char *fmt, ...) {
         char buf[512];
@@ -171,6 +171,6 @@ int fused_blocks_per_sm(fr_ctx *ctx, int pt2pl, int kahan);
 void collect_profile(fr_ctx *ctx, int kernels);
 void free_batch_workspace(fr_ctx *ctx);   // batch.cu
 void free_art_workspace(fr_ctx *ctx);     // articulated.cu
-fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur);
+fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur, bool compact = false);
 fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows);
 }  // namespace fr

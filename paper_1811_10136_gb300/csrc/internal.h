@@ -25,6 +25,10 @@ struct IterParams {
     float inv_sigma2;      // Sigma^{-1} of Eq. 7
     int rebuild;           // lattice rebuilt at this iteration
     int nvert;             // vertices created by this iteration's build (device counter)
+    float vscale;          // power of two applied to 16-bit records (keeps half below its range)
+    float inv_vscale;
+    float ws1, ws2, ws3;   // world units per key unit: 1/(2 s1), 1/(6 s2), 1/(12 s3)
+    int pad[3];
 };
 
 // The per-call job: user buffers and sizes (copied to the device each call so
@@ -61,7 +65,13 @@ struct Table {
     float4 *v1;
     uint32_t mask;         // capacity - 1 (capacity a power of two)
     uint32_t max_probe;    // an insert that probes this many taken slots reports overflow
+    uint4 *cv;             // compact values (16-bit storage modes), one 16-byte record per slot
 };
+
+// Lattice value storage of the slice (fr_storage): float32 planes, or 16-byte
+// records [W, sum b (y - p_v) (3), sum b n (3), 0] in bfloat16 / half, made
+// from the float32 sums once a build completes (p_v: the vertex's position).
+constexpr int kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2;
 
 // Table sizing.  A point creates at most 4 vertices, so 6 N slots can never
 // fill; but a lattice over a surface has far fewer vertices than 4 N (about
@@ -81,16 +91,24 @@ inline uint32_t table_probe_limit(uint32_t cap, bool safe) { return safe ? cap :
 // blocks [gs, gs + gb) build the lattice of iteration `build_it` into table
 // `build` (gb = 0: no build); blocks [gs + gb, gs + gb + gc) clear table
 // `clear` (gc = 0: none).  Any role may be empty.
+// Lattice tables in rotation: a build runs `lead` iterations ahead of the
+// step that reads it (1 with float32 storage; 2 with 16-bit storage, whose
+// records are converted one launch after the build completes), so up to
+// lead + 2 tables are live (cleared, stepped, converted, built).
+constexpr int kMaxTables = 4;
+
 struct IterLaunch {
     const RigidJob *job;
     IterParams *ip;
     int it, build_it, clear_it;  // clear_it: the build whose table is cleared
-    Table step, build, clear;
+    int conv_it;                 // the build whose table is converted
+    Table step, build, clear, conv;
     int *build_list;       // slots claimed by the build (count: ip[build_it].nvert)
     const int *clear_list; // slots to free (count: ip[clear_it].nvert)
+    const int *conv_list;  // slots to convert (count: ip[conv_it].nvert)
     float2 *partials;      // gs rows of kRigidVals (hi, lo) float pairs
     DeviceState *st;
-    int gs, gb, gc;
+    int gs, gv, gb, gc;    // blocks of the roles, in this order
     int check_done;        // roles return at once once st->done is set
 };
 
@@ -132,12 +150,13 @@ struct ArtState {
 struct ArtLaunch {
     const ArtJob *job;
     IterParams *ip;
-    int it, build_it, clear_it;
-    Table step, build, clear;
+    int it, build_it, clear_it, conv_it;
+    Table step, build, clear, conv;
     int *build_list;
     const int *clear_list;
+    const int *conv_list;
     ArtState *st;
-    int gs, gb, gc;
+    int gs, gv, gb, gc;
 };
 
 // One registration of a multi-registration launch (device-resident).
@@ -146,15 +165,16 @@ struct Slot {
     DeviceState *st;
     IterParams *ip;        // [iters] of this registration
     float2 *partials;      // >= step blocks per launch rows of kRigidVals pairs
-    Table tab[3];          // rotating lattice tables
-    int *list[3];          // slots claimed by each table's last build
+    Table tab[kMaxTables]; // rotating lattice tables
+    int *list[kMaxTables]; // slots claimed by each table's last build
 };
 
-enum { kRoleNone = 0, kRoleStep = 1, kRoleBuild = 2, kRoleClear = 3 };
+enum { kRoleNone = 0, kRoleStep = 1, kRoleBuild = 2, kRoleClear = 3, kRoleConvert = 4 };
 
 // A run of nblk consecutive blocks (from blk0) doing one role for one slot:
 // step of iteration `it` on table `tab`; build of iteration `it` into `tab`;
-// or clear of `tab`, whose claimed slots build `it` listed.
+// clear of `tab`, whose claimed slots build `it` listed; or conversion of
+// `tab` (build `it`) to 16-bit records.
 struct Seg {
     int slot, role, it, tab;
     int blk0, nblk;
@@ -162,16 +182,17 @@ struct Seg {
 
 // ---- launchers (kernels.cu) -------------------------------------------------
 void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
-                     const unsigned short *blockseg, int grid, int check_done, cudaStream_t s);
-void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s);
-void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s);
+                     const unsigned short *blockseg, int grid, int check_done, cudaStream_t s,
+                     int storage);
+void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s, int storage);
+void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s, int storage);
 int em_iter_blocks_per_sm(int pt2pl, int kahan);
 // Frees the slots listed by builds (list lists[i], count *counts[i]).
 void launch_clear_lists(const Table *tabs, int *const *lists, const int *const *counts, int n,
                         int grid, cudaStream_t s);
 void launch_blur_pass(Table in, Table out, int dir, int grid, const DeviceState *st, cudaStream_t s);
 void launch_estep_out(int pt2pl, const RigidJob *job, const IterParams *ip, Table t, float *out,
-                      DeviceState *st, int grid, cudaStream_t s);
+                      DeviceState *st, int grid, cudaStream_t s, int storage);
 
 // Lattice primitives.
 void launch_embed(const float4 *P, int n, float s1, float s2, float s3, int *keys, float *bary,

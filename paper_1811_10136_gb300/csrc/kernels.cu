@@ -15,6 +15,8 @@
 //                   the SE(3) exponential update T <- exp(dzeta^) T (Eq. 16).
 //   primitives      embed / build / splat / slice / vertex listing kernels of
 //                   the fr_lattice_* entry points.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -303,6 +305,45 @@ __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *
 // Roles of the fused EM-iteration kernel
 // ---------------------------------------------------------------------------
 
+// World position of the lattice point whose stored key coordinates are
+// z0..z2 (z3 = -(z0 + z1 + z2)), at the feature scales of ip: the elevation's
+// inverse, c_1 = (z0 - z1)/2, c_2 = (z0 + z1 - 2 z2)/6,
+// c_3 = (z0 + z1 + z2 - 3 z3)/12, p_{i-1} = c_i / s_i (the factors 1/(2 s1),
+// 1/(6 s2), 1/(12 s3) come with the iteration's parameters).  Conversion and
+// slice evaluate it alike: the p_v taken out of a record is the one put back.
+__device__ __forceinline__ float3 vertex_position(unsigned long long key, const IterParams &ip) {
+    const int z0 = unpack_coord(key, 0), z1 = unpack_coord(key, 1), z2 = unpack_coord(key, 2);
+    const int z3 = -(z0 + z1 + z2);
+    return make_float3((float)(z0 - z1) * ip.ws1, (float)(z0 + z1 - 2 * z2) * ip.ws2,
+                       (float)(z0 + z1 + z2 - 3 * z3) * ip.ws3);
+}
+
+template <int ST>
+__device__ __forceinline__ unsigned pack2(float a, float b) {
+    if (ST == kStoreBF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const unsigned *>(&h);
+    }
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const unsigned *>(&h);
+}
+
+template <int ST>
+__device__ __forceinline__ float2 unpack2(unsigned u) {
+    if (ST == kStoreBF16) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+    return __half22float2(*reinterpret_cast<const __half2 *>(&u));
+}
+
+// Compact record of a built vertex: [W, sum b (y - p_v), sum b n, 0] -- the
+// float32 sums re-centred on the vertex (values of magnitude ~sigma instead of
+// scene coordinates) and rounded to 16 bits.
+template <int ST>
+__device__ __forceinline__ uint4 compact_record(float4 a, float4 c, float3 p, float sc) {
+    return make_uint4(pack2<ST>(a.x * sc, (a.y - a.x * p.x) * sc),
+                      pack2<ST>((a.z - a.x * p.y) * sc, (a.w - a.x * p.z) * sc),
+                      pack2<ST>(c.x * sc, c.y * sc), pack2<ST>(c.z * sc, 0.0f));
+}
+
 // Build: Section 4.2 "Splat" of the observation with values [1, y] or
 // [1, y, n_y] (Eq. 11), fused with the lattice build (elevate, simplex, hash
 // insert, float4 atomic accumulation).  One thread per point per round.
@@ -313,7 +354,7 @@ __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *
 // round claims are appended to `list` (one atomic per block and round on the
 // build's vertex counter) so that the table can later be freed without
 // scanning it.
-template <bool PT2PL>
+template <bool PT2PL, int ST>
 __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, IterParams *ipp,
                                            Table t, int *list, DeviceState *st, int blk, int nblk) {
     constexpr int kCh = PT2PL ? 7 : 4;
@@ -424,6 +465,23 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
     }
 }
 
+// Convert: once a build is complete (an earlier launch), turn each listed
+// vertex's float32 sums into its 16-bit record (16-bit storage modes only).
+template <bool PT2PL, int ST>
+__device__ __forceinline__ void convert_role(Table t, const int *list, const IterParams *ipp, int blk,
+                                             int nblk) {
+    if constexpr (ST != kStoreF32) {
+        const IterParams ip = *ipp;
+        const int n = __ldcg(&ipp->nvert);
+        for (int e = blk * kBlock + threadIdx.x; e < n; e += nblk * kBlock) {
+            const int slot = __ldcg(list + e);
+            const float4 a = __ldcg(t.v0 + slot);
+            const float4 c = PT2PL ? __ldcg(t.v1 + slot) : make_float4(0.f, 0.f, 0.f, 0.f);
+            t.cv[slot] = compact_record<ST>(a, c, vertex_position(__ldcg(t.keys + slot), ip), ip.vscale);
+        }
+    }
+}
+
 // Clear: free the slots a build listed (keys to empty, values to zero).
 __device__ __forceinline__ void clear_role(Table t, const int *list, int n, int blk, int nblk) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -440,7 +498,7 @@ struct Sums {
     float m0, m1x, m1y, m1z, nx, ny, nz;
 };
 
-template <bool PT2PL>
+template <bool PT2PL, int ST>
 __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, float x2,
                                             const IterParams &ip, Sums &o, int &bad) {
     Simplex sx;
@@ -451,26 +509,60 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
     }
     int slot[kD];
     find4(t.keys, t.mask, sx, slot);
-    float4 a[kD], c[kD];
+    if constexpr (ST != kStoreF32) {
+        // One 16-byte record per vertex; positions restored in float32.
+        uint4 r[kD];
 #pragma unroll
-    for (int k = 0; k < kD; ++k) {
-        a[k] = slot[k] >= 0 ? __ldg(t.v0 + slot[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (PT2PL) c[k] = slot[k] >= 0 ? __ldg(t.v1 + slot[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+        for (int k = 0; k < kD; ++k) r[k] = slot[k] >= 0 ? __ldg(t.cv + slot[k]) : make_uint4(0, 0, 0, 0);
 #pragma unroll
-    for (int k = 0; k < kD; ++k) {
-        const float b = sx.b[k];
-        o.m0 += b * a[k].x;
-        o.m1x += b * a[k].y;
-        o.m1y += b * a[k].z;
-        o.m1z += b * a[k].w;
-        if (PT2PL) {
-            o.nx += b * c[k].x;
-            o.ny += b * c[k].y;
-            o.nz += b * c[k].z;
+        for (int k = 0; k < kD; ++k) {
+            if (slot[k] < 0) continue;
+            const float b = sx.b[k];
+            const float2 w_rx = unpack2<ST>(r[k].x), ry_rz = unpack2<ST>(r[k].y);
+            const float3 p = vertex_position(sx.key[k], ip);
+            const float bw = b * w_rx.x;
+            o.m0 += bw;
+            o.m1x += b * w_rx.y + bw * p.x;
+            o.m1y += b * ry_rz.x + bw * p.y;
+            o.m1z += b * ry_rz.y + bw * p.z;
+            if (PT2PL) {
+                const float2 nx_ny = unpack2<ST>(r[k].z), nz_0 = unpack2<ST>(r[k].w);
+                o.nx += b * nx_ny.x;
+                o.ny += b * nx_ny.y;
+                o.nz += b * nz_0.x;
+            }
         }
+        const float u = ip.inv_vscale;
+        o.m0 *= u;
+        o.m1x *= u;
+        o.m1y *= u;
+        o.m1z *= u;
+        o.nx *= u;
+        o.ny *= u;
+        o.nz *= u;
+        return true;
+    } else {
+        float4 a[kD], c[kD];
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            a[k] = slot[k] >= 0 ? __ldg(t.v0 + slot[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (PT2PL) c[k] = slot[k] >= 0 ? __ldg(t.v1 + slot[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            const float b = sx.b[k];
+            o.m0 += b * a[k].x;
+            o.m1x += b * a[k].y;
+            o.m1y += b * a[k].z;
+            o.m1z += b * a[k].w;
+            if (PT2PL) {
+                o.nx += b * c[k].x;
+                o.ny += b * c[k].y;
+                o.nz += b * c[k].z;
+            }
+        }
+        return true;
     }
-    return true;
 }
 
 // One model point's terms of the M step, handed to add(value index, value):
@@ -557,7 +649,7 @@ __device__ __forceinline__ void load_pose(const double *T, float *P) {
 // Eq. 6 / Eq. 9), outlier weight M0/(M0+c) and residuals (Eq. 7 / Eq. 10),
 // twist Jacobian, reduction of A and b (Eq. 17-18); the last block to finish
 // solves and updates the pose.
-template <bool PT2PL, bool KAHAN>
+template <bool PT2PL, bool KAHAN, int ST>
 __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams *ipp, const Table t,
                                           float2 *partials, DeviceState *st, int blk, int nblk) {
     __shared__ float P[12];
@@ -574,7 +666,7 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
         const float4 r = __ldg(X + i);
         const float x0 = apply_row(P, 0, r), x1 = apply_row(P, 1, r), x2 = apply_row(P, 2, r);
         Sums e;
-        if (!slice_point<PT2PL>(t, x0, x1, x2, ip, e, bad)) continue;
+        if (!slice_point<PT2PL, ST>(t, x0, x1, x2, ip, e, bad)) continue;
         point_terms<PT2PL>(x0, x1, x2, e, ip, renorm, [&](int v, float x) { acc.add(v, x); });
     }
     if (bad) atomicOr(&st->flags, bad);
@@ -594,18 +686,23 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
     if (threadIdx.x == 0) st->ticket = 0;
 }
 
-template <bool PT2PL, bool KAHAN>
+template <bool PT2PL, bool KAHAN, int ST>
 __global__ void __launch_bounds__(kBlock, 3) k_em_iter(IterLaunch L) {
     int b = blockIdx.x;
     if (b < L.gs) {
         if (L.check_done && L.st->done) return;
-        step_role<PT2PL, KAHAN>(L.job, L.ip + L.it, L.step, L.partials, L.st, b, L.gs);
+        step_role<PT2PL, KAHAN, ST>(L.job, L.ip + L.it, L.step, L.partials, L.st, b, L.gs);
         return;
     }
     b -= L.gs;
+    if (b < L.gv) {
+        convert_role<PT2PL, ST>(L.conv, L.conv_list, L.ip + L.conv_it, b, L.gv);
+        return;
+    }
+    b -= L.gv;
     if (b < L.gb) {
         if (L.check_done && L.st->done) return;
-        build_role<PT2PL>(L.job, L.ip + L.build_it, L.build, L.build_list, L.st, b, L.gb);
+        build_role<PT2PL, ST>(L.job, L.ip + L.build_it, L.build, L.build_list, L.st, b, L.gb);
         return;
     }
     b -= L.gb;
@@ -616,7 +713,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_em_iter(IterLaunch L) {
 // of one slot (registration) at that slot's own iteration.  Used by the
 // batched entry point (all slots in lockstep) and the serving loop (slots at
 // different iterations).
-template <bool PT2PL, bool KAHAN>
+template <bool PT2PL, bool KAHAN, int ST>
 __global__ void __launch_bounds__(kBlock, 3) k_em_multi(const Slot *__restrict__ slots,
                                                          const Seg *__restrict__ segs,
                                                          const unsigned short *__restrict__ blockseg,
@@ -628,12 +725,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_em_multi(const Slot *__restrict__
     const int b = blockIdx.x - sg.blk0;
     if (sg.role == kRoleStep) {
         if (check_done && st->done) return;
-        step_role<PT2PL, KAHAN>(sl.job, sl.ip + sg.it, sl.tab[sg.tab], sl.partials, st, b, sg.nblk);
+        step_role<PT2PL, KAHAN, ST>(sl.job, sl.ip + sg.it, sl.tab[sg.tab], sl.partials, st, b, sg.nblk);
     } else if (sg.role == kRoleBuild) {
         if (check_done && st->done) return;
-        build_role<PT2PL>(sl.job, sl.ip + sg.it, sl.tab[sg.tab], sl.list[sg.tab], st, b, sg.nblk);
+        build_role<PT2PL, ST>(sl.job, sl.ip + sg.it, sl.tab[sg.tab], sl.list[sg.tab], st, b, sg.nblk);
     } else if (sg.role == kRoleClear) {
         clear_role(sl.tab[sg.tab], sl.list[sg.tab], __ldcg(&sl.ip[sg.it].nvert), b, sg.nblk);
+    } else if (sg.role == kRoleConvert) {
+        convert_role<PT2PL, ST>(sl.tab[sg.tab], sl.list[sg.tab], sl.ip + sg.it, b, sg.nblk);
     }
 }
 
@@ -866,7 +965,7 @@ __device__ void art_finish(const ArtJob *job, ArtState *st, float stop_twist) {
 // reduction into shared memory, then float64 atomics per touched body.  Each
 // block takes a contiguous range of points (points sorted by body keep the
 // flushes rare).
-template <bool PT2PL>
+template <bool PT2PL, int ST>
 __device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
     __shared__ float Tb[kMaxBodies][12];
     __shared__ float sacc[kMaxBodies][kArtVals];
@@ -903,7 +1002,7 @@ __device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
         const float4 r = __ldg(job->base.X + i);
         const float x0 = apply_row(Tb[b], 0, r), x1 = apply_row(Tb[b], 1, r), x2 = apply_row(Tb[b], 2, r);
         Sums e;
-        if (!slice_point<PT2PL>(L.step, x0, x1, x2, ip, e, bad)) continue;
+        if (!slice_point<PT2PL, ST>(L.step, x0, x1, x2, ip, e, bad)) continue;
         point_terms<PT2PL>(x0, x1, x2, e, ip, renorm, [&](int v, float x) { acc[v] += x; });
     }
     const int lane = threadIdx.x & 31;
@@ -939,18 +1038,23 @@ __device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
     if (threadIdx.x == 0) st->ds.ticket = 0;
 }
 
-template <bool PT2PL>
+template <bool PT2PL, int ST>
 __global__ void __launch_bounds__(kBlock) k_art_iter(ArtLaunch L) {
     int b = blockIdx.x;
     if (b < L.gs) {
         if (L.st->ds.done) return;
-        art_step_role<PT2PL>(L, b, L.gs);
+        art_step_role<PT2PL, ST>(L, b, L.gs);
         return;
     }
     b -= L.gs;
+    if (b < L.gv) {
+        convert_role<PT2PL, ST>(L.conv, L.conv_list, L.ip + L.conv_it, b, L.gv);
+        return;
+    }
+    b -= L.gv;
     if (b < L.gb) {
         if (L.st->ds.done) return;
-        build_role<PT2PL>(&L.job->base, L.ip + L.build_it, L.build, L.build_list, &L.st->ds, b, L.gb);
+        build_role<PT2PL, ST>(&L.job->base, L.ip + L.build_it, L.build, L.build_list, &L.st->ds, b, L.gb);
         return;
     }
     b -= L.gb;
@@ -1003,7 +1107,7 @@ __global__ void k_blur_pass(Table in, Table out, int dir, const DeviceState *st)
 }
 
 // E-step sums at T x for every model point (the fr_estep entry point).
-template <bool PT2PL>
+template <bool PT2PL, int ST>
 __global__ void __launch_bounds__(kBlock) k_estep_out(const RigidJob *__restrict__ job,
                                                        const IterParams *__restrict__ ipa, Table t,
                                                        float *out, DeviceState *st) {
@@ -1017,7 +1121,7 @@ __global__ void __launch_bounds__(kBlock) k_estep_out(const RigidJob *__restrict
         const float4 r = __ldg(job->X + i);
         const float x0 = apply_row(P, 0, r), x1 = apply_row(P, 1, r), x2 = apply_row(P, 2, r);
         Sums e;
-        slice_point<PT2PL>(t, x0, x1, x2, ip, e, bad);
+        slice_point<PT2PL, ST>(t, x0, x1, x2, ip, e, bad);
         float *o = out + (size_t)i * vd;
         o[0] = e.m0; o[1] = e.m1x; o[2] = e.m1y; o[3] = e.m1z;
         if (PT2PL) { o[4] = e.nx; o[5] = e.ny; o[6] = e.nz; }
@@ -1165,41 +1269,53 @@ int grid_for(long long n, int cap_blocks) {
 // Launchers
 // ---------------------------------------------------------------------------
 
-void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s) {
-    const int grid = a.gs + a.gb + a.gc;
+// Instantiated variants: {pt2pt, pt2pl} x (float32 with or without Kahan sums,
+// bfloat16, half); Kahan sums are float32-storage only.
+#define FR_VARIANTS(CALL)                                   \
+    do {                                                    \
+        if (pt2pl) {                                        \
+            if (storage == kStoreBF16) CALL(true, false, 1);      \
+            else if (storage == kStoreF16) CALL(true, false, 2);  \
+            else if (kahan) CALL(true, true, 0);                  \
+            else CALL(true, false, 0);                            \
+        } else {                                            \
+            if (storage == kStoreBF16) CALL(false, false, 1);     \
+            else if (storage == kStoreF16) CALL(false, false, 2); \
+            else if (kahan) CALL(false, true, 0);                 \
+            else CALL(false, false, 0);                           \
+        }                                                   \
+    } while (0)
+
+void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s, int storage) {
+    const int grid = a.gs + a.gv + a.gb + a.gc;
     if (grid <= 0) return;
-    if (pt2pl) {
-        if (kahan) k_em_iter<true, true><<<grid, kBlock, 0, s>>>(a);
-        else k_em_iter<true, false><<<grid, kBlock, 0, s>>>(a);
-    } else {
-        if (kahan) k_em_iter<false, true><<<grid, kBlock, 0, s>>>(a);
-        else k_em_iter<false, false><<<grid, kBlock, 0, s>>>(a);
-    }
+#define FR_CALL(P, K, S) k_em_iter<P, K, S><<<grid, kBlock, 0, s>>>(a)
+    FR_VARIANTS(FR_CALL);
+#undef FR_CALL
 }
 
 void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
-                     const unsigned short *blockseg, int grid, int check_done, cudaStream_t s) {
+                     const unsigned short *blockseg, int grid, int check_done, cudaStream_t s,
+                     int storage) {
     if (grid <= 0) return;
-    if (pt2pl) {
-        if (kahan) k_em_multi<true, true><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
-        else k_em_multi<true, false><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
-    } else {
-        if (kahan) k_em_multi<false, true><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
-        else k_em_multi<false, false><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done);
-    }
+#define FR_CALL(P, K, S) k_em_multi<P, K, S><<<grid, kBlock, 0, s>>>(slots, segs, blockseg, check_done)
+    FR_VARIANTS(FR_CALL);
+#undef FR_CALL
 }
 
-void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s) {
-    const int grid = a.gs + a.gb + a.gc;
+void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s, int storage) {
+    const int grid = a.gs + a.gv + a.gb + a.gc;
     if (grid <= 0) return;
-    if (pt2pl) k_art_iter<true><<<grid, kBlock, 0, s>>>(a);
-    else k_art_iter<false><<<grid, kBlock, 0, s>>>(a);
+    const int kahan = 0;
+#define FR_CALL(P, K, S) k_art_iter<P, S><<<grid, kBlock, 0, s>>>(a)
+    FR_VARIANTS(FR_CALL);
+#undef FR_CALL
 }
 
 int em_iter_blocks_per_sm(int pt2pl, int kahan) {
     int n = 0;
-    const void *f = pt2pl ? (kahan ? (const void *)k_em_iter<true, true> : (const void *)k_em_iter<true, false>)
-                          : (kahan ? (const void *)k_em_iter<false, true> : (const void *)k_em_iter<false, false>);
+    const void *f = pt2pl ? (kahan ? (const void *)k_em_iter<true, true, 0> : (const void *)k_em_iter<true, false, 0>)
+                          : (kahan ? (const void *)k_em_iter<false, true, 0> : (const void *)k_em_iter<false, false, 0>);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kBlock, 0);
     return n > 0 ? n : 1;
 }
@@ -1222,11 +1338,11 @@ void launch_blur_pass(Table in, Table out, int dir, int grid, const DeviceState 
 }
 
 void launch_estep_out(int pt2pl, const RigidJob *job, const IterParams *ip, Table t, float *out,
-                      DeviceState *st, int grid, cudaStream_t s) {
-    if (pt2pl)
-        k_estep_out<true><<<grid, kBlock, 0, s>>>(job, ip, t, out, st);
-    else
-        k_estep_out<false><<<grid, kBlock, 0, s>>>(job, ip, t, out, st);
+                      DeviceState *st, int grid, cudaStream_t s, int storage) {
+    const int kahan = 0;
+#define FR_CALL(P, K, S) k_estep_out<P, S><<<grid, kBlock, 0, s>>>(job, ip, t, out, st)
+    FR_VARIANTS(FR_CALL);
+#undef FR_CALL
 }
 
 void launch_embed(const float4 *P, int n, float s1, float s2, float s3, int *keys, float *bary,
