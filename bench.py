@@ -38,6 +38,7 @@ METRIC = "EM iters/s at 76.8k pts; batched regs/s + p99 latency vs plain, <=0.1 
 UNIT = "EM iters/s"
 ITERS = 20
 SIGMA0, SIGMA1, W_OUT = 0.04, 0.01, 0.1
+ART_ITERS, ART_SIGMA = 15, 0.01      # articulated workload: 15 EM iterations at sigma 1 cm
 
 
 def parse():
@@ -51,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the 16-bit storage lines")
+    ap.add_argument("--no-articulated", action="store_true", help="skip the articulated line")
     return ap.parse_args()
 
 
@@ -329,6 +331,31 @@ def run_ours(args):
                 "max_rot_err_deg_vs_truth": round(max(synth.rotation_angle_deg(T, p.T_gt)
                                                       for (T, _, _), p in zip(res, pairs)), 4)}
 
+    # ---- articulated registration (Algorithm 1): 16 links, 26 DOF, 30k points
+    articulated = None
+    if not args.no_articulated:
+        ap = synth.articulated_pair(args.seed)
+        aX, aY = dev(ap.Xref), dev(ap.Y)
+        abody = torch.from_numpy(ap.body.astype(np.int32)).cuda()
+        articulated = {"workload": "kintree_capsules_16_links_26dof", "M": int(ap.Xref.shape[0]),
+                       "N": int(ap.Y.shape[0]), "em_iters": ART_ITERS, "sigma": ART_SIGMA}
+        res32 = None
+        for name, code in (("f32", fr.FR_FP32), ("bf16", fr.FR_BF16)):
+            aopts = dict(iters=ART_ITERS, sigma_start=ART_SIGMA, sigma_end=ART_SIGMA, w=W_OUT, storage=code)
+            run = lambda: ctx.register_articulated(aX, abody, ap.tree, aY, None, **aopts)
+            for _ in range(max(1, args.warmup)):
+                run()
+            ms, res = timed_steps(run, args.steps)
+            R, q, rep = res
+            entry = {"value": round(ART_ITERS * args.steps / (sum(ms) / 1000.0), 1), "unit": UNIT,
+                     "ms_per_registration": round(statistics.mean(ms), 4),
+                     "max_joint_err_deg_vs_truth": round(float(np.degrees(np.abs(q - ap.q_gt).max())), 4)}
+            if res32 is None:
+                res32 = q
+            else:
+                entry["max_joint_diff_deg_vs_f32"] = round(float(np.degrees(np.abs(q - res32).max())), 5)
+            articulated[name] = entry
+
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
     if not args.no_e2e:
@@ -374,6 +401,7 @@ def run_ours(args):
                          "max_rot_diff_deg_batched_vs_plain": round(mix_rot, 6)},
             "roofline": roofline,
             "precision": precision,
+            "articulated": articulated,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
