@@ -310,6 +310,72 @@ FR_API fr_status fr_register_rigid_batch(fr_ctx *ctx, fr_batch_item *items, int 
 FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items, int n_items,
                                               const fr_options *opt, fr_report *reports);
 
+/* ---- serving: continuous batching -------------------------------------------
+ * A server registers a stream of independent pairs (the rigid EM of
+ * fr_register_rigid, Sections 3.1, 4, 5) with continuous batching: a worker
+ * thread launches one batched EM kernel per tick over every live request,
+ * each at its own iteration (a request's first tick builds its first
+ * lattice; each later tick runs its next iteration; a last tick frees its
+ * tables), admitting queued requests between ticks while their memory fits.
+ * The paper has no counterpart; it runs one registration at a time.
+ *
+ * Memory: fr_server_create reserves `device_mem_budget` bytes on the
+ * context's device once -- half for lattice tables (hash slots kept empty
+ * between requests), half for per-request records and copied clouds -- and
+ * admits a request only when its tables and records fit (first come, first
+ * served).  A request that could never fit is refused at submission
+ * (FR_ENOMEM).  At most `max_live` requests run at once (1..4096).
+ *
+ * The server has its own CUDA stream and thread; the context must outlive
+ * it and may be used for other calls meanwhile.  Options (residual, iters,
+ * kahan, renormalize_normals) are fixed per server; storage must be FR_FP32
+ * and blur 0 (FR_ENOTSUPPORTED otherwise); stop_twist is honoured. */
+typedef struct fr_server fr_server;
+
+/* One request.  Clouds are N x 4 / M x 4 float rows (16-byte aligned).
+ * host == 0: device pointers, borrowed -- they must stay valid and unchanged
+ * until the request completes.  host == 1: host pointers, copied to the
+ * device when the request is admitted -- they too must stay valid until the
+ * request completes (or until fr_server_destroy returns). */
+typedef struct {
+    const float *X;
+    int64_t M;
+    const float *Y;
+    const float *Yn;            /* normals, FR_PT2PL only */
+    int64_t N;
+    float sigma_start, sigma_end, w;
+    double T[16];               /* initial pose, row-major */
+    int32_t host;
+} fr_request;
+
+/* What fr_server_poll reports for a completed request. */
+typedef struct {
+    fr_status status;           /* FR_OK, or the request's own error */
+    double T[16];               /* final pose (initial pose on error) */
+    fr_report report;
+    int64_t submit_ns, admit_ns, complete_ns;  /* steady-clock timestamps */
+} fr_result;
+
+FR_API fr_status fr_server_create(fr_ctx *ctx, size_t device_mem_budget, int max_live,
+                                  const fr_options *opt, fr_server **out);
+/* Queue a request; *ticket identifies it.  FR_EINVAL for bad arguments,
+ * FR_ENOMEM if it cannot fit the server's budget even alone. */
+FR_API fr_status fr_server_submit(fr_server *srv, const fr_request *req, uint64_t *ticket);
+/* *done = 1 and *out filled (nullable) once the request has completed;
+ * *done = 0 otherwise.  A completed ticket stays readable until
+ * fr_server_release.  FR_EINVAL for an unknown ticket. */
+FR_API fr_status fr_server_poll(fr_server *srv, uint64_t ticket, int *done, fr_result *out);
+/* Block until the request completes or timeout_ms passes (< 0: no limit);
+ * FR_ETIMEOUT on timeout. */
+FR_API fr_status fr_server_wait(fr_server *srv, uint64_t ticket, int64_t timeout_ms, fr_result *out);
+/* Forget a completed ticket. */
+FR_API fr_status fr_server_release(fr_server *srv, uint64_t ticket);
+/* Counters: ticks launched, requests completed, kernels launched. */
+FR_API fr_status fr_server_stats(const fr_server *srv, int64_t *ticks, int64_t *completed,
+                                 int64_t *kernel_launches);
+/* Finish every queued and live request, stop the worker, free the memory. */
+FR_API fr_status fr_server_destroy(fr_server *srv);
+
 /* ---- E step without allocation ---------------------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
  * cannot call cudaMalloc -- a host framework whose allocator has reserved

@@ -36,6 +36,8 @@ EXPORTED = [
     "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
     "fr_ctx_transfer_bytes", "fr_estep_noalloc", "fr_register_rigid_batch",
     "fr_register_rigid_batch_host", "fr_register_articulated", "fr_estep_storage",
+    "fr_server_create", "fr_server_submit", "fr_server_poll", "fr_server_wait", "fr_server_release",
+    "fr_server_stats", "fr_server_destroy",
 ]
 FR_NOALLOC_MAX_OBS = 8192
 KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert")
@@ -61,6 +63,18 @@ class fr_report(ctypes.Structure):
                 ("last_cost", ctypes.c_double), ("last_twist_norm", ctypes.c_double),
                 ("lattice_vertices", ctypes.c_int64), ("lattice_builds", ctypes.c_int32),
                 ("lattice_vertices_sum", ctypes.c_int64)]
+
+
+class fr_request(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("M", ctypes.c_int64), ("Y", ctypes.c_void_p),
+                ("Yn", ctypes.c_void_p), ("N", ctypes.c_int64), ("sigma_start", ctypes.c_float),
+                ("sigma_end", ctypes.c_float), ("w", ctypes.c_float), ("T", ctypes.c_double * 16),
+                ("host", ctypes.c_int32)]
+
+
+class fr_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("T", ctypes.c_double * 16), ("report", fr_report),
+                ("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64), ("complete_ns", ctypes.c_int64)]
 
 
 class fr_kintree(ctypes.Structure):
@@ -147,6 +161,14 @@ def load(build_if_missing: bool = True):
     L.fr_register_articulated.argtypes = [_vp, _vp, _vp, _i64, ctypes.POINTER(fr_kintree), _vp, _vp, _i64,
                                           ctypes.POINTER(fr_options), _f64p, _f64p, ctypes.POINTER(fr_report)]
     L.fr_estep_noalloc.argtypes = [_vp, _i64, _vp, _vp, _i64, ctypes.c_float, _f64p, _vp, _vp]
+    L.fr_server_create.argtypes = [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(fr_options),
+                                   ctypes.POINTER(_vp)]
+    L.fr_server_submit.argtypes = [_vp, ctypes.POINTER(fr_request), ctypes.POINTER(ctypes.c_uint64)]
+    L.fr_server_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(fr_result)]
+    L.fr_server_wait.argtypes = [_vp, ctypes.c_uint64, _i64, ctypes.POINTER(fr_result)]
+    L.fr_server_release.argtypes = [_vp, ctypes.c_uint64]
+    L.fr_server_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    L.fr_server_destroy.argtypes = [_vp]
     for name in EXPORTED:  # every entry point must resolve (ctypes restype defaults to int)
         getattr(L, name)
     _lib = L
@@ -476,3 +498,112 @@ class Lattice:
         self._ctx._check(load().fr_lattice_vertices(self._ctx._h, self._h, keys.data_ptr(), vals.data_ptr(),
                                                     ctypes.byref(nv)), "fr_lattice_vertices")
         return keys[: nv.value], vals[: nv.value, :vd]
+
+
+@dataclass
+class ServeResult:
+    status: int
+    T: np.ndarray
+    report: Report
+    submit_ns: int
+    admit_ns: int
+    complete_ns: int
+
+    @property
+    def latency_ms(self) -> float:
+        return (self.complete_ns - self.submit_ns) * 1e-6
+
+
+class Server:
+    """fr_server: continuous batching of rigid registrations on ctx's device.
+
+    submit() borrows the given clouds (CUDA tensors, or host float32 arrays /
+    tensors with host=True) until the request completes; this object keeps
+    them alive until result() / wait() has returned the request."""
+
+    def __init__(self, ctx: "Context", budget_bytes: int = 1 << 30, max_live: int = 256, **opts):
+        L = load()
+        self.ctx = ctx
+        o = options(**opts)
+        self.pt2pl = o.residual == FR_PT2PL
+        h = _vp()
+        st = L.fr_server_create(ctx._h, int(budget_bytes), int(max_live), ctypes.byref(o), ctypes.byref(h))
+        ctx._check(st, "fr_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, X, Y, Yn=None, sigma_start=0.02, sigma_end=None, w=0.1, T0=None, host=False) -> int:
+        L = load()
+        r = fr_request()
+        if host:
+            arrs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None for a in (X, Y, Yn)]
+            for a, name in zip(arrs, ("X", "Y", "Yn")):
+                if a is not None and (a.ndim != 2 or a.shape[1] != 4):
+                    raise ValueError(f"{name} must be (n, 4) float32")
+            ptr = lambda a: a.ctypes.data if a is not None else None
+            r.X, r.Y, r.Yn = ptr(arrs[0]), ptr(arrs[1]), ptr(arrs[2])
+            keep = arrs
+        else:
+            r.X, r.Y = _dev_ptr(X, "X"), _dev_ptr(Y, "Y")
+            r.Yn = _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None
+            keep = (X, Y, Yn)
+        r.M, r.N = X.shape[0], Y.shape[0]
+        r.sigma_start = float(sigma_start)
+        r.sigma_end = float(sigma_start if sigma_end is None else sigma_end)
+        r.w = float(w)
+        T = _pose(T0)
+        for i in range(16):
+            r.T[i] = T.flat[i]
+        r.host = 1 if host else 0
+        t = ctypes.c_uint64()
+        st = L.fr_server_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        self.ctx._check(st, "fr_server_submit")
+        self._keep[t.value] = keep
+        return t.value
+
+    def _take(self, ticket, res):
+        L = load()
+        L.fr_server_release(self._h, ticket)
+        self._keep.pop(ticket, None)
+        return ServeResult(res.status, np.array(res.T[:]).reshape(4, 4), _report(res.report),
+                           res.submit_ns, res.admit_ns, res.complete_ns)
+
+    def poll(self, ticket):
+        """The ServeResult once complete (the ticket is then released), else None."""
+        L = load()
+        done = ctypes.c_int()
+        res = fr_result()
+        st = L.fr_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(res))
+        self.ctx._check(st, "fr_server_poll")
+        return self._take(ticket, res) if done.value else None
+
+    def wait(self, ticket, timeout_ms: int = -1) -> ServeResult:
+        L = load()
+        res = fr_result()
+        st = L.fr_server_wait(self._h, ticket, int(timeout_ms), ctypes.byref(res))
+        self.ctx._check(st, "fr_server_wait")
+        return self._take(ticket, res)
+
+    def stats(self):
+        L = load()
+        a, b, c = _i64(), _i64(), _i64()
+        L.fr_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return {"ticks": a.value, "completed": b.value, "kernel_launches": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fr_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
