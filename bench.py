@@ -39,6 +39,8 @@ UNIT = "EM iters/s"
 ITERS = 20
 SIGMA0, SIGMA1, W_OUT = 0.04, 0.01, 0.1
 ART_ITERS, ART_SIGMA = 15, 0.01      # articulated workload: 15 EM iterations at sigma 1 cm
+SERVE_RATE = 2000.0                   # serving stream: Poisson arrivals per second
+SERVE_BUDGET = 8 << 30                # server device memory (bytes)
 
 
 def parse():
@@ -53,6 +55,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the 16-bit storage lines")
     ap.add_argument("--no-articulated", action="store_true", help="skip the articulated line")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-pool", type=int, default=32, help="distinct rendered frames behind the stream")
     return ap.parse_args()
 
 
@@ -85,6 +90,105 @@ def workload_config(frames, pairs):
 def make_pairs(seed, n):
     from paper_1811_10136_gb300 import synth
     return [synth.depth_frame_pair(seed + i) for i in range(n)]
+
+
+def serving_requests(seed, n_requests, pool_size):
+    """The serving stream: Poisson arrivals, sizes log-uniform in [1k, 300k]
+    points (frames rendered like the 320x240 workload at 4:3, W*H ~ n/0.95,
+    focal length scaled with W), sigma uniform in {0.01, 0.02, 0.04} (fixed per
+    request), 20 iterations.  Rendering 4096 distinct frames would take minutes,
+    so requests draw their clouds from a pool of pool_size rendered pairs whose
+    sizes follow the same distribution; arrival times, sigmas and the pool
+    entry are drawn per request."""
+    import numpy as np
+    from paper_1811_10136_gb300 import synth
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(pool_size):
+        n = float(np.exp(rng.uniform(np.log(1000.0), np.log(300000.0))))
+        W = max(8, int(round(np.sqrt(n / 0.95 * 4.0 / 3.0))))
+        H = max(6, int(round(W * 3 / 4)))
+        pool.append(synth.depth_frame_pair(seed + 50_000 + i, W=W, H=H, fx=300.0 * W / 320, fy=300.0 * W / 320))
+    gaps = rng.exponential(1.0 / SERVE_RATE, n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    which = rng.integers(0, pool_size, n_requests)
+    sigmas = rng.choice(np.array([0.01, 0.02, 0.04], np.float32), n_requests)
+    return pool, arrivals, which, sigmas
+
+
+def run_serving(ctx, args):
+    """Open-loop stream through fr_server (continuous batching) and, on the
+    same arrivals, through the plain path (fr_register_rigid, one request at
+    a time, first come first served).  Latency = completion - arrival."""
+    import numpy as np
+    import torch
+    import paper_1811_10136_gb300 as fr
+    pool, arrivals, which, sigmas = serving_requests(args.seed + 11, args.serve_requests, args.serve_pool)
+    dpool = [(torch.from_numpy(p.X).cuda(), torch.from_numpy(p.Y).cuda(), torch.from_numpy(p.Yn).cuda())
+             for p in pool]
+    n = len(arrivals)
+    opts = dict(residual=fr.FR_PT2PL, iters=ITERS)
+
+    def spin_until(t_ns):
+        while time.monotonic_ns() < t_ns:
+            pass
+
+    def percentiles(lat):
+        lat = np.sort(np.asarray(lat))
+        return (float(np.percentile(lat, 50)), float(np.percentile(lat, 99)))
+
+    out = {"workload": "poisson_stream_1k_300k_points", "requests": n, "arrival_rate_per_s": SERVE_RATE,
+           "pool_frames": len(pool), "em_iters": ITERS, "sigma": "one of 0.01/0.02/0.04 per request, fixed",
+           "sizes_mean_points": int(np.mean([pool[k].Y.shape[0] for k in which]))}
+    with fr.Server(ctx, budget_bytes=SERVE_BUDGET, max_live=1024, **opts) as srv:
+        # warm-up: one of each pool frame
+        for t in [srv.submit(*dpool[i], sigma_start=0.02, w=W_OUT) for i in range(len(pool))]:
+            srv.wait(t)
+        st0 = srv.stats()
+        t0 = time.monotonic_ns() + 2_000_000
+        tickets = []
+        for k in range(n):
+            spin_until(t0 + int(arrivals[k] * 1e9))
+            X, Y, Yn = dpool[which[k]]
+            tickets.append(srv.submit(X, Y, Yn, sigma_start=float(sigmas[k]), w=W_OUT))
+        res = [srv.wait(t) for t in tickets]
+        st1 = srv.stats()
+        lat = [(r.complete_ns - (t0 + int(a * 1e9))) * 1e-6 for r, a in zip(res, arrivals)]
+        span = (max(r.complete_ns for r in res) - t0) * 1e-9
+        p50, p99 = percentiles(lat)
+        out.update({"regs_per_s": round(n / span, 1), "latency_ms_p50": round(p50, 3),
+                    "latency_ms_p99": round(p99, 3),
+                    "ticks": st1["ticks"] - st0["ticks"], "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+                    "failed": sum(1 for r in res if r.status != 0)})
+        # saturated throughput: every request submitted at once
+        t1 = time.monotonic_ns()
+        tk = [srv.submit(*dpool[which[k]], sigma_start=float(sigmas[k]), w=W_OUT) for k in range(n)]
+        sat = [srv.wait(t) for t in tk]
+        out["saturated_regs_per_s"] = round(n / ((max(r.complete_ns for r in sat) - t1) * 1e-9), 1)
+    # the plain path on the same arrivals
+    plain_T = []
+    lat_p = []
+    t0 = time.monotonic_ns() + 2_000_000
+    for k in range(n):
+        a = t0 + int(arrivals[k] * 1e9)
+        spin_until(a)
+        X, Y, Yn = dpool[which[k]]
+        T, _ = ctx.register_rigid(X, Y, Yn, sigma_start=float(sigmas[k]), sigma_end=float(sigmas[k]),
+                                  w=W_OUT, **opts)
+        lat_p.append((time.monotonic_ns() - a) * 1e-6)
+        plain_T.append(T)
+    span_p = (time.monotonic_ns() - t0) * 1e-9
+    q50, q99 = percentiles(lat_p)
+    out["plain"] = {"regs_per_s": round(n / span_p, 1), "latency_ms_p50": round(q50, 3),
+                    "latency_ms_p99": round(q99, 3),
+                    "note": "fr_register_rigid per request, first come first served, same arrivals"}
+    out["max_rot_diff_deg_vs_plain"] = round(max(synth_rot(r.T, T) for r, T in zip(res, plain_T)), 6)
+    return out
+
+
+def synth_rot(A, B):
+    from paper_1811_10136_gb300 import synth
+    return synth.rotation_angle_deg(A, B)
 
 
 # ---------------------------------------------------------------------------
@@ -356,6 +460,9 @@ def run_ours(args):
                 entry["max_joint_diff_deg_vs_f32"] = round(float(np.degrees(np.abs(q - res32).max())), 5)
             articulated[name] = entry
 
+    # ---- serving: Poisson stream through fr_server vs the plain path ---------
+    serving = None if args.no_serving else run_serving(ctx, args)
+
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
     if not args.no_e2e:
@@ -402,6 +509,7 @@ def run_ours(args):
             "roofline": roofline,
             "precision": precision,
             "articulated": articulated,
+            "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -162,6 +162,11 @@ namespace {
 //   annealed:     build(0) -> [step(k) | build(k+1) | clear(k-1)] for each k
 //                 -> clear all three tables
 // with 4 blur passes after every build when blur is on.
+// Instantiated EM-loop graphs kept per context (least recently used out): one
+// per distinct shape (sizes, sigma schedule kind, table size), enough for a
+// stream of ragged requests to stop re-instantiating.
+constexpr size_t kGraphCache = 64;
+
 struct Plan {
     int iters, residual, blur, kahan, profile, annealed, storage;
     int gs, gv, gb, gc, g_blur, g_final;  // block counts of the roles
@@ -330,7 +335,7 @@ fr_status run_plan(fr_ctx *ctx, const Plan &p, bool use_graph) {
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         FR_CUDA(ctx, e);
-        if (ctx->graphs.size() >= 8) {
+        if (ctx->graphs.size() >= kGraphCache) {
             size_t old = 0;
             for (size_t i = 1; i < ctx->graphs.size(); ++i)
                 if (ctx->graphs[i].last_use < ctx->graphs[old].last_use) old = i;

@@ -74,17 +74,19 @@ struct Table {
 constexpr int kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2;
 
 // Table sizing.  A point creates at most 4 vertices, so 6 N slots can never
-// fill; but a lattice over a surface has far fewer vertices than 4 N (about
-// 0.05 N to 0.4 N for depth frames), and a table sized to match keeps its
-// working set in L2.  The compact size is tried first with a bounded probe
-// length; an overflow reruns the registration at the safe size.
+// fill; but a lattice over a surface usually has far fewer vertices than 4 N
+// (0.05 N to 0.5 N for dense depth frames, up to ~1.5 N for sparse ones at a
+// small sigma), and a table sized to match keeps its working set small.  The
+// compact size (3 N, so at most half full up to 1.5 N vertices) is tried
+// first with inserts bounded to 128 probes -- which also bounds every lookup,
+// present or absent; an overflow reruns the registration at the safe size.
 inline uint32_t table_slots(long long n_points, bool safe) {
-    const long long want = safe ? 6 * n_points : (3 * n_points) / 2;
+    const long long want = safe ? 6 * n_points : 3 * n_points;
     uint32_t c = 1024;
     while ((long long)c < want && c < (1u << 30)) c <<= 1;
     return c;
 }
-inline uint32_t table_probe_limit(uint32_t cap, bool safe) { return safe ? cap : (cap < 512 ? cap : 512); }
+inline uint32_t table_probe_limit(uint32_t cap, bool safe) { return safe ? cap : (cap < 128 ? cap : 128); }
 
 // One fused EM-iteration launch: blocks [0, gs) run the step of iteration
 // `it` on table `step` (slice, residuals, reduction, last-block solve);

@@ -100,6 +100,8 @@ struct Request {
     size_t byte_need = 0;
     size_t o_job = 0, o_state = 0, o_ip = 0, o_part = 0, o_list = 0, o_X = 0, o_Y = 0, o_Yn = 0;
     fr_result res{};
+    bool released = false;   // the client forgot the ticket: delete once retired
+    bool retired = false;    // memory back in the arenas (or never taken)
 };
 
 struct Tick {
@@ -208,6 +210,7 @@ struct fr_server {
         r.byte_order = bo;
         r.slot = free_slots.back();
         free_slots.pop_back();
+        r.retired = false;
         r.stage = 0;
         r.state = RState::Live;
         r.res.admit_ns = steady_ns();
@@ -221,6 +224,7 @@ struct fr_server {
         free_slots.push_back(r.slot);
         r.slot = -1;
         r.byte_order = -1;
+        r.retired = true;
     }
     // Descriptors of a newly admitted request, and its copied clouds.
     void upload(Request &r) {
@@ -399,6 +403,10 @@ struct fr_server {
         for (Request *rp : tk.retire) {
             Request &r = *rp;
             release_memory(r);
+            if (r.released) {  // result already taken and the ticket forgotten
+                delete rp;
+                continue;
+            }
             if (r.res.status == FR_ECAPACITY && !r.safe && r.state != RState::Done) {
                 // the compact table overflowed: rerun from the initial pose at the safe size
                 r.safe = true;
@@ -420,23 +428,32 @@ struct fr_server {
         if (!tk.results.empty()) cv_done.notify_all();
     }
 
+    // A CUDA error: the server stops serving.  Every unfinished request
+    // completes with the error; memory is not reused again.
     void fail_all(fr_status st) {
         failed = st;
-        auto done = [&](Request *r) {
-            if (r->state == RState::Done) return;
-            r->res.status = st;
-            for (int i = 0; i < 16; ++i) r->res.T[i] = r->req.T[i];
-            r->res.complete_ns = steady_ns();
-            r->state = RState::Done;
-        };
-        for (Request *r : pending) done(r);
-        for (Request *r : live) done(r);
+        cudaStreamSynchronize(stream);
+        cudaGetLastError();
+        std::set<Request *> all(pending.begin(), pending.end());
+        all.insert(live.begin(), live.end());
         for (Tick &t : inflight) {
-            for (Request *r : t.results) done(r);
-            for (Request *r : t.retire) done(r);
+            all.insert(t.results.begin(), t.results.end());
+            all.insert(t.retire.begin(), t.retire.end());
+            event_pool.push_back(t.ev);
         }
+        inflight.clear();
         pending.clear();
         live.clear();
+        for (Request *r : all) {
+            if (r->state != RState::Done) {
+                r->res.status = st;
+                for (int i = 0; i < 16; ++i) r->res.T[i] = r->req.T[i];
+                r->res.complete_ns = steady_ns();
+                r->state = RState::Done;
+            }
+            r->retired = true;
+            if (r->released) delete r;
+        }
         cv_done.notify_all();
     }
 
@@ -458,9 +475,7 @@ struct fr_server {
                 }
                 if (q != cudaSuccess) {
                     failed_msg = cudaGetErrorString(q);
-                    cudaGetLastError();
                     fail_all(FR_ECUDA);
-                    inflight.clear();
                     break;
                 }
                 finish_tick(inflight.front());
@@ -636,8 +651,12 @@ FR_API fr_status fr_server_release(fr_server *s, uint64_t ticket) {
     auto it = s->table.find(ticket);
     if (it == s->table.end() || it->second->state != RState::Done)
         return s->ctx->fail(FR_EINVAL, "ticket %llu is unknown or not complete", (unsigned long long)ticket);
-    delete it->second;
+    Request *r = it->second;
     s->table.erase(it);
+    if (r->retired)
+        delete r;
+    else
+        r->released = true;  // still clearing its tables: the worker deletes it when retired
     return FR_OK;
 }
 

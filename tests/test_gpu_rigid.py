@@ -180,17 +180,18 @@ def test_invalid_arguments(ctx):
 
 
 def test_compact_table_overflow_reruns_at_safe_size(ctx, orc):
-    # Scattered points at a small sigma create ~4 vertices each, more than the
-    # compact table (1.5 N slots) holds: the registration must transparently
+    # 5,000 points scattered ~11 cm apart at sigma 1 cm: each creates its own 4
+    # vertices, 20,000 in all, more than the compact table's 16,384 slots
+    # (3 N rounded up to a power of two): the registration must transparently
     # rerun with the safe size and still match the oracle.
     rng = np.random.default_rng(77)
-    X = np.zeros((3000, 4), np.float32)
-    X[:, :3] = rng.uniform(-1, 1, size=(3000, 3))
+    X = np.zeros((5000, 4), np.float32)
+    X[:, :3] = rng.uniform(-1, 1, size=(5000, 3))
     T = synth.make_T(synth.random_rotation(rng, 0.002), [0.001, 0.0, -0.001])
     Y = np.zeros_like(X)
     Y[:, :3] = synth.apply_T(T, X)
     p = synth.RigidPair(X, Y, T)
     Tg, rg, To, ro = run_both(ctx, orc, p, False, iters=3, s0=0.01)
-    assert rg.lattice_vertices > 1.5 * 3000          # the compact table could not hold it
+    assert rg.lattice_vertices > 16384               # the compact table could not hold it
     dr, dt = pose_diff(Tg, To)
     assert dr < ROT_TOL and dt < TRANS_TOL

@@ -75,11 +75,12 @@ def test_requests_equal_single_registrations(ctx, pairs, host):
 
 
 def test_small_budget_queues_requests(ctx, pairs):
-    # 64 MiB: the 320x240 request's three tables alone take most of the table
-    # arena, so requests wait for memory and are admitted as others finish.
+    # 128 MiB: the 320x240 request's three tables alone take 3/4 of the table
+    # arena (2^20 slots), so requests wait for memory and are admitted as
+    # others finish.
     import paper_1811_10136_gb300 as fr
     iters = 8
-    with fr.Server(ctx, budget_bytes=64 << 20, max_live=8, residual=fr.FR_PT2PL, iters=iters) as srv:
+    with fr.Server(ctx, budget_bytes=128 << 20, max_live=8, residual=fr.FR_PT2PL, iters=iters) as srv:
         ts = [srv.submit(dev(p.X), dev(p.Y), dev(p.Yn), sigma_start=0.04, sigma_end=0.01) for p in pairs * 2]
         res = [srv.wait(t, 60_000) for t in ts]
     for k, r in enumerate(res):
@@ -105,12 +106,12 @@ def test_point_to_point_and_fixed_sigma(ctx, pairs):
 
 
 def test_overflowing_request_is_rerun(ctx):
-    # Scattered points at a small sigma: ~4 vertices per point overflow the
-    # compact table; the server reruns the request at the safe size.
+    # 5,000 scattered points at sigma 1 cm: 20,000 vertices overflow the
+    # compact table (16,384 slots); the server reruns the request at the safe size.
     import paper_1811_10136_gb300 as fr
     rng = np.random.default_rng(77)
-    X = np.zeros((3000, 4), np.float32)
-    X[:, :3] = rng.uniform(-1, 1, size=(3000, 3))
+    X = np.zeros((5000, 4), np.float32)
+    X[:, :3] = rng.uniform(-1, 1, size=(5000, 3))
     T = synth.make_T(synth.random_rotation(rng, 0.002), [0.001, 0.0, -0.001])
     Y = np.zeros_like(X)
     Y[:, :3] = synth.apply_T(T, X)
@@ -118,7 +119,7 @@ def test_overflowing_request_is_rerun(ctx):
     with fr.Server(ctx, budget_bytes=1 << 28, max_live=4, iters=3) as srv:
         r = srv.wait(srv.submit(dev(X), dev(Y), None, sigma_start=0.01), 60_000)
     assert r.status == 0
-    assert r.report.lattice_vertices > 1.5 * 3000
+    assert r.report.lattice_vertices > 16384
     dr, dt = pose_diff(r.T, Ts)
     assert dr < SAME_ROT and dt < SAME_TRANS
 
@@ -133,7 +134,7 @@ def test_rejects_bad_requests(ctx, pairs):
         with pytest.raises(fr.FilterRegError) as e:   # normals missing for point-to-plane
             srv.submit(dev(p.X), dev(p.Y), None)
         assert e.value.status == fr.FR_EINVAL
-        big = synth.depth_frame_pair(0)               # 3 tables of 131,072 slots exceed 8 MiB
+        big = synth.depth_frame_pair(0)               # 3 tables of 262,144 slots exceed the arena
         with pytest.raises(fr.FilterRegError) as e:
             srv.submit(dev(big.X), dev(big.Y), dev(big.Yn), sigma_start=0.04, sigma_end=0.01)
         assert e.value.status == fr.FR_ENOMEM
