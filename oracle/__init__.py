@@ -22,7 +22,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["estep.c", "lattice.c", "se3.c", "rigid.c", "articulated.c"]
+_SOURCES = ["estep.c", "lattice.c", "se3.c", "rigid.c", "articulated.c", "nodegraph.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
            "-Wall", "-Wno-unused-function"]
@@ -113,6 +113,7 @@ def _declare(L):
     L.or_align_error.restype = ctypes.c_double
     if hasattr(L, "or_register_articulated"):
         _declare_articulated(L)
+        _declare_nodegraph(L)
 
 
 def _pts(a) -> np.ndarray:
@@ -420,3 +421,128 @@ def register_articulated(Xref, body, tree, Y, Yn=None, *, sigma=0.01, sigma_end=
                                         ctypes.byref(rep)), "register_articulated")
     return root_T, q, Report(rep.iters_run, rep.degenerate_iters, rep.last_inliers, rep.last_sum_w,
                              rep.last_cost, rep.last_twist_norm)
+
+
+# ---- node-graph model (Section 5.2, Eq. 21) ----------------------------------
+
+class _NodeGraph(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("node_pos", _f64p), ("E", ctypes.c_int), ("edges", _i32p),
+                ("lam", ctypes.c_double), ("pcg_iters", ctypes.c_int)]
+
+
+def _declare_nodegraph(L):
+    gp = ctypes.POINTER(_NodeGraph)
+    L.or_dq_from_T.argtypes = [_f64p, _f64p]
+    L.or_T_from_dq.argtypes = [_f64p, _f64p]
+    L.or_dqb.argtypes = [_f64p, _i32p, _f32p, _f64p]
+    L.or_nodegraph_warp.argtypes = [_f32p, _i32p, _f32p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p]
+    L.or_nodegraph_warp.restype = ctypes.c_int
+    L.or_nodegraph_normal_equations.argtypes = [_f32p, _i32p, _f32p, ctypes.c_int64, gp, _f32p, _f32p,
+                                                ctypes.c_int64, ctypes.POINTER(_Options), ctypes.c_double,
+                                                _f64p, _f64p, _f64p, ctypes.POINTER(_Report)]
+    L.or_nodegraph_normal_equations.restype = ctypes.c_int
+    L.or_pcg_block_jacobi.argtypes = [ctypes.c_int, _f64p, _f64p, ctypes.c_int, _f64p]
+    L.or_pcg_block_jacobi.restype = ctypes.c_int
+    L.or_register_nodegraph.argtypes = [_f32p, _i32p, _f32p, ctypes.c_int64, gp, _f32p, _f32p,
+                                        ctypes.c_int64, ctypes.POINTER(_Options), _f64p,
+                                        ctypes.POINTER(_Report)]
+    L.or_register_nodegraph.restype = ctypes.c_int
+
+
+def _graph(node_pos, edges, lam, pcg_iters):
+    pos = np.ascontiguousarray(node_pos, dtype=np.float64).reshape(-1, 3)
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    g = _NodeGraph(pos.shape[0], _p(pos, _f64p), e.shape[0], _p(e, _i32p), float(lam), int(pcg_iters))
+    return g, (pos, e)
+
+
+def _skin(knn, skw):
+    return (np.ascontiguousarray(knn, dtype=np.int32).reshape(-1, 4),
+            np.ascontiguousarray(skw, dtype=np.float32).reshape(-1, 4))
+
+
+def dq_from_T(T) -> np.ndarray:
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    dq = np.zeros(8)
+    _L().or_dq_from_T(_p(T, _f64p), _p(dq, _f64p))
+    return dq
+
+
+def T_from_dq(dq) -> np.ndarray:
+    dq = np.ascontiguousarray(dq, dtype=np.float64)
+    T = np.zeros((4, 4))
+    _L().or_T_from_dq(_p(dq, _f64p), _p(T, _f64p))
+    return T
+
+
+def dqb(node_dq, knn4, w4) -> np.ndarray:
+    """Dual-quaternion blend of 4 nodes' poses (node_dq: K x 8)."""
+    node_dq = np.ascontiguousarray(node_dq, dtype=np.float64)
+    knn4 = np.ascontiguousarray(knn4, dtype=np.int32)
+    w4 = np.ascontiguousarray(w4, dtype=np.float32)
+    T = np.zeros((4, 4))
+    _L().or_dqb(_p(node_dq, _f64p), _p(knn4, _i32p), _p(w4, _f32p), _p(T, _f64p))
+    return T
+
+
+def nodegraph_warp(Xref, knn, skw, node_T) -> np.ndarray:
+    Xref = _pts(Xref)
+    knn, skw = _skin(knn, skw)
+    node_T = np.ascontiguousarray(node_T, dtype=np.float64).reshape(-1, 16)
+    X = np.zeros((Xref.shape[0], 3))
+    _check(_L().or_nodegraph_warp(_p(Xref, _f32p), _p(knn, _i32p), _p(skw, _f32p), Xref.shape[0],
+                                  node_T.shape[0], _p(node_T, _f64p), _p(X, _f64p)), "nodegraph_warp")
+    return X
+
+
+def nodegraph_normal_equations(Xref, knn, skw, node_pos, edges, Y, Yn=None, *, sigma, w=0.1, lam=10.0,
+                               residual=PT2PT, backend=LATTICE, node_T=None):
+    """(A (6K, 6K), g (6K), Report) of one E step at the node poses."""
+    Xref, Y = _pts(Xref), _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    knn, skw = _skin(knn, skw)
+    g_, keep = _graph(node_pos, edges, lam, 0)
+    K = g_.K
+    node_T = np.ascontiguousarray(np.tile(np.eye(4), (K, 1, 1)) if node_T is None else node_T,
+                                  dtype=np.float64).reshape(K, 16)
+    A = np.zeros((6 * K, 6 * K))
+    g = np.zeros(6 * K)
+    o = _opts(sigma, sigma, w, 1, residual, backend, False)
+    rep = _Report()
+    _check(_L().or_nodegraph_normal_equations(_p(Xref, _f32p), _p(knn, _i32p), _p(skw, _f32p),
+                                              Xref.shape[0], ctypes.byref(g_), _p(Y, _f32p), _p(Yn, _f32p),
+                                              Y.shape[0], ctypes.byref(o), float(sigma), _p(node_T, _f64p),
+                                              _p(A, _f64p), _p(g, _f64p), ctypes.byref(rep)),
+           "nodegraph_normal_equations")
+    return A, g, Report(rep.iters_run, rep.degenerate_iters, rep.last_inliers, rep.last_sum_w,
+                        rep.last_cost, rep.last_twist_norm)
+
+
+def pcg_block_jacobi(A, b, iters) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    _check(_L().or_pcg_block_jacobi(b.shape[0] // 6, _p(A, _f64p), _p(b, _f64p), int(iters), _p(x, _f64p)),
+           "pcg_block_jacobi")
+    return x
+
+
+def register_nodegraph(Xref, knn, skw, node_pos, edges, Y, Yn=None, *, sigma=0.02, sigma_end=None, w=0.1,
+                       lam=10.0, pcg_iters=20, iters=10, residual=PT2PT, backend=LATTICE, node_T0=None,
+                       stop_twist=0.0):
+    """Node-graph EM registration; returns (node_T (K, 4, 4), Report)."""
+    Xref, Y = _pts(Xref), _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    knn, skw = _skin(knn, skw)
+    g_, keep = _graph(node_pos, edges, lam, pcg_iters)
+    K = g_.K
+    node_T = np.ascontiguousarray(np.tile(np.eye(4), (K, 1, 1)) if node_T0 is None else node_T0,
+                                  dtype=np.float64).reshape(K, 16).copy()
+    o = _opts(sigma, sigma_end, w, iters, residual, backend, False, stop_twist=stop_twist)
+    rep = _Report()
+    _check(_L().or_register_nodegraph(_p(Xref, _f32p), _p(knn, _i32p), _p(skw, _f32p), Xref.shape[0],
+                                      ctypes.byref(g_), _p(Y, _f32p), _p(Yn, _f32p), Y.shape[0],
+                                      ctypes.byref(o), _p(node_T, _f64p), ctypes.byref(rep)),
+           "register_nodegraph")
+    return node_T.reshape(K, 4, 4), Report(rep.iters_run, rep.degenerate_iters, rep.last_inliers,
+                                           rep.last_sum_w, rep.last_cost, rep.last_twist_norm)

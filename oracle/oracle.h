@@ -161,6 +161,46 @@ int or_register_articulated(const float *Xref, const int32_t *body, int64_t M,
                             const or_kintree *t, const float *Y, const float *Yn, int64_t N,
                             const or_options *opt, double root_T[16], double *q, or_report *rep);
 
+/* ---- node-graph deformable model (Section 5.2, Eq. 21) ----------------------
+ * Nodes k = 0..K-1 with reference positions node_pos (K x 3) and poses
+ * node_T (K x 16, row-major).  Model point i has 4 nearest nodes knn[i][0..3]
+ * with skinning weights skw[i][0..3] (summing to 1).  Directed regulariser
+ * edges (j, k) = edges[e][0..1], weight lambda.  The readings that fill the
+ * missing supplement are stated in nodegraph.c.                               */
+typedef struct {
+    int K;
+    const double *node_pos;    /* K x 3 */
+    int E;
+    const int32_t *edges;      /* E x 2 */
+    double lambda;
+    int pcg_iters;
+} or_nodegraph;
+
+/* Dual quaternion (q_r (w, x, y, z), q_d) of a rigid transform and back (the
+ * latter normalises by |q_r|; translation 2 (r0 d - d0 r + r x d)). */
+void or_dq_from_T(const double T[16], double dq[8]);
+void or_T_from_dq(const double dq[8], double T[16]);
+/* Dual-quaternion blend of the poses of nodes knn[0..3] (node_dq: K x 8),
+ * signs aligned with knn[0]'s, weights w (Eq. 21). */
+void or_dqb(const double *node_dq, const int32_t knn[4], const float w[4], double T[16]);
+/* Warped model points X (M x 3) at the node poses. */
+int or_nodegraph_warp(const float *Xref, const int32_t *knn, const float *skw, int64_t M, int K,
+                      const double *node_T, double *X);
+/* One E step at node_T and the Gauss-Newton system: A (6K x 6K, dense) and
+ * g (6K), A dtheta = -g.  rep (nullable) gets inliers, cost (data +
+ * regulariser) and the weight sum. */
+int or_nodegraph_normal_equations(const float *Xref, const int32_t *knn, const float *skw,
+                                  int64_t M, const or_nodegraph *ng, const float *Y,
+                                  const float *Yn, int64_t N, const or_options *opt, double sigma,
+                                  const double *node_T, double *A, double *g, or_report *rep);
+/* x = block-Jacobi PCG solution of A x = b after `iters` iterations from 0
+ * (A: 6 nb x 6 nb dense, blocks of 6). */
+int or_pcg_block_jacobi(int nb, const double *A, const double *b, int iters, double *x);
+/* Node-graph EM registration: node_T in/out. */
+int or_register_nodegraph(const float *Xref, const int32_t *knn, const float *skw, int64_t M,
+                          const or_nodegraph *ng, const float *Y, const float *Yn, int64_t N,
+                          const or_options *opt, double *node_T, or_report *rep);
+
 /* Alignment error of Eq. 22: mean |(T - T_gt) x_ref|. */
 double or_align_error(const float *X, int64_t M, const double T[16], const double Tgt[16]);
 

@@ -387,3 +387,135 @@ def articulated_pair(seed: int, n_points: int = 30000, max_joint_deg: float = 20
     return ArticulatedPair(tree, Xref, body, _pad4(Yw[perm]), _pad4(Nw[perm]), root_gt, q_gt,
                            {"workload": "kintree_capsules", "seed": seed, "M": n_points,
                             "N": Yw.shape[0], "dof": 6 + tree.nj})
+
+
+# ---------------------------------------------------------------------------
+# node-graph workload: a deforming height-field surface
+# ---------------------------------------------------------------------------
+
+@dataclass
+class NodeGraphPair:
+    Xref: np.ndarray         # (M, 4) model points (reference surface)
+    knn: np.ndarray          # (M, 4) int32: the 4 nearest nodes, nearest first
+    skw: np.ndarray          # (M, 4) float32 skinning weights (rows sum to 1)
+    node_pos: np.ndarray     # (K, 3) node positions (farthest-point samples of the model)
+    edges: np.ndarray        # (E, 2) int32 directed node-graph edges (each node -> its 8 nearest)
+    Y: np.ndarray            # (N, 4) observation: the surface resampled and deformed
+    Yn: np.ndarray           # (N, 4) observation normals
+    X_true: np.ndarray       # (M, 3) the model points under the true deformation
+    meta: dict = field(default_factory=dict)
+
+
+def _height_field(rng, n_bumps):
+    c = rng.uniform([-0.4, -0.3], [0.4, 0.3], size=(n_bumps, 2))
+    a = rng.uniform(-0.05, 0.05, n_bumps)
+    s = rng.uniform(0.03, 0.12, n_bumps)
+
+    def surface(x, y):
+        z = np.zeros_like(x)
+        zx = np.zeros_like(x)
+        zy = np.zeros_like(x)
+        for j in range(n_bumps):
+            dx, dy = x - c[j, 0], y - c[j, 1]
+            g = a[j] * np.exp(-(dx * dx + dy * dy) / (2 * s[j] ** 2))
+            z += g
+            zx -= g * dx / s[j] ** 2
+            zy -= g * dy / s[j] ** 2
+        n = np.stack([-zx, -zy, np.ones_like(x)], 1)
+        return np.stack([x, y, z], 1), n / np.linalg.norm(n, axis=1, keepdims=True)
+    return surface
+
+
+def _grid(W, H, shift):
+    u = (np.arange(W) + 0.5 + shift) / W * 0.8 - 0.4
+    v = (np.arange(H) + 0.5 + shift) / H * 0.6 - 0.3
+    x, y = np.meshgrid(u, v)
+    x, y = x.ravel(), y.ravel()
+    keep = (x / 0.408) ** 2 + (y / 0.306) ** 2 <= 1.0      # ~82% of the frame
+    return x[keep], y[keep]
+
+
+def farthest_point_sample(P: np.ndarray, k: int, rng: np.random.Generator) -> np.ndarray:
+    """Indices of k farthest-point samples of P (n, 3)."""
+    idx = np.empty(k, np.int64)
+    idx[0] = rng.integers(P.shape[0])
+    d = np.sum((P - P[idx[0]]) ** 2, 1)
+    for j in range(1, k):
+        idx[j] = int(np.argmax(d))
+        d = np.minimum(d, np.sum((P - P[idx[j]]) ** 2, 1))
+    return idx
+
+
+def nearest(P: np.ndarray, Q: np.ndarray, k: int, chunk: int = 8192):
+    """The k nearest rows of Q for every row of P, nearest first: (dist, index)."""
+    D = np.empty((P.shape[0], k))
+    I = np.empty((P.shape[0], k), np.int64)
+    q2 = np.sum(Q * Q, 1)
+    for s in range(0, P.shape[0], chunk):
+        p = P[s:s + chunk]
+        d2 = np.maximum(np.sum(p * p, 1)[:, None] + q2[None, :] - 2.0 * p @ Q.T, 0.0)
+        part = np.argpartition(d2, k - 1, axis=1)[:, :k]
+        dp = np.take_along_axis(d2, part, 1)
+        order = np.argsort(dp, 1)
+        I[s:s + chunk] = np.take_along_axis(part, order, 1)
+        D[s:s + chunk] = np.sqrt(np.take_along_axis(dp, order, 1))
+    return D, I
+
+
+def skinning(P: np.ndarray, node_pos: np.ndarray):
+    """4 nearest nodes and weights exp(-d^2 / (2 r^2)), r = the mean distance
+    from a model point to its 4 nearest nodes, normalised per point."""
+    D, I = nearest(P, node_pos, 4)
+    r = float(D.mean())
+    w = np.exp(-D ** 2 / (2 * r * r))
+    w /= w.sum(1, keepdims=True)
+    return I.astype(np.int32), w.astype(np.float32), r
+
+
+def nodegraph_pair(seed: int, W: int = 640, H: int = 480, n_nodes: int = 1000, n_bumps: int = 16,
+                   max_disp: float = 0.03, noise: float = 0.001) -> NodeGraphPair:
+    """Model: a 640x480 height field z = sum of 16 Gaussians over an
+    0.8 m x 0.6 m frame, masked to an ellipse (~250k points).  Nodes:
+    farthest-point samples; 4-NN skinning; each node linked to its 8 nearest
+    (all others when there are fewer than 9 nodes).
+    Observation: the surface resampled on the half-pixel-shifted grid and
+    moved by a smooth displacement field (6 Gaussian blobs, largest
+    displacement max_disp), N(0, noise^2) noise; normals carried by the
+    field's Jacobian.  X_true: the model points under the same field."""
+    rng = np.random.default_rng(seed)
+    surface = _height_field(rng, n_bumps)
+    Pm, _ = surface(*_grid(W, H, 0.0))
+    Po, No = surface(*_grid(W, H, 0.5))
+    centres = rng.uniform([-0.4, -0.3, -0.05], [0.4, 0.3, 0.05], size=(6, 3))
+    widths = rng.uniform(0.1, 0.25, 6)
+    amps = rng.normal(size=(6, 3))
+
+    def field_at(P):
+        d = np.zeros_like(P)
+        Jd = np.zeros((P.shape[0], 3, 3))
+        for m in range(6):
+            diff = P - centres[m]
+            g = np.exp(-np.sum(diff * diff, 1) / (2 * widths[m] ** 2))
+            d += g[:, None] * amps[m]
+            Jd += (g[:, None, None] * amps[m][None, :, None]) * (-diff / widths[m] ** 2)[:, None, :]
+        return d, Jd
+
+    d_m, _ = field_at(Pm)
+    scale = max_disp / np.linalg.norm(d_m, axis=1).max()
+    amps *= scale
+    d_m, _ = field_at(Pm)
+    d_o, J_o = field_at(Po)
+    Yp = Po + d_o + rng.normal(scale=noise, size=Po.shape)
+    F = np.eye(3)[None] + J_o
+    Yn = np.einsum("nji,nj->ni", np.linalg.inv(F), No)          # (I + grad d)^-T n
+    Yn /= np.linalg.norm(Yn, axis=1, keepdims=True)
+    nodes = Pm[farthest_point_sample(Pm, n_nodes, rng)]
+    knn, skw, r = skinning(Pm, nodes)
+    deg = min(8, n_nodes - 1)
+    _, nb = nearest(nodes, nodes, deg + 1)
+    edges = np.stack([np.repeat(np.arange(n_nodes), deg), nb[:, 1:].ravel()], 1).astype(np.int32)
+    perm = rng.permutation(Yp.shape[0])
+    return NodeGraphPair(_pad4(Pm), knn, skw, nodes, edges, _pad4(Yp[perm]), _pad4(Yn[perm]), Pm + d_m,
+                         {"workload": "height_field_nodegraph", "seed": seed, "M": int(Pm.shape[0]),
+                          "N": int(Yp.shape[0]), "K": n_nodes, "E": int(edges.shape[0]),
+                          "skin_radius": r})
