@@ -310,6 +310,53 @@ FR_API fr_status fr_register_rigid_batch(fr_ctx *ctx, fr_batch_item *items, int 
 FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items, int n_items,
                                               const fr_options *opt, fr_report *reports);
 
+/* ---- node-graph deformable model (Section 5.2, Eq. 21) ----------------------
+ * Nodes k = 0..K-1 with reference positions p_k and poses T_k; model point i
+ * moves by the dual-quaternion blend of its 4 nodes' poses with fixed
+ * skinning weights (Eq. 21): x_i = normalized(sum_k w_ki dq(T_k)) x_i_ref,
+ * the node dual quaternions sign-aligned with the largest-weight node's.
+ * The supplement the paper defers to for the M step is not available; this
+ * library reads it as: one twist per node, T_k <- exp(dzeta_k^) T_k; a
+ * point's twist is the weighted sum of its nodes' (the first-order blend
+ * derivative), so the rigid point terms (Eq. 7 / Eq. 10) enter block (a, b)
+ * of A with weight w_a w_b; a regulariser adds, for every directed edge
+ * (j, k), the residual sqrt(lambda)/sigma (T_j p_k - T_k p_k); the system is
+ * solved by block-Jacobi preconditioned conjugate gradients, pcg_iters
+ * iterations from zero, in float64 (blocks accumulated in float32). */
+typedef struct fr_nodegraph fr_nodegraph;
+
+/* Prepare a model on ctx's device: d_Xref (M x 4 float), d_knn (M x 4
+ * int32 node ids) and d_skw (M x 4 float weights, >= 0) are device arrays,
+ * copied (sorted by node tuple) -- the caller may free them afterwards;
+ * node_pos (host, K x 3 double) and edges (host, E x 2 int32 directed
+ * regulariser edges, no self-edges).  Synchronises the stream.  FR_EINVAL
+ * for out-of-range ids, negative or non-finite weights, bad sizes. */
+FR_API fr_status fr_nodegraph_create(fr_ctx *ctx, const float *d_Xref, const int32_t *d_knn,
+                                     const float *d_skw, int64_t M, const double *node_pos, int K,
+                                     const int32_t *edges, int E, fr_nodegraph **out);
+/* Free the model (waits for the device; may follow fr_ctx_destroy). */
+FR_API fr_status fr_nodegraph_destroy(fr_nodegraph *g);
+/* opt->iters EM iterations (sigma schedule as fr_register_rigid; the lattice
+ * is rebuilt when sigma changes) of the node-graph model against d_Y (N x 4)
+ * (+ normals d_Yn for FR_PT2PL).  node_T (host, K x 16 row-major) carries
+ * the initial poses in and the result out.  storage must be FR_FP32 and
+ * blur, kahan and stop_twist 0 (FR_ENOTSUPPORTED otherwise); lambda >= 0;
+ * 0 <= pcg_iters <= 10000.  rep (nullable): last iteration's inliers,
+ * weight sum, cost (data + regulariser) and update norm. */
+FR_API fr_status fr_register_nodegraph(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_Yn,
+                                       int64_t N, const fr_options *opt, double lambda, int pcg_iters,
+                                       double *node_T, fr_report *rep);
+/* One E step at sigma = opt->sigma_start and the Gauss-Newton system at the
+ * node poses node_T: A_out (host, dense 6K x 6K, nullable) and g_out (host,
+ * 6K, nullable), A dtheta = -g -- the assembly the registration runs,
+ * exposed for checking. */
+FR_API fr_status fr_nodegraph_system(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_Yn,
+                                     int64_t N, const fr_options *opt, double lambda,
+                                     const double *node_T, double *A_out, double *g_out, fr_report *rep);
+/* The model points warped by node_T (Eq. 21) into d_out (device, M x 4
+ * float, the caller's point order). */
+FR_API fr_status fr_nodegraph_warp(fr_ctx *ctx, fr_nodegraph *g, const double *node_T, float *d_out);
+
 /* ---- serving: continuous batching -------------------------------------------
  * A server registers a stream of independent pairs (the rigid EM of
  * fr_register_rigid, Sections 3.1, 4, 5) with continuous batching: a worker

@@ -7,8 +7,8 @@
  * model point x_i_ref with nearest nodes N_i and fixed skinning weights w_ki
  * moves by the dual-quaternion blend of its nodes' poses (Eq. 21):
  *     T_i = normalized(sum_k w_ki dq(T_k)),   x_i = T_i x_i_ref,
- * each node's dual quaternion sign-aligned with the first neighbour's before
- * summing, the blend divided by the norm of its real part, and the
+ * each node's dual quaternion sign-aligned with that of the neighbour of
+ * largest weight (the first such) before summing, the blend divided by the norm of its real part, and the
  * translation read as 2 (r0 d - d0 r + r x d) (Kavan et al.).
  *
  * The supplement the paper defers to is missing; these readings fill it:
@@ -120,7 +120,11 @@ void or_T_from_dq(const double dq[8], double T[16])
 
 void or_dqb(const double *node_dq, const int32_t knn[4], const float w[4], double T[16])
 {
-    const double *q0 = node_dq + 8 * (size_t)knn[0];
+    int ref = 0;
+    for (int k = 1; k < 4; ++k)
+        if (w[k] > w[ref])
+            ref = k;
+    const double *q0 = node_dq + 8 * (size_t)knn[ref];
     double b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < 4; ++k) {
         const double *q = node_dq + 8 * (size_t)knn[k];

@@ -181,7 +181,8 @@ typedef struct {
 void or_dq_from_T(const double T[16], double dq[8]);
 void or_T_from_dq(const double dq[8], double T[16]);
 /* Dual-quaternion blend of the poses of nodes knn[0..3] (node_dq: K x 8),
- * signs aligned with knn[0]'s, weights w (Eq. 21). */
+ * signs aligned with the largest-weight neighbour's (the first such),
+ * weights w (Eq. 21). */
 void or_dqb(const double *node_dq, const int32_t knn[4], const float w[4], double T[16]);
 /* Warped model points X (M x 3) at the node poses. */
 int or_nodegraph_warp(const float *Xref, const int32_t *knn, const float *skw, int64_t M, int K,

@@ -37,7 +37,8 @@ EXPORTED = [
     "fr_ctx_transfer_bytes", "fr_estep_noalloc", "fr_register_rigid_batch",
     "fr_register_rigid_batch_host", "fr_register_articulated", "fr_estep_storage",
     "fr_server_create", "fr_server_submit", "fr_server_poll", "fr_server_wait", "fr_server_release",
-    "fr_server_stats", "fr_server_destroy",
+    "fr_server_stats", "fr_server_destroy", "fr_nodegraph_create", "fr_nodegraph_destroy",
+    "fr_register_nodegraph", "fr_nodegraph_system", "fr_nodegraph_warp",
 ]
 FR_NOALLOC_MAX_OBS = 8192
 KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert")
@@ -169,6 +170,14 @@ def load(build_if_missing: bool = True):
     L.fr_server_release.argtypes = [_vp, ctypes.c_uint64]
     L.fr_server_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
     L.fr_server_destroy.argtypes = [_vp]
+    L.fr_nodegraph_create.argtypes = [_vp, _vp, _vp, _vp, _i64, _f64p, ctypes.c_int, _vp, ctypes.c_int,
+                                      ctypes.POINTER(_vp)]
+    L.fr_nodegraph_destroy.argtypes = [_vp]
+    L.fr_register_nodegraph.argtypes = [_vp, _vp, _vp, _vp, _i64, ctypes.POINTER(fr_options), ctypes.c_double,
+                                        ctypes.c_int, _f64p, ctypes.POINTER(fr_report)]
+    L.fr_nodegraph_system.argtypes = [_vp, _vp, _vp, _vp, _i64, ctypes.POINTER(fr_options), ctypes.c_double,
+                                      _f64p, _f64p, _f64p, ctypes.POINTER(fr_report)]
+    L.fr_nodegraph_warp.argtypes = [_vp, _vp, _f64p, _vp]
     for name in EXPORTED:  # every entry point must resolve (ctypes restype defaults to int)
         getattr(L, name)
     _lib = L
@@ -601,6 +610,89 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class NodeGraph:
+    """fr_nodegraph: a node-graph model (Section 5.2) prepared on ctx's device.
+
+    Xref (M,4) float32, knn (M,4) int32 and skw (M,4) float32 are CUDA
+    tensors (copied by the library); node_pos (K,3) and edges (E,2) host
+    arrays."""
+
+    def __init__(self, ctx: "Context", Xref, knn, skw, node_pos, edges):
+        import torch
+        L = load()
+        self.ctx = ctx
+        for t, name, dt in ((knn, "knn", torch.int32), (skw, "skw", torch.float32)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()
+                    and tuple(t.shape) == (Xref.shape[0], 4)):
+                raise TypeError(f"{name} must be a contiguous (M, 4) {dt} CUDA tensor")
+        self.node_pos = np.ascontiguousarray(node_pos, dtype=np.float64).reshape(-1, 3)
+        self.edges = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        self.K = self.node_pos.shape[0]
+        self.M = Xref.shape[0]
+        h = _vp()
+        st = L.fr_nodegraph_create(ctx._h, _dev_ptr(Xref, "Xref"), knn.data_ptr(), skw.data_ptr(), self.M,
+                                   self.node_pos.ctypes.data_as(_f64p), self.K,
+                                   self.edges.ctypes.data if self.edges.size else None, self.edges.shape[0],
+                                   ctypes.byref(h))
+        ctx._check(st, "fr_nodegraph_create")
+        self._h = h
+
+    def _poses(self, node_T):
+        if node_T is None:
+            return np.ascontiguousarray(np.tile(np.eye(4), (self.K, 1, 1)))
+        T = np.ascontiguousarray(node_T, dtype=np.float64).reshape(self.K, 4, 4).copy()
+        return T
+
+    def register(self, Y, Yn=None, node_T0=None, lam=10.0, pcg_iters=20, **opts):
+        """EM registration; returns (node_T (K, 4, 4), Report)."""
+        L = load()
+        o = options(**opts)
+        T = self._poses(node_T0)
+        rep = fr_report()
+        st = L.fr_register_nodegraph(self.ctx._h, self._h, _dev_ptr(Y, "Y"),
+                                     _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None,
+                                     Y.shape[0], ctypes.byref(o), float(lam), int(pcg_iters),
+                                     T.ctypes.data_as(_f64p), ctypes.byref(rep))
+        self.ctx._check(st, "fr_register_nodegraph")
+        return T, _report(rep)
+
+    def system(self, Y, Yn=None, node_T=None, lam=10.0, **opts):
+        """(A (6K, 6K), g (6K), Report) of one E step at sigma_start."""
+        L = load()
+        o = options(**opts)
+        T = self._poses(node_T)
+        A = np.zeros((6 * self.K, 6 * self.K))
+        g = np.zeros(6 * self.K)
+        rep = fr_report()
+        st = L.fr_nodegraph_system(self.ctx._h, self._h, _dev_ptr(Y, "Y"),
+                                   _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None,
+                                   Y.shape[0], ctypes.byref(o), float(lam), T.ctypes.data_as(_f64p),
+                                   A.ctypes.data_as(_f64p), g.ctypes.data_as(_f64p), ctypes.byref(rep))
+        self.ctx._check(st, "fr_nodegraph_system")
+        return A, g, _report(rep)
+
+    def warp(self, node_T):
+        """Warped model points (M, 4) float32 CUDA tensor (Eq. 21)."""
+        import torch
+        L = load()
+        T = self._poses(node_T)
+        out = torch.empty((self.M, 4), dtype=torch.float32, device="cuda")
+        st = L.fr_nodegraph_warp(self.ctx._h, self._h, T.ctypes.data_as(_f64p), out.data_ptr())
+        self.ctx._check(st, "fr_nodegraph_warp")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fr_nodegraph_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

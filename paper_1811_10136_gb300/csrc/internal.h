@@ -182,12 +182,77 @@ struct Seg {
     int blk0, nblk;
 };
 
+// ---- node-graph model (Section 5.2, Eq. 21) ----------------------------------
+// Model points are stored sorted by their (node id sorted) 4-node tuple, so a
+// run of points -- a segment -- shares its nodes and its 10 node-pair blocks
+// (a <= b) of A.  Blocks are 6 x 6 float, row-major, rows of node a.
+constexpr int kNgPairs = 10;  // tuple pairs (0,0),(0,1),(0,2),(0,3),(1,1),(1,2),(1,3),(2,2),(2,3),(3,3)
+
+struct NgPoints {
+    const float4 *X;        // model points (reference), segment-sorted
+    const float4 *w;        // their skinning weights, in the tuple's order
+    const int *perm;        // sorted position -> caller's index (warp output)
+    const int *seg_start;   // S + 1
+    const int4 *seg_nodes;  // S tuples (ascending node ids)
+    const int *seg_blk;     // S x 10 block ids of the tuple pairs
+    const float *seg_coef;  // S x 10: 2 for a repeated node off the diagonal, else 1
+    int S;
+    const float *node_dq;   // K x 8 dual quaternions of the node poses
+    Table tab;              // the lattice over the observation
+    const IterParams *ip;
+    int renorm;
+    float *blocks;          // nnzb x 36 accumulators
+    float *g;               // 6 K accumulators
+    double *stats;          // [sum of weights, cost]
+    unsigned long long *inliers;
+    int *flags;
+    float4 *warp_out;       // warp only: warped points in the caller's order
+};
+
+struct NgEdges {
+    const int2 *edges;      // E directed edges (j, k)
+    const int *edge_blk;    // E x 3: blocks (j, j), (k, k), (min, max)
+    int E;
+    const double *node_T;   // K x 16
+    const double *node_pos; // K x 3
+    double lambda;
+    const IterParams *ip;
+    float *blocks, *g;
+    double *stats;
+};
+
+// Block-Jacobi PCG over the node blocks, float64 vectors.
+struct NgPcg {
+    int K;
+    const int *row_ptr;     // K + 1
+    const int2 *ent;        // (block | transposed << 31, partner node)
+    const int *diag_blk;    // K
+    const float *blocks;
+    const float *g;
+    double *P;              // K x 36 preconditioner
+    double *x, *r, *z, *Ap;
+    const double *p_old;
+    double *p_new;
+    double *scal;           // [rz, alpha, beta, stop]
+    double *partial;        // per-block partial sums
+    int *ticket;
+};
+
 // ---- launchers (kernels.cu) -------------------------------------------------
 void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
                      const unsigned short *blockseg, int grid, int check_done, cudaStream_t s,
                      int storage);
 void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s, int storage);
 void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s, int storage);
+void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t s);
+void launch_ng_edges(const NgEdges &a, cudaStream_t s);
+void launch_ng_pcg_init(const NgPcg &a, cudaStream_t s);
+void launch_ng_pcg_spmv(const NgPcg &a, cudaStream_t s);
+void launch_ng_pcg_update(const NgPcg &a, cudaStream_t s);
+// T_k <- exp(dx_k) T_k (dx nullable: none) and the nodes' dual quaternions;
+// |dx|^2 added to *twist2.
+void launch_ng_update(int K, const double *dx, double *node_T, float *node_dq, double *twist2,
+                      cudaStream_t s);
 int em_iter_blocks_per_sm(int pt2pl, int kahan);
 // Frees the slots listed by builds (list lists[i], count *counts[i]).
 void launch_clear_lists(const Table *tabs, int *const *lists, const int *const *counts, int n,

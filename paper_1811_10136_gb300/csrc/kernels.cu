@@ -1263,6 +1263,494 @@ int grid_for(long long n, int cap_blocks) {
     return (int)g;
 }
 
+
+// ---------------------------------------------------------------------------
+// Node-graph model (Section 5.2, Eq. 21)
+// ---------------------------------------------------------------------------
+
+// Tuple positions of the 10 node pairs, and row / column of the 21
+// upper-triangle entries of a 6 x 6 block (tri_index order).
+__constant__ unsigned char c_pair_i[kNgPairs] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
+__constant__ unsigned char c_pair_j[kNgPairs] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
+__constant__ unsigned char c_tri_r[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+__constant__ unsigned char c_tri_c[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
+
+// Eq. 21: the dual-quaternion blend of a point's 4 node poses -- each
+// node's dual quaternion sign-aligned with the largest-weight node's (the
+// first such), the sum divided by the norm of its real part -- as a
+// rotation R (row-major) and a translation t = 2 (r0 d - d0 r + r x d).
+__device__ __forceinline__ void ng_blend(const float (&q)[4][8], const float (&w)[4], float R[9],
+                                         float t[3]) {
+    int ref = 0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (w[k] > w[ref]) ref = k;
+    float r0 = q[0][0], r1 = q[0][1], r2 = q[0][2], r3 = q[0][3];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (ref == k) {
+            r0 = q[k][0];
+            r1 = q[k][1];
+            r2 = q[k][2];
+            r3 = q[k][3];
+        }
+    float b[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float dot = q[k][0] * r0 + q[k][1] * r1 + q[k][2] * r2 + q[k][3] * r3;
+        const float sw = dot < 0.0f ? -w[k] : w[k];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) b[a] += sw * q[k][a];
+    }
+    const float inv = 1.0f / sqrtf(b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3]);
+    const float qw = b[0] * inv, qx = b[1] * inv, qy = b[2] * inv, qz = b[3] * inv;
+    const float d0 = b[4] * inv, dx = b[5] * inv, dy = b[6] * inv, dz = b[7] * inv;
+    R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+    R[1] = 2.0f * (qx * qy - qw * qz);
+    R[2] = 2.0f * (qx * qz + qw * qy);
+    R[3] = 2.0f * (qx * qy + qw * qz);
+    R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
+    R[5] = 2.0f * (qy * qz - qw * qx);
+    R[6] = 2.0f * (qx * qz - qw * qy);
+    R[7] = 2.0f * (qy * qz + qw * qx);
+    R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+    t[0] = 2.0f * (qw * dx - d0 * qx + (qy * dz - qz * dy));
+    t[1] = 2.0f * (qw * dy - d0 * qy + (qz * dx - qx * dz));
+    t[2] = 2.0f * (qw * dz - d0 * qz + (qx * dy - qy * dx));
+}
+
+// One warp per segment (a run of points sharing their 4 nodes): each lane
+// warps a point (Eq. 21), slices the lattice at it (E step) and forms its
+// rigid-model terms H = J^T J (21), h = J^T r (6) (Eq. 7 / Eq. 10); the
+// warp then sums, over the segment, w_i w_j H for the 10 node pairs and
+// w_i h for the 4 nodes (the point twist is the weighted sum of its node
+// twists, so d r / d zeta_k = w_k J) through shared memory -- 234 sums, 8
+// per lane -- and adds them to the pair blocks of A and to g.  With
+// warp_only the kernel writes the warped points and stops.
+template <bool PT2PL>
+__global__ void __launch_bounds__(kBlock) k_ng_points(NgPoints L, int warp_only) {
+    constexpr int kWarps = kBlock / 32;
+    __shared__ float sh[kWarps][32][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x * kWarps + warp;
+    if (seg >= L.S) return;  // whole warps only: no block-wide barrier below
+    const int p0 = L.seg_start[seg], p1 = L.seg_start[seg + 1];
+    const int4 nd = L.seg_nodes[seg];
+    const int nodes[4] = {nd.x, nd.y, nd.z, nd.w};
+    float q[4][8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(L.node_dq) + 2 * nodes[k]);
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(L.node_dq) + 2 * nodes[k] + 1);
+        q[k][0] = a.x; q[k][1] = a.y; q[k][2] = a.z; q[k][3] = a.w;
+        q[k][4] = c.x; q[k][5] = c.y; q[k][6] = c.z; q[k][7] = c.w;
+    }
+    // this lane's sums o = lane + 32 m: products of shared columns ca * cb * cv
+    // (columns 0..20 H, 21..26 h, 27..30 weights, 31 the constant 1)
+    int ca[8], cb[8], cv[8];
+    float acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int o = lane + 32 * m;
+        acc[m] = 0.0f;
+        if (o < kNgPairs * 21) {
+            const int pr = o / 21, e = o % 21;
+            ca[m] = 27 + c_pair_i[pr];
+            cb[m] = 27 + c_pair_j[pr];
+            cv[m] = e;
+        } else if (o < kNgPairs * 21 + 24) {
+            const int n = (o - kNgPairs * 21) / 6, c = (o - kNgPairs * 21) % 6;
+            ca[m] = 27 + n;
+            cb[m] = 31;
+            cv[m] = 21 + c;
+        } else {
+            ca[m] = cb[m] = cv[m] = 31;
+        }
+    }
+    IterParams ip{};
+    if (!warp_only) ip = *L.ip;
+    float sum_w = 0.0f, cost = 0.0f;
+    int inl = 0, bad = 0;
+    float(*row)[33] = sh[warp];
+    for (int base = p0; base < p1; base += 32) {
+        const int i = base + lane;
+        float v[31];
+#pragma unroll
+        for (int c = 0; c < 31; ++c) v[c] = 0.0f;
+        if (i < p1) {
+            const float4 xr = L.X[i];
+            const float4 wt = L.w[i];
+            const float w4[4] = {wt.x, wt.y, wt.z, wt.w};
+            float R[9], t[3];
+            ng_blend(q, w4, R, t);
+            const float x0 = R[0] * xr.x + R[1] * xr.y + R[2] * xr.z + t[0];
+            const float x1 = R[3] * xr.x + R[4] * xr.y + R[5] * xr.z + t[1];
+            const float x2 = R[6] * xr.x + R[7] * xr.y + R[8] * xr.z + t[2];
+            if (warp_only) {
+                L.warp_out[L.perm[i]] = make_float4(x0, x1, x2, 0.0f);
+            } else {
+                Sums e;
+                if (slice_point<PT2PL, kStoreF32>(L.tab, x0, x1, x2, ip, e, bad)) {
+                    float tv[kRigidVals];
+#pragma unroll
+                    for (int c = 0; c < kRigidVals; ++c) tv[c] = 0.0f;
+                    if (point_terms<PT2PL>(x0, x1, x2, e, ip, L.renorm, [&](int c, float a) { tv[c] += a; })) {
+#pragma unroll
+                        for (int c = 0; c < 27; ++c) v[c] = tv[c];
+                        sum_w += tv[27];
+                        cost += tv[28];
+                        ++inl;
+                    }
+                }
+                v[27] = w4[0];
+                v[28] = w4[1];
+                v[29] = w4[2];
+                v[30] = w4[3];
+            }
+        }
+        if (warp_only) continue;
+#pragma unroll
+        for (int c = 0; c < 31; ++c) row[lane][c] = v[c];
+        row[lane][31] = 1.0f;
+        __syncwarp();
+        const int cnt = min(32, p1 - base);
+        for (int pt = 0; pt < cnt; ++pt) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[m] += row[pt][ca[m]] * row[pt][cb[m]] * row[pt][cv[m]];
+        }
+        __syncwarp();
+    }
+    if (warp_only) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int o = lane + 32 * m;
+        if (o < kNgPairs * 21) {
+            const int pr = o / 21, e = o % 21;
+            const int blk = L.seg_blk[seg * kNgPairs + pr];
+            const float val = L.seg_coef[seg * kNgPairs + pr] * acc[m];
+            const int r = c_tri_r[e], c = c_tri_c[e];
+            atomicAdd(L.blocks + (size_t)blk * 36 + r * 6 + c, val);
+            if (r != c) atomicAdd(L.blocks + (size_t)blk * 36 + c * 6 + r, val);
+        } else if (o < kNgPairs * 21 + 24) {
+            const int n = (o - kNgPairs * 21) / 6, c = (o - kNgPairs * 21) % 6;
+            atomicAdd(L.g + 6 * nodes[n] + c, acc[m]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum_w += __shfl_xor_sync(kFull, sum_w, o);
+        cost += __shfl_xor_sync(kFull, cost, o);
+        inl += __shfl_xor_sync(kFull, inl, o);
+        bad |= __shfl_xor_sync(kFull, bad, o);
+    }
+    if (lane == 0) {
+        atomicAdd(L.stats, (double)sum_w);
+        atomicAdd(L.stats + 1, (double)cost);
+        if (inl) atomicAdd(L.inliers, (unsigned long long)inl);
+        if (bad) atomicOr(L.flags, bad);
+    }
+}
+
+// The regulariser, one thread per directed edge (j, k):
+// r = s (T_j p_k - T_k p_k), s = sqrt(lambda) / sigma, with
+// d r / d zeta_j = s [-[T_j p_k]_x, I] and d r / d zeta_k = -s [-[T_k p_k]_x, I];
+// adds J_j^T J_j, J_k^T J_k, the cross block and J^T r (float64 arithmetic).
+__global__ void __launch_bounds__(kBlock) k_ng_edges(NgEdges L) {
+    const int e = gtid();
+    if (e >= L.E) return;
+    const int2 jk = L.edges[e];
+    const double s = sqrt(L.lambda) / (double)L.ip->sigma;
+    const double *Tj = L.node_T + 16 * jk.x, *Tk = L.node_T + 16 * jk.y;
+    const double *pk = L.node_pos + 3 * jk.y;
+    double a[3], b[3], r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[c] = Tj[4 * c] * pk[0] + Tj[4 * c + 1] * pk[1] + Tj[4 * c + 2] * pk[2] + Tj[4 * c + 3];
+        b[c] = Tk[4 * c] * pk[0] + Tk[4 * c + 1] * pk[1] + Tk[4 * c + 2] * pk[2] + Tk[4 * c + 3];
+        r[c] = s * (a[c] - b[c]);
+    }
+    const double Jj[3][6] = {{0.0, s * a[2], -s * a[1], s, 0.0, 0.0},
+                             {-s * a[2], 0.0, s * a[0], 0.0, s, 0.0},
+                             {s * a[1], -s * a[0], 0.0, 0.0, 0.0, s}};
+    const double Jk[3][6] = {{0.0, -s * b[2], s * b[1], -s, 0.0, 0.0},
+                             {s * b[2], 0.0, -s * b[0], 0.0, -s, 0.0},
+                             {-s * b[1], s * b[0], 0.0, 0.0, 0.0, -s}};
+    const int *eb = L.edge_blk + 3 * e;
+    float *Bjj = L.blocks + (size_t)eb[0] * 36, *Bkk = L.blocks + (size_t)eb[1] * 36;
+    float *Bx = L.blocks + (size_t)eb[2] * 36;
+    const bool j_first = jk.x < jk.y;
+    for (int p = 0; p < 6; ++p) {
+        double gj = 0.0, gk = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            gj += Jj[c][p] * r[c];
+            gk += Jk[c][p] * r[c];
+        }
+        atomicAdd(L.g + 6 * jk.x + p, (float)gj);
+        atomicAdd(L.g + 6 * jk.y + p, (float)gk);
+        for (int q = 0; q < 6; ++q) {
+            double mjj = 0.0, mkk = 0.0, mjk = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                mjj += Jj[c][p] * Jj[c][q];
+                mkk += Jk[c][p] * Jk[c][q];
+                mjk += Jj[c][p] * Jk[c][q];
+            }
+            atomicAdd(Bjj + 6 * p + q, (float)mjj);
+            atomicAdd(Bkk + 6 * p + q, (float)mkk);
+            // block (min, max) holds rows of the smaller node: J_j^T J_k, or its transpose
+            atomicAdd(Bx + (j_first ? 6 * p + q : 6 * q + p), (float)mjk);
+        }
+    }
+    atomicAdd(L.stats + 1, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+}
+
+// Sum of v over the grid: every block adds its partial; the last block to
+// finish totals the partials in block order (deterministic) and returns
+// true in its thread 0 with *total set.
+__device__ __forceinline__ bool ng_grid_sum(double v, double *partial, int *ticket, double &total) {
+    __shared__ double s_w[kBlock / 32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 0) s_w[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_w[w];
+        partial[blockIdx.x] = b;
+        __threadfence();
+        s_last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return false;
+    __threadfence();
+    double t = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) t += __ldcg(partial + i);
+    total = t;
+    *ticket = 0;
+    return true;
+}
+
+// PCG set-up: P_k = (A_kk)^-1 by Cholesky (pivot floor 1e-12 of the largest
+// diagonal entry; a block below it gets 1 / that entry), x = 0, r = -g,
+// z = P r, rz = r.z.  One thread per node.
+__global__ void __launch_bounds__(kBlock) k_ng_pcg_init(NgPcg L) {
+    const int k = gtid();
+    double dot = 0.0;
+    if (k < L.K) {
+        const float *B = L.blocks + (size_t)L.diag_blk[k] * 36;
+        double D[36], Lc[36], Pk[36];
+        double dmax = 0.0;
+        for (int a = 0; a < 36; ++a) D[a] = (double)B[a];
+        for (int a = 0; a < 6; ++a) dmax = fmax(dmax, D[7 * a]);
+        bool ok = dmax > 0.0;
+        const double fl = dmax * 1e-12;
+        for (int i = 0; i < 6 && ok; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double sacc = D[6 * i + j];
+                for (int m = 0; m < j; ++m) sacc -= Lc[6 * i + m] * Lc[6 * j + m];
+                if (i == j) {
+                    if (!(sacc > fl)) { ok = false; break; }
+                    Lc[6 * i + i] = sqrt(sacc);
+                } else {
+                    Lc[6 * i + j] = sacc / Lc[6 * j + j];
+                }
+            }
+        if (ok) {
+            for (int c = 0; c < 6; ++c) {  // column c of the inverse
+                double y[6], xcol[6];
+                for (int i = 0; i < 6; ++i) {
+                    double sacc = (i == c) ? 1.0 : 0.0;
+                    for (int m = 0; m < i; ++m) sacc -= Lc[6 * i + m] * y[m];
+                    y[i] = sacc / Lc[6 * i + i];
+                }
+                for (int i = 5; i >= 0; --i) {
+                    double sacc = y[i];
+                    for (int m = i + 1; m < 6; ++m) sacc -= Lc[6 * m + i] * xcol[m];
+                    xcol[i] = sacc / Lc[6 * i + i];
+                }
+                for (int i = 0; i < 6; ++i) Pk[6 * i + c] = xcol[i];
+            }
+        } else {
+            for (int a = 0; a < 36; ++a) Pk[a] = (a % 7 == 0) ? (dmax > 0.0 ? 1.0 / dmax : 1.0) : 0.0;
+        }
+        double rr[6];
+        for (int a = 0; a < 6; ++a) {
+            rr[a] = -(double)L.g[6 * k + a];
+            L.r[6 * k + a] = rr[a];
+            L.x[6 * k + a] = 0.0;
+        }
+        for (int a = 0; a < 36; ++a) L.P[36 * (size_t)k + a] = Pk[a];
+        for (int a = 0; a < 6; ++a) {
+            double z = 0.0;
+            for (int c = 0; c < 6; ++c) z += Pk[6 * a + c] * rr[c];
+            L.z[6 * k + a] = z;
+            dot += rr[a] * z;
+        }
+    }
+    double total;
+    if (ng_grid_sum(dot, L.partial, L.ticket, total)) {
+        L.scal[0] = total;
+        L.scal[1] = 0.0;
+        L.scal[2] = 0.0;
+        L.scal[3] = (total > 0.0) ? 0.0 : 1.0;
+    }
+}
+
+// p = z + beta p_old (the previous iteration's direction update), Ap = A p:
+// one warp per node row over its blocks (A_ab, or A_ba^T for the stored
+// transpose), then alpha = r.z / p.Ap.
+__global__ void __launch_bounds__(kBlock) k_ng_pcg_spmv(NgPcg L) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const bool stop = L.scal[3] != 0.0;
+    const double beta = L.scal[2];
+    double dot = 0.0;
+    if (row < L.K && !stop) {
+        double y[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int e = L.row_ptr[row] + lane; e < L.row_ptr[row + 1]; e += 32) {
+            const int2 en = L.ent[e];
+            const int blk = en.x & 0x7fffffff, b = en.y;
+            const bool tr = en.x < 0;
+            double pb[6];
+            for (int c = 0; c < 6; ++c) pb[c] = L.z[6 * b + c] + beta * L.p_old[6 * b + c];
+            const float *M = L.blocks + (size_t)blk * 36;
+            for (int i = 0; i < 6; ++i) {
+                double acc = 0.0;
+                for (int c = 0; c < 6; ++c) acc += (double)(tr ? M[6 * c + i] : M[6 * i + c]) * pb[c];
+                y[i] += acc;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y[i] += __shfl_xor_sync(kFull, y[i], o);
+        if (lane == 0)
+            for (int i = 0; i < 6; ++i) {
+                const double pn = L.z[6 * row + i] + beta * L.p_old[6 * row + i];
+                L.p_new[6 * row + i] = pn;
+                L.Ap[6 * row + i] = y[i];
+                dot += pn * y[i];
+            }
+    }
+    double total;
+    if (ng_grid_sum(dot, L.partial, L.ticket, total) && !stop) {
+        if (total > 0.0) {
+            L.scal[1] = L.scal[0] / total;
+        } else {
+            L.scal[1] = 0.0;
+            L.scal[3] = 1.0;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha Ap, z = P r, then beta = r.z / rz and rz = r.z.
+__global__ void __launch_bounds__(kBlock) k_ng_pcg_update(NgPcg L) {
+    const int k = gtid();
+    const bool stop = L.scal[3] != 0.0;
+    double dot = 0.0;
+    if (k < L.K && !stop) {
+        const double alpha = L.scal[1];
+        double rr[6];
+        for (int a = 0; a < 6; ++a) {
+            L.x[6 * k + a] += alpha * L.p_new[6 * k + a];
+            rr[a] = L.r[6 * k + a] - alpha * L.Ap[6 * k + a];
+            L.r[6 * k + a] = rr[a];
+        }
+        const double *Pk = L.P + 36 * (size_t)k;
+        for (int a = 0; a < 6; ++a) {
+            double z = 0.0;
+            for (int c = 0; c < 6; ++c) z += Pk[6 * a + c] * rr[c];
+            L.z[6 * k + a] = z;
+            dot += rr[a] * z;
+        }
+    }
+    double total;
+    if (ng_grid_sum(dot, L.partial, L.ticket, total) && !stop) {
+        L.scal[2] = total / L.scal[0];
+        L.scal[0] = total;
+        if (!(total > 0.0)) L.scal[3] = 1.0;
+    }
+}
+
+// T_k <- exp(dx_k^) T_k (float64; A = sin(t)/t, B = (1 - cos t)/t^2,
+// C = (t - sin t)/t^3, their series below t = 1e-3), then the node's dual
+// quaternion (q_r from R, q_d = 1/2 (0, t) q_r) in float.
+__global__ void __launch_bounds__(kBlock) k_ng_update(int K, const double *dx, double *node_T,
+                                                      float *node_dq, double *twist2) {
+    const int k = gtid();
+    if (k >= K) return;
+    double *T = node_T + 16 * (size_t)k;
+    if (dx) {
+        const double *z = dx + 6 * (size_t)k;
+        const double w0 = z[0], w1 = z[1], w2 = z[2];
+        const double th2 = w0 * w0 + w1 * w1 + w2 * w2, th = sqrt(th2);
+        double A, B, C;
+        if (th < 1e-3) {
+            A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+            B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+            C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+        } else {
+            double sn, cs;
+            sincos(th, &sn, &cs);
+            A = sn / th;
+            B = (1.0 - cs) / th2;
+            C = (th - sn) / (th2 * th);
+        }
+        const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+        double W2[9], E[16];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                W2[3 * i + j] = W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j];
+        for (int i = 0; i < 3; ++i) {
+            double tv = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                const double I = (i == j) ? 1.0 : 0.0;
+                E[4 * i + j] = I + A * W[3 * i + j] + B * W2[3 * i + j];
+                tv += (I + B * W[3 * i + j] + C * W2[3 * i + j]) * z[3 + j];
+            }
+            E[4 * i + 3] = tv;
+        }
+        double Tn[12];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 4; ++j)
+                Tn[4 * i + j] = E[4 * i] * T[j] + E[4 * i + 1] * T[4 + j] + E[4 * i + 2] * T[8 + j] +
+                                (j == 3 ? E[4 * i + 3] : 0.0);
+        for (int a = 0; a < 12; ++a) T[a] = Tn[a];
+        atomicAdd(twist2, w0 * w0 + w1 * w1 + w2 * w2 + z[3] * z[3] + z[4] * z[4] + z[5] * z[5]);
+    }
+    // unit quaternion of R (the largest of w, x, y, z pivots)
+    const double m00 = T[0], m01 = T[1], m02 = T[2], m10 = T[4], m11 = T[5], m12 = T[6];
+    const double m20 = T[8], m21 = T[9], m22 = T[10], tr = m00 + m11 + m22;
+    double q[4];
+    if (tr >= m00 && tr >= m11 && tr >= m22) {
+        const double s = sqrt(1.0 + tr) * 2.0;
+        q[0] = 0.25 * s; q[1] = (m21 - m12) / s; q[2] = (m02 - m20) / s; q[3] = (m10 - m01) / s;
+    } else if (m00 >= m11 && m00 >= m22) {
+        const double s = sqrt(1.0 + m00 - m11 - m22) * 2.0;
+        q[0] = (m21 - m12) / s; q[1] = 0.25 * s; q[2] = (m01 + m10) / s; q[3] = (m02 + m20) / s;
+    } else if (m11 >= m22) {
+        const double s = sqrt(1.0 + m11 - m00 - m22) * 2.0;
+        q[0] = (m02 - m20) / s; q[1] = (m01 + m10) / s; q[2] = 0.25 * s; q[3] = (m12 + m21) / s;
+    } else {
+        const double s = sqrt(1.0 + m22 - m00 - m11) * 2.0;
+        q[0] = (m10 - m01) / s; q[1] = (m02 + m20) / s; q[2] = (m12 + m21) / s; q[3] = 0.25 * s;
+    }
+    const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int a = 0; a < 4; ++a) q[a] /= n;
+    const double t0 = T[3], t1 = T[7], t2 = T[11];
+    // (0, t) q_r / 2
+    const double d[4] = {0.5 * (-t0 * q[1] - t1 * q[2] - t2 * q[3]),
+                         0.5 * (t0 * q[0] + t1 * q[3] - t2 * q[2]),
+                         0.5 * (t1 * q[0] + t2 * q[1] - t0 * q[3]),
+                         0.5 * (t2 * q[0] + t0 * q[2] - t1 * q[1])};
+    float4 *out = reinterpret_cast<float4 *>(node_dq) + 2 * (size_t)k;
+    out[0] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+    out[1] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)d[3]);
+}
+
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1364,6 +1852,37 @@ void launch_splat_records(const float *vals, int vdim, int n, const int *rec_slo
 void launch_slice_out(const float4 *Q, int m, float s1, float s2, float s3, Table t, int vdim,
                       float *out, int *flags, cudaStream_t s) {
     k_slice_out<<<grid_for(m, 4096), kBlock, 0, s>>>(Q, m, s1, s2, s3, t, vdim, out, flags);
+}
+
+void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t s) {
+    if (a.S <= 0) return;
+    const int grid = (a.S + kBlock / 32 - 1) / (kBlock / 32);
+    if (pt2pl)
+        k_ng_points<true><<<grid, kBlock, 0, s>>>(a, warp_only);
+    else
+        k_ng_points<false><<<grid, kBlock, 0, s>>>(a, warp_only);
+}
+
+void launch_ng_edges(const NgEdges &a, cudaStream_t s) {
+    if (a.E <= 0) return;
+    k_ng_edges<<<(a.E + kBlock - 1) / kBlock, kBlock, 0, s>>>(a);
+}
+
+void launch_ng_pcg_init(const NgPcg &a, cudaStream_t s) {
+    k_ng_pcg_init<<<(a.K + kBlock - 1) / kBlock, kBlock, 0, s>>>(a);
+}
+
+void launch_ng_pcg_spmv(const NgPcg &a, cudaStream_t s) {
+    k_ng_pcg_spmv<<<(a.K + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(a);
+}
+
+void launch_ng_pcg_update(const NgPcg &a, cudaStream_t s) {
+    k_ng_pcg_update<<<(a.K + kBlock - 1) / kBlock, kBlock, 0, s>>>(a);
+}
+
+void launch_ng_update(int K, const double *dx, double *node_T, float *node_dq, double *twist2,
+                      cudaStream_t s) {
+    k_ng_update<<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(K, dx, node_T, node_dq, twist2);
 }
 
 void launch_vertices(Table t, int vdim, int *keys_out, float *vals_out, int *count,

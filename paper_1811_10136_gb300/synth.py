@@ -403,6 +403,8 @@ class NodeGraphPair:
     Y: np.ndarray            # (N, 4) observation: the surface resampled and deformed
     Yn: np.ndarray           # (N, 4) observation normals
     X_true: np.ndarray       # (M, 3) the model points under the true deformation
+    Xn_true: np.ndarray      # (M, 3) the surface normals there (tangential motion is unobservable
+                             # by point-to-plane residuals; the normal component of an error is)
     meta: dict = field(default_factory=dict)
 
 
@@ -484,7 +486,7 @@ def nodegraph_pair(seed: int, W: int = 640, H: int = 480, n_nodes: int = 1000, n
     field's Jacobian.  X_true: the model points under the same field."""
     rng = np.random.default_rng(seed)
     surface = _height_field(rng, n_bumps)
-    Pm, _ = surface(*_grid(W, H, 0.0))
+    Pm, Nm = surface(*_grid(W, H, 0.0))
     Po, No = surface(*_grid(W, H, 0.5))
     centres = rng.uniform([-0.4, -0.3, -0.05], [0.4, 0.3, 0.05], size=(6, 3))
     widths = rng.uniform(0.1, 0.25, 6)
@@ -503,19 +505,21 @@ def nodegraph_pair(seed: int, W: int = 640, H: int = 480, n_nodes: int = 1000, n
     d_m, _ = field_at(Pm)
     scale = max_disp / np.linalg.norm(d_m, axis=1).max()
     amps *= scale
-    d_m, _ = field_at(Pm)
+    d_m, J_m = field_at(Pm)
     d_o, J_o = field_at(Po)
     Yp = Po + d_o + rng.normal(scale=noise, size=Po.shape)
     F = np.eye(3)[None] + J_o
     Yn = np.einsum("nji,nj->ni", np.linalg.inv(F), No)          # (I + grad d)^-T n
     Yn /= np.linalg.norm(Yn, axis=1, keepdims=True)
+    Xn = np.einsum("nji,nj->ni", np.linalg.inv(np.eye(3)[None] + J_m), Nm)
+    Xn /= np.linalg.norm(Xn, axis=1, keepdims=True)
     nodes = Pm[farthest_point_sample(Pm, n_nodes, rng)]
     knn, skw, r = skinning(Pm, nodes)
     deg = min(8, n_nodes - 1)
     _, nb = nearest(nodes, nodes, deg + 1)
     edges = np.stack([np.repeat(np.arange(n_nodes), deg), nb[:, 1:].ravel()], 1).astype(np.int32)
     perm = rng.permutation(Yp.shape[0])
-    return NodeGraphPair(_pad4(Pm), knn, skw, nodes, edges, _pad4(Yp[perm]), _pad4(Yn[perm]), Pm + d_m,
+    return NodeGraphPair(_pad4(Pm), knn, skw, nodes, edges, _pad4(Yp[perm]), _pad4(Yn[perm]), Pm + d_m, Xn,
                          {"workload": "height_field_nodegraph", "seed": seed, "M": int(Pm.shape[0]),
                           "N": int(Yp.shape[0]), "K": n_nodes, "E": int(edges.shape[0]),
                           "skin_radius": r})
