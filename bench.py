@@ -39,6 +39,7 @@ UNIT = "EM iters/s"
 ITERS = 20
 SIGMA0, SIGMA1, W_OUT = 0.04, 0.01, 0.1
 ART_ITERS, ART_SIGMA = 15, 0.01      # articulated workload: 15 EM iterations at sigma 1 cm
+NG_ITERS, NG_PCG, NG_SIGMA, NG_LAMBDA = 10, 20, 0.02, 10.0  # node-graph workload
 SERVE_RATE = 2000.0                   # serving stream: Poisson arrivals per second
 SERVE_BUDGET = 8 << 30                # server device memory (bytes)
 
@@ -56,6 +57,7 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the 16-bit storage lines")
     ap.add_argument("--no-articulated", action="store_true", help="skip the articulated line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-nodegraph", action="store_true", help="skip the node-graph line")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct rendered frames behind the stream")
     return ap.parse_args()
@@ -460,6 +462,39 @@ def run_ours(args):
                 entry["max_joint_diff_deg_vs_f32"] = round(float(np.degrees(np.abs(q - res32).max())), 5)
             articulated[name] = entry
 
+    # ---- node-graph registration (Section 5.2): ~250k points, 1,000 nodes ---
+    nodegraph = None
+    if not args.no_nodegraph:
+        npair = synth.nodegraph_pair(args.seed)
+        ng = fr.NodeGraph(ctx, dev(npair.Xref), torch.from_numpy(npair.knn).cuda(),
+                          torch.from_numpy(npair.skw).cuda(), npair.node_pos, npair.edges)
+        nY, nYn = dev(npair.Y), dev(npair.Yn)
+        nopts = dict(lam=NG_LAMBDA, pcg_iters=NG_PCG, residual=fr.FR_PT2PL, iters=NG_ITERS,
+                     sigma_start=NG_SIGMA, sigma_end=NG_SIGMA, w=W_OUT)
+        nrun = lambda: ng.register(nY, nYn, **nopts)
+        for _ in range(max(1, args.warmup)):
+            nrun()
+        ms, (Tn, rn) = timed_steps(nrun, args.steps)
+        ctx.set_profiling(True)
+        ctx.profile(reset=True)
+        nrun()
+        nprof = ctx.profile(reset=True)
+        ctx.set_profiling(False)
+        Xw = ng.warp(Tn).cpu().numpy()[:, :3]
+        en0 = float(np.abs(np.sum((npair.Xref[:, :3] - npair.X_true) * npair.Xn_true, 1)).mean())
+        en = float(np.abs(np.sum((Xw - npair.X_true) * npair.Xn_true, 1)).mean())
+        per = lambda k: round(nprof[k][1] / max(1, nprof[k][0]), 4)
+        nodegraph = {"workload": "height_field_640x480_nodegraph", "M": int(npair.Xref.shape[0]),
+                     "N": int(npair.Y.shape[0]), "K": int(npair.node_pos.shape[0]),
+                     "E": int(npair.edges.shape[0]), "em_iters": NG_ITERS, "pcg_iters": NG_PCG,
+                     "sigma": NG_SIGMA, "lambda": NG_LAMBDA,
+                     "value": round(NG_ITERS * args.steps / (sum(ms) / 1000.0), 1), "unit": UNIT,
+                     "ms_per_registration": round(statistics.mean(ms), 4),
+                     "e_step_assembly_ms_per_iter": per("ng_assemble"),
+                     "pcg_update_ms_per_iter": per("ng_solve"), "build_ms": per("build"),
+                     "normal_err_mm": {"before": round(en0 * 1e3, 4), "after": round(en * 1e3, 4)}}
+        ng.close()
+
     # ---- serving: Poisson stream through fr_server vs the plain path ---------
     serving = None if args.no_serving else run_serving(ctx, args)
 
@@ -510,6 +545,7 @@ def run_ours(args):
             "precision": precision,
             "articulated": articulated,
             "serving": serving,
+            "nodegraph": nodegraph,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

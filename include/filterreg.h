@@ -102,8 +102,14 @@ typedef struct {
 
 /* Kernel classes of the per-kernel profile. */
 /* FR_K_CONVERT: a launch that only converts (and builds) ahead of the first
- * step under 16-bit storage; later conversions run inside FR_K_STEP launches. */
-enum { FR_K_CLEAR = 0, FR_K_BUILD = 1, FR_K_BLUR = 2, FR_K_STEP = 3, FR_K_CONVERT = 4, FR_K_CLASSES = 5 };
+ * step under 16-bit storage; later conversions run inside FR_K_STEP launches.
+ * FR_K_NG_ASSEMBLE / FR_K_NG_SOLVE: a node-graph iteration's E step with the
+ * assembly of A and g (point and edge kernels), and its PCG solve with the
+ * node update (timed as spans of launches). */
+enum {
+    FR_K_CLEAR = 0, FR_K_BUILD = 1, FR_K_BLUR = 2, FR_K_STEP = 3, FR_K_CONVERT = 4,
+    FR_K_NG_ASSEMBLE = 5, FR_K_NG_SOLVE = 6, FR_K_CLASSES = 7
+};
 typedef struct {
     int64_t launches[FR_K_CLASSES]; /* kernels of each class timed since the last reset */
     double total_ms[FR_K_CLASSES];  /* their summed durations (CUDA events) */

@@ -41,7 +41,7 @@ EXPORTED = [
     "fr_register_nodegraph", "fr_nodegraph_system", "fr_nodegraph_warp",
 ]
 FR_NOALLOC_MAX_OBS = 8192
-KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert")
+KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert", "ng_assemble", "ng_solve")
 
 
 class FilterRegError(RuntimeError):
@@ -107,7 +107,7 @@ class fr_batch_item(ctypes.Structure):
 
 
 class fr_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 5), ("total_ms", ctypes.c_double * 5)]
+    _fields_ = [("launches", ctypes.c_int64 * 7), ("total_ms", ctypes.c_double * 7)]
 
 
 _vp = ctypes.c_void_p

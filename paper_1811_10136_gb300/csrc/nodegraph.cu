@@ -257,6 +257,28 @@ FR_API fr_status fr_nodegraph_destroy(fr_nodegraph *g) {
 
 namespace {
 
+// With profiling on, event pairs bracket spans of launches (one class each).
+struct Spans {
+    fr_ctx *ctx;
+    int n = 0;
+    void begin(int cls) {
+        if (!ctx->profiling) return;
+        while (ctx->events.size() < 2 * (size_t)(n + 1)) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ctx->events.push_back(e);
+        }
+        if (ctx->event_class.size() < (size_t)(n + 1)) ctx->event_class.resize(n + 1);
+        ctx->event_class[n] = cls;
+        cudaEventRecord(ctx->events[2 * n], ctx->stream);
+    }
+    void end() {
+        if (!ctx->profiling) return;
+        cudaEventRecord(ctx->events[2 * n + 1], ctx->stream);
+        ++n;
+    }
+};
+
 struct NgRun {
     int pt2pl = 0, iters = 0, pcg_iters = 0;
     double lambda = 0.0;
@@ -278,8 +300,9 @@ fr_status ng_validate(fr_ctx *ctx, const fr_nodegraph *g, const float *d_Y, cons
 }
 
 // The E step and assembly of iteration `it` at the current node poses.
-void ng_assemble(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Table t, int it) {
+void ng_assemble(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Table t, int it, Spans &sp) {
     cudaStream_t s = ctx->stream;
+    sp.begin(FR_K_NG_ASSEMBLE);
     cudaMemsetAsync(g->blocks, 0, (size_t)g->nnzb * 36 * sizeof(float), s);
     cudaMemsetAsync(g->g, 0, 6 * (size_t)g->K * sizeof(float), s);
     cudaMemsetAsync(g->stats, 0, 4 * sizeof(double), s);
@@ -315,11 +338,13 @@ void ng_assemble(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Table t, int it
     Ed.g = g->g;
     Ed.stats = g->stats;
     launch_ng_edges(Ed, s);
+    sp.end();
     ctx->launches += 2;
 }
 
-void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run) {
+void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Spans &sp) {
     cudaStream_t s = ctx->stream;
+    sp.begin(FR_K_NG_SOLVE);
     NgPcg L{};
     L.K = g->K;
     L.row_ptr = g->row_ptr;
@@ -344,6 +369,7 @@ void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run) {
         launch_ng_pcg_update(L, s);
     }
     launch_ng_update(g->K, g->x, g->node_T, g->node_dq, g->stats + 2, s);
+    sp.end();
     ctx->launches += 2 + 2 * run.pcg_iters;
 }
 
@@ -378,9 +404,11 @@ fr_status ng_run(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_
     FR_CUDA(ctx, copy_async(ctx, g->node_T, node_T, (size_t)g->K * 16 * sizeof(double), cudaMemcpyHostToDevice));
     launch_ng_update(g->K, nullptr, g->node_T, g->node_dq, nullptr, s);
     ++ctx->launches;
+    Spans sp{ctx};
     // lattice of iteration 0, rebuilt into the other table whenever sigma changes
     int cur = 0, cur_build = 0;
     {
+        sp.begin(FR_K_BUILD);
         IterLaunch b{};
         b.job = ctx->d_job;
         b.ip = ctx->d_ip;
@@ -390,6 +418,7 @@ fr_status ng_run(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_
         b.build_it = 0;
         b.gb = blocks_for(ctx, N, 8);
         launch_em_iter(run.pt2pl, 0, b, s, FR_FP32);
+        sp.end();
         ++ctx->launches;
     }
     for (int it = 0; it < iters; ++it) {
@@ -407,11 +436,13 @@ fr_status ng_run(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_
             b.build_list = ctx->lists[cur];
             b.build_it = it;
             b.gb = blocks_for(ctx, N, 8);
+            sp.begin(FR_K_BUILD);
             launch_em_iter(run.pt2pl, 0, b, s, FR_FP32);
+            sp.end();
             ctx->launches += 2;
         }
-        ng_assemble(ctx, g, run, tab[cur], it);
-        if (run.solve) ng_solve_update(ctx, g, run);
+        ng_assemble(ctx, g, run, tab[cur], it, sp);
+        if (run.solve) ng_solve_update(ctx, g, run, sp);
     }
     {
         int *l = ctx->lists[cur];
@@ -437,6 +468,7 @@ fr_status ng_run(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_
     if (run.solve)
         FR_CUDA(ctx, cudaMemcpyAsync(hT.data(), g->node_T, hT.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     FR_CUDA(ctx, cudaStreamSynchronize(s));
+    if (sp.n) collect_profile(ctx, sp.n);
     FR_TRY(check_flags(ctx, hs->flags));
     if (run.solve) std::copy(hT.begin(), hT.end(), node_T);
     if (!run.solve) {
