@@ -390,7 +390,7 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
         for (int k = 0; k < kD; ++k) {
             key[k] = valid ? sx.key[k] : kEmpty;
             const unsigned long long prev = __shfl_up_sync(kFull, key[k], 1);
-            const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != key[k]);
+            const unsigned heads = __ballot_sync(kFull, (lane & 7) == 0 || prev != key[k]);
             const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
             const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
             const float b = valid ? sx.b[k] : 0.0f;
@@ -405,7 +405,7 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
                 v[6] = b * n.z;
             }
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
+            for (int o = 1; o < 8; o <<= 1) {
 #pragma unroll
                 for (int c = 0; c < kCh; ++c) {
                     const float t = __shfl_up_sync(kFull, v[c], o);

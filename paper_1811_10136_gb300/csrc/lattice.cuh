@@ -44,12 +44,13 @@ __device__ __forceinline__ int unpack_coord(unsigned long long key, int j) {
 
 // 64-bit mix (xor-shift-multiply finaliser) -> table slot.
 __device__ __forceinline__ uint32_t slot_of(unsigned long long k, uint32_t mask) {
-    k ^= k >> 31;
-    k *= 0x7fb5d329728ea185ull;
-    k ^= k >> 27;
-    k *= 0x81dadef4bc2dd44dull;
-    k ^= k >> 33;
-    return (uint32_t)k & mask;
+    uint32_t h = (uint32_t)k * 0x9E3779B1u ^ (uint32_t)(k >> 32) * 0x85EBCA77u;
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    h *= 0x846ca68bu;
+    h ^= h >> 16;
+    return h & mask;
 }
 
 // Elevated coordinates, ranks and remainder-0 point of position p under the
