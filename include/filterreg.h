@@ -442,7 +442,7 @@ FR_API fr_status fr_server_destroy(fr_server *srv);
  * double[16]) -- written to d_out (float, M x 4 or M x 7) on `cuda_stream`
  * (a cudaStream_t, NULL = legacy default) of the current device.  It needs no
  * context and allocates nothing: the hash table lives in a fixed scratch
- * array compiled into the library (about 2.8 MB on every device that loads
+ * array compiled into the library (about 4.5 MB on every device that loads
  * it, held until the process exits).  The first call on a device finds that
  * array's device address and empties it (synchronising the stream once); it
  * should come before any stream capture.  Every call shares the array and

@@ -31,28 +31,21 @@ void free_tables(fr_ctx *ctx) {
     for (int i = 0; i < kMaxTables; ++i) {
         Table &t = ctx->tables[i];
         cudaFree(t.keys);
-        cudaFree(t.v0);
-        cudaFree(t.v1);
-        cudaFree(t.cv);
         cudaFree(ctx->lists[i]);
         ctx->lists[i] = nullptr;
         t = Table{};
     }
-    cudaFree(ctx->blur0);
-    cudaFree(ctx->blur1);
-    ctx->blur0 = ctx->blur1 = nullptr;
+    cudaFree(ctx->blur);
+    ctx->blur = nullptr;
     ctx->table_cap = 0;
 }
 
 fr_status alloc_table(fr_ctx *ctx, int i, uint32_t cap) {
     Table &t = ctx->tables[i];
     FR_CUDA(ctx, dev_alloc(&ctx->lists[i], cap));
-    FR_CUDA(ctx, dev_alloc(&t.keys, cap));
-    FR_CUDA(ctx, dev_alloc(&t.v0, cap));
-    FR_CUDA(ctx, dev_alloc(&t.v1, cap));
-    FR_CUDA(ctx, cudaMemsetAsync(t.keys, 0xFF, cap * sizeof(unsigned long long), ctx->stream));
-    FR_CUDA(ctx, cudaMemsetAsync(t.v0, 0, cap * sizeof(float4), ctx->stream));
-    FR_CUDA(ctx, cudaMemsetAsync(t.v1, 0, cap * sizeof(float4), ctx->stream));
+    FR_CUDA(ctx, dev_alloc(&t.keys, (size_t)cap * kRecWords));
+    FR_CUDA(ctx, cudaMemsetAsync(t.keys, 0, table_bytes(cap), ctx->stream));
+    t.vals = 8;
     t.mask = cap - 1;
     t.max_probe = cap;
     return FR_OK;
@@ -72,16 +65,13 @@ fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur, bool compact) {
         ctx->ws_gen++;
         drop_graphs(ctx);
     }
-    if (compact && !ctx->tables[3].keys) {
+    if (compact && !ctx->tables[3].keys) {  // 16-bit storage: a fourth table in rotation
         FR_TRY(alloc_table(ctx, 3, ctx->table_cap));
-        // written for every listed vertex before any read: no clearing needed
-        for (int i = 0; i < kMaxTables; ++i) FR_CUDA(ctx, dev_alloc(&ctx->tables[i].cv, ctx->table_cap));
         ctx->ws_gen++;
         drop_graphs(ctx);
     }
-    if (blur && !ctx->blur0) {
-        FR_CUDA(ctx, dev_alloc(&ctx->blur0, ctx->table_cap));
-        FR_CUDA(ctx, dev_alloc(&ctx->blur1, ctx->table_cap));
+    if (blur && !ctx->blur) {
+        FR_CUDA(ctx, dev_alloc(&ctx->blur, (size_t)ctx->table_cap * kRecWords));
         ctx->ws_gen++;
         drop_graphs(ctx);
     }
@@ -209,8 +199,7 @@ struct Issuer {
 
 void issue_blur(fr_ctx *ctx, Issuer &k, const Plan &p, const Table &t) {
     Table a = t, b = t;
-    b.v0 = ctx->blur0;
-    b.v1 = ctx->blur1;
+    b.keys = ctx->blur;
     for (int dir = 0; dir < 4; ++dir)
         k(FR_K_BLUR, [&] {
             if (dir % 2 == 0)
@@ -614,21 +603,17 @@ FR_API fr_status fr_lattice_build(fr_ctx *ctx, const float *d_pos, int64_t n, fl
     lat->n = (int)n;
     feature_scales(sigma, lat->scale);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dev_alloc(&lat->keys, lat->cap);
-    if (e == cudaSuccess) e = dev_alloc(&lat->v0, lat->cap);
-    if (e == cudaSuccess) e = dev_alloc(&lat->v1, lat->cap);
+    if (e == cudaSuccess) e = dev_alloc(&lat->keys, (size_t)lat->cap * kRecWords);
     if (e == cudaSuccess) e = dev_alloc(&lat->rec_slot, (size_t)n * 4);
     if (e == cudaSuccess) e = dev_alloc(&lat->rec_w, (size_t)n * 4);
     if (e == cudaSuccess) e = dev_alloc(&lat->counters, 4);
-    if (e == cudaSuccess) e = cudaMemsetAsync(lat->keys, 0xFF, lat->cap * sizeof(unsigned long long), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(lat->v0, 0, lat->cap * sizeof(float4), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(lat->v1, 0, lat->cap * sizeof(float4), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lat->keys, 0, table_bytes(lat->cap), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(lat->counters, 0, 4 * sizeof(int), ctx->stream);
     if (e != cudaSuccess) {
         fr_lattice_destroy(ctx, lat);
         return ctx->cuda(e, "fr_lattice_build allocation");
     }
-    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
+    Table t{lat->keys, lat->cap - 1, lat->cap, lat->vdim > 4 ? 8 : 4};
     launch_build_records((const float4 *)d_pos, (int)n, lat->scale[0], lat->scale[1], lat->scale[2], t,
                          lat->rec_slot, lat->rec_w, lat->counters, ctx->stream);
     ctx->launches += 1;
@@ -656,9 +641,8 @@ FR_API fr_status fr_lattice_splat(fr_ctx *ctx, fr_lattice *lat, const float *d_v
     if (val_dim < 1 || val_dim > 8) return ctx->fail(FR_EINVAL, "val_dim must be 1..8");
     cudaSetDevice(ctx->device);
     lat->vdim = val_dim;
-    FR_CUDA(ctx, cudaMemsetAsync(lat->v0, 0, lat->cap * sizeof(float4), ctx->stream));
-    FR_CUDA(ctx, cudaMemsetAsync(lat->v1, 0, lat->cap * sizeof(float4), ctx->stream));
-    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
+    Table t{lat->keys, lat->cap - 1, lat->cap, 8};
+    launch_zero_values(t, blocks_for(ctx, lat->cap, 16), ctx->stream);
     launch_splat_records(d_vals, val_dim, lat->n, lat->rec_slot, lat->rec_w, t, ctx->stream);
     ctx->launches += 1;
     FR_CUDA(ctx, cudaGetLastError());
@@ -669,12 +653,9 @@ FR_API fr_status fr_lattice_splat(fr_ctx *ctx, fr_lattice *lat, const float *d_v
 FR_API fr_status fr_lattice_blur(fr_ctx *ctx, fr_lattice *lat) {
     if (!ctx || !lat) return FR_EINVAL;
     cudaSetDevice(ctx->device);
-    if (!lat->t0) {
-        FR_CUDA(ctx, dev_alloc(&lat->t0, lat->cap));
-        FR_CUDA(ctx, dev_alloc(&lat->t1, lat->cap));
-    }
-    Table a{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
-    Table b{lat->keys, lat->t0, lat->t1, lat->cap - 1, lat->cap};
+    if (!lat->tkeys) FR_CUDA(ctx, dev_alloc(&lat->tkeys, (size_t)lat->cap * kRecWords));
+    Table a{lat->keys, lat->cap - 1, lat->cap, lat->vdim > 4 ? 8 : 4};
+    Table b{lat->tkeys, lat->cap - 1, lat->cap, lat->vdim > 4 ? 8 : 4};
     int grid = blocks_for(ctx, lat->cap, 16);
     for (int dir = 0; dir < 4; ++dir) {
         if (dir % 2 == 0)
@@ -695,7 +676,7 @@ FR_API fr_status fr_lattice_slice(fr_ctx *ctx, const fr_lattice *lat, const floa
     if (!d_out) return ctx->fail(FR_EINVAL, "d_out is NULL");
     if (lat->vdim < 1) return ctx->fail(FR_EINVAL, "lattice has no values (call fr_lattice_splat)");
     cudaSetDevice(ctx->device);
-    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
+    Table t{lat->keys, lat->cap - 1, lat->cap, lat->vdim > 4 ? 8 : 4};
     FR_CUDA(ctx, cudaMemsetAsync(lat->counters + 1, 0, sizeof(int), ctx->stream));
     launch_slice_out((const float4 *)d_query, (int)m, lat->scale[0], lat->scale[1], lat->scale[2], t,
                      lat->vdim, d_out, lat->counters + 1, ctx->stream);
@@ -712,7 +693,7 @@ FR_API fr_status fr_lattice_vertices(fr_ctx *ctx, const fr_lattice *lat, int32_t
     if (!ctx || !lat) return FR_EINVAL;
     if (!d_keys || !aligned16(d_keys)) return ctx->fail(FR_EINVAL, "d_keys must be a 16-byte aligned buffer");
     cudaSetDevice(ctx->device);
-    Table t{lat->keys, lat->v0, lat->v1, lat->cap - 1, lat->cap};
+    Table t{lat->keys, lat->cap - 1, lat->cap, lat->vdim > 4 ? 8 : 4};
     FR_CUDA(ctx, cudaMemsetAsync(lat->counters + 2, 0, sizeof(int), ctx->stream));
     launch_vertices(t, lat->vdim > 0 ? lat->vdim : 1, d_keys, lat->vdim > 0 ? d_vals : nullptr,
                     lat->counters + 2, ctx->stream);
@@ -741,10 +722,7 @@ FR_API fr_status fr_lattice_destroy(fr_ctx *ctx, fr_lattice *lat) {
         cudaStreamSynchronize(ctx->stream);
     }
     cudaFree(lat->keys);
-    cudaFree(lat->v0);
-    cudaFree(lat->v1);
-    cudaFree(lat->t0);
-    cudaFree(lat->t1);
+    cudaFree(lat->tkeys);
     cudaFree(lat->rec_slot);
     cudaFree(lat->rec_w);
     cudaFree(lat->counters);
@@ -817,8 +795,7 @@ static fr_status estep_impl(fr_ctx *ctx, const float *d_X, int64_t M, const floa
     }
     if (blur) {
         Table a = t, c = t;
-        c.v0 = ctx->blur0;
-        c.v1 = ctx->blur1;
+        c.keys = ctx->blur;
         const int gb = blocks_for(ctx, cap, 8);
         for (int dir = 0; dir < 4; ++dir) {
             if (dir % 2 == 0)

@@ -23,10 +23,8 @@ using namespace fr;
 namespace fr {
 
 struct BatchWorkspace {
-    unsigned long long *keys = nullptr;  // key arena, all empty between calls
-    float4 *v0 = nullptr, *v1 = nullptr; // value arenas, zero between calls
-    size_t slots_cap = 0;                // table slots in each arena
-    uint4 *cv = nullptr;                 // compact values (16-bit storage), slots_cap slots
+    unsigned long long *keys = nullptr;  // slot-record arena, all free (zero) between calls
+    size_t slots_cap = 0;                // table slots in the arena
     unsigned char *misc = nullptr;       // descriptors, lists, partials
     size_t misc_cap = 0;
     unsigned char *h_up = nullptr;       // pinned staging of the uploaded descriptors
@@ -41,9 +39,6 @@ void free_batch_workspace(fr_ctx *ctx) {
     BatchWorkspace *w = ctx->batch;
     if (!w) return;
     cudaFree(w->keys);
-    cudaFree(w->v0);
-    cudaFree(w->v1);
-    cudaFree(w->cv);
     cudaFree(w->misc);
     cudaFree(w->stage);
     cudaFreeHost(w->h_up);
@@ -68,22 +63,13 @@ fr_status ensure_arenas(fr_ctx *ctx, size_t slots, size_t misc, size_t up, size_
         const size_t cap = std::max(slots, w->slots_cap * 3 / 2);
         cudaStreamSynchronize(ctx->stream);
         cudaFree(w->keys);
-        cudaFree(w->v0);
-        cudaFree(w->v1);
-        cudaFree(w->cv);
         w->keys = nullptr;
-        w->v0 = w->v1 = nullptr;
-        w->cv = nullptr;
         w->slots_cap = 0;
-        FR_CUDA(ctx, dev_alloc(&w->keys, cap));
-        FR_CUDA(ctx, dev_alloc(&w->v0, cap));
-        FR_CUDA(ctx, dev_alloc(&w->v1, cap));
-        FR_CUDA(ctx, cudaMemsetAsync(w->keys, 0xFF, cap * sizeof(unsigned long long), ctx->stream));
-        FR_CUDA(ctx, cudaMemsetAsync(w->v0, 0, cap * sizeof(float4), ctx->stream));
-        FR_CUDA(ctx, cudaMemsetAsync(w->v1, 0, cap * sizeof(float4), ctx->stream));
+        FR_CUDA(ctx, dev_alloc(&w->keys, cap * kRecWords));
+        FR_CUDA(ctx, cudaMemsetAsync(w->keys, 0, table_bytes(cap), ctx->stream));
         w->slots_cap = cap;
     }
-    if (compact && !w->cv) FR_CUDA(ctx, dev_alloc(&w->cv, w->slots_cap));
+
     if (misc > w->misc_cap) {
         const size_t cap = std::max(misc, w->misc_cap * 3 / 2);
         cudaStreamSynchronize(ctx->stream);
@@ -217,8 +203,8 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
         s.partials = (float2 *)(D + ip[b].part_off);
         for (int t = 0; t < ntab; ++t) {
             const size_t base = ip[b].tab_off + (size_t)t * ip[b].cap;
-            s.tab[t] = Table{w->keys + base, w->v0 + base, pt2pl ? w->v1 + base : nullptr, ip[b].cap - 1,
-                             table_probe_limit(ip[b].cap, safe), w->cv ? w->cv + base : nullptr};
+            s.tab[t] = Table{w->keys + base * kRecWords, ip[b].cap - 1, table_probe_limit(ip[b].cap, safe),
+                             pt2pl ? 8 : 4};
             s.list[t] = (int *)(D + ip[b].list_off) + (size_t)t * ip[b].cap;
         }
     }

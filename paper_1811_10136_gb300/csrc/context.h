@@ -76,8 +76,8 @@ struct fr_lattice {
     int n = 0;
     int vdim = 0;
     float scale[3] = {0, 0, 0};
-    unsigned long long *keys = nullptr;
-    float4 *v0 = nullptr, *v1 = nullptr, *t0 = nullptr, *t1 = nullptr;
+    unsigned long long *keys = nullptr;   // slot records (see Table)
+    unsigned long long *tkeys = nullptr;  // blur ping-pong records
     int *rec_slot = nullptr;
     float *rec_w = nullptr;
     int *counters = nullptr;  // [0] vertices, [1] flags, [2] scratch count
@@ -99,7 +99,7 @@ struct fr_ctx {
     uint32_t table_cap = 0;
     fr::Table tables[fr::kMaxTables] = {};  // 3 with float32 storage, 4 with 16-bit storage
     int *lists[fr::kMaxTables] = {};        // slots claimed by each table's last build
-    float4 *blur0 = nullptr, *blur1 = nullptr;
+    unsigned long long *blur = nullptr;   // blur ping-pong records (table_cap slots)
     float2 *partials = nullptr;
     int partial_rows = 0;
     fr::DeviceState *d_state = nullptr;

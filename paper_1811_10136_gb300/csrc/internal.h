@@ -57,20 +57,41 @@ struct DeviceState {
     long long nvert_total; // vertices summed over this call's builds
 };
 
-// A lattice hash table: keys plus up to 8 float values per slot, stored as
-// two float4 planes (channels 0..3 and 4..7).
+// A lattice hash table: a power-of-two array of 64-byte slot records, two
+// 32-byte sectors each --
+//   [key (8 B), unused (8 B), 16-bit record (16 B, 16-bit storage modes)]
+//   [v0 = channels 0..3 (float4), v1 = channels 4..7 (float4)]
+// -- so that a lookup, its values and a clear touch one line.  A free slot is
+// all zero: kEmpty = 0 and every valid key has bit 63 set, so clearing a slot
+// is zeroing its record.
+constexpr int kRecWords = 8;  // 64-bit words per record
+constexpr unsigned long long kEmpty = 0ull;
+
 struct Table {
-    unsigned long long *keys;
-    float4 *v0;
-    float4 *v1;
-    uint32_t mask;         // capacity - 1 (capacity a power of two)
-    uint32_t max_probe;    // an insert that probes this many taken slots reports overflow
-    uint4 *cv;             // compact values (16-bit storage modes), one 16-byte record per slot
+    unsigned long long *keys;  // slot s: keys + kRecWords * s
+    uint32_t mask;             // capacity - 1 (capacity a power of two)
+    uint32_t max_probe;        // an insert that probes this many taken slots reports overflow
+    int vals;                  // value channels kept: 4 or 8
 };
 
-// Lattice value storage of the slice (fr_storage): float32 planes, or 16-byte
-// records [W, sum b (y - p_v) (3), sum b n (3), 0] in bfloat16 / half, made
-// from the float32 sums once a build completes (p_v: the vertex's position).
+__host__ __device__ __forceinline__ unsigned long long *rec_key(unsigned long long *keys, uint32_t s) {
+    return keys + (size_t)s * kRecWords;
+}
+__host__ __device__ __forceinline__ uint4 *rec_cv(unsigned long long *keys, uint32_t s) {
+    return reinterpret_cast<uint4 *>(keys + (size_t)s * kRecWords + 2);
+}
+__host__ __device__ __forceinline__ float4 *rec_v0(unsigned long long *keys, uint32_t s) {
+    return reinterpret_cast<float4 *>(keys + (size_t)s * kRecWords + 4);
+}
+__host__ __device__ __forceinline__ float4 *rec_v1(unsigned long long *keys, uint32_t s) {
+    return reinterpret_cast<float4 *>(keys + (size_t)s * kRecWords + 6);
+}
+// Bytes of a table of `slots` records.
+inline size_t table_bytes(size_t slots) { return slots * kRecWords * sizeof(unsigned long long); }
+
+// Lattice value storage of the slice (fr_storage): the float32 sums, or the
+// 16-byte record [W, sum b (y - p_v) (3), sum b n (3), 0] in bfloat16 / half,
+// made from them once a build completes (p_v: the vertex's position).
 constexpr int kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2;
 
 // Table sizing.  A point creates at most 4 vertices, so 6 N slots can never
@@ -244,6 +265,7 @@ void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
                      int storage);
 void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s, int storage);
 void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s, int storage);
+void launch_zero_values(Table t, int grid, cudaStream_t s);
 void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t s);
 void launch_ng_edges(const NgEdges &a, cudaStream_t s);
 void launch_ng_pcg_init(const NgPcg &a, cudaStream_t s);

@@ -426,8 +426,8 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
                 bad |= kFlagCapacity;
                 continue;
             }
-            atomicAdd(t.v0 + sl[k], make_float4(sum[k][0], sum[k][1], sum[k][2], sum[k][3]));
-            if (PT2PL) atomicAdd(t.v1 + sl[k], make_float4(sum[k][4], sum[k][5], sum[k][6], 0.f));
+            atomicAdd(rec_v0(t.keys, sl[k]), make_float4(sum[k][0], sum[k][1], sum[k][2], sum[k][3]));
+            if (PT2PL) atomicAdd(rec_v1(t.keys, sl[k]), make_float4(sum[k][4], sum[k][5], sum[k][6], 0.f));
         }
         // Block-wide exclusive prefix of the claimed counts.
         const int cnt = __popc(mask);
@@ -475,21 +475,24 @@ __device__ __forceinline__ void convert_role(Table t, const int *list, const Ite
         const int n = __ldcg(&ipp->nvert);
         for (int e = blk * kBlock + threadIdx.x; e < n; e += nblk * kBlock) {
             const int slot = __ldcg(list + e);
-            const float4 a = __ldcg(t.v0 + slot);
-            const float4 c = PT2PL ? __ldcg(t.v1 + slot) : make_float4(0.f, 0.f, 0.f, 0.f);
-            t.cv[slot] = compact_record<ST>(a, c, vertex_position(__ldcg(t.keys + slot), ip), ip.vscale);
+            const float4 a = __ldcg(rec_v0(t.keys, slot));
+            const float4 c = PT2PL ? __ldcg(rec_v1(t.keys, slot)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            *rec_cv(t.keys, slot) =
+                compact_record<ST>(a, c, vertex_position(__ldcg(rec_key(t.keys, slot)), ip), ip.vscale);
         }
     }
 }
 
-// Clear: free the slots a build listed (keys to empty, values to zero).
+// Clear: free the slots a build listed by zeroing their records (two whole
+// 32-byte sectors: key, values and 16-bit record).
 __device__ __forceinline__ void clear_role(Table t, const int *list, int n, int blk, int nblk) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int e = blk * kBlock + threadIdx.x; e < n; e += nblk * kBlock) {
-        const int s = __ldcg(list + e);
-        t.keys[s] = kEmpty;
-        t.v0[s] = z;
-        if (t.v1) t.v1[s] = z;
+        float4 *r = reinterpret_cast<float4 *>(rec_key(t.keys, (uint32_t)__ldcg(list + e)));
+        r[0] = z;
+        r[1] = z;
+        r[2] = z;
+        r[3] = z;
     }
 }
 
@@ -513,7 +516,7 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
         // One 16-byte record per vertex; positions restored in float32.
         uint4 r[kD];
 #pragma unroll
-        for (int k = 0; k < kD; ++k) r[k] = slot[k] >= 0 ? __ldg(t.cv + slot[k]) : make_uint4(0, 0, 0, 0);
+        for (int k = 0; k < kD; ++k) r[k] = slot[k] >= 0 ? __ldg(rec_cv(t.keys, slot[k])) : make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
             if (slot[k] < 0) continue;
@@ -545,8 +548,8 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
         float4 a[kD], c[kD];
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
-            a[k] = slot[k] >= 0 ? __ldg(t.v0 + slot[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (PT2PL) c[k] = slot[k] >= 0 ? __ldg(t.v1 + slot[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            a[k] = slot[k] >= 0 ? __ldg(rec_v0(t.keys, slot[k])) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (PT2PL) c[k] = slot[k] >= 0 ? __ldg(rec_v1(t.keys, slot[k])) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
@@ -1074,35 +1077,50 @@ __global__ void k_clear_lists(ClearSet c, int n) {
     clear_role(c.t[which], c.list[which], __ldcg(c.count[which]), blockIdx.x % per, per);
 }
 
+// One blur pass writes every record of `out` (a separate record array of at
+// least in.mask + 1 slots): the key copied (free slots stay free) and the
+// values v + (v(n-) + v(n+)) / 2 along axis `dir`, missing neighbours 0.
 __global__ void k_blur_pass(Table in, Table out, int dir, const DeviceState *st) {
     if (st && st->done) return;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t s = gtid(); s <= in.mask; s += grid_stride()) {
-        const unsigned long long key = __ldg(in.keys + s);
-        if (key == kEmpty) continue;
+        const unsigned long long key = __ldg(rec_key(in.keys, s));
+        float4 *o = reinterpret_cast<float4 *>(rec_key(out.keys, s));
+        if (key == kEmpty) {
+            o[0] = z;
+            o[1] = z;
+            o[2] = z;
+            o[3] = z;
+            continue;
+        }
         const int sm = find_key(in.keys, in.mask, neighbour_key(key, dir, -1));
         const int sp = find_key(in.keys, in.mask, neighbour_key(key, dir, +1));
-        float4 a = __ldg(in.v0 + s);
+        float4 a = __ldg(rec_v0(in.keys, s));
         if (sm >= 0) {
-            const float4 u = __ldg(in.v0 + sm);
+            const float4 u = __ldg(rec_v0(in.keys, sm));
             a.x += 0.5f * u.x; a.y += 0.5f * u.y; a.z += 0.5f * u.z; a.w += 0.5f * u.w;
         }
         if (sp >= 0) {
-            const float4 u = __ldg(in.v0 + sp);
+            const float4 u = __ldg(rec_v0(in.keys, sp));
             a.x += 0.5f * u.x; a.y += 0.5f * u.y; a.z += 0.5f * u.z; a.w += 0.5f * u.w;
         }
-        out.v0[s] = a;
-        if (in.v1) {
-            float4 c = __ldg(in.v1 + s);
+        float4 c = z;
+        if (in.vals > 4) {
+            c = __ldg(rec_v1(in.keys, s));
             if (sm >= 0) {
-                const float4 u = __ldg(in.v1 + sm);
+                const float4 u = __ldg(rec_v1(in.keys, sm));
                 c.x += 0.5f * u.x; c.y += 0.5f * u.y; c.z += 0.5f * u.z; c.w += 0.5f * u.w;
             }
             if (sp >= 0) {
-                const float4 u = __ldg(in.v1 + sp);
+                const float4 u = __ldg(rec_v1(in.keys, sp));
                 c.x += 0.5f * u.x; c.y += 0.5f * u.y; c.z += 0.5f * u.z; c.w += 0.5f * u.w;
             }
-            out.v1[s] = c;
         }
+        reinterpret_cast<unsigned long long *>(o)[0] = key;
+        reinterpret_cast<unsigned long long *>(o)[1] = 0ull;
+        o[1] = z;
+        o[2] = a;
+        o[3] = c;
     }
 }
 
@@ -1205,8 +1223,8 @@ __global__ void k_splat_records(const float *__restrict__ vals, int vdim, int n,
             const int s = rec_slot[(size_t)i * kD + k];
             if (s < 0) continue;
             const float b = rec_w[(size_t)i * kD + k];
-            atomicAdd(t.v0 + s, make_float4(b * v[0], b * v[1], b * v[2], b * v[3]));
-            if (vdim > 4) atomicAdd(t.v1 + s, make_float4(b * v[4], b * v[5], b * v[6], b * v[7]));
+            atomicAdd(rec_v0(t.keys, s), make_float4(b * v[0], b * v[1], b * v[2], b * v[3]));
+            if (vdim > 4) atomicAdd(rec_v1(t.keys, s), make_float4(b * v[4], b * v[5], b * v[6], b * v[7]));
         }
     }
 }
@@ -1224,10 +1242,10 @@ __global__ void k_slice_out(const float4 *__restrict__ Q, int m, float s1, float
             for (int k = 0; k < kD; ++k) {
                 if (slot[k] < 0) continue;
                 const float b = sx.b[k];
-                const float4 a = __ldg(t.v0 + slot[k]);
+                const float4 a = __ldg(rec_v0(t.keys, slot[k]));
                 acc[0] += b * a.x; acc[1] += b * a.y; acc[2] += b * a.z; acc[3] += b * a.w;
                 if (vdim > 4) {
-                    const float4 c = __ldg(t.v1 + slot[k]);
+                    const float4 c = __ldg(rec_v1(t.keys, slot[k]));
                     acc[4] += b * c.x; acc[5] += b * c.y; acc[6] += b * c.z; acc[7] += b * c.w;
                 }
             }
@@ -1238,9 +1256,19 @@ __global__ void k_slice_out(const float4 *__restrict__ Q, int m, float s1, float
     }
 }
 
+// Zeroes the values (and 16-bit record) of every slot, keeping the keys.
+__global__ void k_zero_values(Table t) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t s = gtid(); s <= t.mask; s += grid_stride()) {
+        *rec_cv(t.keys, s) = make_uint4(0, 0, 0, 0);
+        *rec_v0(t.keys, s) = z;
+        *rec_v1(t.keys, s) = z;
+    }
+}
+
 __global__ void k_vertices(Table t, int vdim, int *keys_out, float *vals_out, int *count) {
     for (uint32_t s = gtid(); s <= t.mask; s += grid_stride()) {
-        const unsigned long long key = t.keys[s];
+        const unsigned long long key = *rec_key(t.keys, s);
         if (key == kEmpty) continue;
         const int o = atomicAdd(count, 1);
         int c[3];
@@ -1248,8 +1276,8 @@ __global__ void k_vertices(Table t, int vdim, int *keys_out, float *vals_out, in
         for (int j = 0; j < 3; ++j) c[j] = unpack_coord(key, j);
         reinterpret_cast<int4 *>(keys_out)[o] = make_int4(c[0], c[1], c[2], -(c[0] + c[1] + c[2]));
         if (vals_out) {
-            const float4 a = t.v0[s];
-            const float4 b = t.v1 ? t.v1[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 a = *rec_v0(t.keys, s);
+            const float4 b = t.vals > 4 ? *rec_v1(t.keys, s) : make_float4(0.f, 0.f, 0.f, 0.f);
             const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
             for (int ch = 0; ch < vdim; ++ch) vals_out[(size_t)o * vdim + ch] = v[ch];
         }
@@ -1883,6 +1911,10 @@ void launch_ng_pcg_update(const NgPcg &a, cudaStream_t s) {
 void launch_ng_update(int K, const double *dx, double *node_T, float *node_dq, double *twist2,
                       cudaStream_t s) {
     k_ng_update<<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(K, dx, node_T, node_dq, twist2);
+}
+
+void launch_zero_values(Table t, int grid, cudaStream_t s) {
+    k_zero_values<<<grid, kBlock, 0, s>>>(t);
 }
 
 void launch_vertices(Table t, int vdim, int *keys_out, float *vals_out, int *count,

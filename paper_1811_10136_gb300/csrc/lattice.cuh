@@ -11,20 +11,22 @@
 // the same operations.
 //
 // The hash table is open addressing with linear probing over a power-of-two
-// array of 64-bit keys (three 21-bit two's-complement coordinates; the fourth
-// is minus their sum).  kEmpty marks a free slot.  Slots are claimed with
-// atomicCAS; values live in float4 arrays indexed by slot and are accumulated
-// with float4 atomics (sm_90+ vector atomics).
+// array of 64-byte slot records (see Table) whose first word is the key:
+// three 21-bit two's-complement coordinates (the fourth is minus their sum)
+// and bit 63 set; kEmpty (0) marks a free slot.  Slots are claimed with
+// atomicCAS; the record's values are accumulated with float4 atomics (sm_90+
+// vector atomics).
 #pragma once
 
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "internal.h"
+
 namespace fr {
 
 constexpr int kD = 4;                      // lattice dimension d + 1
 constexpr float kKeyLimit = 1000000.0f;    // |z_j| bound: keys fit 21-bit fields
-constexpr unsigned long long kEmpty = ~0ull;
 
 struct Simplex {
     unsigned long long key[kD];  // packed vertex keys, vertex k = remainder-k point
@@ -33,7 +35,7 @@ struct Simplex {
 
 // Packs coordinates 0..2 of a vertex key (the 4th is implied by sum = 0).
 __device__ __forceinline__ unsigned long long pack_key(int k0, int k1, int k2) {
-    return (unsigned long long)(k0 & 0x1FFFFF) | ((unsigned long long)(k1 & 0x1FFFFF) << 21) |
+    return (1ull << 63) | (unsigned long long)(k0 & 0x1FFFFF) | ((unsigned long long)(k1 & 0x1FFFFF) << 21) |
            ((unsigned long long)(k2 & 0x1FFFFF) << 42);
 }
 
@@ -146,10 +148,10 @@ __device__ __forceinline__ int insert_key(unsigned long long *keys, uint32_t mas
     uint32_t s = start >= 0 ? (uint32_t)start : slot_of(key, mask);
     claimed = false;
     for (uint32_t p = 0; p < max_probe; ++p) {
-        unsigned long long cur = __ldcg(keys + s);
+        unsigned long long cur = __ldcg(rec_key(keys, s));
         if (cur == key) return (int)s;
         if (cur == kEmpty) {
-            cur = atomicCAS(keys + s, kEmpty, key);
+            cur = atomicCAS(rec_key(keys, s), kEmpty, key);
             if (cur == kEmpty) {
                 claimed = true;
                 return (int)s;
@@ -175,10 +177,10 @@ __device__ __forceinline__ int insert4(unsigned long long *keys, uint32_t mask,
 #pragma unroll
     for (int k = 0; k < kD; ++k) s[k] = slot_of(key[k], mask);
 #pragma unroll
-    for (int k = 0; k < kD; ++k) cur[k] = (active >> k & 1) ? __ldcg(keys + s[k]) : key[k];
+    for (int k = 0; k < kD; ++k) cur[k] = (active >> k & 1) ? __ldcg(rec_key(keys, s[k])) : key[k];
 #pragma unroll
     for (int k = 0; k < kD; ++k)
-        old[k] = ((active >> k & 1) && cur[k] == kEmpty) ? atomicCAS(keys + s[k], kEmpty, key[k])
+        old[k] = ((active >> k & 1) && cur[k] == kEmpty) ? atomicCAS(rec_key(keys, s[k]), kEmpty, key[k])
                                                           : cur[k];
     int claimed = 0;
 #pragma unroll
@@ -206,7 +208,7 @@ __device__ __forceinline__ int find_key(const unsigned long long *__restrict__ k
                                         unsigned long long key) {
     uint32_t s = slot_of(key, mask);
     for (uint32_t p = 0; p <= mask; ++p) {
-        const unsigned long long cur = __ldg(keys + s);
+        const unsigned long long cur = __ldg(rec_key(const_cast<unsigned long long *>(keys), s));
         if (cur == key) return (int)s;
         if (cur == kEmpty) return -1;
         s = (s + 1) & mask;
@@ -223,13 +225,13 @@ __device__ __forceinline__ void find4(const unsigned long long *__restrict__ key
 #pragma unroll
     for (int k = 0; k < kD; ++k) s[k] = slot_of(sx.key[k], mask);
 #pragma unroll
-    for (int k = 0; k < kD; ++k) cur[k] = __ldg(keys + s[k]);
+    for (int k = 0; k < kD; ++k) cur[k] = __ldg(rec_key(const_cast<unsigned long long *>(keys), s[k]));
 #pragma unroll
     for (int k = 0; k < kD; ++k) {
         uint32_t p = 0;
         while (cur[k] != sx.key[k] && cur[k] != kEmpty && p < mask) {
             s[k] = (s[k] + 1) & mask;
-            cur[k] = __ldg(keys + s[k]);
+            cur[k] = __ldg(rec_key(const_cast<unsigned long long *>(keys), s[k]));
             ++p;
         }
         slot[k] = (cur[k] == sx.key[k]) ? (int)s[k] : -1;

@@ -9,7 +9,7 @@
 // caller passes its own input and output buffers; the hash table, the list of
 // claimed slots and two counters live in the file-scope array below.
 //
-// The array costs every GPU that loads the library about 2.8 MB until the
+// The array costs every GPU that loads the library about 4.5 MB until the
 // process exits.  It bounds the observation cloud to FR_NOALLOC_MAX_OBS
 // points (the table has 65,536 slots, at least 6 per possible point, which
 // is more than the at most 4 vertices a point creates).
@@ -31,7 +31,6 @@
 namespace {
 
 using fr::kD;
-using fr::kEmpty;
 using fr::Simplex;
 
 constexpr int kThreads = 256;
@@ -39,10 +38,8 @@ constexpr uint32_t kCap = 65536;  // table slots, a power of two >= 6 * FR_NOALL
 static_assert(kCap >= 6u * FR_NOALLOC_MAX_OBS, "table too small for the point bound");
 
 // Byte layout of the scratch array.
-constexpr size_t kKeysOff = 0;                            // kCap x uint64 keys
-constexpr size_t kV0Off = kKeysOff + kCap * 8;            // kCap x float4 [1, y]
-constexpr size_t kV1Off = kV0Off + kCap * 16;             // kCap x float4 [n, 0]
-constexpr size_t kListOff = kV1Off + kCap * 16;           // kCap x int claimed slots
+constexpr size_t kKeysOff = 0;                                       // kCap slot records
+constexpr size_t kListOff = kKeysOff + kCap * fr::kRecWords * 8;     // kCap x int claimed slots
 constexpr size_t kCountOff = kListOff + kCap * 4;         // int[2]: claimed count, flags
 constexpr size_t kScratchBytes = kCountOff + 256;
 
@@ -51,16 +48,13 @@ constexpr int kFlagRange = 1, kFlagCapacity = 2;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 struct View {
-    unsigned long long *keys;
-    float4 *v0, *v1;
+    unsigned long long *keys;  // slot records (key, 16-bit record, v0, v1)
     int *list, *count, *flags;
 };
 
 View view_of(unsigned char *base) {
     View v;
     v.keys = reinterpret_cast<unsigned long long *>(base + kKeysOff);
-    v.v0 = reinterpret_cast<float4 *>(base + kV0Off);
-    v.v1 = reinterpret_cast<float4 *>(base + kV1Off);
     v.list = reinterpret_cast<int *>(base + kListOff);
     v.count = reinterpret_cast<int *>(base + kCountOff);
     v.flags = v.count + 1;
@@ -89,8 +83,8 @@ __global__ void k_na_build(const float4 *__restrict__ Y, const float4 *__restric
         }
         if (claimed) v.list[atomicAdd(v.count, 1)] = s;
         const float b = sx.b[k];
-        atomicAdd(v.v0 + s, make_float4(b, b * y.x, b * y.y, b * y.z));
-        if (Yn) atomicAdd(v.v1 + s, make_float4(b * n.x, b * n.y, b * n.z, 0.f));
+        atomicAdd(fr::rec_v0(v.keys, s), make_float4(b, b * y.x, b * y.y, b * y.z));
+        if (Yn) atomicAdd(fr::rec_v1(v.keys, s), make_float4(b * n.x, b * n.y, b * n.z, 0.f));
     }
 }
 
@@ -120,10 +114,10 @@ __global__ void k_na_slice(const float4 *__restrict__ X, int M, Pose T, float s1
             for (int k = 0; k < kD; ++k) {
                 if (slot[k] < 0) continue;
                 const float b = sx.b[k];
-                const float4 a = __ldcg(v.v0 + slot[k]);
+                const float4 a = __ldcg(fr::rec_v0(v.keys, slot[k]));
                 acc[0] += b * a.x; acc[1] += b * a.y; acc[2] += b * a.z; acc[3] += b * a.w;
                 if (with_normals) {
-                    const float4 c = __ldcg(v.v1 + slot[k]);
+                    const float4 c = __ldcg(fr::rec_v1(v.keys, slot[k]));
                     acc[4] += b * c.x; acc[5] += b * c.y; acc[6] += b * c.z;
                 }
             }
@@ -139,10 +133,11 @@ __global__ void k_na_clear(View v) {
     const int n = *v.count;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const int s = v.list[e];
-        v.keys[s] = kEmpty;
-        v.v0[s] = z;
-        v.v1[s] = z;
+        float4 *r = reinterpret_cast<float4 *>(fr::rec_key(v.keys, (uint32_t)v.list[e]));
+        r[0] = z;
+        r[1] = z;
+        r[2] = z;
+        r[3] = z;
     }
 }
 
@@ -156,8 +151,7 @@ cudaError_t g_setup_err[kMaxDevices];
 void setup_device(int dev, cudaStream_t stream) {
     unsigned char *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, kScratchBytes, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p + kKeysOff, 0xFF, kCap * 8, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, kScratchBytes, stream);  // free slots are zero
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     g_setup_err[dev] = e;
     g_base[dev] = (e == cudaSuccess) ? p : nullptr;

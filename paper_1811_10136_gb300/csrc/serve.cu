@@ -8,7 +8,7 @@
 // the memory is reclaimed after the clearing tick.  Requests are admitted
 // between ticks, first come first served, when their tables and records fit
 // the server's arenas:
-//   - a table arena of hash slots (keys / values planes) that every request
+//   - a table arena of hash-slot records that every request
 //     leaves empty again, so admission needs no clearing;
 //   - a byte arena for each request's descriptors, reduction partials, slot
 //     lists and (host requests) its copied clouds.
@@ -127,8 +127,7 @@ struct fr_server {
     cudaStream_t stream = nullptr;
 
     // arenas
-    unsigned long long *keys = nullptr;
-    float4 *v0 = nullptr, *v1 = nullptr;
+    unsigned long long *keys = nullptr;  // slot records, all free (zero) between requests
     size_t table_slots_total = 0;
     unsigned char *bytes = nullptr;
     size_t bytes_total = 0;
@@ -258,8 +257,8 @@ struct fr_server {
         sl->partials = (float2 *)(D + r.o_part);
         for (int t = 0; t < r.ntab; ++t) {
             const size_t b = r.tab_off[t];  // table arena offsets are in slots
-            sl->tab[t] = Table{keys + b, v0 + b, pt2pl ? v1 + b : nullptr, r.cap - 1,
-                               table_probe_limit(r.cap, r.safe), nullptr};
+            sl->tab[t] = Table{keys + b * kRecWords, r.cap - 1, table_probe_limit(r.cap, r.safe),
+                               pt2pl ? 8 : 4};
             sl->list[t] = (int *)(D + r.o_list) + (size_t)t * r.cap;
         }
         // job, state and iteration parameters sit at the same offsets in the byte block
@@ -550,19 +549,15 @@ FR_API fr_status fr_server_create(fr_ctx *ctx, size_t budget, int max_live, cons
     if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(FR_ECUDA, "stream");
     // table arena: the largest power of two of slots within half the budget
-    const size_t per_slot = sizeof(unsigned long long) + sizeof(float4) * (s->pt2pl ? 2 : 1);
+    const size_t per_slot = table_bytes(1);
     int top = kMinTableOrder;
     while (((size_t)2 << top) * per_slot <= budget / 2 && top < 31) ++top;
     s->table_slots_total = (size_t)1 << top;
     s->tab_buddy.init(top);
     const size_t S = s->table_slots_total;
-    if (cudaMalloc((void **)&s->keys, S * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc((void **)&s->v0, S * sizeof(float4)) != cudaSuccess ||
-        (s->pt2pl && cudaMalloc((void **)&s->v1, S * sizeof(float4)) != cudaSuccess))
+    if (cudaMalloc((void **)&s->keys, table_bytes(S)) != cudaSuccess)
         return bail(FR_ENOMEM, "table arena");
-    cudaMemsetAsync(s->keys, 0xFF, S * sizeof(unsigned long long), s->stream);
-    cudaMemsetAsync(s->v0, 0, S * sizeof(float4), s->stream);
-    if (s->pt2pl) cudaMemsetAsync(s->v1, 0, S * sizeof(float4), s->stream);
+    cudaMemsetAsync(s->keys, 0, table_bytes(S), s->stream);
     // byte arena
     int btop = 0;
     while (((size_t)2 << btop) * kByteUnit <= budget - S * per_slot && btop < 40) ++btop;
@@ -682,8 +677,6 @@ FR_API fr_status fr_server_destroy(fr_server *s) {
     for (auto &kv : s->table) delete kv.second;
     for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
     cudaFree(s->keys);
-    cudaFree(s->v0);
-    cudaFree(s->v1);
     cudaFree(s->bytes);
     cudaFree(s->d_slots);
     cudaFree(s->d_segs);
