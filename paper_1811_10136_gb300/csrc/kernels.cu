@@ -690,7 +690,7 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
 }
 
 template <bool PT2PL, bool KAHAN, int ST>
-__global__ void __launch_bounds__(kBlock, 3) k_em_iter(IterLaunch L) {
+__global__ void __launch_bounds__(kBlock, 4) k_em_iter(IterLaunch L) {
     int b = blockIdx.x;
     if (b < L.gs) {
         if (L.check_done && L.st->done) return;
@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_em_iter(IterLaunch L) {
 // batched entry point (all slots in lockstep) and the serving loop (slots at
 // different iterations).
 template <bool PT2PL, bool KAHAN, int ST>
-__global__ void __launch_bounds__(kBlock, 3) k_em_multi(const Slot *__restrict__ slots,
+__global__ void __launch_bounds__(kBlock, 4) k_em_multi(const Slot *__restrict__ slots,
                                                          const Seg *__restrict__ segs,
                                                          const unsigned short *__restrict__ blockseg,
                                                          int check_done) {
