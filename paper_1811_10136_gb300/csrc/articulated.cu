@@ -142,6 +142,10 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
         T.parent[b] = b == 0 ? -1 : tree->parent[b];
         for (int k = 0; k < 12; ++k) T.offset[b][k] = (float)tree->offset[16 * b + k];
     }
+    for (int b = T.nb - 1; b >= 0; --b) {  // parent[b] < b: children are complete first
+        T.sub[b] |= 1u << b;
+        if (b > 0) T.sub[T.parent[b]] |= T.sub[b];
+    }
     for (int b = 0, j = 0; b <= T.nb; ++b) {
         while (j < T.nj && tree->joint_body[j] < b) ++j;
         T.joint_begin[b] = (b == T.nb) ? T.nj : j;

@@ -147,6 +147,7 @@ constexpr int kArtVals = 30;  // per body: 21 of J^T J, 6 of J^T r, weight sum, 
 struct ArtTree {
     int nb, nj;
     int parent[kMaxBodies];
+    unsigned sub[kMaxBodies];       // bit c set when body c is in the subtree of b (b included)
     int joint_begin[kMaxBodies + 1];
     int joint_body[kMaxJoints];
     float offset[kMaxBodies][12];   // row-major 3 x 4

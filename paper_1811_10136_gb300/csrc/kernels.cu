@@ -744,9 +744,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_em_multi(const Slot *__restrict__
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ bool in_subtree(const ArtTree &t, int b, int a) {  // b under or = a
-    for (int x = b; x >= 0; x = (x == 0) ? -1 : t.parent[x])
-        if (x == a) return true;
-    return false;
+    return (t.sub[a] >> b) & 1u;
 }
 
 // 3 x 4 row-major product C = A * B (float), B's implicit last row 0 0 0 1.
@@ -810,9 +808,11 @@ __device__ void art_finish(const ArtJob *job, ArtState *st, float stop_twist) {
     __shared__ double cj[kMaxJoints][6];
     __shared__ double A[kMaxDof][kMaxDof + 1];
     __shared__ double y[kMaxDof];
+    __shared__ float Af[kMaxDof][kMaxDof + 1];  // float32 LDL^T factor
+    __shared__ double xr[kMaxDof], rr[kMaxDof];
+    __shared__ float zf[kMaxDof];
     __shared__ double ext[kMaxBodies][3];  // per body: weight sum, cost, count
     __shared__ double diag[3];
-    __shared__ double inv_d, floor_;
     __shared__ int ok;
     __shared__ double sm_e[24];
     const ArtTree &t = job->tree;
@@ -892,46 +892,114 @@ __device__ void art_finish(const ArtJob *job, ArtState *st, float stop_twist) {
         A[i][j] = a;
     }
     __syncthreads();
-    if (tid == 0) {
+    // Solve A dtheta = -g on warp 0 (lane i owns rows i, i + 32), float64
+    // answer by iterative refinement: LDL^T in float32 (GB300's float64
+    // latency makes a float64 pivot chain slow), then repeat
+    // x += LDL32^-1 (b - A x) with the residual in float64 until the update
+    // is below 1e-9 |x|.  If the float32 pivots fail (or refinement stalls)
+    // the float64 LDL^T runs instead; its pivot test (1e-12 of the largest
+    // diagonal entry) decides degeneracy.
+    if (tid < 32) {
+        const int lane = tid;
         double md = 0.0;
         for (int i = 0; i < nd; ++i) md = fmax(md, A[i][i]);
-        floor_ = md * 1e-12;
-        ok = md > 0.0;
+        const double fl = md * 1e-12;
+        bool okw = md > 0.0;
+        bool done32 = false;
+        if (okw) {
+            for (int i = lane; i < nd; i += 32)
+                for (int j = 0; j <= i; ++j) Af[i][j] = (float)A[i][j];
+            __syncwarp();
+            bool ok32 = true;
+            const float fl32 = (float)md * 1e-6f;
+            for (int k = 0; k < nd && ok32; ++k) {
+                const float d = Af[k][k];
+                ok32 = d > fl32;
+                if (!ok32) break;
+                const float inv = 1.0f / d;
+                for (int i = k + 1 + lane; i < nd; i += 32) {
+                    const float aik = Af[i][k] * inv;
+                    for (int j = k + 1; j <= i; ++j) Af[i][j] -= aik * Af[j][k];
+                }
+                __syncwarp();
+                for (int i = k + 1 + lane; i < nd; i += 32) Af[i][k] *= inv;
+                __syncwarp();
+            }
+            if (ok32) {
+                for (int i = lane; i < nd; i += 32) {
+                    xr[i] = 0.0;
+                    rr[i] = y[i];
+                }
+                __syncwarp();
+                for (int it = 0; it < 12 && !done32; ++it) {
+                    for (int i = lane; i < nd; i += 32) zf[i] = (float)rr[i];
+                    __syncwarp();
+                    for (int k = 0; k < nd; ++k) {  // L z = r
+                        for (int i = k + 1 + lane; i < nd; i += 32) zf[i] -= Af[i][k] * zf[k];
+                        __syncwarp();
+                    }
+                    for (int i = lane; i < nd; i += 32) zf[i] /= Af[i][i];
+                    __syncwarp();
+                    for (int k = nd - 1; k >= 0; --k) {  // L^T dx = z
+                        for (int i = lane; i < k; i += 32) zf[i] -= Af[k][i] * zf[k];
+                        __syncwarp();
+                    }
+                    double dx2 = 0.0, x2 = 0.0;
+                    for (int i = lane; i < nd; i += 32) {
+                        xr[i] += (double)zf[i];
+                        dx2 += (double)zf[i] * (double)zf[i];
+                        x2 += xr[i] * xr[i];
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        dx2 += __shfl_xor_sync(kFull, dx2, o);
+                        x2 += __shfl_xor_sync(kFull, x2, o);
+                    }
+                    __syncwarp();
+                    for (int i = lane; i < nd; i += 32) {  // r = b - A x (A symmetric, lower stored)
+                        double s0 = y[i], s1 = 0.0;
+                        for (int j = 0; j < nd; j += 2) {
+                            s0 -= (j <= i ? A[i][j] : A[j][i]) * xr[j];
+                            if (j + 1 < nd) s1 -= (j + 1 <= i ? A[i][j + 1] : A[j + 1][i]) * xr[j + 1];
+                        }
+                        rr[i] = s0 + s1;
+                    }
+                    __syncwarp();
+                    done32 = dx2 <= 1e-18 * x2;
+                }
+                if (done32)
+                    for (int i = lane; i < nd; i += 32) y[i] = xr[i];
+                __syncwarp();
+            }
+        }
+        for (int k = 0; k < nd && okw && !done32; ++k) {  // float64 LDL^T
+            const double d = A[k][k];
+            okw = d > fl;
+            if (!okw) break;
+            const double inv = rcp64(d);
+            for (int i = k + 1 + lane; i < nd; i += 32) {  // Schur update of row i
+                const double aik = A[i][k] * inv;
+                for (int j = k + 1; j <= i; ++j) A[i][j] -= aik * A[j][k];
+            }
+            __syncwarp();
+            for (int i = k + 1 + lane; i < nd; i += 32) A[i][k] *= inv;
+            __syncwarp();
+        }
+        if (okw && !done32) {
+            for (int k = 0; k < nd; ++k) {  // L z = rhs
+                for (int i = k + 1 + lane; i < nd; i += 32) y[i] -= A[i][k] * y[k];
+                __syncwarp();
+            }
+            for (int i = lane; i < nd; i += 32) y[i] *= rcp64(A[i][i]);  // D w = z
+            __syncwarp();
+            for (int k = nd - 1; k >= 0; --k) {  // L^T x = w
+                for (int i = lane; i < k; i += 32) y[i] -= A[k][i] * y[k];
+                __syncwarp();
+            }
+        }
+        if (lane == 0) ok = okw;
     }
     __syncthreads();
-    // LDL^T, right-looking: pivot, Schur update of the trailing triangle, scale.
-    for (int k = 0; k < nd && ok; ++k) {
-        if (tid == 0) {
-            const double d = A[k][k];
-            ok = d > floor_;
-            inv_d = ok ? rcp64(d) : 0.0;
-        }
-        __syncthreads();
-        if (!ok) break;
-        const int m = nd - k - 1;
-        for (int e = tid; e < m * (m + 1) / 2; e += kBlock) {
-            int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-            while (r * (r + 1) / 2 > e) --r;
-            while ((r + 1) * (r + 2) / 2 <= e) ++r;
-            const int i = k + 1 + r, j = k + 1 + (e - r * (r + 1) / 2);
-            A[i][j] -= A[i][k] * A[j][k] * inv_d;
-        }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < nd; i += kBlock) A[i][k] *= inv_d;
-        __syncthreads();
-    }
-    if (ok) {
-        for (int k = 0; k < nd; ++k) {           // L z = rhs
-            for (int i = k + 1 + tid; i < nd; i += kBlock) y[i] -= A[i][k] * y[k];
-            __syncthreads();
-        }
-        for (int i = tid; i < nd; i += kBlock) y[i] *= rcp64(A[i][i]);   // D w = z
-        __syncthreads();
-        for (int k = nd - 1; k >= 0; --k) {      // L^T x = w
-            for (int i = tid; i < k; i += kBlock) y[i] -= A[k][i] * y[k];
-            __syncthreads();
-        }
-    }
     // parameter update (warp 0 for the root exponential), diagnostics
     if (tid < 32) {
         const int lane = tid;
@@ -964,8 +1032,9 @@ __device__ void art_finish(const ArtJob *job, ArtState *st, float stop_twist) {
 
 // Articulated step: slice at x = T_{b(i)} x_ref (body poses staged in shared
 // memory), the same point terms as the rigid step, summed per body (Algorithm
-// 1, lines 1-4): thread registers while the body is unchanged, then a warp
-// reduction into shared memory, then float64 atomics per touched body.  Each
+// 1): thread registers while the body is unchanged, then one warp reduction
+// per body present in the warp into shared memory, then float64 atomics per
+// touched body.  Each
 // block takes a contiguous range of points (points sorted by body keep the
 // flushes rare).
 template <bool PT2PL, int ST>
@@ -985,6 +1054,8 @@ __device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
     const int chunk = (M + nblk - 1) / nblk;
     const int start = blk * chunk, end = min(M, start + chunk);
     float acc[kArtVals];
+#pragma unroll
+    for (int v = 0; v < kArtVals; ++v) acc[v] = 0.0f;
     int cur = -1, bad = 0;
     auto flush_lane = [&](int b) {
 #pragma unroll
@@ -1008,20 +1079,22 @@ __device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
         if (!slice_point<PT2PL, ST>(L.step, x0, x1, x2, ip, e, bad)) continue;
         point_terms<PT2PL>(x0, x1, x2, e, ip, renorm, [&](int v, float x) { acc[v] += x; });
     }
+    // One warp reduction per distinct body among the lanes (lanes without a
+    // point, or of another body, add zeros): conflicting per-lane shared
+    // atomics on one body's sums would serialise 32 ways.
     const int lane = threadIdx.x & 31;
-    const int c0 = __shfl_sync(kFull, cur, 0);
-    if (__all_sync(kFull, cur == c0)) {
-        if (c0 >= 0) {
+    unsigned pending = __ballot_sync(kFull, cur >= 0);
+    while (pending) {
+        const int bb = __shfl_sync(kFull, cur, __ffs(pending) - 1);
+        const bool mine = cur == bb;
 #pragma unroll
-            for (int v = 0; v < kArtVals; ++v) {
-                float x = acc[v];
+        for (int v = 0; v < kArtVals; ++v) {
+            float x = mine ? acc[v] : 0.0f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-                if (lane == 0) atomicAdd(&sacc[c0][v], x);
-            }
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+            if (lane == 0) atomicAdd(&sacc[bb][v], x);
         }
-    } else if (cur >= 0) {
-        flush_lane(cur);
+        pending &= ~__ballot_sync(kFull, mine);
     }
     if (bad) atomicOr(&st->ds.flags, bad);
     __syncthreads();
