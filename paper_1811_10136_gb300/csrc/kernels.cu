@@ -1607,8 +1607,9 @@ __global__ void __launch_bounds__(kBlock) k_ng_edges(NgEdges L) {
 }
 
 // Sum of v over the grid: every block adds its partial; the last block to
-// finish totals the partials in block order (deterministic) and returns
-// true in its thread 0 with *total set.
+// finish totals the partials with all its threads (a fixed order: thread t
+// takes partials t, t + blockDim, ..., then a fixed tree) and returns true
+// in its thread 0 with *total set.
 __device__ __forceinline__ bool ng_grid_sum(double v, double *partial, int *ticket, double &total) {
     __shared__ double s_w[kBlock / 32];
     __shared__ int s_last;
@@ -1623,13 +1624,21 @@ __device__ __forceinline__ bool ng_grid_sum(double v, double *partial, int *tick
         partial[blockIdx.x] = b;
         __threadfence();
         s_last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+        if (s_last) __threadfence();
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return false;
-    __threadfence();
+    if (!s_last) return false;
     double t = 0.0;
-    for (int i = 0; i < (int)gridDim.x; ++i) t += __ldcg(partial + i);
-    total = t;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partial + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    __syncthreads();
+    if (lane == 0) s_w[warp] = t;
+    __syncthreads();
+    if (threadIdx.x != 0) return false;
+    double tt = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tt += s_w[w];
+    total = tt;
     *ticket = 0;
     return true;
 }

@@ -22,6 +22,14 @@
 
 using namespace fr;
 
+namespace {
+struct NgGraph {
+    long long key[9];
+    cudaGraphExec_t exec;
+    int kernels;
+};
+}  // namespace
+
 struct fr_nodegraph {
     fr_ctx *ctx = nullptr;   // the creating context (not used by fr_nodegraph_destroy)
     int device = 0;
@@ -47,6 +55,8 @@ struct fr_nodegraph {
     int *ticket = nullptr;
     // host staging
     std::vector<int> h_blocks_a, h_blocks_b;  // the pair of every block
+    // captured registrations, by shape
+    std::vector<NgGraph> graphs;
 };
 
 namespace {
@@ -64,6 +74,8 @@ void free_model(fr_nodegraph *g) {
                     g->node_dq, g->stats, g->inliers, g->node_T, g->P, g->x, g->r, g->z, g->Ap,
                     g->p[0], g->p[1], g->scal, g->partial, g->ticket};
     for (void *q : ptrs) cudaFree(q);
+    for (auto &e : g->graphs) cudaGraphExecDestroy(e.exec);
+    g->graphs.clear();
 }
 
 constexpr int kPairI[kNgPairs] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
@@ -260,6 +272,7 @@ namespace {
 // With profiling on, event pairs bracket spans of launches (one class each).
 struct Spans {
     fr_ctx *ctx;
+    cudaStream_t s;
     int n = 0;
     void begin(int cls) {
         if (!ctx->profiling) return;
@@ -270,11 +283,11 @@ struct Spans {
         }
         if (ctx->event_class.size() < (size_t)(n + 1)) ctx->event_class.resize(n + 1);
         ctx->event_class[n] = cls;
-        cudaEventRecord(ctx->events[2 * n], ctx->stream);
+        cudaEventRecord(ctx->events[2 * n], s);
     }
     void end() {
         if (!ctx->profiling) return;
-        cudaEventRecord(ctx->events[2 * n + 1], ctx->stream);
+        cudaEventRecord(ctx->events[2 * n + 1], s);
         ++n;
     }
 };
@@ -300,8 +313,8 @@ fr_status ng_validate(fr_ctx *ctx, const fr_nodegraph *g, const float *d_Y, cons
 }
 
 // The E step and assembly of iteration `it` at the current node poses.
-void ng_assemble(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Table t, int it, Spans &sp) {
-    cudaStream_t s = ctx->stream;
+void ng_assemble(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Table t, int it, Spans &sp,
+                 cudaStream_t s) {
     sp.begin(FR_K_NG_ASSEMBLE);
     cudaMemsetAsync(g->blocks, 0, (size_t)g->nnzb * 36 * sizeof(float), s);
     cudaMemsetAsync(g->g, 0, 6 * (size_t)g->K * sizeof(float), s);
@@ -342,8 +355,7 @@ void ng_assemble(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Table t, int it
     ctx->launches += 2;
 }
 
-void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Spans &sp) {
-    cudaStream_t s = ctx->stream;
+void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Spans &sp, cudaStream_t s) {
     sp.begin(FR_K_NG_SOLVE);
     NgPcg L{};
     L.K = g->K;
@@ -371,6 +383,100 @@ void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Spans &sp) 
     launch_ng_update(g->K, g->x, g->node_T, g->node_dq, g->stats + 2, s);
     sp.end();
     ctx->launches += 2 + 2 * run.pcg_iters;
+}
+
+// The registration's kernels after the uploads, on stream s: node dual
+// quaternions, the first lattice, then per iteration (a rebuild when sigma
+// changes,) the assembly and the solve with the node update; finally the
+// last table is freed.  Returns the number of kernels.
+int ng_issue(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, const Table tab[2], int iters, int64_t N,
+             cudaStream_t s, Spans &sp) {
+    int launches = 1;
+    launch_ng_update(g->K, nullptr, g->node_T, g->node_dq, nullptr, s);
+    int cur = 0, cur_build = 0;
+    auto build = [&](int t, int it) {
+        IterLaunch b{};
+        b.job = ctx->d_job;
+        b.ip = ctx->d_ip;
+        b.st = ctx->d_state;
+        b.build = tab[t];
+        b.build_list = ctx->lists[t];
+        b.build_it = it;
+        b.gb = blocks_for(ctx, N, 8);
+        sp.begin(FR_K_BUILD);
+        launch_em_iter(run.pt2pl, 0, b, s, FR_FP32);
+        sp.end();
+        ++launches;
+    };
+    auto clear = [&](int t, int it) {
+        Table tc = tab[t];
+        int *l = ctx->lists[t];
+        const int *c = &ctx->d_ip[it].nvert;
+        launch_clear_lists(&tc, &l, &c, 1, blocks_for(ctx, N, 4), s);
+        ++launches;
+    };
+    build(0, 0);
+    for (int it = 0; it < iters; ++it) {
+        if (it > 0 && ctx->h_ip[it].rebuild) {
+            clear(cur, cur_build);
+            cur ^= 1;
+            cur_build = it;
+            build(cur, it);
+        }
+        ng_assemble(ctx, g, run, tab[cur], it, sp, s);
+        launches += 2;
+        if (run.solve) {
+            ng_solve_update(ctx, g, run, sp, s);
+            launches += 2 + 2 * run.pcg_iters;
+        }
+    }
+    clear(cur, cur_build);
+    return launches;
+}
+
+// The same captured once per shape as a CUDA graph and replayed: the
+// per-call data (poses, sigma schedule, observation pointers and size) is
+// read from device descriptors uploaded before the launch.
+fr_status ng_graph_launch(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, const Table tab[2], int iters,
+                          int64_t N, uint32_t cap, unsigned long long rebuilds) {
+    long long lam_bits;
+    std::memcpy(&lam_bits, &run.lambda, sizeof lam_bits);  // lambda is a kernel argument of the graph
+    const long long key[9] = {N, iters, run.pcg_iters, run.pt2pl, (long long)cap, run.solve ? 1 : 0,
+                              (long long)rebuilds, (long long)ctx->ws_gen, lam_bits};
+    NgGraph *hit = nullptr;
+    for (auto &e : g->graphs)
+        if (std::equal(key, key + 9, e.key)) hit = &e;
+    if (!hit) {
+        cudaStream_t cs;
+        FR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        Spans none{ctx, cs};
+        int kernels = 0;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            kernels = ng_issue(ctx, g, run, tab, iters, N, cs, none);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        cudaStreamDestroy(cs);
+        FR_CUDA(ctx, e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        FR_CUDA(ctx, e);
+        if (g->graphs.size() >= 8) {
+            cudaGraphExecDestroy(g->graphs.front().exec);
+            g->graphs.erase(g->graphs.begin());
+        }
+        NgGraph ng{};
+        std::copy(key, key + 9, ng.key);
+        ng.exec = exec;
+        ng.kernels = kernels;
+        g->graphs.push_back(ng);
+        hit = &g->graphs.back();
+    }
+    FR_CUDA(ctx, cudaGraphLaunch(hit->exec, ctx->stream));
+    ctx->launches += hit->kernels;
+    return FR_OK;
 }
 
 fr_status ng_run(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_Yn, int64_t N,
@@ -402,53 +508,18 @@ fr_status ng_run(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_
     FR_CUDA(ctx, copy_async(ctx, ctx->d_ip, ctx->h_ip, o.iters * sizeof(IterParams), cudaMemcpyHostToDevice));
     FR_CUDA(ctx, copy_async(ctx, ctx->d_state, hs, sizeof(DeviceState), cudaMemcpyHostToDevice));
     FR_CUDA(ctx, copy_async(ctx, g->node_T, node_T, (size_t)g->K * 16 * sizeof(double), cudaMemcpyHostToDevice));
-    launch_ng_update(g->K, nullptr, g->node_T, g->node_dq, nullptr, s);
-    ++ctx->launches;
-    Spans sp{ctx};
-    // lattice of iteration 0, rebuilt into the other table whenever sigma changes
-    int cur = 0, cur_build = 0;
-    {
-        sp.begin(FR_K_BUILD);
-        IterLaunch b{};
-        b.job = ctx->d_job;
-        b.ip = ctx->d_ip;
-        b.st = ctx->d_state;
-        b.build = tab[0];
-        b.build_list = ctx->lists[0];
-        b.build_it = 0;
-        b.gb = blocks_for(ctx, N, 8);
-        launch_em_iter(run.pt2pl, 0, b, s, FR_FP32);
-        sp.end();
-        ++ctx->launches;
+    Spans sp{ctx, s};
+    // the rebuild pattern (which iterations rebuild the lattice) shapes the graph
+    unsigned long long rebuilds = 1469598103934665603ull;
+    int cur_build = 0;
+    for (int it = 1; it < iters; ++it) {
+        rebuilds = (rebuilds ^ (unsigned long long)(ctx->h_ip[it].rebuild ? 2 * it + 1 : 2 * it)) * 1099511628211ull;
+        if (ctx->h_ip[it].rebuild) cur_build = it;
     }
-    for (int it = 0; it < iters; ++it) {
-        if (it > 0 && ctx->h_ip[it].rebuild) {
-            int *l = ctx->lists[cur];
-            const int *c = &ctx->d_ip[cur_build].nvert;
-            launch_clear_lists(&tab[cur], &l, &c, 1, blocks_for(ctx, N, 4), s);
-            cur ^= 1;
-            cur_build = it;
-            IterLaunch b{};
-            b.job = ctx->d_job;
-            b.ip = ctx->d_ip;
-            b.st = ctx->d_state;
-            b.build = tab[cur];
-            b.build_list = ctx->lists[cur];
-            b.build_it = it;
-            b.gb = blocks_for(ctx, N, 8);
-            sp.begin(FR_K_BUILD);
-            launch_em_iter(run.pt2pl, 0, b, s, FR_FP32);
-            sp.end();
-            ctx->launches += 2;
-        }
-        ng_assemble(ctx, g, run, tab[cur], it, sp);
-        if (run.solve) ng_solve_update(ctx, g, run, sp);
-    }
-    {
-        int *l = ctx->lists[cur];
-        const int *c = &ctx->d_ip[cur_build].nvert;
-        launch_clear_lists(&tab[cur], &l, &c, 1, blocks_for(ctx, N, 4), s);
-        ++ctx->launches;
+    if (ctx->profiling || !opt->use_graph) {
+        ctx->launches += ng_issue(ctx, g, run, tab, iters, N, s, sp);
+    } else {
+        FR_TRY(ng_graph_launch(ctx, g, run, tab, iters, N, cap, rebuilds));
     }
     FR_CUDA(ctx, cudaGetLastError());
     double st[4];
