@@ -215,44 +215,56 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     unsigned short *bs_pro2 = (unsigned short *)(U + o_bs_pro2);
     unsigned short *bs_epi = (unsigned short *)(U + o_bs_epi);
     auto tab_of = [&](int b, int build) { return ip[b].annealed ? build % ntab : 0; };
-    // iteration k: per item step k | [annealed] build k+lead | convert k+1 (lead 2) | clear k-1
+    // iteration k: every item's step k first, then the builds k+lead (annealed
+    // items), conversions k+1 (lead 2) and clears k-1: blocks are dispatched in
+    // index order, so the steps -- and their float64 tails -- start before the
+    // builds rather than the last items' steps ending the launch.
+    // Phase q: 0 step, 1 build, 2 convert, 3 clear.
+    auto seg_blocks = [&](int b, int q) {
+        if (q == 0) return ip[b].gs;
+        if (!ip[b].annealed) return -1;  // no segment
+        if (q == 1) return ip[b].gb;
+        if (q == 2) return lead == 2 ? ip[b].gv : -1;
+        return ip[b].gc;
+    };
     for (int k = 0; k < iters; ++k) {
         Seg *S = segs + (size_t)k * seg_per_iter;
         int si = 0, blk = 0;
-        for (int b = 0; b < n; ++b) {
-            S[si++] = Seg{b, kRoleStep, k, tab_of(b, k), blk, ip[b].gs};
-            blk += ip[b].gs;
-            if (ip[b].annealed) {
-                const bool build = k + lead < iters, clear = k >= 1;
-                S[si++] = Seg{b, build ? kRoleBuild : kRoleNone, k + lead, tab_of(b, k + lead), blk, ip[b].gb};
-                blk += ip[b].gb;
-                if (lead == 2) {
-                    const bool conv = k + 1 < iters;
-                    S[si++] = Seg{b, conv ? kRoleConvert : kRoleNone, k + 1, tab_of(b, k + 1), blk, ip[b].gv};
-                    blk += ip[b].gv;
+        for (int q = 0; q < 4; ++q)
+            for (int b = 0; b < n; ++b) {
+                const int nb = seg_blocks(b, q);
+                if (nb < 0) continue;
+                Seg sg{b, kRoleNone, 0, 0, blk, nb};
+                if (q == 0) {
+                    sg.role = kRoleStep;
+                    sg.it = k;
+                    sg.tab = tab_of(b, k);
+                } else if (q == 1 && k + lead < iters) {
+                    sg.role = kRoleBuild;
+                    sg.it = k + lead;
+                    sg.tab = tab_of(b, k + lead);
+                } else if (q == 2 && k + 1 < iters) {
+                    sg.role = kRoleConvert;
+                    sg.it = k + 1;
+                    sg.tab = tab_of(b, k + 1);
+                } else if (q == 3 && k >= 1) {
+                    sg.role = kRoleClear;
+                    sg.it = k - 1;
+                    sg.tab = tab_of(b, k - 1);
                 }
-                S[si++] = Seg{b, clear ? kRoleClear : kRoleNone, k - 1, clear ? tab_of(b, k - 1) : 0, blk,
-                              ip[b].gc};
-                blk += ip[b].gc;
+                S[si++] = sg;
+                blk += nb;
             }
-        }
     }
     {
         int si = 0, blk = 0;
-        for (int b = 0; b < n; ++b) {
-            for (int q = 0; q < ip[b].gs; ++q) bs_iter[blk++] = (unsigned short)si;
-            ++si;
-            if (ip[b].annealed) {
-                for (int q = 0; q < ip[b].gb; ++q) bs_iter[blk++] = (unsigned short)si;
-                ++si;
-                if (lead == 2) {
-                    for (int q = 0; q < ip[b].gv; ++q) bs_iter[blk++] = (unsigned short)si;
-                    ++si;
-                }
-                for (int q = 0; q < ip[b].gc; ++q) bs_iter[blk++] = (unsigned short)si;
+        for (int q = 0; q < 4; ++q)
+            for (int b = 0; b < n; ++b) {
+                const int nb = seg_blocks(b, q);
+                if (nb < 0) continue;
+                for (int r = 0; r < nb; ++r) bs_iter[blk++] = (unsigned short)si;
                 ++si;
             }
-        }
     }
     // prologue: build 0; with lead 2 a second launch converts 0 and builds 1
     Seg *Spro = segs + (size_t)iters1 * seg_per_iter;
