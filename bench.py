@@ -70,6 +70,26 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(seed, rank):
+    """Each rank registers its own frames (weak scaling: fixed work per GPU)."""
+    return seed + 7919 * rank
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The slowest rank's time: the job is done when the last rank is."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, slowest_s):
+    """Units processed by all ranks per second of the slowest rank."""
+    return units_per_rank * world / slowest_s
+
+
 def workload_config(frames, pairs):
     Ns = [p.Y.shape[0] for p in pairs]
     return {
@@ -309,7 +329,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    pairs = make_pairs(args.seed + 7919 * rank, args.frames)
+    pairs = make_pairs(rank_seed(args.seed, rank), args.frames)
     dev = lambda a: torch.from_numpy(a).cuda()
     dpairs = [(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs]
     ctx = fr.Context(local)
@@ -342,11 +362,7 @@ def run_ours(args):
         return [a.elapsed_time(b) for a, b in zip(starts, ends)], last
 
     def slowest(total_s):
-        if dist:
-            t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return total_s
+        return max_over_ranks(total_s, dist, "cuda")
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -364,7 +380,7 @@ def run_ours(args):
     launches = ctx.kernel_launches - launches0
     total_s = slowest(sum(step_ms) / 1000.0)
     em_iters_all = ITERS * args.frames * args.steps * ws
-    value = em_iters_all / total_s
+    value = whole_job_rate(ITERS * args.frames * args.steps, ws, total_s)
 
     # ---- the plain path (one registration at a time, float32) on the same frames
     plain_ms, plain_last = timed_steps(plain_step, args.steps)
