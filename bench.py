@@ -41,7 +41,7 @@ SIGMA0, SIGMA1, W_OUT = 0.04, 0.01, 0.1
 ART_ITERS, ART_SIGMA = 15, 0.01      # articulated workload: 15 EM iterations at sigma 1 cm
 NG_ITERS, NG_PCG, NG_SIGMA, NG_LAMBDA = 10, 20, 0.02, 10.0  # node-graph workload
 SERVE_RATE = 2000.0                   # serving stream: Poisson arrivals per second
-SERVE_BUDGET = 8 << 30                # server device memory (bytes)
+SERVE_BUDGET = 32 << 30               # server device memory (bytes): tables and records of ~300 live requests
 
 
 def parse():

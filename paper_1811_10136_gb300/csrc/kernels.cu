@@ -511,7 +511,7 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
         return false;
     }
     int slot[kD];
-    find4(t.keys, t.mask, sx, slot);
+    find4(t.keys, t.mask, sx, slot, t.max_probe);
     if constexpr (ST != kStoreF32) {
         // One 16-byte record per vertex; positions restored in float32.
         uint4 r[kD];
@@ -689,11 +689,17 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
     if (threadIdx.x == 0) st->ticket = 0;
 }
 
+// A registration stops early once stop_twist was reached or a compact table
+// overflowed (its result is discarded and it is rerun at the safe size).
+__device__ __forceinline__ bool stopped(const DeviceState *st) {
+    return __ldcg(&st->done) || (__ldcg(&st->flags) & kFlagCapacity);
+}
+
 template <bool PT2PL, bool KAHAN, int ST>
 __global__ void __launch_bounds__(kBlock, 4) k_em_iter(IterLaunch L) {
     int b = blockIdx.x;
     if (b < L.gs) {
-        if (L.check_done && L.st->done) return;
+        if (L.check_done && stopped(L.st)) return;
         step_role<PT2PL, KAHAN, ST>(L.job, L.ip + L.it, L.step, L.partials, L.st, b, L.gs);
         return;
     }
@@ -704,7 +710,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_em_iter(IterLaunch L) {
     }
     b -= L.gv;
     if (b < L.gb) {
-        if (L.check_done && L.st->done) return;
+        if (L.check_done && stopped(L.st)) return;
         build_role<PT2PL, ST>(L.job, L.ip + L.build_it, L.build, L.build_list, L.st, b, L.gb);
         return;
     }
@@ -727,10 +733,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_em_multi(const Slot *__restrict__
     DeviceState *st = sl.st;
     const int b = blockIdx.x - sg.blk0;
     if (sg.role == kRoleStep) {
-        if (check_done && st->done) return;
+        if (check_done && stopped(st)) return;
         step_role<PT2PL, KAHAN, ST>(sl.job, sl.ip + sg.it, sl.tab[sg.tab], sl.partials, st, b, sg.nblk);
     } else if (sg.role == kRoleBuild) {
-        if (check_done && st->done) return;
+        if (check_done && stopped(st)) return;
         build_role<PT2PL, ST>(sl.job, sl.ip + sg.it, sl.tab[sg.tab], sl.list[sg.tab], st, b, sg.nblk);
     } else if (sg.role == kRoleClear) {
         clear_role(sl.tab[sg.tab], sl.list[sg.tab], __ldcg(&sl.ip[sg.it].nvert), b, sg.nblk);
@@ -1118,7 +1124,7 @@ template <bool PT2PL, int ST>
 __global__ void __launch_bounds__(kBlock) k_art_iter(ArtLaunch L) {
     int b = blockIdx.x;
     if (b < L.gs) {
-        if (L.st->ds.done) return;
+        if (stopped(&L.st->ds)) return;
         art_step_role<PT2PL, ST>(L, b, L.gs);
         return;
     }
@@ -1129,7 +1135,7 @@ __global__ void __launch_bounds__(kBlock) k_art_iter(ArtLaunch L) {
     }
     b -= L.gv;
     if (b < L.gb) {
-        if (L.st->ds.done) return;
+        if (stopped(&L.st->ds)) return;
         build_role<PT2PL, ST>(&L.job->base, L.ip + L.build_it, L.build, L.build_list, &L.st->ds, b, L.gb);
         return;
     }
@@ -1166,8 +1172,8 @@ __global__ void k_blur_pass(Table in, Table out, int dir, const DeviceState *st)
             o[3] = z;
             continue;
         }
-        const int sm = find_key(in.keys, in.mask, neighbour_key(key, dir, -1));
-        const int sp = find_key(in.keys, in.mask, neighbour_key(key, dir, +1));
+        const int sm = find_key(in.keys, in.mask, neighbour_key(key, dir, -1), in.max_probe);
+        const int sp = find_key(in.keys, in.mask, neighbour_key(key, dir, +1), in.max_probe);
         float4 a = __ldg(rec_v0(in.keys, s));
         if (sm >= 0) {
             const float4 u = __ldg(rec_v0(in.keys, sm));
@@ -1310,7 +1316,7 @@ __global__ void k_slice_out(const float4 *__restrict__ Q, int m, float s1, float
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (embed(p.x, p.y, p.z, s1, s2, s3, sx)) {
             int slot[kD];
-            find4(t.keys, t.mask, sx, slot);
+            find4(t.keys, t.mask, sx, slot, t.max_probe);
 #pragma unroll
             for (int k = 0; k < kD; ++k) {
                 if (slot[k] < 0) continue;

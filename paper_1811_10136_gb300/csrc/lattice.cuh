@@ -166,7 +166,7 @@ __device__ __forceinline__ int insert_key(unsigned long long *keys, uint32_t mas
 // Inserts up to four keys at once (key k only where active & (1 << k)):
 // the first probes are loaded together and the needed CASes issued back to
 // back, so the four round trips to L2 overlap; collision chains are walked
-// afterwards by insert_key (at most max_probe more slots).  slot[k] = -1 where
+// afterwards by insert_key (max_probe slots in all, counting the home slot).  slot[k] = -1 where
 // inactive or no free slot was found; bit k of the return value is set where
 // this call created the vertex.
 __device__ __forceinline__ int insert4(unsigned long long *keys, uint32_t mask,
@@ -194,7 +194,8 @@ __device__ __forceinline__ int insert4(unsigned long long *keys, uint32_t mask,
             slot[k] = (int)s[k];
         } else {
             bool c;
-            const int t = insert_key(keys, mask, key[k], max_probe, c, (s[k] + 1) & mask);
+            // the home slot was probe 1: max_probe - 1 more (a lookup probes max_probe slots)
+            const int t = max_probe > 1 ? insert_key(keys, mask, key[k], max_probe - 1, c, (s[k] + 1) & mask) : -1;
             slot[k] = t;
             claimed |= c ? (1 << k) : 0;
         }
@@ -203,11 +204,13 @@ __device__ __forceinline__ int insert4(unsigned long long *keys, uint32_t mask,
 }
 
 // Slot of `key`, or -1 if absent.  The table must not change during the call
-// (read through the read-only path).
+// (read through the read-only path).  An insert never places a key more than
+// max_probe slots past its home, so a lookup stops there too: a full table
+// (one whose build overflowed) costs at most max_probe probes, not a scan.
 __device__ __forceinline__ int find_key(const unsigned long long *__restrict__ keys, uint32_t mask,
-                                        unsigned long long key) {
+                                        unsigned long long key, uint32_t max_probe) {
     uint32_t s = slot_of(key, mask);
-    for (uint32_t p = 0; p <= mask; ++p) {
+    for (uint32_t p = 0; p < max_probe; ++p) {
         const unsigned long long cur = __ldg(rec_key(const_cast<unsigned long long *>(keys), s));
         if (cur == key) return (int)s;
         if (cur == kEmpty) return -1;
@@ -217,9 +220,10 @@ __device__ __forceinline__ int find_key(const unsigned long long *__restrict__ k
 }
 
 // Four lookups with the first probes issued together (independent loads in
-// flight), then any collision chains walked one by one.
+// flight), then any collision chains walked one by one (max_probe slots at
+// most, as find_key).
 __device__ __forceinline__ void find4(const unsigned long long *__restrict__ keys, uint32_t mask,
-                                      const Simplex &sx, int slot[kD]) {
+                                      const Simplex &sx, int slot[kD], uint32_t max_probe) {
     uint32_t s[kD];
     unsigned long long cur[kD];
 #pragma unroll
@@ -228,8 +232,8 @@ __device__ __forceinline__ void find4(const unsigned long long *__restrict__ key
     for (int k = 0; k < kD; ++k) cur[k] = __ldg(rec_key(const_cast<unsigned long long *>(keys), s[k]));
 #pragma unroll
     for (int k = 0; k < kD; ++k) {
-        uint32_t p = 0;
-        while (cur[k] != sx.key[k] && cur[k] != kEmpty && p < mask) {
+        uint32_t p = 1;
+        while (cur[k] != sx.key[k] && cur[k] != kEmpty && p < max_probe) {
             s[k] = (s[k] + 1) & mask;
             cur[k] = __ldg(rec_key(const_cast<unsigned long long *>(keys), s[k]));
             ++p;

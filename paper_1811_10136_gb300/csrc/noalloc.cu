@@ -109,7 +109,7 @@ __global__ void k_na_slice(const float4 *__restrict__ X, int M, Pose T, float s1
         Simplex sx;
         if (fr::embed(x[0], x[1], x[2], s1, s2, s3, sx)) {
             int slot[kD];
-            fr::find4(v.keys, kCap - 1, sx, slot);
+            fr::find4(v.keys, kCap - 1, sx, slot, kCap);
 #pragma unroll
             for (int k = 0; k < kD; ++k) {
                 if (slot[k] < 0) continue;
