@@ -51,7 +51,6 @@ void free_batch_workspace(fr_ctx *ctx) {
 
 namespace {
 
-constexpr int kPointsPerThread = 2;  // step and build blocks cover 512 points
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -130,8 +129,8 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
         p.cap = table_slots(it.N, safe);
         p.tab_off = slots;
         slots += ntab * (size_t)p.cap;
-        p.gs = div_up(it.M, (long long)kBlock * kPointsPerThread);
-        p.gp = div_up(it.N, (long long)kBlock * kPointsPerThread);
+        p.gs = div_up(it.M, (long long)kBlock * kMultiPointsPerThread);
+        p.gp = div_up(it.N, (long long)kBlock * kMultiPointsPerThread);
         p.annealed = (it.sigma_start != it.sigma_end && iters > 1) ? 1 : 0;
         p.gb = p.annealed ? p.gp : 0;
         p.gc = p.annealed ? std::max(1, div_up(it.N, 4096)) : 0;

@@ -80,21 +80,39 @@ struct Acc {
     }
 };
 
-// Block reduction of kRigidVals floats -- warp shuffles, then the 8 warp sums
+// Warp sum of 32 values per lane by recursive halving: at the step of
+// offset o a lane keeps the half of its values whose index has bit o equal to
+// its own lane bit, and adds its partner's copy of that half; 16 + 8 + 4 + 2 +
+// 1 shuffles instead of 32 x 5.  Lane l returns the sum of value l.
+__device__ __forceinline__ float warp_sum32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? v[i] : v[i + o];
+            const float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    return v[0];
+}
+
+// Block reduction of kRigidVals floats -- warp sums, then the 8 warp sums
 // combined as double-float -- written value-major: value v of block blk at
 // partials[v * rows + blk].
 template <bool KAHAN>
 __device__ __forceinline__ void block_partial(const Acc<KAHAN> &acc, float2 *partials, int blk,
                                               int rows) {
+    static_assert(kRigidVals <= 32, "one value per lane");
     __shared__ float sm[kBlock / 32][kRigidVals];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float v[32];
 #pragma unroll
-    for (int v = 0; v < kRigidVals; ++v) {
-        float x = acc.total(v);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-        if (lane == 0) sm[warp][v] = x;
-    }
+    for (int i = 0; i < 32; ++i) v[i] = i < kRigidVals ? acc.total(i) : 0.0f;
+    const float x = warp_sum32(v);
+    if (lane < kRigidVals) sm[warp][lane] = x;
     __syncthreads();
     if (threadIdx.x < kRigidVals) {
         DF a{0.0f, 0.0f};
@@ -1093,13 +1111,11 @@ __device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
     while (pending) {
         const int bb = __shfl_sync(kFull, cur, __ffs(pending) - 1);
         const bool mine = cur == bb;
+        float x[32];
 #pragma unroll
-        for (int v = 0; v < kArtVals; ++v) {
-            float x = mine ? acc[v] : 0.0f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-            if (lane == 0) atomicAdd(&sacc[bb][v], x);
-        }
+        for (int v = 0; v < 32; ++v) x[v] = (v < kArtVals && mine) ? acc[v] : 0.0f;
+        const float sum = warp_sum32(x);
+        if (lane < kArtVals) atomicAdd(&sacc[bb][lane], sum);
         pending &= ~__ballot_sync(kFull, mine);
     }
     if (bad) atomicOr(&st->ds.flags, bad);

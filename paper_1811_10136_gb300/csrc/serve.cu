@@ -36,7 +36,6 @@ int64_t steady_ns() {
         .count();
 }
 
-constexpr int kPointsPerThread = 2;  // step and build blocks cover 512 points
 constexpr int kMaxAhead = 2;         // ticks queued on the GPU before the worker waits
 constexpr size_t kByteUnit = 256;    // byte-arena granularity
 constexpr int kMinTableOrder = 10;   // smallest table: 1024 slots
@@ -167,8 +166,8 @@ struct fr_server {
         r.annealed = (q.sigma_start != q.sigma_end && opt.iters > 1) ? 1 : 0;
         r.ntab = r.annealed ? 3 : 1;
         r.cap = table_slots(q.N, r.safe);
-        r.gs = div_up(q.M, (long long)kBlock * kPointsPerThread);
-        r.gp = div_up(q.N, (long long)kBlock * kPointsPerThread);
+        r.gs = div_up(q.M, (long long)kBlock * kMultiPointsPerThread);
+        r.gp = div_up(q.N, (long long)kBlock * kMultiPointsPerThread);
         r.gb = r.annealed ? r.gp : 0;
         r.gc = r.annealed ? std::max(1, div_up(q.N, 4096)) : 0;
         r.gf = std::max(1, div_up(q.N, 4096));
