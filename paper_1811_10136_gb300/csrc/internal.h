@@ -174,7 +174,7 @@ struct ArtState {
     float body_T[kMaxBodies][12];           // every body's pose at the current parameters
     float jaxis[kMaxJoints][3];             // world joint axes ...
     float jpoint[kMaxJoints][3];            // ... and a world point on each
-    double acc[kMaxBodies][kArtVals];       // per-body sums of the running iteration
+    double acc[kMaxBodies][kArtVals];       // subtree sums of the running iteration (body b: the bodies under b)
 };
 
 struct ArtLaunch {

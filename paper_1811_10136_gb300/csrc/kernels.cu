@@ -229,15 +229,17 @@ __device__ void warp_se3_update(double dz, double *T /* row-major 4x4, global */
     }
     const double A = __shfl_sync(kFull, coef, 0), B = __shfl_sync(kFull, coef, 1),
                  C = __shfl_sync(kFull, coef, 2);
-    // lanes 0..8: R_ij ; lanes 9..17: V_ij v_j
+    // lanes 0..8: R_ij ; lanes 9..17: V_ij v_j (elements picked by selects:
+    // a lane-dependent index into w or v would put them in local memory)
+    auto pick = [](const double (&x)[3], int n) { return n == 0 ? x[0] : (n == 1 ? x[1] : x[2]); };
     if (lane < 18) {
         const int r = lane < 9 ? lane : lane - 9;
         const int i = r / 3, j = r % 3;
-        const double Wij = (i == j) ? 0.0 : ((j == (i + 1) % 3) ? -w[(i + 2) % 3] : w[(i + 1) % 3]);
-        const double W2ij = w[i] * w[j] - (i == j ? th2 : 0.0);
+        const double Wij = (i == j) ? 0.0 : ((j == (i + 1) % 3) ? -pick(w, (i + 2) % 3) : pick(w, (i + 1) % 3));
+        const double W2ij = pick(w, i) * pick(w, j) - (i == j ? th2 : 0.0);
         const double I = (i == j) ? 1.0 : 0.0;
         if (lane < 9) smem[lane] = I + A * Wij + B * W2ij;
-        else smem[lane] = (I + B * Wij + C * W2ij) * v[j];
+        else smem[lane] = (I + B * Wij + C * W2ij) * pick(v, j);
     }
     __syncwarp();
     if (lane < 3) smem[18 + lane] = smem[9 + 3 * lane] + smem[10 + 3 * lane] + smem[11 + 3 * lane];
@@ -784,97 +786,87 @@ __device__ __forceinline__ void mul34(const float *A, const float *B, float *C) 
     for (int k = 0; k < 12; ++k) C[k] = t[k];
 }
 
-// Forward kinematics in float for body b: its pose, and the world axis and
-// point of each of its joints (thread-per-body; each walks its own chain).
-__device__ void art_fk_body(const ArtTree &t, const double *root_T, const double *q, int b,
-                            float *Tb, float (*jaxis)[3], float (*jpoint)[3]) {
-    int chain[kMaxBodies];
-    int n = 0;
-    for (int x = b; x >= 0; x = (x == 0) ? -1 : t.parent[x]) chain[n++] = x;
-    float F[12];
-    for (int k = 0; k < 12; ++k) F[k] = (float)root_T[k];
-    for (int c = n - 1; c >= 0; --c) {
-        const int a = chain[c];
-        mul34(F, t.offset[a], F);
-        for (int j = t.joint_begin[a]; j < t.joint_begin[a + 1]; ++j) {
-            const float *u = t.axis[j];
-            if (a == b) {
-                for (int r = 0; r < 3; ++r) {
-                    jaxis[j][r] = F[4 * r] * u[0] + F[4 * r + 1] * u[1] + F[4 * r + 2] * u[2];
-                    jpoint[j][r] = F[4 * r + 3];
-                }
-            }
-            float sn, cs;
-            sincosf((float)q[j], &sn, &cs);
-            const float v = 1.0f - cs;
-            const float R[12] = {cs + u[0] * u[0] * v, u[0] * u[1] * v - u[2] * sn, u[0] * u[2] * v + u[1] * sn, 0.f,
-                                 u[1] * u[0] * v + u[2] * sn, cs + u[1] * u[1] * v, u[1] * u[2] * v - u[0] * sn, 0.f,
-                                 u[2] * u[0] * v - u[1] * sn, u[2] * u[1] * v + u[0] * sn, cs + u[2] * u[2] * v, 0.f};
-            mul34(F, R, F);
-        }
-    }
-    for (int k = 0; k < 12; ++k) Tb[k] = F[k];
-}
+// Shared memory of the articulated tail (the float32 inverse is dead once the
+// kinematics start, which reuse its space).
+struct ArtTailSmem {
+    ArtTree tree;                      // staged copy of the kinematic tree
+    double q[kMaxJoints];              // joint angles before the update
+    double S[kMaxBodies][21];          // subtree sums of J^T J (upper triangle) ...
+    double sv[kMaxBodies][6];          // ... and of J^T r
+    double cj[kMaxJoints][6];          // twist column of each joint
+    double wj[kMaxJoints][6];          // S_{b(j)} c_j
+    double A[kMaxDof][kMaxDof + 1];    // lower triangle of the normal matrix
+    double y[kMaxDof];                 // right-hand side, then the solution
+    double xr[kMaxDof], rr[kMaxDof];   // refined solution and its residual
+    double diag[3];                    // weight sum, cost, count
+    double sm_e[24];
+    float sc[kMaxDof];                 // Jacobi scale 1 / sqrt(A_ii)
+    float rs[kMaxDof], dz[kMaxDof];
+    union {
+        struct {
+            float Ai[kMaxDof][kMaxDof + 1];    // inverse of the scaled matrix
+            float v[2][kMaxDof + 1], u[2][kMaxDof + 1];  // rank-1 factors (double-buffered); v[.][kMaxDof] = pivot
+        } gj;
+        struct {
+            float T[2][kMaxBodies][12];        // partial chains (ping-pong)
+            float R[kMaxJoints][12];           // joint rotations
+            float ja[kMaxJoints][3], jp[kMaxJoints][3];  // joint axis / point in the parent's frame
+            int anc[2][kMaxBodies];
+        } fk;
+    } u;
+    int use32, done, ok;
+};
 
 // Last block of an articulated step: the normal equations of Algorithm 1 from
-// the per-body sums, a float64 LDL^T solve, the parameter update and the
-// kinematics of the new pose.  With H_b, h_b the body sums and S_b, s_b their
-// sums over the subtree of b, and c_j = (a_j; p_j x a_j) the twist column of
-// joint j (shared by every body under the joint):
+// the subtree sums, the solve, the parameter update and the kinematics of
+// the new pose.  With H_b, h_b the body sums and S_b, s_b their sums over the
+// subtree of b, and c_j = (a_j; p_j x a_j) the twist column of joint j
+// (shared by every body under the joint):
 //   A_rr = S_root,  A_r,j = S_{b(j)} c_j,  g_r = s_root,  g_j = c_j . s_{b(j)},
 //   A_jk = c_j^T S_d c_k  (d the deeper of b(j), b(k) when one is under the
-//   other, else 0) -- the sum of J_sp^T (J^T J)_b J_sp over bodies.
+//   other, else 0) -- the sum of J_sp^T (J^T J)_b J_sp over bodies.  With
+//   w_j = S_{b(j)} c_j every A_jk is a dot product: w_j . c_k when b(j) is the
+//   deeper body, c_j . w_k otherwise.
 __device__ void art_finish(const ArtJob *job, ArtState *st, float stop_twist) {
-    __shared__ double S[kMaxBodies][21];
-    __shared__ double sv[kMaxBodies][6];
-    __shared__ double H[kMaxBodies][21];
-    __shared__ double hv[kMaxBodies][6];
-    __shared__ double cj[kMaxJoints][6];
-    __shared__ double A[kMaxDof][kMaxDof + 1];
-    __shared__ double y[kMaxDof];
-    __shared__ float Af[kMaxDof][kMaxDof + 1];  // float32 LDL^T factor
-    __shared__ double xr[kMaxDof], rr[kMaxDof];
-    __shared__ float zf[kMaxDof];
-    __shared__ double ext[kMaxBodies][3];  // per body: weight sum, cost, count
-    __shared__ double diag[3];
-    __shared__ int ok;
-    __shared__ double sm_e[24];
-    const ArtTree &t = job->tree;
-    const int nb = t.nb, nj = t.nj, nd = 6 + nj;
-    const int tid = threadIdx.x;
+    __shared__ ArtTailSmem sm;
+    const int nb = job->tree.nb, nj = job->tree.nj, nd = 6 + nj;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // Every global input is requested up front (one round trip to L2): the
+    // subtree sums, the tree, the joint angles and the joint axes and points
+    // of the current pose.
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&job->tree);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sm.tree);
+        for (int w = tid; w < (int)(sizeof(ArtTree) / 4); w += kBlock) dst[w] = __ldg(src + w);
+    }
     for (int e = tid; e < nb * kArtVals; e += kBlock) {
         const int b = e / kArtVals, v = e % kArtVals;
         const double x = __ldcg(&st->acc[b][v]);
         st->acc[b][v] = 0.0;                       // ready for the next iteration
-        if (v < 21) H[b][v] = x;
-        else if (v < 27) hv[b][v - 21] = x;
-        else ext[b][v - 27] = x;
-    }
-    __syncthreads();
-    if (tid < 3) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += ext[b][tid];
-        diag[tid] = s;
-    }
-    // subtree sums
-    for (int e = tid; e < nb * 27; e += kBlock) {
-        const int b = e / 27, v = e % 27;
-        double s = 0.0;
-        for (int c = 0; c < nb; ++c)
-            if (in_subtree(t, c, b)) s += (v < 21) ? H[c][v] : hv[c][v - 21];
-        if (v < 21) S[b][v] = s;
-        else sv[b][v - 21] = s;
+        if (v < 21) sm.S[b][v] = x;
+        else if (v < 27) sm.sv[b][v - 21] = x;
+        else if (b == 0) sm.diag[v - 27] = x;      // the root's subtree is every body
     }
     for (int j = tid; j < nj; j += kBlock) {
-        const double a0 = st->jaxis[j][0], a1 = st->jaxis[j][1], a2 = st->jaxis[j][2];
-        const double p0 = st->jpoint[j][0], p1 = st->jpoint[j][1], p2 = st->jpoint[j][2];
-        cj[j][0] = a0; cj[j][1] = a1; cj[j][2] = a2;
-        cj[j][3] = p1 * a2 - p2 * a1;
-        cj[j][4] = p2 * a0 - p0 * a2;
-        cj[j][5] = p0 * a1 - p1 * a0;
+        sm.q[j] = __ldcg(&st->q[j]);
+        const double a0 = __ldcg(&st->jaxis[j][0]), a1 = __ldcg(&st->jaxis[j][1]), a2 = __ldcg(&st->jaxis[j][2]);
+        const double p0 = __ldcg(&st->jpoint[j][0]), p1 = __ldcg(&st->jpoint[j][1]), p2 = __ldcg(&st->jpoint[j][2]);
+        sm.cj[j][0] = a0; sm.cj[j][1] = a1; sm.cj[j][2] = a2;
+        sm.cj[j][3] = p1 * a2 - p2 * a1;
+        sm.cj[j][4] = p2 * a0 - p0 * a2;
+        sm.cj[j][5] = p0 * a1 - p1 * a0;
     }
     __syncthreads();
-    auto Sx = [&](int b, int p, int q) { return p <= q ? S[b][tri_index(p, q)] : S[b][tri_index(q, p)]; };
+    const ArtTree &t = sm.tree;
+    auto Sx = [&](int b, int p, int q) { return p <= q ? sm.S[b][tri_index(p, q)] : sm.S[b][tri_index(q, p)]; };
+    for (int e = tid; e < nj * 6; e += kBlock) {
+        const int j = e / 6, p = e % 6, b = t.joint_body[j];
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s += Sx(b, p, q) * sm.cj[j][q];
+        sm.wj[j][p] = s;
+    }
+    __syncthreads();
     // lower triangle of A (i >= j) and g
     const int nlow = nd * (nd + 1) / 2;
     for (int e = tid; e < nlow + nd; e += kBlock) {
@@ -882,176 +874,337 @@ __device__ void art_finish(const ArtJob *job, ArtState *st, float stop_twist) {
             const int i = e - nlow;
             double gi;
             if (i < 6) {
-                gi = sv[0][i];
+                gi = sm.sv[0][i];
             } else {
                 const int j = i - 6, b = t.joint_body[j];
                 gi = 0.0;
-                for (int p = 0; p < 6; ++p) gi += cj[j][p] * sv[b][p];
+                for (int p = 0; p < 6; ++p) gi += sm.cj[j][p] * sm.sv[b][p];
             }
-            y[i] = -gi;
+            sm.y[i] = -gi;
             continue;
         }
         int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
         while (i * (i + 1) / 2 > e) --i;
         while ((i + 1) * (i + 2) / 2 <= e) ++i;
         const int j = e - i * (i + 1) / 2;
-        double a;
+        double a = 0.0;
         if (i < 6) {
             a = Sx(0, i, j);
         } else if (j < 6) {
-            const int k = i - 6, b = t.joint_body[k];
-            a = 0.0;
-            for (int q = 0; q < 6; ++q) a += Sx(b, j, q) * cj[k][q];
+            a = sm.wj[i - 6][j];
         } else {
             const int k1 = i - 6, k2 = j - 6, b1 = t.joint_body[k1], b2 = t.joint_body[k2];
-            const int d = in_subtree(t, b1, b2) ? b1 : (in_subtree(t, b2, b1) ? b2 : -1);
-            a = 0.0;
-            if (d >= 0)
-                for (int p = 0; p < 6; ++p) {
-                    double u = 0.0;
-                    for (int q = 0; q < 6; ++q) u += Sx(d, p, q) * cj[k2][q];
-                    a += cj[k1][p] * u;
-                }
+            const double *u = nullptr, *v = nullptr;
+            if (in_subtree(t, b1, b2)) { u = sm.wj[k1]; v = sm.cj[k2]; }
+            else if (in_subtree(t, b2, b1)) { u = sm.cj[k1]; v = sm.wj[k2]; }
+            if (u)
+                for (int p = 0; p < 6; ++p) a += u[p] * v[p];
         }
-        A[i][j] = a;
+        sm.A[i][j] = a;
     }
     __syncthreads();
-    // Solve A dtheta = -g on warp 0 (lane i owns rows i, i + 32), float64
-    // answer by iterative refinement: LDL^T in float32 (GB300's float64
-    // latency makes a float64 pivot chain slow), then repeat
-    // x += LDL32^-1 (b - A x) with the residual in float64 until the update
-    // is below 1e-9 |x|.  If the float32 pivots fail (or refinement stalls)
-    // the float64 LDL^T runs instead; its pivot test (1e-12 of the largest
-    // diagonal entry) decides degeneracy.
-    if (tid < 32) {
-        const int lane = tid;
-        double md = 0.0;
-        for (int i = 0; i < nd; ++i) md = fmax(md, A[i][i]);
-        const double fl = md * 1e-12;
-        bool okw = md > 0.0;
-        bool done32 = false;
-        if (okw) {
-            for (int i = lane; i < nd; i += 32)
-                for (int j = 0; j <= i; ++j) Af[i][j] = (float)A[i][j];
-            __syncwarp();
-            bool ok32 = true;
-            const float fl32 = (float)md * 1e-6f;
-            for (int k = 0; k < nd && ok32; ++k) {
-                const float d = Af[k][k];
-                ok32 = d > fl32;
-                if (!ok32) break;
-                const float inv = 1.0f / d;
-                for (int i = k + 1 + lane; i < nd; i += 32) {
-                    const float aik = Af[i][k] * inv;
-                    for (int j = k + 1; j <= i; ++j) Af[i][j] -= aik * Af[j][k];
-                }
-                __syncwarp();
-                for (int i = k + 1 + lane; i < nd; i += 32) Af[i][k] *= inv;
-                __syncwarp();
-            }
-            if (ok32) {
-                for (int i = lane; i < nd; i += 32) {
-                    xr[i] = 0.0;
-                    rr[i] = y[i];
-                }
-                __syncwarp();
-                for (int it = 0; it < 12 && !done32; ++it) {
-                    for (int i = lane; i < nd; i += 32) zf[i] = (float)rr[i];
-                    __syncwarp();
-                    for (int k = 0; k < nd; ++k) {  // L z = r
-                        for (int i = k + 1 + lane; i < nd; i += 32) zf[i] -= Af[i][k] * zf[k];
-                        __syncwarp();
-                    }
-                    for (int i = lane; i < nd; i += 32) zf[i] /= Af[i][i];
-                    __syncwarp();
-                    for (int k = nd - 1; k >= 0; --k) {  // L^T dx = z
-                        for (int i = lane; i < k; i += 32) zf[i] -= Af[k][i] * zf[k];
-                        __syncwarp();
-                    }
-                    double dx2 = 0.0, x2 = 0.0;
-                    for (int i = lane; i < nd; i += 32) {
-                        xr[i] += (double)zf[i];
-                        dx2 += (double)zf[i] * (double)zf[i];
-                        x2 += xr[i] * xr[i];
-                    }
+
+    // ---- solve A dtheta = -g -----------------------------------------------
+    // float64 answer by iterative refinement on the whole block: the
+    // Jacobi-scaled matrix B = D A D (D = diag(1/sqrt(A_ii)), unit diagonal)
+    // is inverted in float32 by Gauss-Jordan elimination (no pivoting: B is
+    // symmetric positive definite), then x += D B^-1 D (y - A x) with the
+    // residual in float64 until the error is below 1e-9 |x|.  A diagonal
+    // entry at most 1e-12 of the largest, an elimination pivot below 1e-5 or
+    // no convergence in 12 rounds hands the system to the float64 LDL^T,
+    // whose pivot test decides degeneracy.
+    if (warp == 0) {
+        float md = 0.0f;
+        for (int i = lane; i < nd; i += 32) md = fmaxf(md, (float)sm.A[i][i]);
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        dx2 += __shfl_xor_sync(kFull, dx2, o);
-                        x2 += __shfl_xor_sync(kFull, x2, o);
-                    }
-                    __syncwarp();
-                    for (int i = lane; i < nd; i += 32) {  // r = b - A x (A symmetric, lower stored)
-                        double s0 = y[i], s1 = 0.0;
-                        for (int j = 0; j < nd; j += 2) {
-                            s0 -= (j <= i ? A[i][j] : A[j][i]) * xr[j];
-                            if (j + 1 < nd) s1 -= (j + 1 <= i ? A[i][j + 1] : A[j + 1][i]) * xr[j + 1];
-                        }
-                        rr[i] = s0 + s1;
-                    }
-                    __syncwarp();
-                    done32 = dx2 <= 1e-18 * x2;
-                }
-                if (done32)
-                    for (int i = lane; i < nd; i += 32) y[i] = xr[i];
-                __syncwarp();
-            }
+        for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(kFull, md, o));
+        bool good = md > 0.0f && md < 1e30f;
+        for (int i = lane; i < nd; i += 32) {
+            const float d = (float)sm.A[i][i];
+            good = good && d > md * 1e-12f;
+            sm.sc[i] = good ? rsqrtf(d) : 0.0f;
         }
-        for (int k = 0; k < nd && okw && !done32; ++k) {  // float64 LDL^T
-            const double d = A[k][k];
-            okw = d > fl;
-            if (!okw) break;
-            const double inv = rcp64(d);
-            for (int i = k + 1 + lane; i < nd; i += 32) {  // Schur update of row i
-                const double aik = A[i][k] * inv;
-                for (int j = k + 1; j <= i; ++j) A[i][j] -= aik * A[j][k];
-            }
-            __syncwarp();
-            for (int i = k + 1 + lane; i < nd; i += 32) A[i][k] *= inv;
-            __syncwarp();
+        good = __all_sync(kFull, good);
+        if (lane == 0) {
+            sm.use32 = good;
+            sm.done = 0;
         }
-        if (okw && !done32) {
-            for (int k = 0; k < nd; ++k) {  // L z = rhs
-                for (int i = k + 1 + lane; i < nd; i += 32) y[i] -= A[i][k] * y[k];
-                __syncwarp();
-            }
-            for (int i = lane; i < nd; i += 32) y[i] *= rcp64(A[i][i]);  // D w = z
-            __syncwarp();
-            for (int k = nd - 1; k >= 0; --k) {  // L^T x = w
-                for (int i = lane; i < k; i += 32) y[i] -= A[k][i] * y[k];
-                __syncwarp();
-            }
-        }
-        if (lane == 0) ok = okw;
     }
     __syncthreads();
+    if (sm.use32) {
+        // Gauss-Jordan in registers.  Warp w holds rows w, w + 8, ... (slot
+        // s), lane l columns l, l + 32.  A pivot step is the rank-1 update
+        // a_ij -= u_i v_j with u_i = a_ik (u_k = p - 1) and v_j = a_kj / p
+        // (v_k = 1 + 1/p), which gives row k / p, column k * (-1/p) and 1/p
+        // at (k, k) with no per-entry case.  The warp owning row k rotates
+        // its slots after each of its pivots, so its next pivot row is always
+        // slot 0 (registers are never indexed by a run-time value).
+        constexpr int kRows = (kMaxDof + 7) / 8, kCols = (kMaxDof + 31) / 32;
+        float a[kRows][kCols];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) {
+                const int i = warp + 8 * r, j = lane + 32 * c;
+                a[r][c] = (i < nd && j < nd)
+                              ? (float)(j <= i ? sm.A[i][j] : sm.A[j][i]) * sm.sc[i] * sm.sc[j]
+                              : 0.0f;
+            }
+        for (int e = tid; e < 2 * (kMaxDof + 1); e += kBlock) {
+            sm.u.gj.u[e / (kMaxDof + 1)][e % (kMaxDof + 1)] = 0.0f;
+            sm.u.gj.v[e / (kMaxDof + 1)][e % (kMaxDof + 1)] = 0.0f;
+        }
+        __syncthreads();
+        int row[kRows];  // row held in each slot (rotated with the slots)
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) row[r] = warp + 8 * r;
+        bool inverted = true;
+        for (int k = 0; k < nd; ++k) {
+            const int buf = k & 1, ck = k >> 5;
+            if (lane == (k & 31)) {  // column k: u_i = a_ik
+#pragma unroll
+                for (int r = 0; r < kRows; ++r) {
+                    const float x = ck ? a[r][kCols - 1] : a[r][0];
+                    if (row[r] < nd) sm.u.gj.u[buf][row[r]] = (row[r] == k) ? x - 1.0f : x;
+                }
+            }
+            if (warp == (k & 7)) {  // row k sits in slot 0
+                const float p = __shfl_sync(kFull, ck ? a[0][kCols - 1] : a[0][0], k & 31);
+                const float ip = 1.0f / p;
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    const int j = lane + 32 * c;
+                    if (j < nd) sm.u.gj.v[buf][j] = (j == k) ? 1.0f + ip : a[0][c] * ip;
+                }
+                if (lane == 0) sm.u.gj.v[buf][kMaxDof] = p;
+            }
+            __syncthreads();
+            if (!(sm.u.gj.v[buf][kMaxDof] > 1e-5f)) {  // the same pivot in every thread
+                inverted = false;
+                break;
+            }
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const float ui = sm.u.gj.u[buf][row[r]];
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) a[r][c] = fmaf(-ui, sm.u.gj.v[buf][lane + 32 * c], a[r][c]);
+            }
+            if (warp == (k & 7)) {
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    const float t0 = a[0][c];
+#pragma unroll
+                    for (int r = 0; r + 1 < kRows; ++r) a[r][c] = a[r + 1][c];
+                    a[kRows - 1][c] = t0;
+                }
+                const int r0 = row[0];
+#pragma unroll
+                for (int r = 0; r + 1 < kRows; ++r) row[r] = row[r + 1];
+                row[kRows - 1] = r0;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) {
+                const int j = lane + 32 * c;
+                if (row[r] < nd && j < nd) sm.u.gj.Ai[row[r]][j] = a[r][c];
+            }
+        __syncthreads();
+        if (tid == 0) sm.done = 0;
+        for (int i = tid; i < nd; i += kBlock) {
+            sm.xr[i] = 0.0;
+            sm.rr[i] = sm.y[i];
+        }
+        __syncthreads();
+        float prev = 0.0f;  // |dz|^2 of the previous round (warp 0)
+        for (int it = 0; it < 12 && inverted; ++it) {
+            for (int i = tid; i < nd; i += kBlock) sm.rs[i] = (float)sm.rr[i] * sm.sc[i];
+            __syncthreads();
+            for (int i = warp; i < nd; i += kBlock / 32) {  // dz = D B^-1 D r, a warp per row
+                float s = 0.0f;
+                for (int j = lane; j < nd; j += 32) s += sm.u.gj.Ai[i][j] * sm.rs[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+                if (lane == 0) sm.dz[i] = s * sm.sc[i];
+            }
+            __syncthreads();
+            if (warp == 0) {
+                float dx2 = 0.0f, x2 = 0.0f;
+                for (int i = lane; i < nd; i += 32) {
+                    const double xi = sm.xr[i] + (double)sm.dz[i];
+                    sm.xr[i] = xi;
+                    dx2 += sm.dz[i] * sm.dz[i];
+                    x2 += (float)xi * (float)xi;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    dx2 += __shfl_xor_sync(kFull, dx2, o);
+                    x2 += __shfl_xor_sync(kFull, x2, o);
+                }
+                // Converged when this correction is below 1e-9 |x|, or when the
+                // error it leaves -- |dz|^2 / |dz_prev| under the observed
+                // contraction, if that is below 1e-2 -- is.
+                const bool small = dx2 <= 1e-18f * x2;
+                const bool fast = prev > 0.0f && dx2 < 1e-4f * prev && dx2 * (dx2 / prev) <= 1e-18f * x2;
+                prev = dx2;
+                if (lane == 0) sm.done = small || fast;
+            }
+            __syncthreads();
+            if (sm.done) break;
+            // r = y - A x in float64: four threads per row, seven columns each
+            if (tid < 4 * nd) {
+                const int i = tid >> 2, q = tid & 3;
+                double s = 0.0;
+                for (int j = q; j < nd; j += 4) s += (j <= i ? sm.A[i][j] : sm.A[j][i]) * sm.xr[j];
+                s += __shfl_xor_sync(0xffffffffu >> (32 - min(32, 4 * nd - (tid & ~31))), s, 1);
+                s += __shfl_xor_sync(0xffffffffu >> (32 - min(32, 4 * nd - (tid & ~31))), s, 2);
+                if (q == 0) sm.rr[i] = sm.y[i] - s;
+            }
+            __syncthreads();
+        }
+        if (sm.done)
+            for (int i = tid; i < nd; i += kBlock) sm.y[i] = sm.xr[i];
+        __syncthreads();
+    }
+    if (warp == 0) {
+        const bool done32 = sm.use32 && sm.done;
+        bool okw = true;
+        if (!done32) {  // float64 LDL^T (lane i owns rows i, i + 32)
+            double md = 0.0;
+            for (int i = 0; i < nd; ++i) md = fmax(md, sm.A[i][i]);
+            const double fl = md * 1e-12;
+            okw = md > 0.0;
+            for (int k = 0; k < nd && okw; ++k) {
+                const double d = sm.A[k][k];
+                okw = d > fl;
+                if (!okw) break;
+                const double inv = rcp64(d);
+                for (int i = k + 1 + lane; i < nd; i += 32) {  // Schur update of row i
+                    const double aik = sm.A[i][k] * inv;
+                    for (int j = k + 1; j <= i; ++j) sm.A[i][j] -= aik * sm.A[j][k];
+                }
+                __syncwarp();
+                for (int i = k + 1 + lane; i < nd; i += 32) sm.A[i][k] *= inv;
+                __syncwarp();
+            }
+            if (okw) {
+                for (int k = 0; k < nd; ++k) {  // L z = rhs
+                    for (int i = k + 1 + lane; i < nd; i += 32) sm.y[i] -= sm.A[i][k] * sm.y[k];
+                    __syncwarp();
+                }
+                for (int i = lane; i < nd; i += 32) sm.y[i] *= rcp64(sm.A[i][i]);  // D w = z
+                __syncwarp();
+                for (int k = nd - 1; k >= 0; --k) {  // L^T x = w
+                    for (int i = lane; i < k; i += 32) sm.y[i] -= sm.A[k][i] * sm.y[k];
+                    __syncwarp();
+                }
+            }
+        }
+        if (lane == 0) sm.ok = okw;
+    }
+    __syncthreads();
+    const bool ok = sm.ok;
     // parameter update (warp 0 for the root exponential), diagnostics
-    if (tid < 32) {
-        const int lane = tid;
+    if (warp == 0) {
         if (lane == 0) {
             st->ds.iters_run += 1;
-            st->ds.sum_w = diag[0];
-            st->ds.cost = diag[1];
-            st->ds.inliers = (long long)(diag[2] + 0.5);
+            st->ds.sum_w = sm.diag[0];
+            st->ds.cost = sm.diag[1];
+            st->ds.inliers = (long long)(sm.diag[2] + 0.5);
             if (!ok) st->ds.degenerate += 1;
         }
         if (ok) {
-            warp_se3_update(lane < 6 ? y[lane] : 0.0, st->root_T, sm_e);
+            warp_se3_update(lane < 6 ? sm.y[lane] : 0.0, st->root_T, sm.sm_e);
             float n2 = 0.0f;
-            for (int i = 0; i < nd; ++i) n2 += (float)y[i] * (float)y[i];
+            for (int i = lane; i < nd; i += 32) n2 += (float)sm.y[i] * (float)sm.y[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(kFull, n2, o);
             if (lane == 0) {
                 st->ds.twist_norm = sqrtf(n2);
                 if (stop_twist > 0.0f && sqrtf(n2) < stop_twist) st->ds.done = 1;
             }
         }
-    }
-    if (ok)
-        for (int j = tid; j < nj; j += kBlock) {
-            double qj = st->q[j] + y[6 + j];
+    } else if (ok) {
+        for (int j = tid - 32; j < nj; j += kBlock - 32) {
+            double qj = sm.q[j] + sm.y[6 + j];
             qj = fmin(fmax(qj, t.q_min[j]), t.q_max[j]);
             st->q[j] = qj;
+            sm.q[j] = qj;
         }
+    }
     __syncthreads();
-    for (int b = tid; b < nb; b += kBlock) art_fk_body(t, st->root_T, st->q, b, st->body_T[b], st->jaxis, st->jpoint);
+
+    // ---- forward kinematics in float -----------------------------------------
+    // Body b's pose is T_parent * L_b with L_b = offset_b * R(q_j) ... over its
+    // joints (body 0: root_T * offset_0 * ...).  Every L_b is formed at once,
+    // then the chains are composed by pointer jumping (log2 of the depth
+    // rounds); each joint's world axis and point follow from its parent's pose.
+    for (int j = tid; j < nj; j += kBlock) {
+        const float *a = t.axis[j];
+        float sn, cs;
+        sincosf((float)sm.q[j], &sn, &cs);
+        const float v = 1.0f - cs;
+        float *R = sm.u.fk.R[j];
+        R[0] = cs + a[0] * a[0] * v;        R[1] = a[0] * a[1] * v - a[2] * sn; R[2] = a[0] * a[2] * v + a[1] * sn;
+        R[4] = a[1] * a[0] * v + a[2] * sn; R[5] = cs + a[1] * a[1] * v;        R[6] = a[1] * a[2] * v - a[0] * sn;
+        R[8] = a[2] * a[0] * v - a[1] * sn; R[9] = a[2] * a[1] * v + a[0] * sn; R[10] = cs + a[2] * a[2] * v;
+        R[3] = R[7] = R[11] = 0.0f;
+    }
+    __syncthreads();
+    for (int b = tid; b < nb; b += kBlock) {
+        float F[12];
+        if (b == 0) {
+            float Rt[12];
+            for (int k = 0; k < 12; ++k) Rt[k] = (float)st->root_T[k];
+            mul34(Rt, t.offset[0], F);
+        } else {
+            for (int k = 0; k < 12; ++k) F[k] = t.offset[b][k];
+        }
+        for (int j = t.joint_begin[b]; j < t.joint_begin[b + 1]; ++j) {
+            const float *a = t.axis[j];
+            for (int r = 0; r < 3; ++r) {  // in the parent's frame (world for body 0)
+                sm.u.fk.ja[j][r] = F[4 * r] * a[0] + F[4 * r + 1] * a[1] + F[4 * r + 2] * a[2];
+                sm.u.fk.jp[j][r] = F[4 * r + 3];
+            }
+            mul34(F, sm.u.fk.R[j], F);
+        }
+        for (int k = 0; k < 12; ++k) sm.u.fk.T[0][b][k] = F[k];
+        sm.u.fk.anc[0][b] = b == 0 ? -1 : t.parent[b];
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int round = 0; round < 5; ++round) {  // depth < 32
+        for (int b = tid; b < nb; b += kBlock) {
+            const int a = sm.u.fk.anc[cur][b];
+            if (a >= 0) {
+                mul34(sm.u.fk.T[cur][a], sm.u.fk.T[cur][b], sm.u.fk.T[cur ^ 1][b]);
+                sm.u.fk.anc[cur ^ 1][b] = sm.u.fk.anc[cur][a];
+            } else {
+                for (int k = 0; k < 12; ++k) sm.u.fk.T[cur ^ 1][b][k] = sm.u.fk.T[cur][b][k];
+                sm.u.fk.anc[cur ^ 1][b] = -1;
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    for (int e = tid; e < nb * 12; e += kBlock) st->body_T[e / 12][e % 12] = sm.u.fk.T[cur][e / 12][e % 12];
+    for (int j = tid; j < nj; j += kBlock) {
+        const int b = t.joint_body[j];
+        if (b == 0) {
+            for (int r = 0; r < 3; ++r) {
+                st->jaxis[j][r] = sm.u.fk.ja[j][r];
+                st->jpoint[j][r] = sm.u.fk.jp[j][r];
+            }
+        } else {
+            const float *P = sm.u.fk.T[cur][t.parent[b]];
+            const float *a = sm.u.fk.ja[j], *p = sm.u.fk.jp[j];
+            for (int r = 0; r < 3; ++r) {
+                st->jaxis[j][r] = P[4 * r] * a[0] + P[4 * r + 1] * a[1] + P[4 * r + 2] * a[2];
+                st->jpoint[j][r] = P[4 * r] * p[0] + P[4 * r + 1] * p[1] + P[4 * r + 2] * p[2] + P[4 * r + 3];
+            }
+        }
+    }
 }
 
 // Articulated step: slice at x = T_{b(i)} x_ref (body poses staged in shared
@@ -1120,9 +1273,17 @@ __device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
     }
     if (bad) atomicOr(&st->ds.flags, bad);
     __syncthreads();
+    // The tail needs only subtree sums (S_b over the bodies under b): each
+    // block adds its sums of every subtree that holds one of its points.
     for (int e = threadIdx.x; e < nb * kArtVals; e += kBlock) {
-        const int b = e / kArtVals;
-        if (sacc[b][kArtVals - 1] > 0.0f) atomicAdd(&st->acc[b][e % kArtVals], (double)sacc[b][e % kArtVals]);
+        const int b = e / kArtVals, v = e % kArtVals;
+        float sum = 0.0f, cnt = 0.0f;
+        for (unsigned m = __ldg(&job->tree.sub[b]); m; m &= m - 1) {
+            const int c = __ffs(m) - 1;
+            sum += sacc[c][v];
+            cnt += sacc[c][kArtVals - 1];
+        }
+        if (cnt > 0.0f) atomicAdd(&st->acc[b][v], (double)sum);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1137,7 +1298,7 @@ __device__ void art_step_role(const ArtLaunch &L, int blk, int nblk) {
 }
 
 template <bool PT2PL, int ST>
-__global__ void __launch_bounds__(kBlock) k_art_iter(ArtLaunch L) {
+__global__ void __launch_bounds__(kBlock, 3) k_art_iter(ArtLaunch L) {
     int b = blockIdx.x;
     if (b < L.gs) {
         if (stopped(&L.st->ds)) return;

@@ -71,6 +71,25 @@ def test_annealed_point_to_plane(ctx, orc):
     assert rg.lattice_builds == 8
 
 
+def test_body_without_points_is_degenerate(ctx, orc):
+    # A leaf body with joints but no model points leaves its joints' columns
+    # of the normal matrix zero: every iteration is degenerate on both sides
+    # (no update; the float32 elimination hands the system to the float64
+    # factorisation, whose pivot test rejects it).
+    p = synth.articulated_pair(13, n_points=6000)
+    t = p.tree
+    leaves = [b for b in range(1, t.nb) if b not in set(t.parent.tolist()) and (t.joint_body == b).any()]
+    assert leaves
+    keep = p.body != leaves[0]
+    Xref, body = p.Xref[keep], p.body[keep]
+    Rg, qg, rg = ctx.register_articulated(dev(Xref), dev(body, np.int32), t, dev(p.Y), None, iters=3,
+                                          sigma_start=f32(0.02), sigma_end=f32(0.02), w=f32(0.1))
+    Ro, qo, ro = orc.register_articulated(Xref, body, t, p.Y, None, sigma=f32(0.02), w=f32(0.1), iters=3)
+    assert ro.degenerate_iters == 3 and rg.degenerate_iters == 3
+    assert np.array_equal(Rg, np.eye(4)) and not np.any(qg)
+    assert rg.last_inliers == ro.last_inliers
+
+
 def test_exact_correspondences_recover_planted_pose(ctx):
     tree = synth.random_kintree(3)
     rng = np.random.default_rng(4)
