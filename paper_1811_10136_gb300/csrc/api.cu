@@ -268,20 +268,14 @@ int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
         if (p.blur && L.gb) issue_blur(ctx, k, p, L.build);
     }
     if (p.iters > 0) {
-        // Free what is left: the last build's table (and, annealed, the one
-        // before it, in case the loop stopped early).
-        Table t[2];
-        int *lists[2];
-        const int *counts[2];
-        int n = 0;
+        // Free what is left: the last build's table.  Every other table was
+        // cleared by the launch after its step (clear roles run even after
+        // the registration stopped).
         const int last = p.annealed ? p.iters - 1 : 0;
-        for (int b = (p.annealed && last > 0) ? last - 1 : last; b <= last; ++b) {
-            t[n] = tab[which(b)];
-            lists[n] = ctx->lists[which(b)];
-            counts[n] = &ctx->d_ip[b].nvert;
-            ++n;
-        }
-        k(FR_K_CLEAR, [&] { launch_clear_lists(t, lists, counts, n, p.g_final, s); });
+        Table t[1] = {tab[which(last)]};
+        int *lists[1] = {ctx->lists[which(last)]};
+        const int *counts[1] = {&ctx->d_ip[last].nvert};
+        k(FR_K_CLEAR, [&] { launch_clear_lists(t, lists, counts, 1, p.g_final, s); });
     }
     return k.kernels;
 }

@@ -228,18 +228,12 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
         ctx->launches += 1;
     }
     if (opt->iters > 0) {
-        Table t[2];
-        int *lists[2];
-        const int *counts[2];
-        int n = 0;
+        // the last build's table (the launch after each step cleared the others)
         const int last = annealed ? opt->iters - 1 : 0;
-        for (int b = (annealed && last > 0) ? last - 1 : last; b <= last; ++b) {
-            t[n] = tab[tab_of(b)];
-            lists[n] = ctx->lists[tab_of(b)];
-            counts[n] = &ctx->d_ip[b].nvert;
-            ++n;
-        }
-        launch_clear_lists(t, lists, counts, n, blocks_for(ctx, N, 2), ctx->stream);
+        Table t[1] = {tab[tab_of(last)]};
+        int *lists[1] = {ctx->lists[tab_of(last)]};
+        const int *counts[1] = {&ctx->d_ip[last].nvert};
+        launch_clear_lists(t, lists, counts, 1, blocks_for(ctx, N, 2), ctx->stream);
         ctx->launches += 1;
     }
     FR_CUDA(ctx, cudaGetLastError());

@@ -103,6 +103,7 @@ struct ItemPlan {
     uint32_t cap;
     int annealed;
     int gs, gb, gc, gp, gv;    // step, build, clear blocks per launch; first-build blocks; convert
+    int gf;                    // blocks of the final clear
     size_t tab_off;            // first slot of its tables in the arenas
     size_t list_off, part_off; // in misc (bytes)
 };
@@ -135,14 +136,15 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
         p.gb = p.annealed ? p.gp : 0;
         p.gc = p.annealed ? std::max(1, div_up(it.N, 4096)) : 0;
         p.gv = lead == 2 ? std::max(1, div_up(it.N, 2048)) : 0;
+        p.gf = std::max(1, div_up(it.N, 1024));
         seg_per_iter += 1 + (p.annealed ? 2 + (lead - 1) : 0);
         grid_iter += p.gs + p.gb + p.gc + (p.annealed ? p.gv : 0);
         grid_pro += p.gp;
         grid_pro2 += p.gv + (p.annealed ? p.gb : 0);
-        grid_epi += (p.annealed && iters > 1) ? 2 * p.gc : std::max(1, div_up(it.N, 4096));
+        grid_epi += p.gf;
     }
     if (lead == 1) grid_pro2 = 0;
-    const int seg_pro = n, seg_pro2 = 2 * n, seg_epi_max = 2 * n;
+    const int seg_pro = n, seg_pro2 = 2 * n, seg_epi_max = n;
     // upload region (also the device layout of the misc arena's head)
     size_t off = 0;
     const size_t o_jobs = off; off = align256(off + n * sizeof(RigidJob));
@@ -264,6 +266,7 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
                 for (int r = 0; r < nb; ++r) bs_iter[blk++] = (unsigned short)si;
                 ++si;
             }
+        if (blk != grid_iter) return ctx->fail(FR_EINVAL, "internal: iteration block map");
     }
     // prologue: build 0; with lead 2 a second launch converts 0 and builds 1
     Seg *Spro = segs + (size_t)iters1 * seg_per_iter;
@@ -273,6 +276,7 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
             Spro[b] = Seg{b, kRoleBuild, 0, 0, blk, ip[b].gp};
             for (int q = 0; q < ip[b].gp; ++q) bs_pro[blk++] = (unsigned short)b;
         }
+        if (blk != grid_pro) return ctx->fail(FR_EINVAL, "internal: first build block map");
     }
     Seg *Spro2 = Spro + seg_pro;
     if (lead == 2) {
@@ -287,23 +291,21 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
                 ++si;
             }
         }
-        grid_pro2 = blk;
+        if (blk != grid_pro2) return ctx->fail(FR_EINVAL, "internal: second prologue block map");
     }
     Seg *Sepi = Spro2 + seg_pro2;
     int n_epi = 0;
     {
         int blk = 0;
         for (int b = 0; b < n; ++b) {
+            // Every other table was cleared by the launch after its step
+            // (clears run even after a registration stopped).
             const int last = ip[b].annealed ? iters - 1 : 0;
-            const int first = (ip[b].annealed && last > 0) ? last - 1 : last;
-            const int g = ip[b].annealed ? ip[b].gc : std::max(1, div_up(items[b].N, 4096));
-            for (int bl = first; bl <= last; ++bl) {
-                Sepi[n_epi] = Seg{b, kRoleClear, bl, tab_of(b, bl), blk, g};
-                for (int q = 0; q < g; ++q) bs_epi[blk++] = (unsigned short)n_epi;
-                ++n_epi;
-            }
+            Sepi[n_epi] = Seg{b, kRoleClear, last, tab_of(b, last), blk, ip[b].gf};
+            for (int q = 0; q < ip[b].gf; ++q) bs_epi[blk++] = (unsigned short)n_epi;
+            ++n_epi;
         }
-        grid_epi = blk;
+        if (blk != grid_epi) return ctx->fail(FR_EINVAL, "internal: final clear block map");
     }
 
     // ---- upload, launch, read back ---------------------------------------------

@@ -11,11 +11,11 @@ namespace fr {
 // entries of A = sum J^T J, the 6 of b = sum J^T r (Eq. 18), then
 // sum of outlier weights, sum of squared residuals and the inlier count.
 constexpr int kRigidVals = 30;
-// Points per thread of the step and build blocks of a multi-registration
-// launch: fewer, fuller blocks amortise each step block's 30-value reduction
-// and each build block's list append, while the other registrations keep the
-// GPU full.  (A single registration runs one point per thread: its blocks
-// must fill the GPU by themselves.)
+// Points per thread of the step and build blocks of a batched launch: fewer,
+// fuller blocks amortise each step block's 30-value reduction and each build
+// block's list append, while the other registrations keep the GPU full.  (A
+// single registration runs one point per thread: its blocks must fill the GPU
+// by themselves; a serving tick, rarely a full GPU, runs two.)
 constexpr int kMultiPointsPerThread = 8;
 constexpr int kBlock = 256;
 

@@ -37,6 +37,10 @@ int64_t steady_ns() {
 }
 
 constexpr int kMaxAhead = 2;         // ticks queued on the GPU before the worker waits
+// Points per thread of a request's step and build blocks.  A serving tick is
+// rarely a full GPU, so its duration is the longest per-thread chain: short
+// chains (more, smaller blocks) keep the latency down.
+constexpr int kServePointsPerThread = 2;
 constexpr size_t kByteUnit = 256;    // byte-arena granularity
 constexpr int kMinTableOrder = 10;   // smallest table: 1024 slots
 
@@ -166,8 +170,8 @@ struct fr_server {
         r.annealed = (q.sigma_start != q.sigma_end && opt.iters > 1) ? 1 : 0;
         r.ntab = r.annealed ? 3 : 1;
         r.cap = table_slots(q.N, r.safe);
-        r.gs = div_up(q.M, (long long)kBlock * kMultiPointsPerThread);
-        r.gp = div_up(q.N, (long long)kBlock * kMultiPointsPerThread);
+        r.gs = div_up(q.M, (long long)kBlock * kServePointsPerThread);
+        r.gp = div_up(q.N, (long long)kBlock * kServePointsPerThread);
         r.gb = r.annealed ? r.gp : 0;
         r.gc = r.annealed ? std::max(1, div_up(q.N, 4096)) : 0;
         r.gf = std::max(1, div_up(q.N, 4096));
@@ -298,9 +302,10 @@ struct fr_server {
                 if (r.annealed && k >= 1) add(r, kRoleClear, k - 1, tab_of(r, k - 1), r.gc);
                 if (k == last_it) tk.results.push_back(rp);
             } else {
+                // the last build's table; every other one was cleared by the
+                // tick after its step (clears run even after a stop)
                 const int last = r.annealed ? last_it : 0;
-                for (int b = (r.annealed && last > 0) ? last - 1 : last; b <= last; ++b)
-                    add(r, kRoleClear, b, tab_of(r, b), r.gf);
+                add(r, kRoleClear, last, tab_of(r, last), r.gf);
                 tk.retire.push_back(rp);
             }
             ++r.stage;

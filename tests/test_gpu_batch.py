@@ -126,3 +126,23 @@ def test_batch_overflowing_item_reruns(ctx):
         dr, dt = pose_diff(T, Ts)
         assert dr < SAME_ROT and dt < SAME_TRANS
     assert out[1][1].lattice_vertices > 1.5 * 3000
+
+
+def test_full_size_batch_equals_single_registrations(ctx):
+    # The benchmark's launch configuration: 16 pairs of 320x240 frames,
+    # point-to-plane, sigma 0.04 -> 0.01 over 20 iterations, twice (the
+    # second call must find every table left clean by the first).
+    pairs = [synth.depth_frame_pair(1000 + i) for i in range(16)]
+    dp = [(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs]
+    opts = dict(residual=1, iters=20, sigma_start=0.04, sigma_end=0.01, w=0.1)
+    first = ctx.register_rigid_batch(dp, **opts)
+    second = ctx.register_rigid_batch(dp, **opts)
+    for (X, Y, Yn), (T, rep, st), (T2, rep2, st2) in zip(dp, first, second):
+        assert st == 0 and st2 == 0
+        Ts, rs = ctx.register_rigid(X, Y, Yn, **opts)
+        dr, dt = pose_diff(T, Ts)
+        assert dr < SAME_ROT and dt < SAME_TRANS, (dr, dt)
+        assert rep.last_inliers == rs.last_inliers
+        assert rep.lattice_vertices == rs.lattice_vertices == rep2.lattice_vertices
+        dr2, dt2 = pose_diff(T, T2)
+        assert dr2 < SAME_ROT and dt2 < SAME_TRANS
