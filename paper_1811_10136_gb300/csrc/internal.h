@@ -250,12 +250,26 @@ struct NgEdges {
 };
 
 // Block-Jacobi PCG over the node blocks, float64 vectors.
+// The per-node PCG kernels give each node six consecutive lanes (one per
+// component; lanes 30 and 31 of a warp idle) and run 64-thread blocks, so
+// that their float64 work spreads over many SMs.
+constexpr int kNgPcgBlock = 64;
+constexpr int kNgNodesPerWarp = 5;
+inline int ng_pcg_grid(int K) {
+    const int per_block = kNgPcgBlock / 32 * kNgNodesPerWarp;
+    return (K + per_block - 1) / per_block;
+}
+// The block-row product runs one warp per row.
+inline int ng_spmv_grid(int K) { return (K + kNgPcgBlock / 32 - 1) / (kNgPcgBlock / 32); }
+
 struct NgPcg {
     int K;
+    int nnzb;
     const int *row_ptr;     // K + 1
     const int2 *ent;        // (block | transposed << 31, partner node)
     const int *diag_blk;    // K
     const float *blocks;
+    double *blocks_d;       // float64 copy of the blocks, made by the set-up kernel
     const float *g;
     double *P;              // K x 36 preconditioner
     double *x, *r, *z, *Ap;

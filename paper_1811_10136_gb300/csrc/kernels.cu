@@ -378,13 +378,19 @@ template <bool PT2PL, int ST>
 __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, IterParams *ipp,
                                            Table t, int *list, DeviceState *st, int blk, int nblk) {
     constexpr int kCh = PT2PL ? 7 : 4;
-    __shared__ int s_warp[kBlock / 32];
-    __shared__ int s_base;
+    constexpr int kClaimCap = 1024;
+    __shared__ int s_claim[kClaimCap];
+    __shared__ int s_n, s_fit, s_base;
+    if (threadIdx.x == 0) {
+        s_n = 0;
+        s_fit = 0;
+    }
+    __syncthreads();
     const IterParams ip = *ipp;
     const int N = job->N;
     const float4 *__restrict__ Y = job->Y;
     const float4 *__restrict__ Yn = job->Yn;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int per_round = nblk * kBlock;
     const int rounds = (N + per_round - 1) / per_round;
     int bad = 0;
@@ -401,8 +407,9 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
             if (!valid) bad |= kFlagRange;
         }
         // Merge runs of equal keys across neighbouring lanes: a segmented
-        // inclusive scan (five shuffle steps, lane order) leaves each run's sum
-        // at its last lane, which alone inserts the key and issues the atomics.
+        // inclusive scan within 8-lane chunks (three shuffle steps, lane
+        // order) leaves each run's sum at its last lane, which alone inserts
+        // the key and issues the atomics.
         unsigned long long key[kD];
         float sum[kD][kCh];
         int tails = 0;
@@ -449,7 +456,9 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
             atomicAdd(rec_v0(t.keys, sl[k]), make_float4(sum[k][0], sum[k][1], sum[k][2], sum[k][3]));
             if (PT2PL) atomicAdd(rec_v1(t.keys, sl[k]), make_float4(sum[k][4], sum[k][5], sum[k][6], 0.f));
         }
-        // Block-wide exclusive prefix of the claimed counts.
+        // The warp's claimed slots go to the block's buffer (a shared
+        // counter, no barrier); a warp that would not fit appends to the list
+        // itself.
         const int cnt = __popc(mask);
         int pre = cnt;
 #pragma unroll
@@ -457,32 +466,40 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
             const int v = __shfl_up_sync(kFull, pre, o);
             if (lane >= o) pre += v;
         }
-        if (lane == 31) s_warp[warp] = pre;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < kBlock / 32; ++w) {
-                const int c = s_warp[w];
-                s_warp[w] = tot;
-                tot += c;
-            }
-            s_base = tot ? atomicAdd(&ipp->nvert, tot) : 0;
-            claimed_total += tot;
-        }
-        __syncthreads();
-        int o = s_base + s_warp[warp] + pre - cnt;
+        const int wtot = __shfl_sync(kFull, pre, 31);
+        if (wtot) {
+            int wbase = 0;
+            if (lane == 31) wbase = atomicAdd(&s_n, wtot);
+            wbase = __shfl_sync(kFull, wbase, 31);
+            int o = pre - cnt;
+            if (wbase + wtot <= kClaimCap) {
 #pragma unroll
-        for (int k = 0; k < kD; ++k)
-            if (mask & (1 << k)) list[o++] = sl[k];
-        __syncthreads();
+                for (int k = 0; k < kD; ++k)
+                    if (mask & (1 << k)) s_claim[wbase + o++] = sl[k];
+                if (lane == 31) atomicMax(&s_fit, wbase + wtot);
+            } else {
+                int g = 0;
+                if (lane == 31) g = atomicAdd(&ipp->nvert, wtot);
+                g = __shfl_sync(kFull, g, 31);
+#pragma unroll
+                for (int k = 0; k < kD; ++k)
+                    if (mask & (1 << k)) list[g + o++] = sl[k];
+                if (lane == 31) claimed_total += wtot;
+            }
+        }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_base = s_fit ? atomicAdd(&ipp->nvert, s_fit) : 0;
+        claimed_total += s_fit;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s_fit; e += kBlock) list[s_base + e] = s_claim[e];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bad |= __shfl_xor_sync(kFull, bad, o);
     if (lane == 0 && bad) atomicOr(&st->flags, bad);
-    if (threadIdx.x == 0) {
-        if (claimed_total) atomicAdd((unsigned long long *)&st->nvert_total, claimed_total);
-        if (blk == 0) atomicAdd(&st->builds, 1);
-    }
+    if (claimed_total) atomicAdd((unsigned long long *)&st->nvert_total, claimed_total);
+    if (threadIdx.x == 0 && blk == 0) atomicAdd(&st->builds, 1);
 }
 
 // Convert: once a build is complete (an earlier launch), turn each listed
@@ -1738,55 +1755,70 @@ __global__ void __launch_bounds__(kBlock) k_ng_points(NgPoints L, int warp_only)
 // The regulariser, one thread per directed edge (j, k):
 // r = s (T_j p_k - T_k p_k), s = sqrt(lambda) / sigma, with
 // d r / d zeta_j = s [-[T_j p_k]_x, I] and d r / d zeta_k = -s [-[T_k p_k]_x, I];
-// adds J_j^T J_j, J_k^T J_k, the cross block and J^T r (float64 arithmetic).
+// adds J_j^T J_j, J_k^T J_k, the cross block and J^T r.
 __global__ void __launch_bounds__(kBlock) k_ng_edges(NgEdges L) {
     const int e = gtid();
-    if (e >= L.E) return;
-    const int2 jk = L.edges[e];
-    const double s = sqrt(L.lambda) / (double)L.ip->sigma;
-    const double *Tj = L.node_T + 16 * jk.x, *Tk = L.node_T + 16 * jk.y;
-    const double *pk = L.node_pos + 3 * jk.y;
-    double a[3], b[3], r[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        a[c] = Tj[4 * c] * pk[0] + Tj[4 * c + 1] * pk[1] + Tj[4 * c + 2] * pk[2] + Tj[4 * c + 3];
-        b[c] = Tk[4 * c] * pk[0] + Tk[4 * c + 1] * pk[1] + Tk[4 * c + 2] * pk[2] + Tk[4 * c + 3];
-        r[c] = s * (a[c] - b[c]);
-    }
-    const double Jj[3][6] = {{0.0, s * a[2], -s * a[1], s, 0.0, 0.0},
-                             {-s * a[2], 0.0, s * a[0], 0.0, s, 0.0},
-                             {s * a[1], -s * a[0], 0.0, 0.0, 0.0, s}};
-    const double Jk[3][6] = {{0.0, -s * b[2], s * b[1], -s, 0.0, 0.0},
-                             {s * b[2], 0.0, -s * b[0], 0.0, -s, 0.0},
-                             {-s * b[1], s * b[0], 0.0, 0.0, 0.0, -s}};
-    const int *eb = L.edge_blk + 3 * e;
-    float *Bjj = L.blocks + (size_t)eb[0] * 36, *Bkk = L.blocks + (size_t)eb[1] * 36;
-    float *Bx = L.blocks + (size_t)eb[2] * 36;
-    const bool j_first = jk.x < jk.y;
-    for (int p = 0; p < 6; ++p) {
-        double gj = 0.0, gk = 0.0;
+    double rr = 0.0;
+    if (e < L.E) {
+        const int2 jk = L.edges[e];
+        const double s = sqrt(L.lambda) / (double)L.ip->sigma;
+        const double *Tj = L.node_T + 16 * jk.x, *Tk = L.node_T + 16 * jk.y;
+        const double *pk = L.node_pos + 3 * jk.y;
+        // the two predictions of node k's position and their difference in
+        // float64 (they nearly cancel); the Jacobian terms in float32, which
+        // is what the float block sums keep of them
+        float a[3], b[3], r[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            gj += Jj[c][p] * r[c];
-            gk += Jk[c][p] * r[c];
+            const double ad = Tj[4 * c] * pk[0] + Tj[4 * c + 1] * pk[1] + Tj[4 * c + 2] * pk[2] + Tj[4 * c + 3];
+            const double bd = Tk[4 * c] * pk[0] + Tk[4 * c + 1] * pk[1] + Tk[4 * c + 2] * pk[2] + Tk[4 * c + 3];
+            const double rd = s * (ad - bd);
+            rr += rd * rd;
+            a[c] = (float)(s * ad);
+            b[c] = (float)(s * bd);
+            r[c] = (float)rd;
         }
-        atomicAdd(L.g + 6 * jk.x + p, (float)gj);
-        atomicAdd(L.g + 6 * jk.y + p, (float)gk);
-        for (int q = 0; q < 6; ++q) {
-            double mjj = 0.0, mkk = 0.0, mjk = 0.0;
+        const float sf = (float)s;
+        const float Jj[3][6] = {{0.0f, a[2], -a[1], sf, 0.0f, 0.0f},
+                                {-a[2], 0.0f, a[0], 0.0f, sf, 0.0f},
+                                {a[1], -a[0], 0.0f, 0.0f, 0.0f, sf}};
+        const float Jk[3][6] = {{0.0f, -b[2], b[1], -sf, 0.0f, 0.0f},
+                                {b[2], 0.0f, -b[0], 0.0f, -sf, 0.0f},
+                                {-b[1], b[0], 0.0f, 0.0f, 0.0f, -sf}};
+        const int *eb = L.edge_blk + 3 * e;
+        float *Bjj = L.blocks + (size_t)eb[0] * 36, *Bkk = L.blocks + (size_t)eb[1] * 36;
+        float *Bx = L.blocks + (size_t)eb[2] * 36;
+        const bool j_first = jk.x < jk.y;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            float gj = 0.0f, gk = 0.0f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                mjj += Jj[c][p] * Jj[c][q];
-                mkk += Jk[c][p] * Jk[c][q];
-                mjk += Jj[c][p] * Jk[c][q];
+                gj += Jj[c][p] * r[c];
+                gk += Jk[c][p] * r[c];
             }
-            atomicAdd(Bjj + 6 * p + q, (float)mjj);
-            atomicAdd(Bkk + 6 * p + q, (float)mkk);
-            // block (min, max) holds rows of the smaller node: J_j^T J_k, or its transpose
-            atomicAdd(Bx + (j_first ? 6 * p + q : 6 * q + p), (float)mjk);
+            atomicAdd(L.g + 6 * jk.x + p, gj);
+            atomicAdd(L.g + 6 * jk.y + p, gk);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                float mjj = 0.0f, mkk = 0.0f, mjk = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    mjj += Jj[c][p] * Jj[c][q];
+                    mkk += Jk[c][p] * Jk[c][q];
+                    mjk += Jj[c][p] * Jk[c][q];
+                }
+                atomicAdd(Bjj + 6 * p + q, mjj);
+                atomicAdd(Bkk + 6 * p + q, mkk);
+                // block (min, max) holds rows of the smaller node: J_j^T J_k, or its transpose
+                atomicAdd(Bx + (j_first ? 6 * p + q : 6 * q + p), mjk);
+            }
         }
     }
-    atomicAdd(L.stats + 1, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    // the regulariser's cost: one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(kFull, rr, o);
+    if ((threadIdx.x & 31) == 0 && rr != 0.0) atomicAdd(L.stats + 1, rr);
 }
 
 // Sum of v over the grid: every block adds its partial; the last block to
@@ -1826,62 +1858,90 @@ __device__ __forceinline__ bool ng_grid_sum(double v, double *partial, int *tick
     return true;
 }
 
-// PCG set-up: P_k = (A_kk)^-1 by Cholesky (pivot floor 1e-12 of the largest
-// diagonal entry; a block below it gets 1 / that entry), x = 0, r = -g,
-// z = P r, rz = r.z.  One thread per node.
-__global__ void __launch_bounds__(kBlock) k_ng_pcg_init(NgPcg L) {
-    const int k = gtid();
+// Lane layout of the per-node PCG kernels: node `node` (of warp-group grp)
+// component `i`; `base` is the group's first lane.  Lanes past the last node
+// (and lanes 30, 31) are inactive but still take part in the shuffles.
+struct NgLane {
+    int node, i, base;
+    bool active;
+};
+
+__device__ __forceinline__ NgLane ng_lane(int K) {
+    const int lane = threadIdx.x & 31, grp = lane / 6;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    NgLane l;
+    l.node = warp * kNgNodesPerWarp + grp;
+    l.i = lane - 6 * grp;
+    l.base = 6 * grp;
+    l.active = grp < kNgNodesPerWarp && l.node < K;
+    return l;
+}
+
+// Component c of a node's 6-vector whose component i sits in lane base + i.
+__device__ __forceinline__ double ng_comp(double v, const NgLane &l, int c) {
+    return __shfl_sync(kFull, v, (l.base + c) & 31);
+}
+
+// PCG set-up: the float64 copy of the blocks, P_k = (A_kk)^-1 by Cholesky
+// (pivot floor 1e-12 of the largest diagonal entry; a block below it gets
+// 1 / that entry), x = 0, r = -g, z = P r, rz = r.z.  The six lanes of a
+// node factor its block alike; lane i then solves for column i of the
+// inverse.
+__global__ void __launch_bounds__(kNgPcgBlock) k_ng_pcg_init(NgPcg L) {
+    for (int e = gtid(); e < L.nnzb * 36; e += grid_stride()) L.blocks_d[e] = (double)L.blocks[e];
+    const NgLane l = ng_lane(L.K);
     double dot = 0.0;
-    if (k < L.K) {
-        const float *B = L.blocks + (size_t)L.diag_blk[k] * 36;
-        double D[36], Lc[36], Pk[36];
+    double ri = 0.0, zi = 0.0;
+    double Pc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // column i of P (= row i)
+    if (l.active) {
+        const float *B = L.blocks + (size_t)L.diag_blk[l.node] * 36;
+        double Lc[36];
         double dmax = 0.0;
-        for (int a = 0; a < 36; ++a) D[a] = (double)B[a];
-        for (int a = 0; a < 6; ++a) dmax = fmax(dmax, D[7 * a]);
+        for (int a = 0; a < 6; ++a) dmax = fmax(dmax, (double)B[7 * a]);
         bool ok = dmax > 0.0;
         const double fl = dmax * 1e-12;
-        for (int i = 0; i < 6 && ok; ++i)
-            for (int j = 0; j <= i; ++j) {
-                double sacc = D[6 * i + j];
-                for (int m = 0; m < j; ++m) sacc -= Lc[6 * i + m] * Lc[6 * j + m];
-                if (i == j) {
+        for (int r = 0; r < 6 && ok; ++r)
+            for (int c = 0; c <= r; ++c) {
+                double sacc = (double)B[6 * r + c];
+                for (int m = 0; m < c; ++m) sacc -= Lc[6 * r + m] * Lc[6 * c + m];
+                if (r == c) {
                     if (!(sacc > fl)) { ok = false; break; }
-                    Lc[6 * i + i] = sqrt(sacc);
+                    Lc[6 * r + r] = sqrt(sacc);
                 } else {
-                    Lc[6 * i + j] = sacc / Lc[6 * j + j];
+                    Lc[6 * r + c] = sacc / Lc[6 * c + c];
                 }
             }
         if (ok) {
-            for (int c = 0; c < 6; ++c) {  // column c of the inverse
-                double y[6], xcol[6];
-                for (int i = 0; i < 6; ++i) {
-                    double sacc = (i == c) ? 1.0 : 0.0;
-                    for (int m = 0; m < i; ++m) sacc -= Lc[6 * i + m] * y[m];
-                    y[i] = sacc / Lc[6 * i + i];
-                }
-                for (int i = 5; i >= 0; --i) {
-                    double sacc = y[i];
-                    for (int m = i + 1; m < 6; ++m) sacc -= Lc[6 * m + i] * xcol[m];
-                    xcol[i] = sacc / Lc[6 * i + i];
-                }
-                for (int i = 0; i < 6; ++i) Pk[6 * i + c] = xcol[i];
+            double y[6];
+            for (int r = 0; r < 6; ++r) {  // L y = e_i
+                double sacc = (r == l.i) ? 1.0 : 0.0;
+                for (int m = 0; m < r; ++m) sacc -= Lc[6 * r + m] * y[m];
+                y[r] = sacc / Lc[6 * r + r];
+            }
+            for (int r = 5; r >= 0; --r) {  // L^T x = y
+                double sacc = y[r];
+                for (int m = r + 1; m < 6; ++m) sacc -= Lc[6 * m + r] * Pc[m];
+                Pc[r] = sacc / Lc[6 * r + r];
             }
         } else {
-            for (int a = 0; a < 36; ++a) Pk[a] = (a % 7 == 0) ? (dmax > 0.0 ? 1.0 / dmax : 1.0) : 0.0;
+            for (int r = 0; r < 6; ++r) Pc[r] = (r == l.i) ? (dmax > 0.0 ? 1.0 / dmax : 1.0) : 0.0;
         }
-        double rr[6];
-        for (int a = 0; a < 6; ++a) {
-            rr[a] = -(double)L.g[6 * k + a];
-            L.r[6 * k + a] = rr[a];
-            L.x[6 * k + a] = 0.0;
-        }
-        for (int a = 0; a < 36; ++a) L.P[36 * (size_t)k + a] = Pk[a];
-        for (int a = 0; a < 6; ++a) {
-            double z = 0.0;
-            for (int c = 0; c < 6; ++c) z += Pk[6 * a + c] * rr[c];
-            L.z[6 * k + a] = z;
-            dot += rr[a] * z;
-        }
+        double *Pk = L.P + 36 * (size_t)l.node;
+        for (int r = 0; r < 6; ++r) Pk[6 * r + l.i] = Pc[r];
+        ri = -(double)L.g[6 * l.node + l.i];
+        L.r[6 * l.node + l.i] = ri;
+        L.x[6 * l.node + l.i] = 0.0;
+    }
+    __syncwarp();  // the node's P is complete (written by its six lanes)
+    // z_i = sum_c P_ic r_c
+    const double *Pk = L.P + 36 * (size_t)(l.active ? l.node : 0);
+    for (int c = 0; c < 6; ++c) {
+        const double rc = ng_comp(ri, l, c);
+        if (l.active) zi += Pk[6 * l.i + c] * rc;
+    }
+    if (l.active) {
+        L.z[6 * l.node + l.i] = zi;
+        dot = ri * zi;
     }
     double total;
     if (ng_grid_sum(dot, L.partial, L.ticket, total)) {
@@ -1893,39 +1953,51 @@ __global__ void __launch_bounds__(kBlock) k_ng_pcg_init(NgPcg L) {
 }
 
 // p = z + beta p_old (the previous iteration's direction update), Ap = A p:
-// one warp per node row over its blocks (A_ab, or A_ba^T for the stored
-// transpose), then alpha = r.z / p.Ap.
-__global__ void __launch_bounds__(kBlock) k_ng_pcg_spmv(NgPcg L) {
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+// one warp per block row.  Its five six-lane groups take the row's blocks
+// g, g + 5, ... (A_ab, or A_ba^T for the stored transpose): lane i of a group
+// loads component i of the partner's direction, gathers the other five by
+// shuffles and forms component i of the block's product; the five groups'
+// sums meet in shared memory.  Then alpha = r.z / p.Ap.
+__global__ void __launch_bounds__(kNgPcgBlock) k_ng_pcg_spmv(NgPcg L) {
+    __shared__ double part[kNgPcgBlock / 32][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int grp = lane / 6, i = lane - 6 * grp, base = 6 * grp;
     const bool stop = L.scal[3] != 0.0;
     const double beta = L.scal[2];
     double dot = 0.0;
-    if (row < L.K && !stop) {
-        double y[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int e = L.row_ptr[row] + lane; e < L.row_ptr[row + 1]; e += 32) {
-            const int2 en = L.ent[e];
+    if (!stop && row < L.K) {  // warp-uniform
+        const int e0 = L.row_ptr[row], e1 = L.row_ptr[row + 1];
+        double y = 0.0;
+        for (int t0 = e0; t0 < e1; t0 += kNgNodesPerWarp) {
+            const int e = t0 + grp;
+            const bool has = grp < kNgNodesPerWarp && e < e1;
+            const int2 en = has ? L.ent[e] : make_int2(0, 0);
             const int blk = en.x & 0x7fffffff, b = en.y;
             const bool tr = en.x < 0;
+            const double pbi = has ? L.z[6 * b + i] + beta * L.p_old[6 * b + i] : 0.0;
             double pb[6];
-            for (int c = 0; c < 6; ++c) pb[c] = L.z[6 * b + c] + beta * L.p_old[6 * b + c];
-            const float *M = L.blocks + (size_t)blk * 36;
-            for (int i = 0; i < 6; ++i) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) pb[c] = __shfl_sync(kFull, pbi, (base + c) & 31);
+            if (has) {
+                const double *M = L.blocks_d + (size_t)blk * 36;
                 double acc = 0.0;
-                for (int c = 0; c < 6; ++c) acc += (double)(tr ? M[6 * c + i] : M[6 * i + c]) * pb[c];
-                y[i] += acc;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) acc += (tr ? M[6 * c + i] : M[6 * i + c]) * pb[c];
+                y += acc;
             }
         }
+        part[wib][lane] = y;  // lanes 30, 31 hold 0
+        __syncwarp();
+        if (lane < 6) {
+            double s = 0.0;
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) y[i] += __shfl_xor_sync(kFull, y[i], o);
-        if (lane == 0)
-            for (int i = 0; i < 6; ++i) {
-                const double pn = L.z[6 * row + i] + beta * L.p_old[6 * row + i];
-                L.p_new[6 * row + i] = pn;
-                L.Ap[6 * row + i] = y[i];
-                dot += pn * y[i];
-            }
+            for (int g = 0; g < kNgNodesPerWarp; ++g) s += part[wib][6 * g + lane];
+            const double pn = L.z[6 * row + lane] + beta * L.p_old[6 * row + lane];
+            L.p_new[6 * row + lane] = pn;
+            L.Ap[6 * row + lane] = s;
+            dot = pn * s;
+        }
     }
     double total;
     if (ng_grid_sum(dot, L.partial, L.ticket, total) && !stop) {
@@ -1938,25 +2010,31 @@ __global__ void __launch_bounds__(kBlock) k_ng_pcg_spmv(NgPcg L) {
     }
 }
 
-// x += alpha p, r -= alpha Ap, z = P r, then beta = r.z / rz and rz = r.z.
-__global__ void __launch_bounds__(kBlock) k_ng_pcg_update(NgPcg L) {
-    const int k = gtid();
+// x += alpha p, r -= alpha Ap, z = P r, then beta = r.z / rz and rz = r.z
+// (one lane per component).
+__global__ void __launch_bounds__(kNgPcgBlock) k_ng_pcg_update(NgPcg L) {
+    const NgLane l = ng_lane(L.K);
     const bool stop = L.scal[3] != 0.0;
     double dot = 0.0;
-    if (k < L.K && !stop) {
+    if (!stop) {
         const double alpha = L.scal[1];
-        double rr[6];
-        for (int a = 0; a < 6; ++a) {
-            L.x[6 * k + a] += alpha * L.p_new[6 * k + a];
-            rr[a] = L.r[6 * k + a] - alpha * L.Ap[6 * k + a];
-            L.r[6 * k + a] = rr[a];
+        double ri = 0.0;
+        if (l.active) {
+            const size_t o = 6 * (size_t)l.node + l.i;
+            L.x[o] += alpha * L.p_new[o];
+            ri = L.r[o] - alpha * L.Ap[o];
+            L.r[o] = ri;
         }
-        const double *Pk = L.P + 36 * (size_t)k;
-        for (int a = 0; a < 6; ++a) {
-            double z = 0.0;
-            for (int c = 0; c < 6; ++c) z += Pk[6 * a + c] * rr[c];
-            L.z[6 * k + a] = z;
-            dot += rr[a] * z;
+        double zi = 0.0;
+        const double *Pk = L.P + 36 * (size_t)(l.active ? l.node : 0);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const double rc = ng_comp(ri, l, c);
+            if (l.active) zi += Pk[6 * l.i + c] * rc;
+        }
+        if (l.active) {
+            L.z[6 * (size_t)l.node + l.i] = zi;
+            dot = ri * zi;
         }
     }
     double total;
@@ -2158,24 +2236,26 @@ void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t 
 
 void launch_ng_edges(const NgEdges &a, cudaStream_t s) {
     if (a.E <= 0) return;
-    k_ng_edges<<<(a.E + kBlock - 1) / kBlock, kBlock, 0, s>>>(a);
+    k_ng_edges<<<(a.E + 63) / 64, 64, 0, s>>>(a);  // small blocks: spread over the SMs
 }
 
 void launch_ng_pcg_init(const NgPcg &a, cudaStream_t s) {
-    k_ng_pcg_init<<<(a.K + kBlock - 1) / kBlock, kBlock, 0, s>>>(a);
+    k_ng_pcg_init<<<ng_pcg_grid(a.K), kNgPcgBlock, 0, s>>>(a);
 }
 
 void launch_ng_pcg_spmv(const NgPcg &a, cudaStream_t s) {
-    k_ng_pcg_spmv<<<(a.K + kBlock / 32 - 1) / (kBlock / 32), kBlock, 0, s>>>(a);
+    k_ng_pcg_spmv<<<ng_spmv_grid(a.K), kNgPcgBlock, 0, s>>>(a);
 }
 
 void launch_ng_pcg_update(const NgPcg &a, cudaStream_t s) {
-    k_ng_pcg_update<<<(a.K + kBlock - 1) / kBlock, kBlock, 0, s>>>(a);
+    k_ng_pcg_update<<<ng_pcg_grid(a.K), kNgPcgBlock, 0, s>>>(a);
 }
 
 void launch_ng_update(int K, const double *dx, double *node_T, float *node_dq, double *twist2,
                       cudaStream_t s) {
-    k_ng_update<<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(K, dx, node_T, node_dq, twist2);
+    // one node per thread, 32-thread blocks: the float64 exponentials of a
+    // thousand nodes spread over ~32 SMs instead of 4
+    k_ng_update<<<(K + 31) / 32, 32, 0, s>>>(K, dx, node_T, node_dq, twist2);
 }
 
 void launch_zero_values(Table t, int grid, cudaStream_t s) {

@@ -47,6 +47,7 @@ struct fr_nodegraph {
     int2 *ent = nullptr;
     // workspace (device)
     float *blocks = nullptr, *g = nullptr, *node_dq = nullptr;
+    double *blocks_d = nullptr;   // float64 copy for the PCG
     double *stats = nullptr;  // [sum_w, cost, twist^2, pad]
     unsigned long long *inliers = nullptr;
     double *node_T = nullptr, *P = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *Ap = nullptr;
@@ -70,7 +71,7 @@ cudaError_t up(T **d, const std::vector<T> &h) {
 
 void free_model(fr_nodegraph *g) {
     void *ptrs[] = {g->X, g->w, g->perm, g->seg_start, g->seg_blk, g->seg_nodes, g->seg_coef, g->edges,
-                    g->edge_blk, g->node_pos, g->row_ptr, g->diag_blk, g->ent, g->blocks, g->g,
+                    g->edge_blk, g->node_pos, g->row_ptr, g->diag_blk, g->ent, g->blocks, g->blocks_d, g->g,
                     g->node_dq, g->stats, g->inliers, g->node_T, g->P, g->x, g->r, g->z, g->Ap,
                     g->p[0], g->p[1], g->scal, g->partial, g->ticket};
     for (void *q : ptrs) cudaFree(q);
@@ -214,7 +215,7 @@ FR_API fr_status fr_nodegraph_create(fr_ctx *ctx, const float *d_Xref, const int
     g->E = E;
     g->S = S;
     g->nnzb = nnzb;
-    g->grid_max = std::max((K + kBlock - 1) / kBlock, (K + kBlock / 32 - 1) / (kBlock / 32));
+    g->grid_max = std::max(ng_pcg_grid(K), ng_spmv_grid(K));  // the grid-sum kernels
     g->h_blocks_a = ba;
     g->h_blocks_b = bb;
     std::vector<int> perm(order.begin(), order.end());
@@ -237,6 +238,7 @@ FR_API fr_status fr_nodegraph_create(fr_ctx *ctx, const float *d_Xref, const int
     chk(up(&g->ent, ent));
     const size_t n6 = 6 * (size_t)K;
     chk(cudaMalloc((void **)&g->blocks, (size_t)nnzb * 36 * sizeof(float)));
+    chk(cudaMalloc((void **)&g->blocks_d, (size_t)nnzb * 36 * sizeof(double)));
     chk(cudaMalloc((void **)&g->g, n6 * sizeof(float)));
     chk(cudaMalloc((void **)&g->node_dq, (size_t)K * 8 * sizeof(float)));
     chk(cudaMalloc((void **)&g->stats, 4 * sizeof(double)));
@@ -362,7 +364,9 @@ void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Spans &sp, 
     L.row_ptr = g->row_ptr;
     L.ent = g->ent;
     L.diag_blk = g->diag_blk;
+    L.nnzb = g->nnzb;
     L.blocks = g->blocks;
+    L.blocks_d = g->blocks_d;
     L.g = g->g;
     L.P = g->P;
     L.x = g->x;
