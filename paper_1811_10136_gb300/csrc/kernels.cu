@@ -409,15 +409,16 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
         // Merge runs of equal keys across neighbouring lanes: a segmented
         // inclusive scan within 8-lane chunks (three shuffle steps, lane
         // order) leaves each run's sum at its last lane, which alone inserts
-        // the key and issues the atomics.
-        unsigned long long key[kD];
-        float sum[kD][kCh];
-        int tails = 0;
+        // the key and issues the atomics.  One vertex at a time: only its
+        // seven sums are live (holding all four vertices' sums for a joint
+        // four-probe insert spilled more than the overlapped probes saved).
+        int sl[kD];
+        int mask = 0;
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
-            key[k] = valid ? sx.key[k] : kEmpty;
-            const unsigned long long prev = __shfl_up_sync(kFull, key[k], 1);
-            const unsigned heads = __ballot_sync(kFull, (lane & 7) == 0 || prev != key[k]);
+            const unsigned long long key = valid ? sx.key[k] : kEmpty;
+            const unsigned long long prev = __shfl_up_sync(kFull, key, 1);
+            const unsigned heads = __ballot_sync(kFull, (lane & 7) == 0 || prev != key);
             const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
             const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
             const float b = valid ? sx.b[k] : 0.0f;
@@ -435,26 +436,22 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
             for (int o = 1; o < 8; o <<= 1) {
 #pragma unroll
                 for (int c = 0; c < kCh; ++c) {
-                    const float t = __shfl_up_sync(kFull, v[c], o);
-                    if (lane - o >= head) v[c] += t;
+                    const float tv = __shfl_up_sync(kFull, v[c], o);
+                    if (lane - o >= head) v[c] += tv;
                 }
             }
-#pragma unroll
-            for (int c = 0; c < kCh; ++c) sum[k][c] = v[c];
-            tails |= (valid && tail) ? (1 << k) : 0;
-        }
-        // Run tails insert their keys (four probes in flight) and accumulate.
-        int sl[kD];
-        const int mask = insert4(t.keys, t.mask, key, tails, sl, t.max_probe);
-#pragma unroll
-        for (int k = 0; k < kD; ++k) {
-            if (!(tails >> k & 1)) continue;
-            if (sl[k] < 0) {
-                bad |= kFlagCapacity;
-                continue;
+            sl[k] = -1;
+            if (valid && tail) {
+                bool c;
+                sl[k] = insert_key(t.keys, t.mask, key, t.max_probe, c);
+                if (sl[k] < 0) {
+                    bad |= kFlagCapacity;
+                } else {
+                    mask |= c ? (1 << k) : 0;
+                    atomicAdd(rec_v0(t.keys, sl[k]), make_float4(v[0], v[1], v[2], v[3]));
+                    if (PT2PL) atomicAdd(rec_v1(t.keys, sl[k]), make_float4(v[4], v[5], v[6], 0.f));
+                }
             }
-            atomicAdd(rec_v0(t.keys, sl[k]), make_float4(sum[k][0], sum[k][1], sum[k][2], sum[k][3]));
-            if (PT2PL) atomicAdd(rec_v1(t.keys, sl[k]), make_float4(sum[k][4], sum[k][5], sum[k][6], 0.f));
         }
         // The warp's claimed slots go to the block's buffer (a shared
         // counter, no barrier); a warp that would not fit appends to the list

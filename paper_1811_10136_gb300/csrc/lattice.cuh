@@ -163,46 +163,6 @@ __device__ __forceinline__ int insert_key(unsigned long long *keys, uint32_t mas
     return -1;
 }
 
-// Inserts up to four keys at once (key k only where active & (1 << k)):
-// the first probes are loaded together and the needed CASes issued back to
-// back, so the four round trips to L2 overlap; collision chains are walked
-// afterwards by insert_key (max_probe slots in all, counting the home slot).  slot[k] = -1 where
-// inactive or no free slot was found; bit k of the return value is set where
-// this call created the vertex.
-__device__ __forceinline__ int insert4(unsigned long long *keys, uint32_t mask,
-                                       const unsigned long long key[kD], int active, int slot[kD],
-                                       uint32_t max_probe) {
-    uint32_t s[kD];
-    unsigned long long cur[kD], old[kD];
-#pragma unroll
-    for (int k = 0; k < kD; ++k) s[k] = slot_of(key[k], mask);
-#pragma unroll
-    for (int k = 0; k < kD; ++k) cur[k] = (active >> k & 1) ? __ldcg(rec_key(keys, s[k])) : key[k];
-#pragma unroll
-    for (int k = 0; k < kD; ++k)
-        old[k] = ((active >> k & 1) && cur[k] == kEmpty) ? atomicCAS(rec_key(keys, s[k]), kEmpty, key[k])
-                                                          : cur[k];
-    int claimed = 0;
-#pragma unroll
-    for (int k = 0; k < kD; ++k) {
-        slot[k] = -1;
-        if (!(active >> k & 1)) continue;
-        if (cur[k] == kEmpty && old[k] == kEmpty) {
-            claimed |= 1 << k;
-            slot[k] = (int)s[k];
-        } else if (old[k] == key[k]) {
-            slot[k] = (int)s[k];
-        } else {
-            bool c;
-            // the home slot was probe 1: max_probe - 1 more (a lookup probes max_probe slots)
-            const int t = max_probe > 1 ? insert_key(keys, mask, key[k], max_probe - 1, c, (s[k] + 1) & mask) : -1;
-            slot[k] = t;
-            claimed |= c ? (1 << k) : 0;
-        }
-    }
-    return claimed;
-}
-
 // Slot of `key`, or -1 if absent.  The table must not change during the call
 // (read through the read-only path).  An insert never places a key more than
 // max_probe slots past its home, so a lookup stops there too: a full table
