@@ -146,3 +146,27 @@ def test_full_size_batch_equals_single_registrations(ctx):
         assert rep.lattice_vertices == rs.lattice_vertices == rep2.lattice_vertices
         dr2, dt2 = pose_diff(T, T2)
         assert dr2 < SAME_ROT and dt2 < SAME_TRANS
+
+
+@pytest.mark.parametrize("iters", [1, 3])
+def test_batch_tiny_items_match_oracle(ctx, orc, iters):
+    # Items of 1 to a few thousand points (one block, partial blocks, a ragged
+    # tail) with one or three EM iterations, annealed and fixed sigma mixed:
+    # each matches the oracle's registration.
+    sizes = [(1, 1), (37, 29), (1000, 257), (2999, 5003)]
+    sig = [(0.1, 0.1), (0.12, 0.08), (0.1, 0.1), (0.12, 0.08)]
+    pairs = []
+    for M, N in sizes:
+        src = synth.sphere_bumps_pair(M + N, n_model=max(M, 8), n_obs=max(N, 8), outlier_frac=0.0,
+                                      max_angle_deg=1.0, max_trans=0.005)
+        pairs.append(synth.RigidPair(src.X[:M], src.Y[:N], src.T_gt))
+    out = ctx.register_rigid_batch([(dev(p.X), dev(p.Y), None) for p in pairs], sigmas=sig, residual=0,
+                                   iters=iters, w=0.1)
+    for p, (s0, s1), (T, rep, st) in zip(pairs, sig, out):
+        assert st == 0
+        To, ro = orc.register_rigid(p.X, p.Y, None, sigma=np.float32(s0), sigma_end=np.float32(s1),
+                                    w=np.float32(0.1), iters=iters)
+        dr, dt = pose_diff(T, To)
+        assert dr < ROT_TOL and dt < TRANS_TOL, (dr, dt)
+        assert rep.iters_run == iters
+        assert rep.degenerate_iters == ro.degenerate_iters
