@@ -227,8 +227,11 @@ FR_API fr_status fr_estep_storage(fr_ctx *ctx, const float *d_X, int64_t M, cons
  * delta zeta = -A^{-1} b in float64 on the device and update
  * T <- exp(delta zeta^) T.  T_inout (host) carries the initial pose in and
  * the result out; report (nullable) receives diagnostics.  Synchronises the
- * stream.  FR_EINVAL for bad arguments or out-of-range inputs; FR_ECAPACITY
- * if the lattice table fills (it is sized 8 N slots, so this indicates a bug). */
+ * stream.  FR_EINVAL for bad arguments or out-of-range inputs.  The lattice
+ * table starts at 3 N slots (a power of two, inserts bounded to 128 probes);
+ * a registration whose table overflows is rerun from its initial pose at
+ * 6 N slots, which holds every vertex (at most 4 N), so FR_ECAPACITY here
+ * indicates a bug. */
 FR_API fr_status fr_register_rigid(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                                    const float *d_Yn, int64_t N, const fr_options *opt,
                                    double T_inout[16], fr_report *report);
