@@ -308,7 +308,11 @@ typedef struct {
  * and clear run side by side, so that one item's float64 solve overlaps the
  * others' work.  Items may differ in size and sigma schedule; they share
  * opt->residual, iters, kahan, renormalize_normals and stop_twist (blur is
- * not supported: FR_ENOTSUPPORTED).  reports (nullable) has n_items entries.
+ * not supported: FR_ENOTSUPPORTED).  1 <= n_items <= 16384 (13107 with 16-bit
+ * storage: a launch's block-to-role map indexes its segments with 16 bits).
+ * reports (nullable) has n_items entries.  An item whose compact lattice
+ * table overflows is rerun (from its initial pose) with the items that
+ * overflowed, at the size that cannot.
  * Returns FR_OK, or the status of the first failed item (each item's own
  * outcome is in its status field; failed items keep their input pose).
  * Synchronises the stream. */
