@@ -127,6 +127,12 @@ FR_API const char *fr_status_string(fr_status s);
 FR_API fr_status fr_ctx_create(int device, void *cuda_stream, fr_ctx **out);
 FR_API fr_status fr_ctx_destroy(fr_ctx *ctx);
 FR_API fr_status fr_ctx_set_stream(fr_ctx *ctx, void *cuda_stream);
+/* fr_ctx_set_workspace_limit: the most device memory (bytes) the lattice-table
+ * arena of batched registrations may hold; 0 (the default) = no limit.  A
+ * batched call whose tables would need more fails with FR_ENOMEM before it
+ * allocates -- including the safe-size rerun of items whose compact tables
+ * overflowed, which then report FR_ENOMEM in their own status field. */
+FR_API fr_status fr_ctx_set_workspace_limit(fr_ctx *ctx, size_t bytes);
 FR_API const char *fr_ctx_last_error(const fr_ctx *ctx);
 /* Number of kernels this context has launched (graph replays count each node). */
 FR_API int64_t fr_ctx_kernel_launches(const fr_ctx *ctx);
@@ -452,7 +458,9 @@ FR_API fr_status fr_server_destroy(fr_server *srv);
  * array compiled into the library (about 4.5 MB on every device that loads
  * it, held until the process exits).  The first call on a device finds that
  * array's device address and empties it (synchronising the stream once); it
- * should come before any stream capture.  Every call shares the array and
+ * should come before any stream capture: made on a capturing stream it
+ * returns FR_EINVAL and the set-up is tried again by the next call (a failed
+ * set-up is never remembered).  Every call shares the array and
  * leaves it empty; calls that overlap on the GPU race and give wrong results.
  * Synchronises the stream.  FR_EINVAL for null or misaligned pointers,
  * M < 1, N < 1, N > FR_NOALLOC_MAX_OBS, sigma <= 0, a non-finite pose or

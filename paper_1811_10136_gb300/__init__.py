@@ -34,6 +34,7 @@ EXPORTED = [
     "fr_lattice_build", "fr_lattice_splat", "fr_lattice_blur", "fr_lattice_slice",
     "fr_lattice_vertices", "fr_lattice_info", "fr_lattice_destroy", "fr_estep",
     "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
+    "fr_ctx_set_workspace_limit",
     "fr_ctx_transfer_bytes", "fr_estep_noalloc", "fr_register_rigid_batch",
     "fr_register_rigid_batch_host", "fr_register_articulated", "fr_estep_storage",
     "fr_server_create", "fr_server_submit", "fr_server_poll", "fr_server_wait", "fr_server_release",
@@ -154,6 +155,7 @@ def load(build_if_missing: bool = True):
                                     _f64p, ctypes.POINTER(fr_report)]
     L.fr_register_rigid_host.argtypes = L.fr_register_rigid.argtypes
     L.fr_ctx_set_profiling.argtypes = [_vp, ctypes.c_int]
+    L.fr_ctx_set_workspace_limit.argtypes = [_vp, ctypes.c_size_t]
     L.fr_ctx_profile.argtypes = [_vp, ctypes.POINTER(fr_profile), ctypes.c_int]
     L.fr_ctx_transfer_bytes.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
     L.fr_register_rigid_batch.argtypes = [_vp, ctypes.POINTER(fr_batch_item), ctypes.c_int,
@@ -296,6 +298,10 @@ class Context:
         self._check(load().fr_ctx_transfer_bytes(self._h, ctypes.byref(a), ctypes.byref(b)),
                     "fr_ctx_transfer_bytes")
         return a.value, b.value
+
+    def set_workspace_limit(self, nbytes: int):
+        """Cap the lattice-table arena of batched calls at nbytes (0: none)."""
+        self._check(load().fr_ctx_set_workspace_limit(self._h, int(nbytes)), "fr_ctx_set_workspace_limit")
 
     def set_profiling(self, on: bool):
         self._check(load().fr_ctx_set_profiling(self._h, int(bool(on))), "fr_ctx_set_profiling")

@@ -529,6 +529,12 @@ FR_API fr_status fr_ctx_set_stream(fr_ctx *ctx, void *cuda_stream) {
     return FR_OK;
 }
 
+FR_API fr_status fr_ctx_set_workspace_limit(fr_ctx *ctx, size_t bytes) {
+    if (!ctx) return FR_EINVAL;
+    ctx->ws_limit = bytes;
+    return FR_OK;
+}
+
 FR_API const char *fr_ctx_last_error(const fr_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 FR_API int64_t fr_ctx_kernel_launches(const fr_ctx *ctx) { return ctx ? ctx->launches : 0; }

@@ -59,7 +59,11 @@ fr_status ensure_arenas(fr_ctx *ctx, size_t slots, size_t misc, size_t up, size_
     if (!ctx->batch) ctx->batch = new BatchWorkspace();
     BatchWorkspace *w = ctx->batch;
     if (slots > w->slots_cap) {
-        const size_t cap = std::max(slots, w->slots_cap * 3 / 2);
+        if (ctx->ws_limit && table_bytes(slots) > ctx->ws_limit)
+            return ctx->fail(FR_ENOMEM, "batch tables need %zu bytes, above the context's workspace limit %zu",
+                             table_bytes(slots), ctx->ws_limit);
+        size_t cap = std::max(slots, w->slots_cap * 3 / 2);
+        if (ctx->ws_limit) cap = std::min(cap, ctx->ws_limit / table_bytes(1));
         cudaStreamSynchronize(ctx->stream);
         cudaFree(w->keys);
         w->keys = nullptr;
@@ -393,25 +397,47 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     return first_bad;
 }
 
+// Status of an item that run_batch has not reached yet: a call that fails
+// before its per-item results (an allocation, a CUDA error) leaves it set.
+constexpr fr_status kUnset = (fr_status)-1;
+
 // Compact tables first; items whose table overflowed are rerun (from their
-// initial poses) at the size that cannot overflow.
+// initial poses) at the size that cannot overflow.  Every item leaves with
+// its own outcome: an item the call never reached takes the call's status,
+// and a rerun that fails takes the rerun's status, not its earlier one.
 fr_status run_batch_sized(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *opt,
                           fr_report *reports) {
     std::vector<fr_batch_item> init(items, items + n);
+    for (int b = 0; b < n; ++b) items[b].status = kUnset;
     fr_status st = run_batch(ctx, items, n, opt, reports, false);
+    bool reached = true;
+    for (int b = 0; b < n; ++b)
+        if (items[b].status == kUnset) {
+            items[b] = init[b];
+            items[b].status = st != FR_OK ? st : FR_ECUDA;
+            reached = false;
+        }
+    if (!reached) return st != FR_OK ? st : FR_ECUDA;
     std::vector<int> redo;
     for (int b = 0; b < n; ++b)
         if (items[b].status == FR_ECAPACITY) redo.push_back(b);
     if (redo.empty()) return st;
     std::vector<fr_batch_item> sub;
     std::vector<fr_report> subrep(redo.size());
-    for (int b : redo) sub.push_back(init[b]);
-    run_batch(ctx, sub.data(), (int)sub.size(), opt, reports ? subrep.data() : nullptr, true);
-    st = FR_OK;
+    for (int b : redo) {
+        sub.push_back(init[b]);
+        sub.back().status = kUnset;
+    }
+    const fr_status rs = run_batch(ctx, sub.data(), (int)sub.size(), opt, reports ? subrep.data() : nullptr, true);
     for (size_t q = 0; q < redo.size(); ++q) {
+        if (sub[q].status == kUnset) {
+            sub[q] = init[redo[q]];
+            sub[q].status = rs != FR_OK ? rs : FR_ECUDA;
+        }
         items[redo[q]] = sub[q];
         if (reports) reports[redo[q]] = subrep[q];
     }
+    st = FR_OK;
     for (int b = 0; b < n; ++b)
         if (items[b].status != FR_OK && st == FR_OK) st = items[b].status;
     return st;

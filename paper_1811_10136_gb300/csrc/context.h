@@ -89,6 +89,7 @@ struct fr_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
     int num_sms = 0;
+    size_t ws_limit = 0;  // largest lattice-table arena a batched call may hold (0: no limit)
     int64_t launches = 0;
     int64_t h2d_bytes = 0, d2h_bytes = 0;
 

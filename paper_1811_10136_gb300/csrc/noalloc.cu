@@ -142,19 +142,36 @@ __global__ void k_na_clear(View v) {
 }
 
 // Per-device set-up: the device address of the array (host code may not use
-// the symbol itself) and an empty table, done once per device.
+// the symbol itself) and an empty table.  It runs under a per-device mutex
+// and is marked done only when it succeeded, so a failed set-up (say a first
+// call made while the stream was being captured, which is refused) is tried
+// again by the next call instead of failing every later one.
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
-unsigned char *g_base[kMaxDevices];
-cudaError_t g_setup_err[kMaxDevices];
+std::mutex g_setup_mu[kMaxDevices];
+unsigned char *g_base[kMaxDevices];  // written under the mutex, then only read
+bool g_ready[kMaxDevices];
 
-void setup_device(int dev, cudaStream_t stream) {
+// FR_OK once device `dev` has its scratch address and an empty table.
+fr_status setup_device(int dev, cudaStream_t stream) {
+    std::lock_guard<std::mutex> lock(g_setup_mu[dev]);
+    if (g_ready[dev]) return FR_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return FR_ECUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return FR_EINVAL;  // set-up synchronises: not while capturing
     unsigned char *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
     if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, kScratchBytes, stream);  // free slots are zero
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    g_setup_err[dev] = e;
-    g_base[dev] = (e == cudaSuccess) ? p : nullptr;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FR_ECUDA;
+    }
+    g_base[dev] = p;
+    g_ready[dev] = true;
+    return FR_OK;
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -177,8 +194,8 @@ extern "C" FR_API fr_status fr_estep_noalloc(const float *d_X, int64_t M, const 
         cudaGetLastError();
         return FR_ECUDA;
     }
-    std::call_once(g_once[dev], setup_device, dev, stream);
-    if (g_setup_err[dev] != cudaSuccess || !g_base[dev]) return FR_ECUDA;
+    const fr_status ss = setup_device(dev, stream);
+    if (ss != FR_OK) return ss;
     const View v = view_of(g_base[dev]);
 
     // Feature scales alpha / (sqrt(i (i+1)) sigma), alpha = sqrt(2/3) (d+1).

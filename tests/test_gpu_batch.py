@@ -170,3 +170,38 @@ def test_batch_tiny_items_match_oracle(ctx, orc, iters):
         assert dr < ROT_TOL and dt < TRANS_TOL, (dr, dt)
         assert rep.iters_run == iters
         assert rep.degenerate_iters == ro.degenerate_iters
+
+
+def test_failed_rerun_reports_its_own_status():
+    # An item that overflows its compact table is rerun at the safe size; when
+    # that rerun cannot get its tables (here a workspace cap between the two
+    # sizes refuses the allocation on the host), the item must report the
+    # rerun's failure (FR_ENOMEM) and keep its initial pose, while the other
+    # item keeps its own successful result.
+    import paper_1811_10136_gb300 as fr
+    c = fr.Context(0)
+    rng = np.random.default_rng(79)
+    n = 20000
+    X = np.zeros((n, 4), np.float32)
+    X[:, :3] = rng.uniform(-1, 1, size=(n, 3))   # sparse at sigma 1 cm: ~4 new vertices per point
+    Y = X.copy()
+    Y[:, 0] += 0.001
+    good = synth.depth_frame_pair(311, W=64, H=48)
+    pairs = [(dev(good.X), dev(good.Y), None), (dev(X), dev(Y), None)]
+    slot_bytes = 64
+    compact = slot_bytes * 3 * (16384 + 65536)     # both items' compact tables (3 N rounded up, 3 each)
+    safe = slot_bytes * 3 * 131072                 # the overflowing item's safe tables (6 N rounded up)
+    assert compact < safe
+    c.set_workspace_limit((compact + safe) // 2)
+    out = c.register_rigid_batch(pairs, residual=0, iters=3, sigma_start=0.01, sigma_end=0.01)
+    assert out[0][2] == fr.FR_OK
+    assert out[1][2] == fr.FR_ENOMEM
+    assert np.array_equal(out[1][0], np.eye(4))
+    Ts, _ = c.register_rigid(pairs[0][0], pairs[0][1], residual=0, iters=3, sigma_start=0.01, sigma_end=0.01)
+    dr, dt = pose_diff(out[0][0], Ts)
+    assert dr < SAME_ROT and dt < SAME_TRANS
+    # without the cap the same batch succeeds
+    c.set_workspace_limit(0)
+    out = c.register_rigid_batch(pairs, residual=0, iters=3, sigma_start=0.01, sigma_end=0.01)
+    assert out[0][2] == fr.FR_OK and out[1][2] == fr.FR_OK
+    c.close()

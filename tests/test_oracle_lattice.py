@@ -225,3 +225,66 @@ def test_sigma_schedule(orc):
     r = s[1:].astype(np.float64) / s[:-1]
     np.testing.assert_allclose(r, 0.25 ** (1 / 19), rtol=1e-6)
     assert (orc.sigma_schedule(0.02, 0.02, 5) == np.float32(0.02)).all()
+
+
+def _blur_stencil():
+    """The blur of Section 4.2 as one convolution: one (1/2, 1, 1/2) pass
+    along each of the d + 1 = 4 lattice axes, the neighbour along axis j being
+    offset by e_j = (1, 1, 1, 1) - 4 delta_j.  Offsets sum_j a_j e_j with
+    a_j in {-1, 0, 1} and weights prod_j (1/2 if a_j != 0 else 1); because
+    e_0 + ... + e_3 = 0, different a give the same offset and their weights
+    add up."""
+    import itertools
+    e = [np.array([1, 1, 1, 1]) - 4 * np.eye(4, dtype=int)[j] for j in range(4)]
+    out = {}
+    for a in itertools.product((-1, 0, 1), repeat=4):
+        off = tuple(int(x) for x in sum(aj * ej for aj, ej in zip(a, e)))
+        out[off] = out.get(off, 0.0) + float(np.prod([0.5 if aj else 1.0 for aj in a]))
+    return out
+
+
+def test_blur_is_the_four_axis_stencil(orc):
+    # A unit value at the lattice point 0 (a point at the origin sits on it
+    # exactly: barycentric weight 1 there, 0 on the other three vertices),
+    # inside a dense cloud of zero-valued points so that every vertex the
+    # stencil reaches exists.  After the blur every vertex must hold exactly
+    # the stencil weight of its offset from 0 (dyadic sums: exact in float64),
+    # and every other vertex 0.  A pass along a repeated or wrong axis, a sign
+    # error in the offset or a dropped pass changes some of these values.
+    stencil = _blur_stencil()
+    assert len(stencil) == 65 and sum(stencil.values()) == 16.0
+    assert stencil[(0, 0, 0, 0)] == 1.0 + 2 * 0.5 ** 4   # a = 0 and a = +-(1, 1, 1, 1) fold onto 0
+    rng = np.random.default_rng(16)
+    n = 200_000
+    P = np.zeros((n + 1, 4), np.float32)
+    P[1:, :3] = rng.uniform(-5.0, 5.0, size=(n, 3))
+    V = np.zeros((n + 1, 1))
+    V[0, 0] = 1.0
+    lat = orc.Lattice(P, V, 1.0, blur=True)
+    keys, vals = lat.vertices()
+    assert (keys.sum(1) == 0).all()
+    expect = np.array([stencil.get(tuple(int(x) for x in k), 0.0) for k in keys])
+    np.testing.assert_array_equal(vals[:, 0], expect)
+    # every stencil offset is present (the neighbourhood was complete)
+    present = {tuple(int(x) for x in k) for k in keys}
+    assert set(stencil) <= present
+
+
+def test_blur_second_moment_is_isotropic(orc):
+    # The blurred unit impulse as a distribution over the lattice: mass 2^4,
+    # mean 0 and, each pass adding variance 1/2 e_j e_j^T, second moment
+    # 1/2 sum_j e_j e_j^T = 8 (I - 11^T / 4) -- isotropic within the hyperplane
+    # sum z = 0, which the elevation maps feature space onto by a similarity.
+    rng = np.random.default_rng(17)
+    n = 200_000
+    P = np.zeros((n + 1, 4), np.float32)
+    P[1:, :3] = rng.uniform(-5.0, 5.0, size=(n, 3))
+    V = np.zeros((n + 1, 1))
+    V[0, 0] = 1.0
+    keys, vals = orc.Lattice(P, V, 1.0, blur=True).vertices()
+    w = vals[:, 0]
+    z = keys.astype(np.float64)
+    assert w.sum() == 16.0
+    np.testing.assert_array_equal(w @ z, np.zeros(4))
+    second = (z * w[:, None]).T @ z / w.sum()
+    np.testing.assert_allclose(second, 8.0 * (np.eye(4) - np.ones((4, 4)) / 4.0), rtol=0, atol=1e-12)
