@@ -65,11 +65,16 @@ struct DeviceState {
 
 // A lattice hash table: a power-of-two array of 64-byte slot records, two
 // 32-byte sectors each --
-//   [key (8 B), unused (8 B), 16-bit record (16 B, 16-bit storage modes)]
-//   [v0 = channels 0..3 (float4), v1 = channels 4..7 (float4)]
-// -- so that a lookup, its values and a clear touch one line.  A free slot is
-// all zero: kEmpty = 0 and every valid key has bit 63 set, so clearing a slot
-// is zeroing its record.
+//   sector 0: [key (8 B), unused (8 B), v0 = channels 0..3 (float4)]
+//   sector 1: [v1 = channels 4..7 (float4), unused (16 B)]
+// -- so that one 256-bit load of sector 0 returns a key with its weight and
+// value sums (a lookup and its values in one access), an insert's CAS and
+// atomics touch one line, and a clear writes whole sectors.  With 16-bit
+// storage the record [W, sum b (y - p_v), sum b n, 0] (16 B) is written over
+// bytes 8..23 of sector 0 once the build is complete (its float32 sums have
+// been read), so the 16-bit slice reads sector 0 alone.  A free slot is all
+// zero: kEmpty = 0 and every valid key has bit 63 set, so clearing a slot is
+// zeroing its record.
 constexpr int kRecWords = 8;  // 64-bit words per record
 constexpr unsigned long long kEmpty = 0ull;
 
@@ -83,14 +88,15 @@ struct Table {
 __host__ __device__ __forceinline__ unsigned long long *rec_key(unsigned long long *keys, uint32_t s) {
     return keys + (size_t)s * kRecWords;
 }
-__host__ __device__ __forceinline__ uint4 *rec_cv(unsigned long long *keys, uint32_t s) {
-    return reinterpret_cast<uint4 *>(keys + (size_t)s * kRecWords + 2);
+// The 16-bit record: bytes 8..23, two 8-byte halves (8-byte aligned).
+__host__ __device__ __forceinline__ uint2 *rec_cv(unsigned long long *keys, uint32_t s) {
+    return reinterpret_cast<uint2 *>(keys + (size_t)s * kRecWords + 1);
 }
 __host__ __device__ __forceinline__ float4 *rec_v0(unsigned long long *keys, uint32_t s) {
-    return reinterpret_cast<float4 *>(keys + (size_t)s * kRecWords + 4);
+    return reinterpret_cast<float4 *>(keys + (size_t)s * kRecWords + 2);
 }
 __host__ __device__ __forceinline__ float4 *rec_v1(unsigned long long *keys, uint32_t s) {
-    return reinterpret_cast<float4 *>(keys + (size_t)s * kRecWords + 6);
+    return reinterpret_cast<float4 *>(keys + (size_t)s * kRecWords + 4);
 }
 // Bytes of a table of `slots` records.
 inline size_t table_bytes(size_t slots) { return slots * kRecWords * sizeof(unsigned long long); }

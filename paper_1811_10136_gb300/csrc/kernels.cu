@@ -364,6 +364,19 @@ __device__ __forceinline__ uint4 compact_record(float4 a, float4 c, float3 p, fl
                       pack2<ST>(c.x * sc, c.y * sc), pack2<ST>(c.z * sc, 0.0f));
 }
 
+// Writes the 16-bit record over bytes 8..23 of slot s's first sector.
+__device__ __forceinline__ void store_compact(unsigned long long *keys, uint32_t s, uint4 r) {
+    uint2 *d = rec_cv(keys, s);
+    d[0] = make_uint2(r.x, r.y);
+    d[1] = make_uint2(r.z, r.w);
+}
+
+// Vector float atomic add without a returned value (a reduction at L2).
+__device__ __forceinline__ void red_add4(float4 *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
 // Build: Section 4.2 "Splat" of the observation with values [1, y] or
 // [1, y, n_y] (Eq. 11), fused with the lattice build (elevate, simplex, hash
 // insert, float4 atomic accumulation).  One thread per point per round.
@@ -448,8 +461,8 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
                     bad |= kFlagCapacity;
                 } else {
                     mask |= c ? (1 << k) : 0;
-                    atomicAdd(rec_v0(t.keys, sl[k]), make_float4(v[0], v[1], v[2], v[3]));
-                    if (PT2PL) atomicAdd(rec_v1(t.keys, sl[k]), make_float4(v[4], v[5], v[6], 0.f));
+                    red_add4(rec_v0(t.keys, sl[k]), v[0], v[1], v[2], v[3]);
+                    if (PT2PL) red_add4(rec_v1(t.keys, sl[k]), v[4], v[5], v[6], 0.f);
                 }
             }
         }
@@ -511,8 +524,8 @@ __device__ __forceinline__ void convert_role(Table t, const int *list, const Ite
             const int slot = __ldcg(list + e);
             const float4 a = __ldcg(rec_v0(t.keys, slot));
             const float4 c = PT2PL ? __ldcg(rec_v1(t.keys, slot)) : make_float4(0.f, 0.f, 0.f, 0.f);
-            *rec_cv(t.keys, slot) =
-                compact_record<ST>(a, c, vertex_position(__ldcg(rec_key(t.keys, slot)), ip), ip.vscale);
+            store_compact(t.keys, slot,
+                          compact_record<ST>(a, c, vertex_position(__ldcg(rec_key(t.keys, slot)), ip), ip.vscale));
         }
     }
 }
@@ -544,41 +557,13 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
         bad |= kFlagRange;
         return false;
     }
-    int slot[kD];
-    find4(t.keys, t.mask, sx, slot, t.max_probe);
-    if constexpr (ST != kStoreF32) {
-        // One 16-byte record per vertex; positions restored in float32.
-        uint4 r[kD];
-#pragma unroll
-        for (int k = 0; k < kD; ++k) r[k] = slot[k] >= 0 ? __ldg(rec_cv(t.keys, slot[k])) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int k = 0; k < kD; ++k) {
-            if (slot[k] < 0) continue;
-            const float b = sx.b[k];
-            const float2 w_rx = unpack2<ST>(r[k].x), ry_rz = unpack2<ST>(r[k].y);
-            const float3 p = vertex_position(sx.key[k], ip);
-            const float bw = b * w_rx.x;
-            o.m0 += bw;
-            o.m1x += b * w_rx.y + bw * p.x;
-            o.m1y += b * ry_rz.x + bw * p.y;
-            o.m1z += b * ry_rz.y + bw * p.z;
-            if (PT2PL) {
-                const float2 nx_ny = unpack2<ST>(r[k].z), nz_0 = unpack2<ST>(r[k].w);
-                o.nx += b * nx_ny.x;
-                o.ny += b * nx_ny.y;
-                o.nz += b * nz_0.x;
-            }
-        }
-        const float u = ip.inv_vscale;
-        o.m0 *= u;
-        o.m1x *= u;
-        o.m1y *= u;
-        o.m1z *= u;
-        o.nx *= u;
-        o.ny *= u;
-        o.nz *= u;
-        return true;
-    } else {
+    if constexpr (ST == kStoreF32) {
+        // Key probes of the four vertices together, then their value sums
+        // (v0 in the key's sector, v1 in the next) -- the four-sector form
+        // (key and v0 in one 256-bit load) needs registers the step does not
+        // have at four blocks per SM, and measured slower.
+        int slot[kD];
+        find4(t.keys, t.mask, sx, slot, t.max_probe);
         float4 a[kD], c[kD];
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
@@ -598,6 +583,39 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
                 o.nz += b * c[k].z;
             }
         }
+        return true;
+    } else {
+        // One 256-bit load per vertex: the key and its 16-byte record share
+        // sector 0; positions restored in float32.
+        Sector0 sec[kD];
+        int slot[kD];
+        find4_sectors(t.keys, t.mask, sx, t.max_probe, sec, slot);
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            if (slot[k] < 0) continue;
+            const float b = sx.b[k];
+            const float2 w_rx = unpack2<ST>(sec[k].w[2]), ry_rz = unpack2<ST>(sec[k].w[3]);
+            const float3 p = vertex_position(sx.key[k], ip);
+            const float bw = b * w_rx.x;
+            o.m0 += bw;
+            o.m1x += b * w_rx.y + bw * p.x;
+            o.m1y += b * ry_rz.x + bw * p.y;
+            o.m1z += b * ry_rz.y + bw * p.z;
+            if (PT2PL) {
+                const float2 nx_ny = unpack2<ST>(sec[k].w[4]), nz_0 = unpack2<ST>(sec[k].w[5]);
+                o.nx += b * nx_ny.x;
+                o.ny += b * nx_ny.y;
+                o.nz += b * nz_0.x;
+            }
+        }
+        const float u = ip.inv_vscale;
+        o.m0 *= u;
+        o.m1x *= u;
+        o.m1y *= u;
+        o.m1z *= u;
+        o.nx *= u;
+        o.ny *= u;
+        o.nz *= u;
         return true;
     }
 }
@@ -1388,9 +1406,9 @@ __global__ void k_blur_pass(Table in, Table out, int dir, const DeviceState *st)
         }
         reinterpret_cast<unsigned long long *>(o)[0] = key;
         reinterpret_cast<unsigned long long *>(o)[1] = 0ull;
-        o[1] = z;
-        o[2] = a;
-        o[3] = c;
+        o[1] = a;   // v0
+        o[2] = c;   // v1
+        o[3] = z;
     }
 }
 
@@ -1493,8 +1511,8 @@ __global__ void k_splat_records(const float *__restrict__ vals, int vdim, int n,
             const int s = rec_slot[(size_t)i * kD + k];
             if (s < 0) continue;
             const float b = rec_w[(size_t)i * kD + k];
-            atomicAdd(rec_v0(t.keys, s), make_float4(b * v[0], b * v[1], b * v[2], b * v[3]));
-            if (vdim > 4) atomicAdd(rec_v1(t.keys, s), make_float4(b * v[4], b * v[5], b * v[6], b * v[7]));
+            red_add4(rec_v0(t.keys, s), b * v[0], b * v[1], b * v[2], b * v[3]);
+            if (vdim > 4) red_add4(rec_v1(t.keys, s), b * v[4], b * v[5], b * v[6], b * v[7]);
         }
     }
 }
@@ -1530,7 +1548,7 @@ __global__ void k_slice_out(const float4 *__restrict__ Q, int m, float s1, float
 __global__ void k_zero_values(Table t) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t s = gtid(); s <= t.mask; s += grid_stride()) {
-        *rec_cv(t.keys, s) = make_uint4(0, 0, 0, 0);
+        *rec_cv(t.keys, s) = make_uint2(0, 0);
         *rec_v0(t.keys, s) = z;
         *rec_v1(t.keys, s) = z;
     }

@@ -12,10 +12,11 @@
 //
 // The hash table is open addressing with linear probing over a power-of-two
 // array of 64-byte slot records (see Table) whose first word is the key:
-// three 21-bit two's-complement coordinates (the fourth is minus their sum)
-// and bit 63 set; kEmpty (0) marks a free slot.  Slots are claimed with
-// atomicCAS; the record's values are accumulated with float4 atomics (sm_90+
-// vector atomics).
+// three 21-bit coordinates biased by 2^20 (the fourth is minus their sum) and
+// bit 63 set; kEmpty (0) marks a free slot.  With non-negative fields, moving
+// to a neighbouring vertex is one 64-bit addition of packed offsets.  Slots
+// are claimed with atomicCAS; the record's values are accumulated with float4
+// atomics (sm_90+ vector atomics).
 #pragma once
 
 #include <cstdint>
@@ -33,24 +34,25 @@ struct Simplex {
     float b[kD];                 // barycentric weight of vertex k
 };
 
+constexpr int kKeyBias = 1 << 20;                      // stored field = coordinate + 2^20
+constexpr unsigned long long kKeyOne = 1ull | (1ull << 21) | (1ull << 42);  // +1 on every field
+
 // Packs coordinates 0..2 of a vertex key (the 4th is implied by sum = 0).
+// |coordinate| < 2^20 (kKeyLimit keeps it so), so every field is in [0, 2^21).
 __device__ __forceinline__ unsigned long long pack_key(int k0, int k1, int k2) {
-    return (1ull << 63) | (unsigned long long)(k0 & 0x1FFFFF) | ((unsigned long long)(k1 & 0x1FFFFF) << 21) |
-           ((unsigned long long)(k2 & 0x1FFFFF) << 42);
+    return (1ull << 63) | (unsigned long long)(unsigned)(k0 + kKeyBias) |
+           ((unsigned long long)(unsigned)(k1 + kKeyBias) << 21) |
+           ((unsigned long long)(unsigned)(k2 + kKeyBias) << 42);
 }
 
 __device__ __forceinline__ int unpack_coord(unsigned long long key, int j) {
-    int v = (int)((key >> (21 * j)) & 0x1FFFFF);
-    return (v ^ 0x100000) - 0x100000;  // sign-extend 21 bits
+    return (int)((key >> (21 * j)) & 0x1FFFFF) - kKeyBias;
 }
 
-// 64-bit mix (xor-shift-multiply finaliser) -> table slot.
+// Key -> table slot: the two 32-bit halves multiplied by odd constants and
+// summed, the high half folded onto the low bits.
 __device__ __forceinline__ uint32_t slot_of(unsigned long long k, uint32_t mask) {
-    uint32_t h = (uint32_t)k * 0x9E3779B1u ^ (uint32_t)(k >> 32) * 0x85EBCA77u;
-    h ^= h >> 16;
-    h *= 0x7feb352du;
-    h ^= h >> 15;
-    h *= 0x846ca68bu;
+    uint32_t h = (uint32_t)k * 0x9E3779B1u + (uint32_t)(k >> 32) * 0x85EBCA77u;
     h ^= h >> 16;
     return h & mask;
 }
@@ -64,78 +66,64 @@ __device__ __forceinline__ bool embed(float px, float py, float pz, float s1, fl
     const float c2 = __fmul_rn(py, s2);
     const float c3 = __fmul_rn(pz, s3);
     // z_j = sum_{i > j} c_i - j c_j, accumulated from the last axis down.
-    float z[kD];
-    z[3] = __fsub_rn(0.0f, __fmul_rn(3.0f, c3));
+    const float z3 = __fsub_rn(0.0f, __fmul_rn(3.0f, c3));
     float t = __fadd_rn(0.0f, c3);
-    z[2] = __fsub_rn(t, __fmul_rn(2.0f, c2));
+    const float z2 = __fsub_rn(t, __fmul_rn(2.0f, c2));
     t = __fadd_rn(t, c2);
-    z[1] = __fsub_rn(t, __fmul_rn(1.0f, c1));
+    const float z1 = __fsub_rn(t, __fmul_rn(1.0f, c1));
     t = __fadd_rn(t, c1);
-    z[0] = t;
+    const float z0 = t;
+    if (!(fabsf(z0) < kKeyLimit && fabsf(z1) < kKeyLimit && fabsf(z2) < kKeyLimit && fabsf(z3) < kKeyLimit))
+        return false;
 
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < kD; ++j) ok = ok && (fabsf(z[j]) < kKeyLimit);
-    if (!ok) return false;
-
-    // Nearest remainder-0 point (round half to even), coordinate-wise.
-    int r0[kD];
-    int sum = 0;
-#pragma unroll
-    for (int j = 0; j < kD; ++j) {
-        const float q = rintf(__fmul_rn(z[j], 0.25f));
-        r0[j] = (int)q * kD;
-        sum += (int)q;
-    }
-    float dl[kD];
-#pragma unroll
-    for (int j = 0; j < kD; ++j) dl[j] = __fsub_rn(z[j], (float)r0[j]);
-
-    // Rank of each difference, descending, ties to the lower index.
-    int rk[kD];
-#pragma unroll
-    for (int j = 0; j < kD; ++j) {
-        int r = 0;
-#pragma unroll
-        for (int k = 0; k < kD; ++k) r += (dl[k] > dl[j]) || (k < j && dl[k] == dl[j]);
-        rk[j] = r;
-    }
+    // Nearest remainder-0 point (round half to even), coordinate-wise: 4 q_j.
+    const float q0 = rintf(__fmul_rn(z0, 0.25f)), q1 = rintf(__fmul_rn(z1, 0.25f));
+    const float q2 = rintf(__fmul_rn(z2, 0.25f)), q3 = rintf(__fmul_rn(z3, 0.25f));
+    const int sum = (int)q0 + (int)q1 + (int)q2 + (int)q3;
     if (sum > kD || sum < -kD) return false;
-    // Repair the coordinate sum to zero.
-#pragma unroll
-    for (int j = 0; j < kD; ++j) {
-        if (sum > 0) {
-            const bool mv = rk[j] >= kD - sum;
-            r0[j] -= mv ? kD : 0;
-            rk[j] += mv ? sum - kD : sum;
-        } else if (sum < 0) {
-            const bool mv = rk[j] < -sum;
-            r0[j] += mv ? kD : 0;
-            rk[j] += mv ? kD + sum : sum;
-        }
-    }
+    const float d0 = __fsub_rn(z0, 4.0f * q0), d1 = __fsub_rn(z1, 4.0f * q1);
+    const float d2 = __fsub_rn(z2, 4.0f * q2), d3 = __fsub_rn(z3, 4.0f * q3);
+
+    // Rank of each difference, descending, ties to the lower index: of a
+    // pair j < k, j comes first iff d_j >= d_k.  The ranks start at the
+    // coordinate sum, which the repair below adds to every rank.
+    const bool p01 = d0 >= d1, p02 = d0 >= d2, p03 = d0 >= d3;
+    const bool p12 = d1 >= d2, p13 = d1 >= d3, p23 = d2 >= d3;
+    int r0 = sum + !p01 + !p02 + !p03;
+    int r1 = sum + p01 + !p12 + !p13;
+    int r2 = sum + p02 + p12 + !p23;
+    int r3 = sum + p03 + p13 + p23;
+    // Repair of the coordinate sum to zero: a coordinate whose shifted rank
+    // leaves [0, D) wraps around (rank mod D) and its remainder-0 coordinate
+    // moves by -D floor(rank / D).
+    const int m0 = (int)q0 - (r0 >> 2), m1 = (int)q1 - (r1 >> 2);
+    const int m2 = (int)q2 - (r2 >> 2), m3 = (int)q3 - (r3 >> 2);
+    r0 &= 3; r1 &= 3; r2 &= 3; r3 &= 3;
+
     // u_r = (z_j - r0_j) / D for the coordinate j of rank r.
-    float u[kD];
-#pragma unroll
-    for (int r = 0; r < kD; ++r) u[r] = 0.0f;
-#pragma unroll
-    for (int j = 0; j < kD; ++j) {
-        const float v = __fmul_rn(__fsub_rn(z[j], (float)r0[j]), 0.25f);
-#pragma unroll
-        for (int r = 0; r < kD; ++r) u[r] = (rk[j] == r) ? v : u[r];
-    }
+    const float v0 = __fmul_rn(__fsub_rn(z0, (float)(4 * m0)), 0.25f);
+    const float v1 = __fmul_rn(__fsub_rn(z1, (float)(4 * m1)), 0.25f);
+    const float v2 = __fmul_rn(__fsub_rn(z2, (float)(4 * m2)), 0.25f);
+    const float v3 = __fmul_rn(__fsub_rn(z3, (float)(4 * m3)), 0.25f);
+    auto of_rank = [&](int r) { return r0 == r ? v0 : (r1 == r ? v1 : (r2 == r ? v2 : v3)); };
+    const float u0 = of_rank(0), u1 = of_rank(1), u2 = of_rank(2), u3 = of_rank(3);
     // b_m = u_{D-1-m} - u_{D-m} (m = 1..3), b_0 = u_{D-1} + (1 - u_0).
-    out.b[0] = __fadd_rn(u[3], __fadd_rn(1.0f, -u[0]));
-    out.b[1] = __fsub_rn(u[2], u[3]);
-    out.b[2] = __fsub_rn(u[1], u[2]);
-    out.b[3] = __fsub_rn(u[0], u[1]);
+    out.b[0] = __fadd_rn(u3, __fadd_rn(1.0f, -u0));
+    out.b[1] = __fsub_rn(u2, u3);
+    out.b[2] = __fsub_rn(u1, u2);
+    out.b[3] = __fsub_rn(u0, u1);
     // Vertex k: coordinate j is r0_j + k, minus D where rank_j > D - 1 - k.
+    // Vertex k follows from vertex k - 1 by +1 on every coordinate and -D on
+    // the coordinate of rank D - k (no stored field when that is coordinate 3).
+    unsigned long long key = pack_key(4 * m0, 4 * m1, 4 * m2);
+    out.key[0] = key;
 #pragma unroll
-    for (int k = 0; k < kD; ++k) {
-        int c[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) c[j] = r0[j] + k - (rk[j] > kD - 1 - k ? kD : 0);
-        out.key[k] = pack_key(c[0], c[1], c[2]);
+    for (int k = 1; k < kD; ++k) {
+        const int r = kD - k;
+        const unsigned long long down = (r0 == r ? 4ull : 0ull) | (r1 == r ? 4ull << 21 : 0ull) |
+                                        (r2 == r ? 4ull << 42 : 0ull);
+        key = key + kKeyOne - down;
+        out.key[k] = key;
     }
     return true;
 }
@@ -199,6 +187,59 @@ __device__ __forceinline__ void find4(const unsigned long long *__restrict__ key
             ++p;
         }
         slot[k] = (cur[k] == sx.key[k]) ? (int)s[k] : -1;
+    }
+}
+
+// Sector 0 of slot s (key, bytes 8..15, v0) in one 256-bit read-only load:
+// w[0..1] the key, w[2..3] bytes 8..15, w[4..7] v0.  The table must not
+// change during the kernel (a build in an earlier launch).
+struct Sector0 {
+    unsigned w[8];
+    __device__ __forceinline__ unsigned long long key() const {
+        return (unsigned long long)w[0] | ((unsigned long long)w[1] << 32);
+    }
+};
+__device__ __forceinline__ Sector0 ld_sector0(const unsigned long long *keys, uint32_t s) {
+    Sector0 r;
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]), "=r"(r.w[4]), "=r"(r.w[5]), "=r"(r.w[6]),
+          "=r"(r.w[7])
+        : "l"(keys + (size_t)s * kRecWords));
+    return r;
+}
+
+// Sector 0 of each of a simplex's four vertices: the home slots' sectors are
+// requested together (one access per vertex: key and values), collision
+// chains walked one by one (max_probe slots at most) and the sector of a key
+// found beyond its home reloaded.  found[k] is false (and the sector zero)
+// for a vertex absent from the table.
+__device__ __forceinline__ void find4_sectors(const unsigned long long *__restrict__ keys, uint32_t mask,
+                                              const Simplex &sx, uint32_t max_probe, Sector0 sec[kD],
+                                              int slot[kD]) {
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        slot[k] = (int)slot_of(sx.key[k], mask);
+        sec[k] = ld_sector0(keys, (uint32_t)slot[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        unsigned long long cur = sec[k].key();
+        if (cur == sx.key[k]) continue;
+        uint32_t s = (uint32_t)slot[k];
+        uint32_t p = 1;
+        while (cur != sx.key[k] && cur != kEmpty && p < max_probe) {
+            s = (s + 1) & mask;
+            cur = __ldg(rec_key(const_cast<unsigned long long *>(keys), s));
+            ++p;
+        }
+        if (cur == sx.key[k]) {
+            slot[k] = (int)s;
+            sec[k] = ld_sector0(keys, s);
+        } else {
+            slot[k] = -1;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sec[k].w[i] = 0u;
+        }
     }
 }
 
