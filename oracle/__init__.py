@@ -24,35 +24,58 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SOURCES = ["estep.c", "lattice.c", "se3.c", "rigid.c", "articulated.c", "nodegraph.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_OMP_LIB_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           "-Wall", "-Wno-unused-function"]
+           "-Wall", "-Wno-unused-function", "-Wno-unknown-pragmas"]
 
 PT2PT, PT2PL = 0, 1
 EXACT, LATTICE = 0, 1
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` with gcc (idempotent)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (idempotent): ``oracle/liboracle.so``, one
+    thread, or with ``openmp`` ``oracle/liboracle_omp.so`` (-fopenmp: the same
+    sources, per-point loops in parallel, bit-identical results)."""
+    path = _OMP_LIB_PATH if openmp else _LIB_PATH
     srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
     deps = srcs + [os.path.join(_HERE, "oracle.h")]
-    if not force and os.path.exists(_LIB_PATH):
-        if os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(d) for d in deps):
-            return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", *_CFLAGS, "-o", tmp, *srcs, "-lm"], check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    if not force and os.path.exists(path):
+        if os.path.getmtime(path) >= max(os.path.getmtime(d) for d in deps):
+            return path
+    tmp = path + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *_CFLAGS, *(["-fopenmp"] if openmp else []), "-o", tmp, *srcs, "-lm"], check=True)
+    os.replace(tmp, path)
+    return path
 
 
-_lib = None
+_libs = {}
+_parallel = False
+
+
+def _load(openmp: bool):
+    if openmp not in _libs:
+        L = ctypes.CDLL(build(openmp=openmp))
+        _declare(L)
+        _libs[openmp] = L
+    return _libs[openmp]
 
 
 def _L():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
-        _declare(_lib)
-    return _lib
+    return _load(_parallel)
+
+
+def set_parallel(on: bool, threads: int | None = None) -> None:
+    """Route later calls to the OpenMP build (on) or the single-thread one;
+    threads > 0 sets the OpenMP build's thread count."""
+    global _parallel
+    _parallel = bool(on)
+    if on and threads:
+        _load(True).or_set_threads(int(threads))
+
+
+def num_threads() -> int:
+    """Threads the calls currently routed use (1 for the single-thread build)."""
+    return int(_L().or_num_threads())
 
 
 _f32p = ctypes.POINTER(ctypes.c_float)
@@ -111,6 +134,10 @@ def _declare(L):
     L.or_estep.restype = ctypes.c_int
     L.or_align_error.argtypes = [_f32p, ctypes.c_int64, _f64p, _f64p]
     L.or_align_error.restype = ctypes.c_double
+    L.or_num_threads.argtypes = []
+    L.or_num_threads.restype = ctypes.c_int
+    L.or_set_threads.argtypes = [ctypes.c_int]
+    L.or_set_threads.restype = None
     if hasattr(L, "or_register_articulated"):
         _declare_articulated(L)
         _declare_nodegraph(L)
@@ -196,7 +223,8 @@ class Lattice:
         if V.ndim == 1:
             V = V[:, None].copy()
         st = ctypes.c_int(0)
-        self._h = _L().or_lattice_build(_p(P, _f32p), _p(V, _f64p), P.shape[0], V.shape[1],
+        self._lib = _L()
+        self._h = self._lib.or_lattice_build(_p(P, _f32p), _p(V, _f64p), P.shape[0], V.shape[1],
                                         ctypes.c_float(sigma), ctypes.byref(st))
         if not self._h:
             raise OracleError(f"lattice build failed ({st.value})")
@@ -204,28 +232,29 @@ class Lattice:
         self.vdim = V.shape[1]
         self.sigma = sigma
         if blur:
-            _L().or_lattice_blur(self._h)
+            self._lib.or_lattice_blur(self._h)
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h and _lib is not None:
-            _lib.or_lattice_free(h)
+        lib = getattr(self, "_lib", None)
+        if h and lib is not None:
+            lib.or_lattice_free(h)
             self._h = None
 
     def __len__(self):
-        return int(_L().or_lattice_size(self._h))
+        return int(self._lib.or_lattice_size(self._h))
 
     def slice(self, Q):
         Q = _pts(Q)
         out = np.zeros((Q.shape[0], self.vdim), np.float64)
-        st = _L().or_lattice_slice(self._h, _p(Q, _f32p), Q.shape[0], _p(out, _f64p))
+        st = self._lib.or_lattice_slice(self._h, _p(Q, _f32p), Q.shape[0], _p(out, _f64p))
         return out, st
 
     def vertices(self):
         nv = len(self)
         keys = np.zeros((nv, 4), np.int32)
         vals = np.zeros((nv, self.vdim), np.float64)
-        _L().or_lattice_vertices(self._h, _p(keys, _i32p), _p(vals, _f64p))
+        self._lib.or_lattice_vertices(self._h, _p(keys, _i32p), _p(vals, _f64p))
         return keys, vals
 
 

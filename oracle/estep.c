@@ -37,6 +37,7 @@ void or_exact_sums_at(const double x[3], const float *Y, const float *Yn, int64_
 void or_estep_exact(const float *X, int64_t M, const float *Y, const float *Yn,
                     int64_t N, double sigma, double *M0, double *M1, double *Ns)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < M; ++i) {
         double x[3] = {X[4 * i], X[4 * i + 1], X[4 * i + 2]}, ns[3];
         or_exact_sums_at(x, Y, Yn, N, sigma, M0 + i, M1 + 3 * i, ns);

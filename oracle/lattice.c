@@ -28,7 +28,9 @@
  * a fixed order (compile with -ffp-contract=off), with round-half-to-even
  * rounding, so that the integer keys are reproducible bit for bit.  Splat,
  * blur and slice sums are in double.  The vertex set is kept key-sorted and
- * searched by bisection: plain and obviously ordered, not fast.
+ * searched by bisection: plain and obviously ordered, not fast.  Built with
+ * OpenMP, the per-point loops run in parallel and the sort is chunked; every
+ * sum keeps its order, so results are bit-identical to the serial build.
  */
 #include "oracle.h"
 
@@ -203,6 +205,51 @@ static int cmp_entry(const void *pa, const void *pb)
     return a->k - b->k;
 }
 
+/* Sorts the splat entries by (key, source point, vertex): a total order, so
+ * the result does not depend on how the work is split.  Built with OpenMP,
+ * chunks are sorted in parallel and merged pairwise; otherwise one qsort. */
+static void sort_entries(splat_entry *e, int64_t n)
+{
+#ifdef _OPENMP
+    const int64_t chunk = 16384;
+    if (n > 2 * chunk) {
+        const int64_t nc = (n + chunk - 1) / chunk;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t c = 0; c < nc; ++c) {
+            const int64_t lo = c * chunk, hi = lo + chunk < n ? lo + chunk : n;
+            qsort(e + lo, (size_t)(hi - lo), sizeof *e, cmp_entry);
+        }
+        splat_entry *tmp = (splat_entry *)malloc((size_t)n * sizeof *e);
+        if (tmp) {
+            splat_entry *src = e, *dst = tmp;
+            for (int64_t w = chunk; w < n; w *= 2) {
+                const int64_t np = (n + 2 * w - 1) / (2 * w);
+#pragma omp parallel for schedule(dynamic, 1)
+                for (int64_t q = 0; q < np; ++q) {
+                    const int64_t lo = q * 2 * w;
+                    const int64_t mid = lo + w < n ? lo + w : n, hi = lo + 2 * w < n ? lo + 2 * w : n;
+                    int64_t a = lo, b = mid, o = lo;
+                    while (a < mid && b < hi)
+                        dst[o++] = cmp_entry(src + b, src + a) < 0 ? src[b++] : src[a++];
+                    while (a < mid)
+                        dst[o++] = src[a++];
+                    while (b < hi)
+                        dst[o++] = src[b++];
+                }
+                splat_entry *t = src;
+                src = dst;
+                dst = t;
+            }
+            if (src != e)
+                memcpy(e, src, (size_t)n * sizeof *e);
+            free(tmp);
+            return;
+        }
+    }
+#endif
+    qsort(e, (size_t)n, sizeof *e, cmp_entry);
+}
+
 /* Index of key in the sorted vertex array, or -1. */
 static int64_t find_vertex(const or_lattice *lat, const int32_t key[LD1])
 {
@@ -240,22 +287,31 @@ or_lattice *or_lattice_build(const float *P, const double *V, int64_t n, int vdi
         *status = OR_ENOMEM;
         return NULL;
     }
-    int64_t ne = 0;
+    /* Point i's entries go to slots 4 i .. 4 i + 3 (a point outside the key
+     * range leaves them marked unused), then the used ones are packed in
+     * point order: the same entry array for any number of threads. */
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (int64_t i = 0; i < n; ++i) {
         simplex sx;
-        if (!embed_point(P + 4 * i, lat->scale, &sx)) {
-            *status = OR_EINVAL;
-            continue;
-        }
+        const int ok = embed_point(P + 4 * i, lat->scale, &sx);
+        if (!ok)
+            bad = 1;
         for (int k = 0; k < LD1; ++k) {
-            memcpy(e[ne].key, sx.key[k], sizeof e[ne].key);
-            e[ne].src = i;
-            e[ne].k = k;
-            e[ne].b = sx.b[k];
-            ++ne;
+            splat_entry *t = e + LD1 * i + k;
+            memcpy(t->key, sx.key[k], sizeof t->key);
+            t->src = ok ? i : -1;
+            t->k = k;
+            t->b = ok ? sx.b[k] : 0.0f;
         }
     }
-    qsort(e, (size_t)ne, sizeof *e, cmp_entry);
+    if (bad)
+        *status = OR_EINVAL;
+    int64_t ne = 0;
+    for (int64_t t = 0; t < n * LD1; ++t)
+        if (e[t].src >= 0)
+            e[ne++] = e[t];
+    sort_entries(e, ne);
 
     int64_t nv = 0;
     for (int64_t t = 0; t < ne; ++t)
@@ -319,13 +375,14 @@ void or_lattice_blur(or_lattice *lat)
 int or_lattice_slice(const or_lattice *lat, const float *Q, int64_t m, double *out)
 {
     const int vdim = lat->vdim;
-    int status = OR_OK;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (int64_t i = 0; i < m; ++i) {
         for (int c = 0; c < vdim; ++c)
             out[i * vdim + c] = 0.0;
         simplex sx;
         if (!embed_point(Q + 4 * i, lat->scale, &sx)) {
-            status = OR_EINVAL;
+            bad = 1;
             continue;
         }
         for (int k = 0; k < LD1; ++k) {
@@ -336,7 +393,7 @@ int or_lattice_slice(const or_lattice *lat, const float *Q, int64_t m, double *o
                 out[i * vdim + c] += (double)sx.b[k] * lat->vals[v * vdim + c];
         }
     }
-    return status;
+    return bad ? OR_EINVAL : OR_OK;
 }
 
 int64_t or_lattice_size(const or_lattice *lat) { return lat->nv; }

@@ -1,7 +1,7 @@
 /*
  * FilterReg CPU oracle -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded restatement of what the registration hot path
+ * A plain, slow restatement of what the registration hot path
  * computes, written from the paper (Gao & Tedrake, "FilterReg", CVPR 2019) and
  * from the permutohedral-lattice construction it cites (Adams et al. 2010).
  * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
@@ -18,6 +18,12 @@
  *     (elevation, rounding, rank sort, barycentric weights) is evaluated in
  *     float with no fused multiply-add, in a fixed operation order, because
  *     those float results decide integer lattice keys.
+ *
+ * Threads: built plain (liboracle.so) everything runs on one thread; built
+ * with -fopenmp (liboracle_omp.so, the benchmark's all-core baseline) the
+ * per-point loops of the rigid path run in parallel.  Every sum keeps a fixed
+ * order (chunks of fixed size, reduced in chunk order), so the two builds
+ * return bit-identical results.
  *
  * Parity status of each function is stated beside it; every function is
  * pinned by the CPU tests (tests/test_oracle_*.py) against closed forms,
@@ -204,6 +210,10 @@ int or_register_nodegraph(const float *Xref, const int32_t *knn, const float *sk
 
 /* Alignment error of Eq. 22: mean |(T - T_gt) x_ref|. */
 double or_align_error(const float *X, int64_t M, const double T[16], const double Tgt[16]);
+
+/* Threads the OpenMP build uses (1 for the plain build); set them (n > 0). */
+int or_num_threads(void);
+void or_set_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -35,6 +35,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 double or_outlier_constant(double w, int64_t N, int64_t M, double sigma, int backend, int blur)
 {
@@ -89,6 +92,11 @@ int or_point_terms(const double x[3], double M0, const double M1[3], const doubl
     return 1;
 }
 
+/* Points per fixed summation chunk of the Gauss-Newton sums, and the values
+ * each chunk carries. */
+#define GN_CHUNK 4096
+#define GN_VALS 45
+
 static void transform_point(const double T[16], const float *p, double x[3])
 {
     for (int a = 0; a < 3; ++a)
@@ -116,6 +124,7 @@ static int estep_at(const float *X, int64_t M, const float *Y, const float *Yn, 
     float *xs = (float *)malloc((size_t)(M ? M : 1) * 4 * sizeof(float));
     if (!xs)
         return OR_ENOMEM;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < M; ++i) {
         double x[3];
         transform_point(T, X + 4 * i, x);
@@ -128,6 +137,7 @@ static int estep_at(const float *X, int64_t M, const float *Y, const float *Yn, 
         status = or_lattice_slice(lat, xs, M, out);
     } else {
         /* The exact sums use the double-precision moved points. */
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < M; ++i) {
             double x[3], m0, m1[3], ns[3];
             transform_point(T, X + 4 * i, x);
@@ -226,32 +236,57 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
             break;
 
         const double c_eff = or_outlier_constant(opt->w, N, M, sigma, opt->backend, opt->blur);
-        double A[36] = {0}, b[6] = {0}, sum_w = 0.0, cost = 0.0;
-        int64_t inliers = 0;
-        for (int64_t i = 0; i < M; ++i) {
-            double x[3];
-            transform_point(T, X + 4 * i, x);
-            const double *e = es + i * vdim;
-            double Ns[3] = {0, 0, 0};
-            if (vdim == 7)
-                for (int c = 0; c < 3; ++c)
-                    Ns[c] = e[4 + c];
-            double Wt, r[3], J[18];
-            int rows = or_point_terms(x, e[0], e + 1, Ns, c_eff, sigma, opt->residual,
-                                      opt->renormalize_normals, &Wt, r, J);
-            if (rows == 0)
-                continue;
-            ++inliers;
-            sum_w += Wt;
-            for (int a = 0; a < rows; ++a) {
-                cost += r[a] * r[a];
-                for (int p = 0; p < 6; ++p) {
-                    b[p] += J[6 * a + p] * r[a];
-                    for (int q = 0; q < 6; ++q)
-                        A[6 * p + q] += J[6 * a + p] * J[6 * a + q];
+        /* A = sum J^T J, b = sum J^T r (Eq. 17-18): each fixed chunk of
+         * GN_CHUNK points summed in point order, then the chunk sums in chunk
+         * order -- the same result whatever the number of threads. */
+        const int64_t nchunk = (M + GN_CHUNK - 1) / GN_CHUNK;
+        double *part = (double *)calloc((size_t)nchunk * GN_VALS, sizeof(double));
+        if (!part) {
+            status = OR_ENOMEM;
+            break;
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t ch = 0; ch < nchunk; ++ch) {
+            double *q = part + ch * GN_VALS; /* A (36), b (6), sum_w, cost, inliers */
+            const int64_t i1 = (ch + 1) * GN_CHUNK < M ? (ch + 1) * GN_CHUNK : M;
+            for (int64_t i = ch * GN_CHUNK; i < i1; ++i) {
+                double x[3];
+                transform_point(T, X + 4 * i, x);
+                const double *e = es + i * vdim;
+                double Ns[3] = {0, 0, 0};
+                if (vdim == 7)
+                    for (int c = 0; c < 3; ++c)
+                        Ns[c] = e[4 + c];
+                double Wt, r[3], J[18];
+                int rows = or_point_terms(x, e[0], e + 1, Ns, c_eff, sigma, opt->residual,
+                                          opt->renormalize_normals, &Wt, r, J);
+                if (rows == 0)
+                    continue;
+                q[44] += 1.0;
+                q[42] += Wt;
+                for (int a = 0; a < rows; ++a) {
+                    q[43] += r[a] * r[a];
+                    for (int p = 0; p < 6; ++p) {
+                        q[36 + p] += J[6 * a + p] * r[a];
+                        for (int qq = 0; qq < 6; ++qq)
+                            q[6 * p + qq] += J[6 * a + p] * J[6 * a + qq];
+                    }
                 }
             }
         }
+        double A[36] = {0}, b[6] = {0}, sum_w = 0.0, cost = 0.0;
+        int64_t inliers = 0;
+        for (int64_t ch = 0; ch < nchunk; ++ch) {
+            const double *q = part + ch * GN_VALS;
+            for (int v = 0; v < 36; ++v)
+                A[v] += q[v];
+            for (int p = 0; p < 6; ++p)
+                b[p] += q[36 + p];
+            sum_w += q[42];
+            cost += q[43];
+            inliers += (int64_t)q[44];
+        }
+        free(part);
         rep->iters_run = it + 1;
         rep->last_inliers = inliers;
         rep->last_sum_w = sum_w;
@@ -279,6 +314,25 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
     free(V);
     free(es);
     return status;
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 double or_align_error(const float *X, int64_t M, const double T[16], const double Tgt[16])

@@ -72,6 +72,9 @@ fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur, bool compact) {
     }
     if (blur && !ctx->blur) {
         FR_CUDA(ctx, dev_alloc(&ctx->blur, (size_t)ctx->table_cap * kRecWords));
+        // Blur passes write only the slots their lattice holds and free them
+        // afterwards: the scratch table starts empty and stays so.
+        FR_CUDA(ctx, cudaMemsetAsync(ctx->blur, 0, table_bytes(ctx->table_cap), ctx->stream));
         ctx->ws_gen++;
         drop_graphs(ctx);
     }
@@ -197,16 +200,22 @@ struct Issuer {
     }
 };
 
-void issue_blur(fr_ctx *ctx, Issuer &k, const Plan &p, const Table &t) {
+// The four blur passes of the lattice a build left in table t (its claimed
+// slots in `list`, their count at `count`), ping-ponging with the scratch
+// table, which is emptied again afterwards.
+void issue_blur(fr_ctx *ctx, Issuer &k, const Plan &p, const Table &t, const int *list, const int *count) {
     Table a = t, b = t;
     b.keys = ctx->blur;
     for (int dir = 0; dir < 4; ++dir)
         k(FR_K_BLUR, [&] {
             if (dir % 2 == 0)
-                launch_blur_pass(a, b, dir, p.g_blur, ctx->d_state, k.s);
+                launch_blur_list(a, b, dir, list, count, p.g_blur, ctx->d_state, k.s);
             else
-                launch_blur_pass(b, a, dir, p.g_blur, ctx->d_state, k.s);
+                launch_blur_list(b, a, dir, list, count, p.g_blur, ctx->d_state, k.s);
         });
+    int *lists[1] = {const_cast<int *>(list)};
+    const int *counts[1] = {count};
+    k(FR_K_BLUR, [&] { launch_clear_lists(&b, lists, counts, 1, p.g_blur, k.s); });
 }
 
 // Builds run `lead` iterations ahead of the step that reads them: 1 with
@@ -249,7 +258,7 @@ int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
         if (j >= 1) add_conv(L, j - 1);
         if (L.gb + L.gv == 0) continue;
         k(j == 0 ? FR_K_BUILD : FR_K_CONVERT, [&] { launch_em_iter(p.residual, p.kahan, L, s, p.storage); });
-        if (p.blur && L.gb) issue_blur(ctx, k, p, L.build);
+        if (p.blur && L.gb) issue_blur(ctx, k, p, L.build, L.build_list, &ctx->d_ip[L.build_it].nvert);
     }
     for (int it = 0; it < p.iters; ++it) {
         IterLaunch L = base;
@@ -265,7 +274,7 @@ int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
             L.gc = p.gc;
         }
         k(FR_K_STEP, [&] { launch_em_iter(p.residual, p.kahan, L, s, p.storage); });
-        if (p.blur && L.gb) issue_blur(ctx, k, p, L.build);
+        if (p.blur && L.gb) issue_blur(ctx, k, p, L.build, L.build_list, &ctx->d_ip[L.build_it].nvert);
     }
     if (p.iters > 0) {
         // Free what is left: the last build's table.  Every other table was
@@ -284,9 +293,9 @@ int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
 int plan_kernels(const Plan &p) {
     int n = 0;
     const int lead = p.storage != FR_FP32 ? 2 : 1;
-    if (p.iters > 0) n += 2 + (p.blur ? 4 : 0) + (lead - 1);  // prologue (+ blur), final clear
+    if (p.iters > 0) n += 2 + (p.blur ? 5 : 0) + (lead - 1);  // prologue (+ blur, scratch clear), final clear
     n += p.iters;
-    if (p.annealed && p.blur && p.iters > 1) n += 4 * (p.iters - 1);
+    if (p.annealed && p.blur && p.iters > 1) n += 5 * (p.iters - 1);
     return n;
 }
 
@@ -444,7 +453,7 @@ void plan_grids(fr_ctx *ctx, Plan &p, int64_t M, int64_t N, uint32_t cap) {
     p.gv = (int)gv;
     p.gb = (int)gb;
     p.gc = (int)gc;
-    p.g_blur = blocks_for(ctx, cap, 8);
+    p.g_blur = blocks_for(ctx, 2 * N, 8);  // blur passes walk the build's vertex list (<= 4 N)
     p.g_final = (int)std::max<long long>(8, std::min<long long>(resident / 2, (N + kBlock - 1) / kBlock));
 }
 
@@ -796,14 +805,17 @@ static fr_status estep_impl(fr_ctx *ctx, const float *d_X, int64_t M, const floa
     if (blur) {
         Table a = t, c = t;
         c.keys = ctx->blur;
-        const int gb = blocks_for(ctx, cap, 8);
+        const int gb = blocks_for(ctx, N, 8);
+        const int *cnt = &ctx->d_ip[0].nvert;
         for (int dir = 0; dir < 4; ++dir) {
             if (dir % 2 == 0)
-                launch_blur_pass(a, c, dir, gb, ctx->d_state, ctx->stream);
+                launch_blur_list(a, c, dir, ctx->lists[0], cnt, gb, ctx->d_state, ctx->stream);
             else
-                launch_blur_pass(c, a, dir, gb, ctx->d_state, ctx->stream);
+                launch_blur_list(c, a, dir, ctx->lists[0], cnt, gb, ctx->d_state, ctx->stream);
         }
-        ctx->launches += 4;
+        int *lc = ctx->lists[0];
+        launch_clear_lists(&c, &lc, &cnt, 1, gb, ctx->stream);
+        ctx->launches += 5;
     }
     launch_estep_out(pt2pl, ctx->d_job, ctx->d_ip, t, d_out, ctx->d_state, blocks_for(ctx, M, 8),
                      ctx->stream, storage);

@@ -307,6 +307,9 @@ int em_iter_blocks_per_sm(int pt2pl, int kahan);
 void launch_clear_lists(const Table *tabs, int *const *lists, const int *const *counts, int n,
                         int grid, cudaStream_t s);
 void launch_blur_pass(Table in, Table out, int dir, int grid, const DeviceState *st, cudaStream_t s);
+// A blur pass over the `*count` slots of `list` (a build's claimed slots).
+void launch_blur_list(Table in, Table out, int dir, const int *list, const int *count, int grid,
+                      const DeviceState *st, cudaStream_t s);
 void launch_estep_out(int pt2pl, const RigidJob *job, const IterParams *ip, Table t, float *out,
                       DeviceState *st, int grid, cudaStream_t s, int storage);
 

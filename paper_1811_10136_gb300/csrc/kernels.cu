@@ -1412,6 +1412,48 @@ __global__ void k_blur_pass(Table in, Table out, int dir, const DeviceState *st)
     }
 }
 
+// The same pass over the slots a build listed (the table's every vertex)
+// instead of the whole table: `out` holds the same keys at the same slots as
+// `in` after the pass, so lookups in either find the same vertices, and it is
+// empty elsewhere -- the caller frees the listed slots of the scratch table
+// once the last pass has read it.
+__global__ void k_blur_list(Table in, Table out, int dir, const int *list, const int *count,
+                            const DeviceState *st) {
+    if (st && st->done) return;
+    const int n = __ldcg(count);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = gtid(); e < n; e += grid_stride()) {
+        const uint32_t s = (uint32_t)__ldcg(list + e);
+        const unsigned long long key = __ldg(rec_key(in.keys, s));
+        const int sm = find_key(in.keys, in.mask, neighbour_key(key, dir, -1), in.max_probe);
+        const int sp = find_key(in.keys, in.mask, neighbour_key(key, dir, +1), in.max_probe);
+        float4 a = __ldg(rec_v0(in.keys, s));
+        float4 c = in.vals > 4 ? __ldg(rec_v1(in.keys, s)) : z;
+        if (sm >= 0) {
+            const float4 u = __ldg(rec_v0(in.keys, sm));
+            a.x += 0.5f * u.x; a.y += 0.5f * u.y; a.z += 0.5f * u.z; a.w += 0.5f * u.w;
+            if (in.vals > 4) {
+                const float4 v = __ldg(rec_v1(in.keys, sm));
+                c.x += 0.5f * v.x; c.y += 0.5f * v.y; c.z += 0.5f * v.z; c.w += 0.5f * v.w;
+            }
+        }
+        if (sp >= 0) {
+            const float4 u = __ldg(rec_v0(in.keys, sp));
+            a.x += 0.5f * u.x; a.y += 0.5f * u.y; a.z += 0.5f * u.z; a.w += 0.5f * u.w;
+            if (in.vals > 4) {
+                const float4 v = __ldg(rec_v1(in.keys, sp));
+                c.x += 0.5f * v.x; c.y += 0.5f * v.y; c.z += 0.5f * v.z; c.w += 0.5f * v.w;
+            }
+        }
+        float4 *o = reinterpret_cast<float4 *>(rec_key(out.keys, s));
+        reinterpret_cast<unsigned long long *>(o)[0] = key;
+        reinterpret_cast<unsigned long long *>(o)[1] = 0ull;
+        o[1] = a;
+        o[2] = c;
+        o[3] = z;
+    }
+}
+
 // E-step sums at T x for every model point (the fr_estep entry point).
 template <bool PT2PL, int ST>
 __global__ void __launch_bounds__(kBlock) k_estep_out(const RigidJob *__restrict__ job,
@@ -2209,6 +2251,11 @@ void launch_clear_lists(const Table *tabs, int *const *lists, const int *const *
 
 void launch_blur_pass(Table in, Table out, int dir, int grid, const DeviceState *st, cudaStream_t s) {
     k_blur_pass<<<grid, kBlock, 0, s>>>(in, out, dir, st);
+}
+
+void launch_blur_list(Table in, Table out, int dir, const int *list, const int *count, int grid,
+                      const DeviceState *st, cudaStream_t s) {
+    k_blur_list<<<grid, kBlock, 0, s>>>(in, out, dir, list, count, st);
 }
 
 void launch_estep_out(int pt2pl, const RigidJob *job, const IterParams *ip, Table t, float *out,

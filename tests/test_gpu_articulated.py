@@ -123,3 +123,32 @@ def test_invalid_tree(ctx):
     with pytest.raises(fr.FilterRegError) as e:
         ctx.register_articulated(X, dev(np.zeros(10), np.int32), bad, X, iters=1)
     assert e.value.status == fr.FR_EINVAL
+
+
+def test_joint_limits_clamp_alike(ctx, orc):
+    # Joint limits narrowed to +-3 degrees while the observation is posed with
+    # joints up to +-8 degrees: the updates push joints past their limits and
+    # both implementations clamp them (Section 5.1's joint-limited model).
+    # Clamped joints sit exactly on a limit on both sides (the same set of
+    # joints); every other parameter agrees within the articulated bar.
+    import dataclasses
+    wide = synth.random_kintree(21)
+    p = synth.articulated_pair(21, n_points=12000, max_joint_deg=8.0, root_deg=1.0, root_trans=0.002,
+                               outlier_frac=0.0, tree=wide)
+    lim = np.radians(3.0)
+    narrow = dataclasses.replace(wide, q_min=np.full_like(wide.q_min, -lim), q_max=np.full_like(wide.q_max, lim))
+    assert (np.abs(p.q_gt) > lim).sum() >= 4
+    args = dict(iters=10, sigma=f32(0.01), w=f32(0.1))
+    Rg, qg, rg = ctx.register_articulated(dev(p.Xref), dev(p.body, np.int32), narrow, dev(p.Y), None,
+                                          iters=args["iters"], sigma_start=args["sigma"], sigma_end=args["sigma"],
+                                          w=args["w"])
+    Ro, qo, ro = orc.register_articulated(p.Xref, p.body, narrow, p.Y, None, sigma=args["sigma"],
+                                          w=args["w"], iters=args["iters"])
+    at_lim_g = np.isclose(np.abs(qg), lim, rtol=0, atol=0)
+    at_lim_o = np.isclose(np.abs(qo), lim, rtol=0, atol=0)
+    assert at_lim_o.sum() >= 2, qo
+    np.testing.assert_array_equal(at_lim_g, at_lim_o)
+    np.testing.assert_array_equal(qg[at_lim_g], qo[at_lim_o])
+    assert (np.abs(qg) <= lim).all() and (np.abs(qo) <= lim).all()
+    dr, dt, dq = diffs(Rg, qg, Ro, qo)
+    assert dr < 1e-3 and dt < 1e-4 and dq < 1e-3, (dr, dt, dq)
