@@ -139,16 +139,41 @@ def serving_requests(seed, n_requests, pool_size):
     return pool, arrivals, which, sigmas
 
 
-def run_serving(ctx, args):
+def serving_pool(args):
+    import torch
+    pool, arrivals, which, sigmas = serving_requests(args.seed + 11, args.serve_requests, args.serve_pool)
+    dpool = [(torch.from_numpy(p.X).cuda(), torch.from_numpy(p.Y).cuda(), torch.from_numpy(p.Yn).cuda())
+             for p in pool]
+    return pool, dpool, arrivals, which, sigmas
+
+
+def tune_serving(ctx, pool, dpool):
+    """Latency objective per size class: points per thread of a serving
+    tick's blocks, timed on up to 4 pool frames of the class."""
+    import numpy as np
+    import paper_1811_10136_gb300 as fr
+    bounds = [4096, 16384, 65536, 262144, 1 << 62]
+    out = {}
+    for c, hi in enumerate(bounds):
+        lo = bounds[c - 1] if c else 0
+        idx = [i for i, p in enumerate(pool) if lo < p.Y.shape[0] <= hi][:4]
+        if not idx:
+            continue
+        best, b_ms, d_ms = ctx.autotune_batch([dpool[i] for i in idx], objective=fr.FR_TUNE_LATENCY, reps=3,
+                                              residual=fr.FR_PT2PL, iters=ITERS, sigma_start=0.02,
+                                              sigma_end=0.02, w=W_OUT)
+        out[f"N<={hi}" if hi < (1 << 62) else f"N>{lo}"] = {
+            "serve_points_per_thread": best["serve_points_per_thread"], "ms": round(b_ms, 4),
+            "default_ms": round(d_ms, 4), "frames": len(idx)}
+    return out
+
+
+def run_serving(ctx, args, pool, dpool, arrivals, which, sigmas, plain=True):
     """Open-loop stream through fr_server (continuous batching) and, on the
     same arrivals, through the plain path (fr_register_rigid, one request at
     a time, first come first served).  Latency = completion - arrival."""
     import numpy as np
-    import torch
     import paper_1811_10136_gb300 as fr
-    pool, arrivals, which, sigmas = serving_requests(args.seed + 11, args.serve_requests, args.serve_pool)
-    dpool = [(torch.from_numpy(p.X).cuda(), torch.from_numpy(p.Y).cuda(), torch.from_numpy(p.Yn).cuda())
-             for p in pool]
     n = len(arrivals)
     opts = dict(residual=fr.FR_PT2PL, iters=ITERS)
 
@@ -188,6 +213,8 @@ def run_serving(ctx, args):
         tk = [srv.submit(*dpool[which[k]], sigma_start=float(sigmas[k]), w=W_OUT) for k in range(n)]
         sat = [srv.wait(t) for t in tk]
         out["saturated_regs_per_s"] = round(n / ((max(r.complete_ns for r in sat) - t1) * 1e-9), 1)
+    if not plain:
+        return out
     # the plain path on the same arrivals
     plain_T = []
     lat_p = []
@@ -202,9 +229,16 @@ def run_serving(ctx, args):
         plain_T.append(T)
     span_p = (time.monotonic_ns() - t0) * 1e-9
     q50, q99 = percentiles(lat_p)
+    # saturated plain path: every request queued, registered one at a time
+    t1 = time.monotonic_ns()
+    for k in range(n):
+        ctx.register_rigid(*dpool[which[k]], sigma_start=float(sigmas[k]), sigma_end=float(sigmas[k]),
+                           w=W_OUT, **opts)
+    sat_p = n / ((time.monotonic_ns() - t1) * 1e-9)
     out["plain"] = {"regs_per_s": round(n / span_p, 1), "latency_ms_p50": round(q50, 3),
-                    "latency_ms_p99": round(q99, 3),
-                    "note": "fr_register_rigid per request, first come first served, same arrivals"}
+                    "latency_ms_p99": round(q99, 3), "saturated_regs_per_s": round(sat_p, 1),
+                    "note": "fr_register_rigid per request, first come first served, same arrivals; "
+                            "saturated: all requests queued, one at a time"}
     out["max_rot_diff_deg_vs_plain"] = round(max(synth_rot(r.T, T) for r, T in zip(res, plain_T)), 6)
     return out
 
@@ -333,7 +367,7 @@ def run_ours(args):
     pairs = make_pairs(rank_seed(args.seed, rank), args.frames)
     dev = lambda a: torch.from_numpy(a).cuda()
     dpairs = [(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs]
-    ctx = fr.Context(local)
+    ctx = fr.Context(local, tune_table=None)   # built-in shapes; tuned in this run below
     opts = dict(residual=fr.FR_PT2PL, iters=ITERS, sigma_start=SIGMA0, sigma_end=SIGMA1, w=W_OUT)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -369,6 +403,14 @@ def run_ours(args):
         flush.fill_(1.0)
         batched_step()
         plain_step()
+
+    # ---- launch-shape autotuning of the batched path (outside the timed region)
+    best, tuned_ms, default_ms = ctx.autotune_batch(dpairs, objective=fr.FR_TUNE_THROUGHPUT, reps=3, **opts)
+    tuning = {"params": best, "em_iters_per_s_tuned": round(ITERS * args.frames / (tuned_ms * 1e-3), 1),
+              "em_iters_per_s_default": round(ITERS * args.frames / (default_ms * 1e-3), 1),
+              "timing": "median of 3 whole batched calls (CUDA events) per candidate shape, L2 warm"}
+    for _ in range(2):
+        batched_step()
 
     # ---- timed region: K batched steps (the headline) ------------------------
     launches0 = ctx.kernel_launches
@@ -513,7 +555,14 @@ def run_ours(args):
         ng.close()
 
     # ---- serving: Poisson stream through fr_server vs the plain path ---------
-    serving = None if args.no_serving else run_serving(ctx, args)
+    serving = None
+    if not args.no_serving:
+        sp = serving_pool(args)
+        serving = run_serving(ctx, args, *sp)          # default launch shapes
+        serving["tuning"] = tune_serving(ctx, sp[0], sp[1])
+        tuned = run_serving(ctx, args, *sp, plain=False)
+        serving["tuned"] = {k: tuned[k] for k in ("regs_per_s", "latency_ms_p50", "latency_ms_p99",
+                                                   "saturated_regs_per_s", "failed")}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
@@ -559,6 +608,7 @@ def run_ours(args):
                          "max_trans_err_vs_truth": round(trans_err, 6),
                          "max_rot_diff_deg_batched_vs_plain": round(mix_rot, 6)},
             "roofline": roofline,
+            "tuning": tuning,
             "precision": precision,
             "articulated": articulated,
             "serving": serving,

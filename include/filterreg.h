@@ -319,15 +319,70 @@ typedef struct {
  * reports (nullable) has n_items entries.  An item whose compact lattice
  * table overflows is rerun (from its initial pose) with the items that
  * overflowed, at the size that cannot.
+ * Launch shapes come from the context's tuning table (fr_tune_*); the
+ * call's launch sequence is captured once per shape (item sizes, iteration
+ * count, options) into a CUDA graph that later calls replay with new
+ * descriptors.
  * Returns FR_OK, or the status of the first failed item (each item's own
  * outcome is in its status field; failed items keep their input pose).
  * Synchronises the stream. */
 FR_API fr_status fr_register_rigid_batch(fr_ctx *ctx, fr_batch_item *items, int n_items,
                                          const fr_options *opt, fr_report *reports);
 /* The same with the items' clouds in host memory: they are copied into a
- * context-owned device staging area on the context's stream first. */
+ * context-owned device staging area on the context's stream first -- by one
+ * gather kernel reading across the host link when every cloud lies in
+ * page-locked (pinned) host memory, else by one copy per cloud.  Launches
+ * are replayed from a CUDA graph cached per launch shape, as below. */
 FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items, int n_items,
                                               const fr_options *opt, fr_report *reports);
+
+/* ---- launch-shape tuning ------------------------------------------------------
+ * The batched path and the server size their launches from a per-context
+ * table with five size classes by a cloud's observation count N (<= 4096,
+ * <= 16384, <= 65536, <= 262144, larger); a class holds the parameters below.
+ * Systems choices only (the paper has no counterpart): every setting
+ * computes the same registration, up to float32 summation order.
+ *   step_points_per_thread   model points per thread of a batched step block
+ *   build_points_per_thread  observation points per thread of a batched
+ *                            build block
+ *   table_slots_x2           a compact lattice table holds at least
+ *                            table_slots_x2 / 2 slots per observation point
+ *                            (rounded up to a power of two; too small a table
+ *                            overflows and the item reruns at the safe size)
+ *   serve_points_per_thread  points per thread of a server tick's step and
+ *                            build blocks (short chains keep ticks short)
+ * Defaults: 8, 8, 6, 2; fr_ctx_create loads the table file named by the
+ * environment variable FR_TUNE_TABLE, if set and well formed.
+ * fr_tune_get / fr_tune_set read / write the class
+ * that n_points falls in (FR_EINVAL outside 1..64 points per thread or 2..12
+ * slots); fr_tune_save writes the table as text (one class per line),
+ * fr_tune_load reads such a file (FR_EINVAL if malformed, the table
+ * unchanged). */
+typedef struct {
+    int32_t step_points_per_thread;
+    int32_t build_points_per_thread;
+    int32_t table_slots_x2;
+    int32_t serve_points_per_thread;
+} fr_tune_params;
+#define FR_TUNE_CLASSES 5
+FR_API fr_status fr_tune_get(const fr_ctx *ctx, int64_t n_points, fr_tune_params *out);
+FR_API fr_status fr_tune_set(fr_ctx *ctx, int64_t n_points, const fr_tune_params *p);
+FR_API fr_status fr_tune_save(const fr_ctx *ctx, const char *path);
+FR_API fr_status fr_tune_load(fr_ctx *ctx, const char *path);
+/* fr_autotune_batch: time candidate launch shapes on the caller's batch
+ * (device pointers, as for fr_register_rigid_batch; the items' poses and
+ * statuses are left untouched) and install the fastest in the size class of
+ * the items' mean N.  objective FR_TUNE_THROUGHPUT chooses the batched
+ * parameters (step / build points per thread, table slots) by the whole
+ * batch's time; FR_TUNE_LATENCY chooses serve_points_per_thread by the time
+ * of the same batch run with one shape for step and build blocks (a serving
+ * tick).  Each candidate runs `reps` times (median of CUDA-event times on the
+ * context's stream).  *best receives the installed parameters; best_ms and
+ * default_ms (nullable) the times of the chosen and of the default shape. */
+enum { FR_TUNE_THROUGHPUT = 0, FR_TUNE_LATENCY = 1 };
+FR_API fr_status fr_autotune_batch(fr_ctx *ctx, const fr_batch_item *items, int n_items,
+                                   const fr_options *opt, int objective, int reps,
+                                   fr_tune_params *best, double *best_ms, double *default_ms);
 
 /* ---- node-graph deformable model (Section 5.2, Eq. 21) ----------------------
  * Nodes k = 0..K-1 with reference positions p_k and poses T_k; model point i

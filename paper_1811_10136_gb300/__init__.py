@@ -34,7 +34,8 @@ EXPORTED = [
     "fr_lattice_build", "fr_lattice_splat", "fr_lattice_blur", "fr_lattice_slice",
     "fr_lattice_vertices", "fr_lattice_info", "fr_lattice_destroy", "fr_estep",
     "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
-    "fr_ctx_set_workspace_limit",
+    "fr_ctx_set_workspace_limit", "fr_tune_get", "fr_tune_set", "fr_tune_save", "fr_tune_load",
+    "fr_autotune_batch",
     "fr_ctx_transfer_bytes", "fr_estep_noalloc", "fr_register_rigid_batch",
     "fr_register_rigid_batch_host", "fr_register_articulated", "fr_estep_storage",
     "fr_server_create", "fr_server_submit", "fr_server_poll", "fr_server_wait", "fr_server_release",
@@ -107,6 +108,17 @@ class fr_batch_item(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class fr_tune_params(ctypes.Structure):
+    _fields_ = [("step_points_per_thread", ctypes.c_int32), ("build_points_per_thread", ctypes.c_int32),
+                ("table_slots_x2", ctypes.c_int32), ("serve_points_per_thread", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+FR_TUNE_THROUGHPUT, FR_TUNE_LATENCY = 0, 1
+
+
 class fr_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 7), ("total_ms", ctypes.c_double * 7)]
 
@@ -156,6 +168,13 @@ def load(build_if_missing: bool = True):
     L.fr_register_rigid_host.argtypes = L.fr_register_rigid.argtypes
     L.fr_ctx_set_profiling.argtypes = [_vp, ctypes.c_int]
     L.fr_ctx_set_workspace_limit.argtypes = [_vp, ctypes.c_size_t]
+    L.fr_tune_get.argtypes = [_vp, _i64, ctypes.POINTER(fr_tune_params)]
+    L.fr_tune_set.argtypes = [_vp, _i64, ctypes.POINTER(fr_tune_params)]
+    L.fr_tune_save.argtypes = [_vp, ctypes.c_char_p]
+    L.fr_tune_load.argtypes = [_vp, ctypes.c_char_p]
+    L.fr_autotune_batch.argtypes = [_vp, ctypes.POINTER(fr_batch_item), ctypes.c_int, ctypes.POINTER(fr_options),
+                                    ctypes.c_int, ctypes.c_int, ctypes.POINTER(fr_tune_params),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.fr_ctx_profile.argtypes = [_vp, ctypes.POINTER(fr_profile), ctypes.c_int]
     L.fr_ctx_transfer_bytes.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
     L.fr_register_rigid_batch.argtypes = [_vp, ctypes.POINTER(fr_batch_item), ctypes.c_int,
@@ -258,7 +277,10 @@ def estep_noalloc(X, Y, Yn=None, sigma=0.02, T=None, out=None, stream=None):
 class Context:
     """An fr_ctx bound to a CUDA device and (by default) torch's current stream."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, tune_table: str | None = "default"):
+        """tune_table: a launch-shape table (fr_tune_load) -- "default" the
+        one shipped beside the library (tuning_gb300.txt), None the built-in
+        defaults, or a path."""
         import torch
         L = load()
         if stream is None:
@@ -270,6 +292,12 @@ class Context:
             raise FilterRegError(st, f"fr_ctx_create(device={device}) failed")
         self._h = h
         self.device = device
+        if tune_table == "default":
+            tune_table = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.txt")
+            if not os.path.exists(tune_table):
+                tune_table = None
+        if tune_table:
+            self.tune_load(tune_table)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -302,6 +330,39 @@ class Context:
     def set_workspace_limit(self, nbytes: int):
         """Cap the lattice-table arena of batched calls at nbytes (0: none)."""
         self._check(load().fr_ctx_set_workspace_limit(self._h, int(nbytes)), "fr_ctx_set_workspace_limit")
+
+    # ---- launch-shape tuning ----------------------------------------------
+    def tune_get(self, n_points: int) -> dict:
+        """Tuning parameters of the size class of n_points."""
+        p = fr_tune_params()
+        self._check(load().fr_tune_get(self._h, int(n_points), ctypes.byref(p)), "fr_tune_get")
+        return p.as_dict()
+
+    def tune_set(self, n_points: int, **params):
+        """Set (some of) the tuning parameters of n_points' size class."""
+        cur = self.tune_get(n_points)
+        cur.update(params)
+        p = fr_tune_params(**cur)
+        self._check(load().fr_tune_set(self._h, int(n_points), ctypes.byref(p)), "fr_tune_set")
+
+    def tune_save(self, path: str):
+        self._check(load().fr_tune_save(self._h, os.fsencode(path)), "fr_tune_save")
+
+    def tune_load(self, path: str):
+        self._check(load().fr_tune_load(self._h, os.fsencode(path)), "fr_tune_load")
+
+    def autotune_batch(self, pairs, objective=FR_TUNE_THROUGHPUT, reps=3, sigmas=None, ws=None, **opts):
+        """Time candidate launch shapes on this batch (CUDA tensors, as for
+        register_rigid_batch) and install the fastest; returns (params dict,
+        best ms, default ms)."""
+        items, _ = self._batch_items(pairs, sigmas, ws, None, False, options(**opts))
+        o = options(**opts)
+        best = fr_tune_params()
+        b_ms, d_ms = ctypes.c_double(), ctypes.c_double()
+        self._check(load().fr_autotune_batch(self._h, items, len(pairs), ctypes.byref(o), int(objective), int(reps),
+                                             ctypes.byref(best), ctypes.byref(b_ms), ctypes.byref(d_ms)),
+                    "fr_autotune_batch")
+        return best.as_dict(), b_ms.value, d_ms.value
 
     def set_profiling(self, on: bool):
         self._check(load().fr_ctx_set_profiling(self._h, int(bool(on))), "fr_ctx_set_profiling")
@@ -381,19 +442,9 @@ class Context:
         self._check(r, "fr_register_articulated")
         return R, q, _report(rep)
 
-    def register_rigid_batch(self, pairs, sigmas=None, ws=None, T0s=None, host=False, **opts):
-        """Register a batch of pairs in one launch per EM iteration.
-
-        pairs: list of (X, Y, Yn) -- CUDA tensors (host=False) or float32 (n, 4)
-        host arrays / tensors (host=True); Yn may be None for point-to-point.
-        sigmas: list of (sigma_start, sigma_end) per item (default: the
-        options' schedule); ws: outlier ratios; T0s: initial poses.
-        Returns a list of (T (4,4), Report, status) per item."""
-        L = load()
-        o = options(**opts)
+    def _batch_items(self, pairs, sigmas, ws, T0s, host, o):
         n = len(pairs)
         items = (fr_batch_item * n)()
-        reps = (fr_report * n)()
         keep = []
         for b, (X, Y, Yn) in enumerate(pairs):
             it = items[b]
@@ -413,6 +464,20 @@ class Context:
             T = _pose(T0s[b] if T0s is not None else None)
             for i in range(16):
                 it.T[i] = T.ravel()[i]
+        return items, keep
+
+    def register_rigid_batch(self, pairs, sigmas=None, ws=None, T0s=None, host=False, **opts):
+        """Register many (X, Y, Yn) pairs with one launch per EM iteration.
+        pairs: list of (X, Y, Yn) -- CUDA tensors (host=False) or float32 (n, 4)
+        host arrays / tensors (host=True); Yn may be None for point-to-point.
+        sigmas: list of (sigma_start, sigma_end) per item (default: the
+        options' schedule); ws: outlier ratios; T0s: initial poses.
+        Returns a list of (T (4,4), Report, status) per item."""
+        L = load()
+        o = options(**opts)
+        n = len(pairs)
+        items, keep = self._batch_items(pairs, sigmas, ws, T0s, host, o)
+        reps = (fr_report * n)()
         f = L.fr_register_rigid_batch_host if host else L.fr_register_rigid_batch
         st = f(self._h, items, n, ctypes.byref(o), reps)
         if st != FR_OK and not any(items[b].status != FR_OK for b in range(n)):

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -507,6 +508,11 @@ FR_API fr_status fr_ctx_create(int device, void *cuda_stream, fr_ctx **out) {
     ctx->stream = (cudaStream_t)cuda_stream;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (ctx->num_sms < 1) ctx->num_sms = 1;
+    // A launch-shape table named by FR_TUNE_TABLE is loaded when it parses
+    // (a missing or malformed one leaves the built-in defaults).
+    if (const char *tt = std::getenv("FR_TUNE_TABLE"))
+        if (*tt) fr_tune_load(ctx, tt);
+    ctx->err.clear();
     *out = ctx;
     return FR_OK;
 }
@@ -541,6 +547,57 @@ FR_API fr_status fr_ctx_set_stream(fr_ctx *ctx, void *cuda_stream) {
 FR_API fr_status fr_ctx_set_workspace_limit(fr_ctx *ctx, size_t bytes) {
     if (!ctx) return FR_EINVAL;
     ctx->ws_limit = bytes;
+    return FR_OK;
+}
+
+FR_API fr_status fr_tune_get(const fr_ctx *ctx, int64_t n_points, fr_tune_params *out) {
+    if (!ctx || !out || n_points < 1) return FR_EINVAL;
+    *out = ctx->tune[tune_class(n_points)];
+    return FR_OK;
+}
+
+FR_API fr_status fr_tune_set(fr_ctx *ctx, int64_t n_points, const fr_tune_params *p) {
+    if (!ctx || !p || n_points < 1) return FR_EINVAL;
+    if (!tune_valid(*p)) return ctx->fail(FR_EINVAL, "tuning parameters out of range");
+    ctx->tune[tune_class(n_points)] = *p;
+    return FR_OK;
+}
+
+// File format: one line per size class, "class step build table_x2 serve".
+FR_API fr_status fr_tune_save(const fr_ctx *ctx, const char *path) {
+    if (!ctx || !path) return FR_EINVAL;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return FR_EINVAL;
+    std::fprintf(f, "# filterreg launch tuning: class step_ppt build_ppt table_slots_x2 serve_ppt\n");
+    for (int c = 0; c < kTuneClasses; ++c) {
+        const fr_tune_params &p = ctx->tune[c];
+        std::fprintf(f, "%d %d %d %d %d\n", c, p.step_points_per_thread, p.build_points_per_thread,
+                     p.table_slots_x2, p.serve_points_per_thread);
+    }
+    return std::fclose(f) == 0 ? FR_OK : FR_EINVAL;
+}
+
+FR_API fr_status fr_tune_load(fr_ctx *ctx, const char *path) {
+    if (!ctx || !path) return FR_EINVAL;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return ctx->fail(FR_EINVAL, "cannot open tuning table %s", path);
+    fr_tune_params t[kTuneClasses];
+    for (int c = 0; c < kTuneClasses; ++c) t[c] = ctx->tune[c];
+    char line[256];
+    bool ok = true;
+    while (ok && std::fgets(line, sizeof line, f)) {
+        if (line[0] == '#' || line[0] == '\n') continue;
+        int c, a, b, x, v;
+        if (std::sscanf(line, "%d %d %d %d %d", &c, &a, &b, &x, &v) != 5 || c < 0 || c >= kTuneClasses) {
+            ok = false;
+            break;
+        }
+        t[c] = fr_tune_params{a, b, x, v};
+        ok = tune_valid(t[c]);
+    }
+    std::fclose(f);
+    if (!ok) return ctx->fail(FR_EINVAL, "malformed tuning table %s", path);
+    for (int c = 0; c < kTuneClasses; ++c) ctx->tune[c] = t[c];
     return FR_OK;
 }
 

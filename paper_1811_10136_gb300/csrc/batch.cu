@@ -1,14 +1,19 @@
 // Batched rigid registration: many registrations advanced together, one
 // launch of k_em_multi per EM iteration for the whole batch.
 //
-// Each registration ("slot") gets its own three rotating lattice tables, its
-// own reduction partials, pose state and per-iteration constants; one launch
+// Each registration ("slot") gets its own rotating lattice tables, its own
+// reduction partials, pose state and per-iteration constants; one launch
 // runs, for every slot, the step of iteration k (slice + reduction, the last
 // block of the slot solving its 6x6 system), the build of iteration k+1 when
 // the slot's sigma is annealed, and the clear of the table of build k-1.
 // While one slot's last block runs its float64 solve, the other slots'
 // blocks keep the SMs busy -- the latency tail of a single registration is
 // hidden by the batch.
+//
+// Launch shapes (points per thread of step and build blocks, compact table
+// size) come from the context's tuning table, per size class; a call's
+// launch sequence is captured once per shape into a CUDA graph and replayed
+// by later calls of the same shape, only the descriptors being uploaded.
 //
 // Memory: the key and value arenas hold every slot's tables.  They are empty
 // (keys all-ones, values zero) between calls -- every call frees what it
@@ -22,6 +27,14 @@ using namespace fr;
 
 namespace fr {
 
+// A captured batched launch sequence and the shape it was captured for.
+struct BatchGraph {
+    std::vector<long long> key;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+    uint64_t last_use = 0;
+};
+
 struct BatchWorkspace {
     unsigned long long *keys = nullptr;  // slot-record arena, all free (zero) between calls
     size_t slots_cap = 0;                // table slots in the arena
@@ -33,11 +46,25 @@ struct BatchWorkspace {
     size_t h_down_cap = 0;
     float4 *stage = nullptr;             // inputs of the host-buffer variant
     size_t stage_cap = 0;
+    void *d_chunks = nullptr;            // gather chunk table (device) ...
+    void *h_chunks = nullptr;            // ... and its pinned staging
+    size_t chunks_cap = 0;               // bytes of each
+    std::vector<BatchGraph> graphs;      // least recently used out
+    uint64_t use_clock = 0;
 };
+
+void drop_batch_graphs(BatchWorkspace *w) {
+    for (auto &g : w->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    w->graphs.clear();
+}
 
 void free_batch_workspace(fr_ctx *ctx) {
     BatchWorkspace *w = ctx->batch;
     if (!w) return;
+    drop_batch_graphs(w);
+    cudaFree(w->d_chunks);
+    cudaFreeHost(w->h_chunks);
     cudaFree(w->keys);
     cudaFree(w->misc);
     cudaFree(w->stage);
@@ -76,6 +103,7 @@ fr_status ensure_arenas(fr_ctx *ctx, size_t slots, size_t misc, size_t up, size_
     if (misc > w->misc_cap) {
         const size_t cap = std::max(misc, w->misc_cap * 3 / 2);
         cudaStreamSynchronize(ctx->stream);
+        drop_batch_graphs(w);
         cudaFree(w->misc);
         w->misc = nullptr;
         w->misc_cap = 0;
@@ -112,8 +140,83 @@ struct ItemPlan {
     size_t list_off, part_off; // in misc (bytes)
 };
 
+constexpr size_t kBatchGraphCache = 16;
+
+// One launch of the batched sequence: its segment table, block -> segment
+// map, grid and profile class.
+struct BatchLaunch {
+    size_t segs_off, map_off;  // in the misc arena
+    int grid, check_done, cls;
+};
+
+// Issues the launch sequence on `s` (plain, or inside a stream capture);
+// with profiling on, an event pair brackets each launch (an external record
+// inside a capture, so that the graph keeps it).
+void issue_batch(fr_ctx *ctx, const std::vector<BatchLaunch> &L, const Slot *dslots, unsigned char *D,
+                 int pt2pl, int kahan, int storage, cudaStream_t s, bool capturing) {
+    for (size_t i = 0; i < L.size(); ++i) {
+        if (ctx->profiling) {
+            while (ctx->events.size() < 2 * (i + 1)) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                ctx->events.push_back(e);
+            }
+            if (ctx->event_class.size() < i + 1) ctx->event_class.resize(i + 1);
+            ctx->event_class[i] = L[i].cls;
+            if (capturing) cudaEventRecordWithFlags(ctx->events[2 * i], s, cudaEventRecordExternal);
+            else cudaEventRecord(ctx->events[2 * i], s);
+        }
+        launch_em_multi(pt2pl, kahan, dslots, (const Seg *)(D + L[i].segs_off),
+                        (const unsigned short *)(D + L[i].map_off), L[i].grid, L[i].check_done, s, storage);
+        if (ctx->profiling) {
+            if (capturing) cudaEventRecordWithFlags(ctx->events[2 * i + 1], s, cudaEventRecordExternal);
+            else cudaEventRecord(ctx->events[2 * i + 1], s);
+        }
+    }
+}
+
+// Replays the cached graph of this launch shape, capturing it first when
+// new; without a graph (capture refused) the launches are issued directly.
+fr_status run_launches(fr_ctx *ctx, const std::vector<long long> &key, const std::vector<BatchLaunch> &L,
+                       const Slot *dslots, unsigned char *D, int pt2pl, int kahan, int storage) {
+    BatchWorkspace *w = ctx->batch;
+    BatchGraph *hit = nullptr;
+    for (auto &g : w->graphs)
+        if (g.key == key) hit = &g;
+    if (!hit) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            issue_batch(ctx, L, dslots, D, pt2pl, kahan, storage, ctx->stream, true);
+            const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+            if (e == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();
+        if (!exec) {  // direct launches
+            issue_batch(ctx, L, dslots, D, pt2pl, kahan, storage, ctx->stream, false);
+            ctx->launches += (int64_t)L.size();
+            return ctx->cuda(cudaGetLastError(), "batched launch");
+        }
+        if (w->graphs.size() >= kBatchGraphCache) {
+            auto lru = std::min_element(w->graphs.begin(), w->graphs.end(),
+                                        [](const BatchGraph &a, const BatchGraph &b) { return a.last_use < b.last_use; });
+            cudaGraphExecDestroy(lru->exec);
+            w->graphs.erase(lru);
+        }
+        w->graphs.push_back(BatchGraph{key, exec, (int)L.size(), 0});
+        hit = &w->graphs.back();
+    }
+    hit->last_use = ++w->use_clock;
+    FR_CUDA(ctx, cudaGraphLaunch(hit->exec, ctx->stream));
+    ctx->launches += hit->kernels;
+    return FR_OK;
+}
+
+// `force` (nullable) gives every item the same launch shape (the autotuner);
+// otherwise each item takes its size class's entry of the tuning table.
 fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *opt,
-                    fr_report *reports, bool safe) {
+                    fr_report *reports, bool safe, const fr_tune_params *force = nullptr) {
     const int pt2pl = opt->residual == FR_PT2PL;
     const int kahan = opt->kahan ? 1 : 0;
     const int iters = opt->iters;
@@ -131,11 +234,12 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     for (int b = 0; b < n; ++b) {
         const fr_batch_item &it = items[b];
         ItemPlan &p = ip[b];
-        p.cap = table_slots(it.N, safe);
+        const fr_tune_params &tp = force ? *force : ctx->tune[tune_class(it.N)];
+        p.cap = safe ? table_slots(it.N, true) : tuned_table_slots(it.N, tp.table_slots_x2);
         p.tab_off = slots;
         slots += ntab * (size_t)p.cap;
-        p.gs = div_up(it.M, (long long)kBlock * kMultiPointsPerThread);
-        p.gp = div_up(it.N, (long long)kBlock * kMultiPointsPerThread);
+        p.gs = div_up(it.M, (long long)kBlock * tp.step_points_per_thread);
+        p.gp = div_up(it.N, (long long)kBlock * tp.build_points_per_thread);
         p.annealed = (it.sigma_start != it.sigma_end && iters > 1) ? 1 : 0;
         p.gb = p.annealed ? p.gp : 0;
         p.gc = p.annealed ? std::max(1, div_up(it.N, 4096)) : 0;
@@ -312,51 +416,33 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
         if (blk != grid_epi) return ctx->fail(FR_EINVAL, "internal: final clear block map");
     }
 
-    // ---- upload, launch, read back ---------------------------------------------
+    // ---- upload, launch (a cached graph per launch shape), read back -------------
     FR_CUDA(ctx, copy_async(ctx, D, U, up_bytes, cudaMemcpyHostToDevice));
     const Slot *dslots = (const Slot *)(D + o_slots);
-    const Seg *dsegs = (const Seg *)(D + o_segs);
-    // With profiling on, an event pair brackets each launch (classes: first
-    // build, EM iteration, final clear).
-    int nprof = 0;
-    auto timed = [&](int cls, auto &&launch) {
-        if (ctx->profiling) {
-            while (ctx->events.size() < 2 * (size_t)(nprof + 1)) {
-                cudaEvent_t e;
-                cudaEventCreate(&e);
-                ctx->events.push_back(e);
-            }
-            if (ctx->event_class.size() < (size_t)(nprof + 1)) ctx->event_class.resize(nprof + 1);
-            ctx->event_class[nprof] = cls;
-            cudaEventRecord(ctx->events[2 * nprof], ctx->stream);
-        }
-        launch();
-        if (ctx->profiling) cudaEventRecord(ctx->events[2 * nprof + 1], ctx->stream);
-        ++nprof;
-    };
+    // Profile classes: first build, EM iteration, final clear.
+    std::vector<BatchLaunch> launches;
     if (iters > 0) {
-        timed(FR_K_BUILD, [&] {
-            launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter,
-                            (const unsigned short *)(D + o_bs_pro), grid_pro, 0, ctx->stream, opt->storage);
-        });
+        const size_t seg0 = o_segs + (size_t)iters1 * seg_per_iter * sizeof(Seg);
+        launches.push_back(BatchLaunch{seg0, o_bs_pro, grid_pro, 0, FR_K_BUILD});
         if (lead == 2)
-            timed(FR_K_CONVERT, [&] {
-                launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter + seg_pro,
-                                (const unsigned short *)(D + o_bs_pro2), grid_pro2, 0, ctx->stream,
-                                opt->storage);
-            });
+            launches.push_back(BatchLaunch{seg0 + seg_pro * sizeof(Seg), o_bs_pro2, grid_pro2, 0, FR_K_CONVERT});
         for (int k = 0; k < iters; ++k)
-            timed(FR_K_STEP, [&] {
-                launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)k * seg_per_iter,
-                                (const unsigned short *)(D + o_bs_iter), grid_iter, 1, ctx->stream,
-                                opt->storage);
-            });
-        timed(FR_K_CLEAR, [&] {
-            launch_em_multi(pt2pl, kahan, dslots, dsegs + (size_t)iters1 * seg_per_iter + seg_pro + seg_pro2,
-                            (const unsigned short *)(D + o_bs_epi), grid_epi, 0, ctx->stream, opt->storage);
-        });
-        ctx->launches += iters + 2 + (lead - 1);
+            launches.push_back(BatchLaunch{o_segs + (size_t)k * seg_per_iter * sizeof(Seg), o_bs_iter, grid_iter, 1,
+                                           FR_K_STEP});
+        launches.push_back(BatchLaunch{seg0 + (size_t)(seg_pro + seg_pro2) * sizeof(Seg), o_bs_epi, grid_epi, 0,
+                                       FR_K_CLEAR});
     }
+    if (!launches.empty()) {
+        std::vector<long long> key = {n, iters, lead, pt2pl, kahan, (long long)opt->storage, ctx->profiling,
+                                      (long long)(uintptr_t)D, (long long)up_bytes};
+        for (const BatchLaunch &l : launches) {
+            key.push_back((long long)l.segs_off);
+            key.push_back((long long)l.map_off);
+            key.push_back(l.grid);
+        }
+        FR_TRY(run_launches(ctx, key, launches, dslots, D, pt2pl, kahan, opt->storage));
+    }
+    const int nprof = (int)launches.size();
     FR_CUDA(ctx, cudaGetLastError());
     unsigned char *H = w->h_down;
     FR_CUDA(ctx, copy_async(ctx, H, D + o_states, n * sizeof(DeviceState), cudaMemcpyDeviceToHost));
@@ -397,6 +483,47 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     return first_bad;
 }
 
+// One chunk of a host -> device gather: `count` float4 from src to dst.
+struct GatherChunk {
+    const float4 *src;
+    float4 *dst;
+    long long count;
+};
+constexpr long long kGatherChunk = 16384;  // float4 per block (256 KiB)
+
+// Copies every chunk (block c takes chunk c) with eight 16-byte loads in
+// flight per thread: reading page-locked host memory across the host link in
+// one launch instead of one copy per cloud.
+__global__ void __launch_bounds__(256) k_gather(const GatherChunk *chunks) {
+    const GatherChunk g = chunks[blockIdx.x];
+    constexpr int kU = 8;
+    for (long long e0 = (long long)threadIdx.x; e0 < g.count; e0 += 256LL * kU) {
+        float4 v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const long long e = e0 + 256LL * u;
+            if (e < g.count) v[u] = g.src[e];
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const long long e = e0 + 256LL * u;
+            if (e < g.count) g.dst[e] = v[u];
+        }
+    }
+}
+
+// Device address of page-locked host memory at p (nullptr when p is
+// pageable, device or misaligned memory: copy it instead).
+const void *mapped_host(const void *p) {
+    if (!p || ((uintptr_t)p & 15u)) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Status of an item that run_batch has not reached yet: a call that fails
 // before its per-item results (an allocation, a CUDA error) leaves it set.
 constexpr fr_status kUnset = (fr_status)-1;
@@ -406,10 +533,10 @@ constexpr fr_status kUnset = (fr_status)-1;
 // its own outcome: an item the call never reached takes the call's status,
 // and a rerun that fails takes the rerun's status, not its earlier one.
 fr_status run_batch_sized(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *opt,
-                          fr_report *reports) {
+                          fr_report *reports, const fr_tune_params *force = nullptr) {
     std::vector<fr_batch_item> init(items, items + n);
     for (int b = 0; b < n; ++b) items[b].status = kUnset;
-    fr_status st = run_batch(ctx, items, n, opt, reports, false);
+    fr_status st = run_batch(ctx, items, n, opt, reports, false, force);
     bool reached = true;
     for (int b = 0; b < n; ++b)
         if (items[b].status == kUnset) {
@@ -428,7 +555,7 @@ fr_status run_batch_sized(fr_ctx *ctx, fr_batch_item *items, int n, const fr_opt
         sub.push_back(init[b]);
         sub.back().status = kUnset;
     }
-    const fr_status rs = run_batch(ctx, sub.data(), (int)sub.size(), opt, reports ? subrep.data() : nullptr, true);
+    const fr_status rs = run_batch(ctx, sub.data(), (int)sub.size(), opt, reports ? subrep.data() : nullptr, true, force);
     for (size_t q = 0; q < redo.size(); ++q) {
         if (sub[q].status == kUnset) {
             sub[q] = init[redo[q]];
@@ -499,23 +626,53 @@ FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items,
         FR_CUDA(ctx, dev_alloc(&w->stage, need));
         w->stage_cap = need;
     }
+    // The clouds go to the staging area: one gather launch when every cloud
+    // is page-locked host memory, else one copy per cloud.
+    struct Src { const void *h, *d; size_t n; float4 *dst; };
+    std::vector<Src> src;
     std::vector<fr_batch_item> dev(items, items + n_items);
     float4 *p = w->stage;
+    bool mapped = true;
+    auto add = [&](const float *h, size_t n) {
+        const void *d = mapped_host(h);
+        mapped = mapped && d;
+        src.push_back(Src{h, d, n, p});
+        p += n;
+        return (const float *)src.back().dst;
+    };
     for (int b = 0; b < n_items; ++b) {
         const fr_batch_item &h = items[b];
-        FR_CUDA(ctx, copy_async(ctx, p, h.d_X, h.M * sizeof(float4), cudaMemcpyHostToDevice));
-        dev[b].d_X = (const float *)p;
-        p += h.M;
-        FR_CUDA(ctx, copy_async(ctx, p, h.d_Y, h.N * sizeof(float4), cudaMemcpyHostToDevice));
-        dev[b].d_Y = (const float *)p;
-        p += h.N;
-        if (pt2pl) {
-            FR_CUDA(ctx, copy_async(ctx, p, h.d_Yn, h.N * sizeof(float4), cudaMemcpyHostToDevice));
-            dev[b].d_Yn = (const float *)p;
-            p += h.N;
-        } else {
-            dev[b].d_Yn = nullptr;
+        dev[b].d_X = add(h.d_X, (size_t)h.M);
+        dev[b].d_Y = add(h.d_Y, (size_t)h.N);
+        dev[b].d_Yn = pt2pl ? add(h.d_Yn, (size_t)h.N) : nullptr;
+    }
+    if (mapped) {
+        std::vector<GatherChunk> chunks;
+        for (const Src &c : src)
+            for (size_t o = 0; o < c.n; o += kGatherChunk)
+                chunks.push_back(GatherChunk{(const float4 *)c.d + o, c.dst + o,
+                                             (long long)std::min<size_t>(kGatherChunk, c.n - o)});
+        const size_t bytes = chunks.size() * sizeof(GatherChunk);
+        if (bytes > w->chunks_cap) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(w->d_chunks);
+            cudaFreeHost(w->h_chunks);
+            w->d_chunks = w->h_chunks = nullptr;
+            w->chunks_cap = 0;
+            const size_t cap = std::max(bytes * 2, (size_t)4096);
+            FR_CUDA(ctx, cudaMalloc(&w->d_chunks, cap));
+            FR_CUDA(ctx, cudaMallocHost(&w->h_chunks, cap));
+            w->chunks_cap = cap;
         }
+        // (every call ends synchronised, so the pinned table is free to rewrite)
+        std::memcpy(w->h_chunks, chunks.data(), bytes);
+        FR_CUDA(ctx, cudaMemcpyAsync(w->d_chunks, w->h_chunks, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        k_gather<<<(int)chunks.size(), 256, 0, ctx->stream>>>((const GatherChunk *)w->d_chunks);
+        FR_CUDA(ctx, cudaGetLastError());
+        ctx->launches += 1;
+        for (const Src &c : src) ctx->h2d_bytes += (int64_t)(c.n * sizeof(float4));
+    } else {
+        for (const Src &c : src) FR_CUDA(ctx, copy_async(ctx, c.dst, c.h, c.n * sizeof(float4), cudaMemcpyHostToDevice));
     }
     const fr_status st = run_batch_sized(ctx, dev.data(), n_items, opt, reports);
     for (int b = 0; b < n_items; ++b) {
@@ -523,6 +680,90 @@ FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items,
         for (int i = 0; i < 16; ++i) items[b].T[i] = dev[b].T[i];
     }
     return st;
+}
+
+FR_API fr_status fr_autotune_batch(fr_ctx *ctx, const fr_batch_item *items, int n_items, const fr_options *opt,
+                                   int objective, int reps, fr_tune_params *best, double *best_ms,
+                                   double *default_ms) {
+    if (!ctx || !best) return FR_EINVAL;
+    if (objective != FR_TUNE_THROUGHPUT && objective != FR_TUNE_LATENCY)
+        return ctx->fail(FR_EINVAL, "objective must be FR_TUNE_THROUGHPUT or FR_TUNE_LATENCY");
+    if (reps < 1 || reps > 50) return ctx->fail(FR_EINVAL, "reps must be in 1..50");
+    FR_TRY(validate_batch(ctx, items, n_items, opt, false));
+    cudaSetDevice(ctx->device);
+    long long nsum = 0;
+    for (int b = 0; b < n_items; ++b) nsum += items[b].N;
+    const int cls = tune_class(nsum / n_items);
+    const fr_tune_params cur = ctx->tune[cls];
+    std::vector<fr_tune_params> cand;
+    if (objective == FR_TUNE_THROUGHPUT) {
+        for (int sp : {2, 4, 8, 16})
+            for (int bp : {4, 8, 16})
+                for (int x2 : {3, 6}) cand.push_back(fr_tune_params{sp, bp, x2, cur.serve_points_per_thread});
+    } else {
+        for (int pp : {1, 2, 4, 8}) cand.push_back(fr_tune_params{pp, pp, cur.table_slots_x2, pp});
+    }
+    cudaEvent_t e0, e1;
+    FR_CUDA(ctx, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return ctx->cuda(cudaGetLastError(), "cudaEventCreate");
+    }
+    std::vector<fr_batch_item> work(items, items + n_items);
+    // Median time of `reps` calls (after one untimed call that captures the graph).
+    auto measure = [&](const fr_tune_params &tp, double &ms) -> fr_status {
+        std::vector<double> t;
+        for (int r = 0; r <= reps; ++r) {
+            std::copy(items, items + n_items, work.begin());
+            cudaEventRecord(e0, ctx->stream);
+            const fr_status st = run_batch_sized(ctx, work.data(), n_items, opt, nullptr, &tp);
+            cudaEventRecord(e1, ctx->stream);
+            if (st != FR_OK) return st;
+            FR_CUDA(ctx, cudaEventSynchronize(e1));
+            float f = 0.0f;
+            cudaEventElapsedTime(&f, e0, e1);
+            if (r > 0) t.push_back(f);
+        }
+        std::sort(t.begin(), t.end());
+        ms = t[t.size() / 2];
+        return FR_OK;
+    };
+    fr_status st = FR_OK;
+    fr_tune_params dflt = tune_default();
+    if (objective == FR_TUNE_LATENCY)
+        dflt = fr_tune_params{dflt.serve_points_per_thread, dflt.serve_points_per_thread, cur.table_slots_x2,
+                              dflt.serve_points_per_thread};
+    double d_ms = 0.0, b_ms = 1e300;
+    fr_tune_params win = dflt;
+    st = measure(dflt, d_ms);
+    if (st == FR_OK) {
+        b_ms = d_ms;
+        for (const fr_tune_params &c : cand) {
+            double ms = 0.0;
+            st = measure(c, ms);
+            if (st != FR_OK) break;
+            if (ms < b_ms) {
+                b_ms = ms;
+                win = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FR_OK) return st;
+    fr_tune_params inst = cur;
+    if (objective == FR_TUNE_THROUGHPUT) {
+        inst.step_points_per_thread = win.step_points_per_thread;
+        inst.build_points_per_thread = win.build_points_per_thread;
+        inst.table_slots_x2 = win.table_slots_x2;
+    } else {
+        inst.serve_points_per_thread = win.serve_points_per_thread;
+    }
+    ctx->tune[cls] = inst;
+    *best = inst;
+    if (best_ms) *best_ms = b_ms;
+    if (default_ms) *default_ms = d_ms;
+    return FR_OK;
 }
 
 }  // extern "C"

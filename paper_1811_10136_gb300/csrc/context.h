@@ -57,6 +57,25 @@ struct GraphKey {
     }
 };
 
+// Launch-shape tuning table: five size classes by observation count.
+constexpr int kTuneClasses = 5;
+inline int tune_class(long long n) {
+    return n <= 4096 ? 0 : n <= 16384 ? 1 : n <= 65536 ? 2 : n <= 262144 ? 3 : 4;
+}
+inline fr_tune_params tune_default() { return fr_tune_params{8, 8, 6, 2}; }
+inline bool tune_valid(const fr_tune_params &p) {
+    auto ppt = [](int v) { return v >= 1 && v <= 64; };
+    return ppt(p.step_points_per_thread) && ppt(p.build_points_per_thread) && ppt(p.serve_points_per_thread) &&
+           p.table_slots_x2 >= 2 && p.table_slots_x2 <= 12;
+}
+// Compact table slots for N observation points: at least x2 / 2 per point.
+inline uint32_t tuned_table_slots(long long n_points, int x2) {
+    const long long want = (x2 * n_points + 1) / 2;
+    uint32_t c = 1024;
+    while ((long long)c < want && c < (1u << 30)) c <<= 1;
+    return c;
+}
+
 struct CachedGraph {
     GraphKey key;
     cudaGraphExec_t exec = nullptr;
@@ -119,6 +138,8 @@ struct fr_ctx {
     uint64_t use_clock = 0;
     int bpsm[2][2] = {{0, 0}, {0, 0}};  // resident fused-kernel blocks per SM
 
+    fr_tune_params tune[fr::kTuneClasses] = {fr::tune_default(), fr::tune_default(), fr::tune_default(),
+                                             fr::tune_default(), fr::tune_default()};
     fr::BatchWorkspace *batch = nullptr;  // batched-registration workspace (batch.cu)
     fr::ArtWorkspace *art = nullptr;      // articulated-registration workspace (articulated.cu)
 

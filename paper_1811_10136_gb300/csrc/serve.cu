@@ -37,10 +37,10 @@ int64_t steady_ns() {
 }
 
 constexpr int kMaxAhead = 2;         // ticks queued on the GPU before the worker waits
-// Points per thread of a request's step and build blocks.  A serving tick is
-// rarely a full GPU, so its duration is the longest per-thread chain: short
-// chains (more, smaller blocks) keep the latency down.
-constexpr int kServePointsPerThread = 2;
+// Points per thread of a request's step and build blocks come from the
+// context's tuning table (serve_points_per_thread, default 2): a serving tick
+// is rarely a full GPU, so its duration is the longest per-thread chain, and
+// short chains (more, smaller blocks) keep the latency down.
 constexpr size_t kByteUnit = 256;    // byte-arena granularity
 constexpr int kMinTableOrder = 10;   // smallest table: 1024 slots
 
@@ -169,9 +169,10 @@ struct fr_server {
         const fr_request &q = r.req;
         r.annealed = (q.sigma_start != q.sigma_end && opt.iters > 1) ? 1 : 0;
         r.ntab = r.annealed ? 3 : 1;
-        r.cap = table_slots(q.N, r.safe);
-        r.gs = div_up(q.M, (long long)kBlock * kServePointsPerThread);
-        r.gp = div_up(q.N, (long long)kBlock * kServePointsPerThread);
+        const fr_tune_params &tp = ctx->tune[tune_class(q.N)];
+        r.cap = r.safe ? table_slots(q.N, true) : tuned_table_slots(q.N, tp.table_slots_x2);
+        r.gs = div_up(q.M, (long long)kBlock * tp.serve_points_per_thread);
+        r.gp = div_up(q.N, (long long)kBlock * tp.serve_points_per_thread);
         r.gb = r.annealed ? r.gp : 0;
         r.gc = r.annealed ? std::max(1, div_up(q.N, 4096)) : 0;
         r.gf = std::max(1, div_up(q.N, 4096));

@@ -1,0 +1,150 @@
+"""Launch-shape tuning of the batched path and the server (a systems layer;
+the paper has no counterpart): the tuning table's round trips, results that
+do not depend on the launch shape (within float32 summation order), CUDA-graph
+replay on new data, the page-locked host gather, and the autotuner."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1811_10136_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SAME_ROT, SAME_TRANS = 1e-4, 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1811_10136_gb300 as fr
+    return fr.Context(0)
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def pose_diff(A, B):
+    return math.radians(synth.rotation_angle_deg(A, B)), float(np.linalg.norm(A[:3, 3] - B[:3, 3]))
+
+
+def rounding_bar(ctx, X, Y, Yn, opts):
+    """(T alone, rotation bar, translation bar): 10x the difference between
+    two float32 runs alone (plain and Kahan-compensated sums) -- the view's
+    sensitivity to summation order -- at least 1e-4 rad / 1e-5, at most the
+    method's 1e-3 rad / 1e-4."""
+    Ta, _ = ctx.register_rigid(X, Y, Yn, **opts)
+    Tk, _ = ctx.register_rigid(X, Y, Yn, kahan=1, **opts)
+    kr, kt = pose_diff(Ta, Tk)
+    return Ta, min(1e-3, max(SAME_ROT, 10 * kr)), min(1e-4, max(SAME_TRANS, 10 * kt))
+
+
+def views():
+    return [synth.depth_frame_pair(seed, W=w, H=h) for w, h, seed in
+            [(96, 72, 105), (160, 120, 103), (64, 48, 109), (200, 150, 105)]]
+
+
+def test_tune_table_round_trip(tmp_path):
+    import paper_1811_10136_gb300 as fr
+    c = fr.Context(0, tune_table=None)
+    assert c.tune_get(1000) == {"step_points_per_thread": 8, "build_points_per_thread": 8,
+                                "table_slots_x2": 6, "serve_points_per_thread": 2}
+    c.tune_set(70000, step_points_per_thread=4, table_slots_x2=3)
+    assert c.tune_get(65537)["step_points_per_thread"] == 4      # same class (65,537 .. 262,144)
+    assert c.tune_get(65536)["step_points_per_thread"] == 8      # the class below is unchanged
+    path = str(tmp_path / "tune.txt")
+    c.tune_save(path)
+    d = fr.Context(0, tune_table=None)
+    d.tune_load(path)
+    for n in (1000, 10000, 50000, 100000, 500000):
+        assert d.tune_get(n) == c.tune_get(n)
+    with pytest.raises(fr.FilterRegError):
+        c.tune_set(1000, step_points_per_thread=0)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("0 8 8 6\n")
+    with pytest.raises(fr.FilterRegError):
+        d.tune_load(str(bad))
+    assert d.tune_get(100000) == c.tune_get(100000)              # unchanged by the failed load
+
+
+@pytest.mark.parametrize("shape", [(2, 4, 3), (16, 16, 6), (1, 2, 12)])
+def test_results_do_not_depend_on_launch_shape(shape):
+    import paper_1811_10136_gb300 as fr
+    c = fr.Context(0)
+    pairs = views()
+    dp = [(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs]
+    opts = dict(residual=1, iters=10, sigma_start=0.04, sigma_end=0.012, w=0.1)
+    ref = c.register_rigid_batch(dp, **opts)
+    sp, bp, x2 = shape
+    for n in (5000, 30000):
+        c.tune_set(n, step_points_per_thread=sp, build_points_per_thread=bp, table_slots_x2=x2)
+    out = c.register_rigid_batch(dp, **opts)
+    for (T, rep, st), (Tr, rr, sr) in zip(out, ref):
+        assert st == 0 and sr == 0
+        dr, dt = pose_diff(T, Tr)
+        assert dr < SAME_ROT and dt < SAME_TRANS, (shape, dr, dt)
+        assert rep.lattice_vertices == rr.lattice_vertices
+
+
+def test_graph_replay_on_new_data(ctx):
+    # Two batches of one launch shape (sizes within the same block counts,
+    # other clouds and poses): the second call replays the first's graph with
+    # new descriptors and must give each item its own single-registration
+    # result.
+    a = [synth.depth_frame_pair(400 + i, W=96, H=72) for i in range(3)]
+    b = [synth.depth_frame_pair(500 + i, W=96, H=72) for i in range(3)]
+    opts = dict(residual=1, iters=8, sigma_start=0.04, sigma_end=0.015, w=0.1)
+    for pairs in (a, b, a):
+        dp = [(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs]
+        launches0 = ctx.kernel_launches
+        out = ctx.register_rigid_batch(dp, **opts)
+        assert ctx.kernel_launches - launches0 == opts["iters"] + 2
+        for (X, Y, Yn), (T, rep, st) in zip(dp, out):
+            Ts, br, bt = rounding_bar(ctx, X, Y, Yn, opts)
+            dr, dt = pose_diff(T, Ts)
+            assert st == 0 and dr < br and dt < bt, (dr, dt, br, bt)
+
+
+def test_pinned_host_gather_equals_device(ctx):
+    import torch
+    pairs = views()
+    dp = [(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs]
+    pinned = [tuple(torch.from_numpy(a).pin_memory() for a in (p.X, p.Y, p.Yn)) for p in pairs]
+    hp = [tuple(t.numpy() for t in trip) for trip in pinned]
+    opts = dict(residual=1, iters=6, sigma_start=0.04, sigma_end=0.02)
+    a = ctx.register_rigid_batch(dp, **opts)
+    h0 = ctx.transfer_bytes()[0]
+    b = ctx.register_rigid_batch(hp, host=True, **opts)
+    moved = ctx.transfer_bytes()[0] - h0
+    assert moved >= sum(16 * (p.X.shape[0] + 2 * p.Y.shape[0]) for p in pairs)
+    for (Ta, ra, _), (Tb, rb, _) in zip(a, b):
+        dr, dt = pose_diff(Ta, Tb)
+        assert dr < SAME_ROT and dt < SAME_TRANS
+        assert ra.last_inliers == rb.last_inliers
+
+
+def test_autotune_installs_a_valid_shape():
+    import paper_1811_10136_gb300 as fr
+    c = fr.Context(0)
+    pairs = [synth.depth_frame_pair(600 + i, W=96, H=72) for i in range(3)]
+    dp = [(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs]
+    opts = dict(residual=1, iters=4, sigma_start=0.04, sigma_end=0.02, w=0.1)
+    best, b_ms, d_ms = c.autotune_batch(dp, objective=fr.FR_TUNE_THROUGHPUT, reps=1, **opts)
+    assert 0 < b_ms <= d_ms
+    assert c.tune_get(pairs[0].Y.shape[0]) == best
+    lat, l_ms, ld_ms = c.autotune_batch(dp, objective=fr.FR_TUNE_LATENCY, reps=1, **opts)
+    assert lat["serve_points_per_thread"] in (1, 2, 4, 8) and 0 < l_ms <= ld_ms
+    out = c.register_rigid_batch(dp, **opts)
+    for (X, Y, Yn), (T, rep, st) in zip(dp, out):
+        Ts, br, bt = rounding_bar(c, X, Y, Yn, opts)
+        dr, dt = pose_diff(T, Ts)
+        assert st == 0 and dr < br and dt < bt, (dr, dt, br, bt)
+
+
+def test_shipped_table_loads():
+    import paper_1811_10136_gb300 as fr
+    c = fr.Context(0)                      # the table beside the library
+    d = fr.Context(0, tune_table=None)     # built-in defaults
+    assert c.tune_get(2000)["serve_points_per_thread"] == 1
+    assert d.tune_get(2000)["serve_points_per_thread"] == 2
