@@ -168,10 +168,12 @@ def tune_serving(ctx, pool, dpool):
     return out
 
 
-def run_serving(ctx, args, pool, dpool, arrivals, which, sigmas, plain=True):
+def run_serving(ctx, args, pool, dpool, arrivals, which, sigmas, plain=True, storage=0):
     """Open-loop stream through fr_server (continuous batching) and, on the
     same arrivals, through the plain path (fr_register_rigid, one request at
-    a time, first come first served).  Latency = completion - arrival."""
+    a time, first come first served).  Latency = completion - arrival.
+    storage != FR_FP32: the server keeps 16-bit lattice records, and the
+    largest pose difference from a float32 server run is reported."""
     import numpy as np
     import paper_1811_10136_gb300 as fr
     n = len(arrivals)
@@ -188,7 +190,7 @@ def run_serving(ctx, args, pool, dpool, arrivals, which, sigmas, plain=True):
     out = {"workload": "poisson_stream_1k_300k_points", "requests": n, "arrival_rate_per_s": SERVE_RATE,
            "pool_frames": len(pool), "em_iters": ITERS, "sigma": "one of 0.01/0.02/0.04 per request, fixed",
            "sizes_mean_points": int(np.mean([pool[k].Y.shape[0] for k in which]))}
-    with fr.Server(ctx, budget_bytes=SERVE_BUDGET, max_live=1024, **opts) as srv:
+    with fr.Server(ctx, budget_bytes=SERVE_BUDGET, max_live=1024, storage=storage, **opts) as srv:
         # warm-up: one of each pool frame
         for t in [srv.submit(*dpool[i], sigma_start=0.02, w=W_OUT) for i in range(len(pool))]:
             srv.wait(t)
@@ -204,6 +206,7 @@ def run_serving(ctx, args, pool, dpool, arrivals, which, sigmas, plain=True):
         lat = [(r.complete_ns - (t0 + int(a * 1e9))) * 1e-6 for r, a in zip(res, arrivals)]
         span = (max(r.complete_ns for r in res) - t0) * 1e-9
         p50, p99 = percentiles(lat)
+        out["_T"] = [r.T for r in res]
         out.update({"regs_per_s": round(n / span, 1), "latency_ms_p50": round(p50, 3),
                     "latency_ms_p99": round(p99, 3),
                     "ticks": st1["ticks"] - st0["ticks"], "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
@@ -531,6 +534,11 @@ def run_ours(args):
         nopts = dict(lam=NG_LAMBDA, pcg_iters=NG_PCG, residual=fr.FR_PT2PL, iters=NG_ITERS,
                      sigma_start=NG_SIGMA, sigma_end=NG_SIGMA, w=W_OUT)
         nrun = lambda: ng.register(nY, nYn, **nopts)
+        # bfloat16 lattice records (float32 accumulation), the same registration
+        nrun16 = lambda: ng.register(nY, nYn, storage=fr.FR_BF16, **nopts)
+        for _ in range(max(1, args.warmup)):
+            nrun16()
+        ms16, (Tn16, _) = timed_steps(nrun16, args.steps)
         for _ in range(max(1, args.warmup)):
             nrun()
         ms, (Tn, rn) = timed_steps(nrun, args.steps)
@@ -540,8 +548,10 @@ def run_ours(args):
         nprof = ctx.profile(reset=True)
         ctx.set_profiling(False)
         Xw = ng.warp(Tn).cpu().numpy()[:, :3]
+        Xw16 = ng.warp(Tn16).cpu().numpy()[:, :3]
         en0 = float(np.abs(np.sum((npair.Xref[:, :3] - npair.X_true) * npair.Xn_true, 1)).mean())
         en = float(np.abs(np.sum((Xw - npair.X_true) * npair.Xn_true, 1)).mean())
+        en16 = float(np.abs(np.sum((Xw16 - npair.X_true) * npair.Xn_true, 1)).mean())
         per = lambda k: round(nprof[k][1] / max(1, nprof[k][0]), 4)
         nodegraph = {"workload": "height_field_640x480_nodegraph", "M": int(npair.Xref.shape[0]),
                      "N": int(npair.Y.shape[0]), "K": int(npair.node_pos.shape[0]),
@@ -551,7 +561,11 @@ def run_ours(args):
                      "ms_per_registration": round(statistics.mean(ms), 4),
                      "e_step_assembly_ms_per_iter": per("ng_assemble"),
                      "pcg_update_ms_per_iter": per("ng_solve"), "build_ms": per("build"),
-                     "normal_err_mm": {"before": round(en0 * 1e3, 4), "after": round(en * 1e3, 4)}}
+                     "normal_err_mm": {"before": round(en0 * 1e3, 4), "after": round(en * 1e3, 4)},
+                     "bf16": {"value": round(NG_ITERS * args.steps / (sum(ms16) / 1000.0), 1), "unit": UNIT,
+                              "ms_per_registration": round(statistics.mean(ms16), 4),
+                              "normal_err_mm_after": round(en16 * 1e3, 4),
+                              "rms_warp_diff_vs_f32_mm": round(float(np.sqrt(((Xw16 - Xw) ** 2).sum(1).mean())) * 1e3, 5)}}
         ng.close()
 
     # ---- serving: Poisson stream through fr_server vs the plain path ---------
@@ -559,10 +573,17 @@ def run_ours(args):
     if not args.no_serving:
         sp = serving_pool(args)
         serving = run_serving(ctx, args, *sp)          # default launch shapes
+        serving.pop("_T")
         serving["tuning"] = tune_serving(ctx, sp[0], sp[1])
         tuned = run_serving(ctx, args, *sp, plain=False)
         serving["tuned"] = {k: tuned[k] for k in ("regs_per_s", "latency_ms_p50", "latency_ms_p99",
                                                    "saturated_regs_per_s", "failed")}
+        # the batched, served, mixed-precision form: bfloat16 lattice records
+        mixed = run_serving(ctx, args, *sp, plain=False, storage=fr.FR_BF16)
+        serving["tuned_bf16"] = {k: mixed[k] for k in ("regs_per_s", "latency_ms_p50", "latency_ms_p99",
+                                                        "saturated_regs_per_s", "failed")}
+        serving["tuned_bf16"]["max_rot_diff_deg_vs_f32_server"] = round(
+            max(synth_rot(a, b) for a, b in zip(mixed["_T"], tuned["_T"])), 6)
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None

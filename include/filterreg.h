@@ -77,8 +77,7 @@ typedef struct {
     int32_t storage;            /* lattice values read by the slice: FR_FP32, or
                                    FR_BF16 / FR_FP16 16-byte records made from the
                                    float32 sums (see fr_estep_storage); the 16-bit
-                                   modes take neither blur nor kahan
-                                   (FR_ENOTSUPPORTED)                              [FP32]*/
+                                   modes take no blur (FR_ENOTSUPPORTED)          [FP32]*/
     int32_t kahan;              /* 1 = Kahan-compensated float partial sums       [0]   */
     int32_t renormalize_normals;/* pt2pl: unit-normalise N_x of Eq. 9             [0]   */
     float stop_twist;           /* stop once |delta zeta| < stop_twist (Section 6.1's
@@ -413,8 +412,10 @@ FR_API fr_status fr_nodegraph_destroy(fr_nodegraph *g);
 /* opt->iters EM iterations (sigma schedule as fr_register_rigid; the lattice
  * is rebuilt when sigma changes) of the node-graph model against d_Y (N x 4)
  * (+ normals d_Yn for FR_PT2PL).  node_T (host, K x 16 row-major) carries
- * the initial poses in and the result out.  storage must be FR_FP32 and
- * blur, kahan and stop_twist 0 (FR_ENOTSUPPORTED otherwise); lambda >= 0;
+ * the initial poses in and the result out.  storage may be FR_FP32 or a
+ * 16-bit mode (records converted after each build, read by the point
+ * kernel); blur, kahan and stop_twist must be 0 (FR_ENOTSUPPORTED
+ * otherwise); lambda >= 0;
  * 0 <= pcg_iters <= 10000.  rep (nullable): last iteration's inliers,
  * weight sum, cost (data + regulariser) and update norm. */
 FR_API fr_status fr_register_nodegraph(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_Yn,
@@ -449,8 +450,10 @@ FR_API fr_status fr_nodegraph_warp(fr_ctx *ctx, fr_nodegraph *g, const double *n
  *
  * The server has its own CUDA stream and thread; the context must outlive
  * it and may be used for other calls meanwhile.  Options (residual, iters,
- * kahan, renormalize_normals) are fixed per server; storage must be FR_FP32
- * and blur 0 (FR_ENOTSUPPORTED otherwise); stop_twist is honoured. */
+ * kahan, renormalize_normals, storage) are fixed per server; with 16-bit
+ * storage a build's records are converted in the tick after it (one more
+ * tick per request); blur must be 0 (FR_ENOTSUPPORTED otherwise);
+ * stop_twist is honoured. */
 typedef struct fr_server fr_server;
 
 /* One request.  Clouds are N x 4 / M x 4 float rows (16-byte aligned).

@@ -364,8 +364,8 @@ fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
     if (!(o->w >= 0.0f && o->w < 1.0f)) return ctx->fail(FR_EINVAL, "w must lie in [0, 1)");
     if (o->storage != FR_FP32 && o->storage != FR_BF16 && o->storage != FR_FP16)
         return ctx->fail(FR_EINVAL, "storage must be FR_FP32, FR_BF16 or FR_FP16");
-    if (o->storage != FR_FP32 && (o->kahan || o->blur))
-        return ctx->fail(FR_ENOTSUPPORTED, "16-bit lattice storage is implemented without blur and Kahan sums");
+    if (o->storage != FR_FP32 && o->blur)
+        return ctx->fail(FR_ENOTSUPPORTED, "16-bit lattice storage is implemented without blur");
     return FR_OK;
 }
 }  // namespace fr

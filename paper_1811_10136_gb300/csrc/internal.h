@@ -67,13 +67,12 @@ struct DeviceState {
 // 32-byte sectors each --
 //   sector 0: [key (8 B), unused (8 B), v0 = channels 0..3 (float4)]
 //   sector 1: [v1 = channels 4..7 (float4), unused (16 B)]
-// -- so that one 256-bit load of sector 0 returns a key with its weight and
-// value sums (a lookup and its values in one access), an insert's CAS and
-// atomics touch one line, and a clear writes whole sectors.  With 16-bit
-// storage the record [W, sum b (y - p_v), sum b n, 0] (16 B) is written over
-// bytes 8..23 of sector 0 once the build is complete (its float32 sums have
-// been read), so the 16-bit slice reads sector 0 alone.  A free slot is all
-// zero: kEmpty = 0 and every valid key has bit 63 set, so clearing a slot is
+// -- so that a lookup and its values, an insert's CAS and atomics touch one
+// line, and a clear writes whole sectors.  With 16-bit storage the record
+// [W, sum b (y - p_v), sum b n, 0] (16 B) is written over v0 once the build
+// is complete (the convert role has read the float32 sums), so a 16-bit
+// lookup reads one 16-byte record beside its key.  A free slot is all zero:
+// kEmpty = 0 and every valid key has bit 63 set, so clearing a slot is
 // zeroing its record.
 constexpr int kRecWords = 8;  // 64-bit words per record
 constexpr unsigned long long kEmpty = 0ull;
@@ -88,9 +87,9 @@ struct Table {
 __host__ __device__ __forceinline__ unsigned long long *rec_key(unsigned long long *keys, uint32_t s) {
     return keys + (size_t)s * kRecWords;
 }
-// The 16-bit record: bytes 8..23, two 8-byte halves (8-byte aligned).
-__host__ __device__ __forceinline__ uint2 *rec_cv(unsigned long long *keys, uint32_t s) {
-    return reinterpret_cast<uint2 *>(keys + (size_t)s * kRecWords + 1);
+// The 16-bit record (16-bit storage modes, after conversion): v0's place.
+__host__ __device__ __forceinline__ uint4 *rec_cv(unsigned long long *keys, uint32_t s) {
+    return reinterpret_cast<uint4 *>(keys + (size_t)s * kRecWords + 2);
 }
 __host__ __device__ __forceinline__ float4 *rec_v0(unsigned long long *keys, uint32_t s) {
     return reinterpret_cast<float4 *>(keys + (size_t)s * kRecWords + 2);
@@ -293,7 +292,7 @@ void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
 void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s, int storage);
 void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s, int storage);
 void launch_zero_values(Table t, int grid, cudaStream_t s);
-void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t s);
+void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t s, int storage = kStoreF32);
 void launch_ng_edges(const NgEdges &a, cudaStream_t s);
 void launch_ng_pcg_init(const NgPcg &a, cudaStream_t s);
 void launch_ng_pcg_spmv(const NgPcg &a, cudaStream_t s);

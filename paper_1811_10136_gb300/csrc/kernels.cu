@@ -364,11 +364,9 @@ __device__ __forceinline__ uint4 compact_record(float4 a, float4 c, float3 p, fl
                       pack2<ST>(c.x * sc, c.y * sc), pack2<ST>(c.z * sc, 0.0f));
 }
 
-// Writes the 16-bit record over bytes 8..23 of slot s's first sector.
+// Writes the 16-bit record over slot s's float32 v0 (already read).
 __device__ __forceinline__ void store_compact(unsigned long long *keys, uint32_t s, uint4 r) {
-    uint2 *d = rec_cv(keys, s);
-    d[0] = make_uint2(r.x, r.y);
-    d[1] = make_uint2(r.z, r.w);
+    *rec_cv(keys, s) = r;
 }
 
 // Vector float atomic add without a returned value (a reduction at L2).
@@ -585,16 +583,18 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
         }
         return true;
     } else {
-        // One 256-bit load per vertex: the key and its 16-byte record share
-        // sector 0; positions restored in float32.
-        Sector0 sec[kD];
+        // Key probes, then one 16-byte record per vertex (beside its key);
+        // positions restored in float32.
         int slot[kD];
-        find4_sectors(t.keys, t.mask, sx, t.max_probe, sec, slot);
+        find4(t.keys, t.mask, sx, slot, t.max_probe);
+        uint4 r[kD];
+#pragma unroll
+        for (int k = 0; k < kD; ++k) r[k] = slot[k] >= 0 ? __ldg(rec_cv(t.keys, slot[k])) : make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
             if (slot[k] < 0) continue;
             const float b = sx.b[k];
-            const float2 w_rx = unpack2<ST>(sec[k].w[2]), ry_rz = unpack2<ST>(sec[k].w[3]);
+            const float2 w_rx = unpack2<ST>(r[k].x), ry_rz = unpack2<ST>(r[k].y);
             const float3 p = vertex_position(sx.key[k], ip);
             const float bw = b * w_rx.x;
             o.m0 += bw;
@@ -602,7 +602,7 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
             o.m1y += b * ry_rz.x + bw * p.y;
             o.m1z += b * ry_rz.y + bw * p.z;
             if (PT2PL) {
-                const float2 nx_ny = unpack2<ST>(sec[k].w[4]), nz_0 = unpack2<ST>(sec[k].w[5]);
+                const float2 nx_ny = unpack2<ST>(r[k].z), nz_0 = unpack2<ST>(r[k].w);
                 o.nx += b * nx_ny.x;
                 o.ny += b * nx_ny.y;
                 o.nz += b * nz_0.x;
@@ -1590,7 +1590,6 @@ __global__ void k_slice_out(const float4 *__restrict__ Q, int m, float s1, float
 __global__ void k_zero_values(Table t) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t s = gtid(); s <= t.mask; s += grid_stride()) {
-        *rec_cv(t.keys, s) = make_uint2(0, 0);
         *rec_v0(t.keys, s) = z;
         *rec_v1(t.keys, s) = z;
     }
@@ -1685,7 +1684,7 @@ __device__ __forceinline__ void ng_blend(const float (&q)[4][8], const float (&w
 // twists, so d r / d zeta_k = w_k J) through shared memory -- 234 sums, 8
 // per lane -- and adds them to the pair blocks of A and to g.  With
 // warp_only the kernel writes the warped points and stops.
-template <bool PT2PL>
+template <bool PT2PL, int ST>
 __global__ void __launch_bounds__(kBlock) k_ng_points(NgPoints L, int warp_only) {
     constexpr int kWarps = kBlock / 32;
     __shared__ float sh[kWarps][32][33];
@@ -1748,7 +1747,7 @@ __global__ void __launch_bounds__(kBlock) k_ng_points(NgPoints L, int warp_only)
                 L.warp_out[L.perm[i]] = make_float4(x0, x1, x2, 0.0f);
             } else {
                 Sums e;
-                if (slice_point<PT2PL, kStoreF32>(L.tab, x0, x1, x2, ip, e, bad)) {
+                if (slice_point<PT2PL, ST>(L.tab, x0, x1, x2, ip, e, bad)) {
                     float tv[kRigidVals];
 #pragma unroll
                     for (int c = 0; c < kRigidVals; ++c) tv[c] = 0.0f;
@@ -2185,21 +2184,27 @@ __global__ void __launch_bounds__(kBlock) k_ng_update(int K, const double *dx, d
 // Launchers
 // ---------------------------------------------------------------------------
 
-// Instantiated variants: {pt2pt, pt2pl} x (float32 with or without Kahan sums,
-// bfloat16, half); Kahan sums are float32-storage only.
-#define FR_VARIANTS(CALL)                                   \
-    do {                                                    \
-        if (pt2pl) {                                        \
-            if (storage == kStoreBF16) CALL(true, false, 1);      \
-            else if (storage == kStoreF16) CALL(true, false, 2);  \
-            else if (kahan) CALL(true, true, 0);                  \
-            else CALL(true, false, 0);                            \
-        } else {                                            \
-            if (storage == kStoreBF16) CALL(false, false, 1);     \
-            else if (storage == kStoreF16) CALL(false, false, 2); \
-            else if (kahan) CALL(false, true, 0);                 \
-            else CALL(false, false, 0);                           \
-        }                                                   \
+// Instantiated variants: {pt2pt, pt2pl} x {float32, bfloat16, half storage}
+// x {plain, Kahan-compensated float partial sums}.
+#define FR_VARIANTS(CALL)                                           \
+    do {                                                            \
+        if (pt2pl) {                                                \
+            if (storage == kStoreBF16) {                            \
+                if (kahan) CALL(true, true, 1); else CALL(true, false, 1);   \
+            } else if (storage == kStoreF16) {                      \
+                if (kahan) CALL(true, true, 2); else CALL(true, false, 2);   \
+            } else {                                                \
+                if (kahan) CALL(true, true, 0); else CALL(true, false, 0);   \
+            }                                                       \
+        } else {                                                    \
+            if (storage == kStoreBF16) {                            \
+                if (kahan) CALL(false, true, 1); else CALL(false, false, 1); \
+            } else if (storage == kStoreF16) {                      \
+                if (kahan) CALL(false, true, 2); else CALL(false, false, 2); \
+            } else {                                                \
+                if (kahan) CALL(false, true, 0); else CALL(false, false, 0); \
+            }                                                       \
+        }                                                           \
     } while (0)
 
 void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s, int storage) {
@@ -2287,13 +2292,13 @@ void launch_slice_out(const float4 *Q, int m, float s1, float s2, float s3, Tabl
     k_slice_out<<<grid_for(m, 4096), kBlock, 0, s>>>(Q, m, s1, s2, s3, t, vdim, out, flags);
 }
 
-void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t s) {
+void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t s, int storage) {
     if (a.S <= 0) return;
     const int grid = (a.S + kBlock / 32 - 1) / (kBlock / 32);
-    if (pt2pl)
-        k_ng_points<true><<<grid, kBlock, 0, s>>>(a, warp_only);
-    else
-        k_ng_points<false><<<grid, kBlock, 0, s>>>(a, warp_only);
+    const int kahan = 0;
+#define FR_CALL(P, K, S) k_ng_points<P, S><<<grid, kBlock, 0, s>>>(a, warp_only)
+    FR_VARIANTS(FR_CALL);
+#undef FR_CALL
 }
 
 void launch_ng_edges(const NgEdges &a, cudaStream_t s) {

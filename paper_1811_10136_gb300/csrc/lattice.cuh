@@ -190,59 +190,6 @@ __device__ __forceinline__ void find4(const unsigned long long *__restrict__ key
     }
 }
 
-// Sector 0 of slot s (key, bytes 8..15, v0) in one 256-bit read-only load:
-// w[0..1] the key, w[2..3] bytes 8..15, w[4..7] v0.  The table must not
-// change during the kernel (a build in an earlier launch).
-struct Sector0 {
-    unsigned w[8];
-    __device__ __forceinline__ unsigned long long key() const {
-        return (unsigned long long)w[0] | ((unsigned long long)w[1] << 32);
-    }
-};
-__device__ __forceinline__ Sector0 ld_sector0(const unsigned long long *keys, uint32_t s) {
-    Sector0 r;
-    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]), "=r"(r.w[4]), "=r"(r.w[5]), "=r"(r.w[6]),
-          "=r"(r.w[7])
-        : "l"(keys + (size_t)s * kRecWords));
-    return r;
-}
-
-// Sector 0 of each of a simplex's four vertices: the home slots' sectors are
-// requested together (one access per vertex: key and values), collision
-// chains walked one by one (max_probe slots at most) and the sector of a key
-// found beyond its home reloaded.  found[k] is false (and the sector zero)
-// for a vertex absent from the table.
-__device__ __forceinline__ void find4_sectors(const unsigned long long *__restrict__ keys, uint32_t mask,
-                                              const Simplex &sx, uint32_t max_probe, Sector0 sec[kD],
-                                              int slot[kD]) {
-#pragma unroll
-    for (int k = 0; k < kD; ++k) {
-        slot[k] = (int)slot_of(sx.key[k], mask);
-        sec[k] = ld_sector0(keys, (uint32_t)slot[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < kD; ++k) {
-        unsigned long long cur = sec[k].key();
-        if (cur == sx.key[k]) continue;
-        uint32_t s = (uint32_t)slot[k];
-        uint32_t p = 1;
-        while (cur != sx.key[k] && cur != kEmpty && p < max_probe) {
-            s = (s + 1) & mask;
-            cur = __ldg(rec_key(const_cast<unsigned long long *>(keys), s));
-            ++p;
-        }
-        if (cur == sx.key[k]) {
-            slot[k] = (int)s;
-            sec[k] = ld_sector0(keys, s);
-        } else {
-            slot[k] = -1;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) sec[k].w[i] = 0u;
-        }
-    }
-}
-
 // Offsets of the lattice neighbour along axis `dir` in the stored coordinates
 // 0..2: +1 on every coordinate and -D on coordinate `dir` (sum stays 0).
 __device__ __forceinline__ unsigned long long neighbour_key(unsigned long long key, int dir,

@@ -24,7 +24,7 @@ using namespace fr;
 
 namespace {
 struct NgGraph {
-    long long key[9];
+    long long key[10];
     cudaGraphExec_t exec;
     int kernels;
 };
@@ -296,6 +296,7 @@ struct Spans {
 
 struct NgRun {
     int pt2pl = 0, iters = 0, pcg_iters = 0;
+    int storage = FR_FP32;  // lattice values the point kernel reads (16-bit: converted after each build)
     double lambda = 0.0;
     bool solve = true;  // false: assemble A, g once (fr_nodegraph_system)
 };
@@ -307,8 +308,8 @@ fr_status ng_validate(fr_ctx *ctx, const fr_nodegraph *g, const float *d_Y, cons
     FR_TRY(validate_options(ctx, opt));
     FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));
     if (opt->residual == FR_PT2PL) FR_TRY(validate_cloud(ctx, d_Yn, N, "d_Yn"));
-    if (opt->storage != FR_FP32 || opt->blur || opt->kahan || opt->stop_twist > 0.0f)
-        return ctx->fail(FR_ENOTSUPPORTED, "node graphs run float32 storage without blur, Kahan sums or stop_twist");
+    if (opt->blur || opt->kahan || opt->stop_twist > 0.0f)
+        return ctx->fail(FR_ENOTSUPPORTED, "node graphs run without blur, Kahan sums or stop_twist");
     if (!(lambda >= 0.0) || !std::isfinite(lambda)) return ctx->fail(FR_EINVAL, "lambda must be >= 0");
     if (pcg_iters < 0 || pcg_iters > 10000) return ctx->fail(FR_EINVAL, "pcg_iters out of range");
     return FR_OK;
@@ -340,7 +341,7 @@ void ng_assemble(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Table t, int it
     P.stats = g->stats;
     P.inliers = g->inliers;
     P.flags = &ctx->d_state->flags;
-    launch_ng_points(run.pt2pl, P, 0, s);
+    launch_ng_points(run.pt2pl, P, 0, s, run.storage);
     NgEdges Ed{};
     Ed.edges = g->edges;
     Ed.edge_blk = g->edge_blk;
@@ -408,9 +409,23 @@ int ng_issue(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, const Table tab[2],
         b.build_it = it;
         b.gb = blocks_for(ctx, N, 8);
         sp.begin(FR_K_BUILD);
-        launch_em_iter(run.pt2pl, 0, b, s, FR_FP32);
+        launch_em_iter(run.pt2pl, 0, b, s, run.storage);
         sp.end();
         ++launches;
+        if (run.storage != FR_FP32) {  // 16-bit records of the completed build
+            IterLaunch c{};
+            c.job = ctx->d_job;
+            c.ip = ctx->d_ip;
+            c.st = ctx->d_state;
+            c.conv = tab[t];
+            c.conv_list = ctx->lists[t];
+            c.conv_it = it;
+            c.gv = blocks_for(ctx, N, 4);
+            sp.begin(FR_K_CONVERT);
+            launch_em_iter(run.pt2pl, 0, c, s, run.storage);
+            sp.end();
+            ++launches;
+        }
     };
     auto clear = [&](int t, int it) {
         Table tc = tab[t];
@@ -445,11 +460,11 @@ fr_status ng_graph_launch(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, const 
                           int64_t N, uint32_t cap, unsigned long long rebuilds) {
     long long lam_bits;
     std::memcpy(&lam_bits, &run.lambda, sizeof lam_bits);  // lambda is a kernel argument of the graph
-    const long long key[9] = {N, iters, run.pcg_iters, run.pt2pl, (long long)cap, run.solve ? 1 : 0,
-                              (long long)rebuilds, (long long)ctx->ws_gen, lam_bits};
+    const long long key[10] = {N, iters, run.pcg_iters, run.pt2pl, (long long)cap, run.solve ? 1 : 0,
+                               (long long)rebuilds, (long long)ctx->ws_gen, lam_bits, run.storage};
     NgGraph *hit = nullptr;
     for (auto &e : g->graphs)
-        if (std::equal(key, key + 9, e.key)) hit = &e;
+        if (std::equal(key, key + 10, e.key)) hit = &e;
     if (!hit) {
         cudaStream_t cs;
         FR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -472,7 +487,7 @@ fr_status ng_graph_launch(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, const 
             g->graphs.erase(g->graphs.begin());
         }
         NgGraph ng{};
-        std::copy(key, key + 9, ng.key);
+        std::copy(key, key + 10, ng.key);
         ng.exec = exec;
         ng.kernels = kernels;
         g->graphs.push_back(ng);
@@ -589,6 +604,7 @@ FR_API fr_status fr_register_nodegraph(fr_ctx *ctx, fr_nodegraph *g, const float
     cudaSetDevice(ctx->device);
     NgRun run;
     run.pt2pl = opt->residual == FR_PT2PL;
+    run.storage = opt->storage;
     run.iters = opt->iters;
     run.pcg_iters = pcg_iters;
     run.lambda = lambda;
@@ -609,6 +625,7 @@ FR_API fr_status fr_nodegraph_system(fr_ctx *ctx, fr_nodegraph *g, const float *
     cudaSetDevice(ctx->device);
     NgRun run;
     run.pt2pl = opt->residual == FR_PT2PL;
+    run.storage = opt->storage;
     run.lambda = lambda;
     run.solve = false;
     std::vector<double> T(node_T, node_T + 16 * (size_t)g->K);

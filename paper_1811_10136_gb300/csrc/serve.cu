@@ -1,10 +1,13 @@
 // Serving: continuous batching of independent rigid registrations.
 //
 // A worker thread launches one k_em_multi per tick over every live request,
-// each at its own stage: stage 0 builds its first lattice; stage 1 + k runs
-// EM iteration k (step k, build k+1 and clear k-1 when sigma is annealed,
-// Section 3.2); the stage after the last iteration clears its remaining
-// tables.  The result is read back after the tick of the last iteration and
+// each at its own stage.  With float32 storage (lead L = 1): stage 0 builds
+// its first lattice; stage 1 + k runs EM iteration k (step k, build k+1 and
+// clear k-1 when sigma is annealed, Section 3.2).  With 16-bit storage
+// (L = 2) a build's records are converted in the tick after it: stages 0 and
+// 1 build 0 and 1 (and convert 0), stage 2 + k runs step k, converts k+1,
+// builds k+2 and clears k-1.  The stage after the last iteration clears the
+// remaining table.  The result is read back after the tick of the last iteration and
 // the memory is reclaimed after the clearing tick.  Requests are admitted
 // between ticks, first come first served, when their tables and records fit
 // the server's arenas:
@@ -95,9 +98,9 @@ struct Request {
     bool safe = false;       // table sized so that it cannot overflow (after an overflow)
     int annealed = 0, ntab = 1;
     uint32_t cap = 0;
-    int gs = 0, gp = 0, gb = 0, gc = 0, gf = 0;
+    int gs = 0, gp = 0, gb = 0, gc = 0, gf = 0, gv = 0;
     int slot = -1, stage = 0;
-    size_t tab_off[3] = {0, 0, 0};
+    size_t tab_off[kMaxTables] = {0, 0, 0, 0};
     size_t byte_off = 0;
     int byte_order = -1;
     size_t byte_need = 0;
@@ -126,6 +129,7 @@ struct fr_server {
     fr_ctx *ctx = nullptr;
     fr_options opt{};
     int pt2pl = 0, kahan = 0, iters1 = 1;
+    int lead = 1;  // builds run this many ticks ahead of their step (2 with 16-bit storage)
     int max_live = 0;
     cudaStream_t stream = nullptr;
 
@@ -168,7 +172,7 @@ struct fr_server {
     void plan(Request &r) const {
         const fr_request &q = r.req;
         r.annealed = (q.sigma_start != q.sigma_end && opt.iters > 1) ? 1 : 0;
-        r.ntab = r.annealed ? 3 : 1;
+        r.ntab = r.annealed ? lead + 2 : 1;
         const fr_tune_params &tp = ctx->tune[tune_class(q.N)];
         r.cap = r.safe ? table_slots(q.N, true) : tuned_table_slots(q.N, tp.table_slots_x2);
         r.gs = div_up(q.M, (long long)kBlock * tp.serve_points_per_thread);
@@ -176,6 +180,7 @@ struct fr_server {
         r.gb = r.annealed ? r.gp : 0;
         r.gc = r.annealed ? std::max(1, div_up(q.N, 4096)) : 0;
         r.gf = std::max(1, div_up(q.N, 4096));
+        r.gv = lead == 2 ? std::max(1, div_up(q.N, 2048)) : 0;
         size_t off = 0;
         r.o_job = off; off = align256(off + sizeof(RigidJob));
         r.o_state = off; off = align256(off + sizeof(DeviceState));
@@ -279,7 +284,7 @@ struct fr_server {
     }
 
     // ---- one tick (lock held) ------------------------------------------------
-    int tab_of(const Request &r, int build) const { return r.annealed ? build % 3 : 0; }
+    int tab_of(const Request &r, int build) const { return r.annealed ? build % r.ntab : 0; }
 
     fr_status launch_tick() {
         std::vector<Seg> segs;
@@ -294,12 +299,16 @@ struct fr_server {
         const int last_it = opt.iters - 1;
         for (Request *rp : live) {
             Request &r = *rp;
-            if (r.stage == 0) {
-                add(r, kRoleBuild, 0, 0, r.gp);
-            } else if (r.stage <= opt.iters) {
-                const int k = r.stage - 1;
+            if (r.stage < lead) {
+                // prologue: build j (fixed sigma builds only 0), convert j - 1
+                const int j = r.stage;
+                if (j == 0 || (r.annealed && j < opt.iters)) add(r, kRoleBuild, j, tab_of(r, j), r.gp);
+                if (j >= 1) add(r, kRoleConvert, j - 1, tab_of(r, j - 1), r.gv);
+            } else if (r.stage < lead + opt.iters) {
+                const int k = r.stage - lead;
                 add(r, kRoleStep, k, tab_of(r, k), r.gs);
-                if (r.annealed && k + 1 < opt.iters) add(r, kRoleBuild, k + 1, tab_of(r, k + 1), r.gb);
+                if (r.annealed && k + lead < opt.iters) add(r, kRoleBuild, k + lead, tab_of(r, k + lead), r.gb);
+                if (r.annealed && lead == 2 && k + 1 < opt.iters) add(r, kRoleConvert, k + 1, tab_of(r, k + 1), r.gv);
                 if (r.annealed && k >= 1) add(r, kRoleClear, k - 1, tab_of(r, k - 1), r.gc);
                 if (k == last_it) tk.results.push_back(rp);
             } else {
@@ -343,7 +352,7 @@ struct fr_server {
             for (int q = 0; q < segs[si].nblk; ++q) map[segs[si].blk0 + q] = (unsigned short)si;
         cudaMemcpyAsync(d_segs, H, segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, stream);
         cudaMemcpyAsync(d_map, map, (size_t)grid * sizeof(unsigned short), cudaMemcpyHostToDevice, stream);
-        launch_em_multi(pt2pl, kahan, d_slots, d_segs, d_map, grid, 1, stream, FR_FP32);
+        launch_em_multi(pt2pl, kahan, d_slots, d_segs, d_map, grid, 1, stream, opt.storage);
         launches.fetch_add(1);
         for (Request *rp : tk.results) {
             unsigned char *D = bytes + rp->byte_off;
@@ -370,7 +379,7 @@ struct fr_server {
         inflight.push_back(std::move(tk));
         // requests whose tables are being cleared leave the live set now
         live.erase(std::remove_if(live.begin(), live.end(),
-                                  [&](Request *r) { return r->stage > opt.iters + 1; }),
+                                  [&](Request *r) { return r->stage > opt.iters + lead; }),
                    live.end());
         return FR_OK;
     }
@@ -534,8 +543,7 @@ FR_API fr_status fr_server_create(fr_ctx *ctx, size_t budget, int max_live, cons
     if (!ctx || !out) return FR_EINVAL;
     *out = nullptr;
     FR_TRY(validate_options(ctx, opt));
-    if (opt->storage != FR_FP32 || opt->blur)
-        return ctx->fail(FR_ENOTSUPPORTED, "the server runs float32 storage without blur");
+    if (opt->blur) return ctx->fail(FR_ENOTSUPPORTED, "the server runs without blur");
     if (opt->iters < 1) return ctx->fail(FR_EINVAL, "the server needs iters >= 1");
     if (max_live < 1 || max_live > 4096) return ctx->fail(FR_EINVAL, "max_live must be in 1..4096");
     if (budget < ((size_t)1 << 24)) return ctx->fail(FR_EINVAL, "device_mem_budget must be >= 16 MiB");
@@ -546,6 +554,7 @@ FR_API fr_status fr_server_create(fr_ctx *ctx, size_t budget, int max_live, cons
     s->pt2pl = opt->residual == FR_PT2PL;
     s->kahan = opt->kahan ? 1 : 0;
     s->iters1 = opt->iters > 0 ? opt->iters : 1;
+    s->lead = opt->storage != FR_FP32 ? 2 : 1;
     s->max_live = max_live;
     auto bail = [&](fr_status st, const char *what) {
         fr_server_destroy(s);

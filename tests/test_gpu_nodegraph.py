@@ -158,5 +158,5 @@ def test_rejects_bad_models(ctx, small):
     assert e.value.status == fr.FR_EINVAL
     ng = model(ctx, small)
     with pytest.raises(fr.FilterRegError) as e:
-        ng.register(dev(small.Y), None, storage=fr.FR_BF16, iters=2)
+        ng.register(dev(small.Y), None, blur=1, iters=2)
     assert e.value.status == fr.FR_ENOTSUPPORTED

@@ -116,13 +116,12 @@ def test_half_storage_does_not_overflow(ctx, orc):
     assert max(worst.values()) <= 1.0, worst
 
 
-def test_storage_rejects_blur_and_kahan(ctx):
+def test_storage_rejects_blur(ctx):
     import paper_1811_10136_gb300 as fr
     p = synth.sphere_bumps_pair(0)
-    for kw in ({"blur": 1}, {"kahan": 1}):
-        with pytest.raises(fr.FilterRegError) as e:
-            ctx.register_rigid(dev(p.X), dev(p.Y), None, storage=1, iters=2, **kw)
-        assert e.value.status == fr.FR_ENOTSUPPORTED
+    with pytest.raises(fr.FilterRegError) as e:
+        ctx.register_rigid(dev(p.X), dev(p.Y), None, storage=1, iters=2, blur=1)
+    assert e.value.status == fr.FR_ENOTSUPPORTED
     with pytest.raises(fr.FilterRegError) as e:
         ctx.register_rigid(dev(p.X), dev(p.Y), None, storage=7, iters=2)
     assert e.value.status == fr.FR_EINVAL
@@ -157,6 +156,56 @@ def test_registration_within_rounding_bound(ctx, depth_oracle, storage):
     dt = float(np.linalg.norm(Tg[:3, 3] - To[:3, 3]))
     assert dr <= 1e-3 + e / rms_radius(p.X) and dt <= 1e-4 + e, (dr, dt, e)
     assert rg.iters_run == 20 and rg.degenerate_iters == 0
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_kahan_sums_with_16bit_storage(ctx, depth_oracle, storage):
+    # 16-bit lattice records with Kahan-compensated float32 partial sums of
+    # J^T W J: the same bound as plain 16-bit storage (compensation only
+    # shrinks the float32 part of the error).
+    p, To = depth_oracle
+    Tg, rg = ctx.register_rigid(dev(p.X), dev(p.Y), dev(p.Yn), residual=1, iters=20, sigma_start=f32(0.04),
+                                sigma_end=f32(0.01), w=f32(0.1), storage=storage, kahan=1)
+    e = 6 * U[storage] * math.sqrt(1.5) * 0.01
+    dr = math.radians(synth.rotation_angle_deg(Tg, To))
+    dt = float(np.linalg.norm(Tg[:3, 3] - To[:3, 3]))
+    assert dr <= 1e-3 + e / rms_radius(p.X) and dt <= 1e-4 + e, (dr, dt, e)
+    res = ctx.register_rigid_batch([(dev(p.X), dev(p.Y), dev(p.Yn))], residual=1, iters=20, sigma_start=f32(0.04),
+                                   sigma_end=f32(0.01), w=f32(0.1), storage=storage, kahan=1)
+    dr = math.radians(synth.rotation_angle_deg(res[0][0], To))
+    assert res[0][2] == 0 and dr <= 1e-3 + e / rms_radius(p.X)
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_nodegraph_16bit_storage(ctx, storage):
+    # The height-field node graph (configs[3] shape: ~250k points, 1,000
+    # nodes, sigma 2 cm, 10 EM x 20 PCG, lambda 10) with 16-bit lattice
+    # records against the float32 records.  Each target moves by at most
+    # e = 6 u R; the regularised least-squares fit of the node poses to the
+    # targets moves the warped surface by at most e (rms) -- plus the float32
+    # path's own 1e-4 -- and its error along the true normals by at most e.
+    import paper_1811_10136_gb300 as fr
+    p = synth.nodegraph_pair(0)
+    ng = fr.NodeGraph(ctx, dev(p.Xref), torch_int(p.knn), dev(p.skw), p.node_pos, p.edges)
+    sigma = f32(0.02)
+    kw = dict(lam=10.0, pcg_iters=20, residual=1, iters=10, sigma_start=sigma, sigma_end=sigma, w=f32(0.1))
+    T32, r32 = ng.register(dev(p.Y), dev(p.Yn), **kw)
+    T16, r16 = ng.register(dev(p.Y), dev(p.Yn), storage=storage, **kw)
+    X32 = ng.warp(T32).cpu().numpy()[:, :3].astype(np.float64)
+    X16 = ng.warp(T16).cpu().numpy()[:, :3].astype(np.float64)
+    e = 6 * U[storage] * math.sqrt(1.5) * 0.02
+    rms = float(np.sqrt(((X16 - X32) ** 2).sum(1).mean()))
+    assert rms <= 1e-4 + e, (rms, e)
+    en32 = np.abs(np.sum((X32 - p.X_true) * p.Xn_true, 1)).mean()
+    en16 = np.abs(np.sum((X16 - p.X_true) * p.Xn_true, 1)).mean()
+    assert en16 <= en32 + e, (en16, en32, e)
+    assert r16.iters_run == 10 and r16.lattice_vertices == r32.lattice_vertices
+    ng.close()
+
+
+def torch_int(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
 
 
 @pytest.mark.parametrize("storage", [1, 2])

@@ -139,7 +139,7 @@ def test_rejects_bad_requests(ctx, pairs):
             srv.submit(dev(big.X), dev(big.Y), dev(big.Yn), sigma_start=0.04, sigma_end=0.01)
         assert e.value.status == fr.FR_ENOMEM
     with pytest.raises(fr.FilterRegError) as e:
-        fr.Server(ctx, budget_bytes=1 << 24, storage=fr.FR_BF16)
+        fr.Server(ctx, budget_bytes=1 << 24, blur=1)
     assert e.value.status == fr.FR_ENOTSUPPORTED
 
 
@@ -220,3 +220,37 @@ def test_stream_configuration_requests_equal_alone(ctx):
     # the sparse request overflowed its compact table (more vertices than
     # 3 N slots hold) and was rerun at the safe size
     assert results[-1].report.lattice_vertices > 1.5 * 20000
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_16bit_storage_requests_equal_single_registrations(ctx, pairs, storage):
+    # bfloat16 / half lattice records in the server (a build's records are
+    # converted in the tick after it): each request equals the single path
+    # with the same storage, within the batched path's bar plus one 16-bit
+    # ulp flip of the targets (float32 sums in another order may round a
+    # record to the other neighbour): e = 6 u R moves the pose by at most e
+    # (translation) and e / r (rotation, r the model's rms radius).
+    import paper_1811_10136_gb300 as fr
+    U = {1: 2.0 ** -8, 2: 2.0 ** -11}
+    iters = 12
+    with fr.Server(ctx, budget_bytes=1 << 30, max_live=64, residual=fr.FR_PT2PL, iters=iters,
+                   storage=storage) as srv:
+        reqs = []
+        for r in range(2):
+            for i, p in enumerate(pairs):
+                s0, s1 = SIGMAS[(i + r) % len(SIGMAS)]
+                reqs.append((i, s0, s1, srv.submit(dev(p.X), dev(p.Y), dev(p.Yn), sigma_start=s0, sigma_end=s1,
+                                                   w=0.1)))
+        results = [(i, s0, s1, srv.wait(t, 60_000)) for i, s0, s1, t in reqs]
+    for i, s0, s1, res in results:
+        assert res.status == 0
+        p = pairs[i]
+        Ts, rs = ctx.register_rigid(dev(p.X), dev(p.Y), dev(p.Yn), residual=1, iters=iters, sigma_start=s0,
+                                    sigma_end=s1, w=0.1, storage=storage)
+        P = p.X[:, :3].astype(np.float64)
+        rr = float(np.sqrt(((P - P.mean(0)) ** 2).sum(1).mean()))
+        e = 6 * U[storage] * math.sqrt(1.5) * min(s0, s1)
+        dr, dt = pose_diff(res.T, Ts)
+        assert dr <= SAME_ROT + e / rr and dt <= SAME_TRANS + e, (i, s0, s1, dr, dt)
+        assert res.report.iters_run == rs.iters_run == iters
+        assert res.report.lattice_builds == rs.lattice_builds
