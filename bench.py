@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-articulated", action="store_true", help="skip the articulated line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-nodegraph", action="store_true", help="skip the node-graph line")
+    ap.add_argument("--no-exact", action="store_true", help="skip the exact Gauss-transform line")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct rendered frames behind the stream")
     return ap.parse_args()
@@ -568,6 +569,47 @@ def run_ours(args):
                               "rms_warp_diff_vs_f32_mm": round(float(np.sqrt(((Xw16 - Xw) ** 2).sum(1).mean())) * 1e3, 5)}}
         ng.close()
 
+    # ---- the exact Gauss transform on the GPU (O(N M)) beside the lattice -----
+    exact = None
+    if not args.no_exact:
+        X0, Y0, Yn0 = dpairs[0]
+        p0 = pairs[0]
+        sig = float(SIGMA1)
+
+        def ev_time(fn, reps=5):
+            fn()
+            ts = []
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            return statistics.median(ts)
+
+        ex_ms = ev_time(lambda: ctx.gauss_transform(X0, Y0, Yn0, sigma=sig, T=p0.T_gt))
+        la_ms = ev_time(lambda: ctx.estep(X0, Y0, Yn0, sigma=sig, T=p0.T_gt))
+        ex = ctx.gauss_transform(X0, Y0, Yn0, sigma=sig, T=p0.T_gt).double().cpu().numpy()
+        la = ctx.estep(X0, Y0, Yn0, sigma=sig, T=p0.T_gt).double().cpu().numpy()
+        live = ex[:, 0] > 1e-3 * ex[:, 0].max()
+        terr = np.linalg.norm(la[live, 1:4] / la[live, :1] - ex[live, 1:4] / ex[live, :1], axis=1) / sig
+        npairs = float(p0.X.shape[0]) * float(p0.Y.shape[0])
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sms * 128 * 2.07e9 / 15.0   # FP32 lanes x max SM clock / FP32 operations per pair
+        achieved = npairs / (ex_ms * 1e-3)
+        exact = {"workload": f"one 320x240 pair, {p0.X.shape[0]} x {p0.Y.shape[0]} points, pt2pl, sigma {SIGMA1}",
+                 "ms_per_estep": round(ex_ms, 4), "pairs_per_s": round(achieved, 1),
+                 "lattice_estep_ms": round(la_ms, 4),
+                 "lattice_target_err_over_sigma": {"median": round(float(np.median(terr)), 5),
+                                                   "p99": round(float(np.percentile(terr, 99)), 5)},
+                 "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
+                              "unit": "pairs/s", "frac": round(achieved / peak, 4),
+                              "peak_source": f"{sms} SMs x 128 FP32 lanes x 2.07 GHz / 15 FP32 operations "
+                                             "per pair (3 differences, squared distance 3, exponent scale 1, "
+                                             "sums 7, exp2 argument 1)"}}
+
     # ---- serving: Poisson stream through fr_server vs the plain path ---------
     serving = None
     if not args.no_serving:
@@ -634,6 +676,7 @@ def run_ours(args):
             "articulated": articulated,
             "serving": serving,
             "nodegraph": nodegraph,
+            "exact": exact,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

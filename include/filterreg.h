@@ -208,6 +208,17 @@ FR_API fr_status fr_lattice_destroy(fr_ctx *ctx, fr_lattice *lat);
 FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                           const float *d_Yn, int64_t N, float sigma, int blur,
                           const double T[16], float *d_out);
+/* fr_gauss_transform: the exact E step (Section 4.1's Gauss transform, the
+ * sums the lattice approximates): at x_i = T x_i (T host double[16], NULL =
+ * identity) M0_i = sum_j K_ij, M1_i = sum_j K_ij y_j and, with d_Yn, the
+ * normal sums of Eq. 9, K_ij = exp(-|x_i - y_j|^2 / (2 sigma^2)) unnormalised
+ * (Eq. 11), over every observation -- O(N M) float32 work (each thread sums
+ * 256-observation tiles before adding them to its totals).  d_out (float,
+ * M x 4 or M x 7, as fr_estep) is overwritten.  FR_EINVAL for invalid
+ * clouds, sigma <= 0 or a non-finite pose.  Synchronises the stream. */
+FR_API fr_status fr_gauss_transform(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                    const float *d_Yn, int64_t N, float sigma, const double T[16],
+                                    float *d_out);
 /* fr_estep_storage: fr_estep without blur, with the lattice values read by
  * the slice stored as `storage` (fr_storage).  FR_FP32 is fr_estep itself;
  * FR_BF16 / FR_FP16 keep the splat's float32 sums and, once the build is

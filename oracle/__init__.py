@@ -87,13 +87,15 @@ class _Options(ctypes.Structure):
     _fields_ = [("backend", ctypes.c_int), ("residual", ctypes.c_int), ("blur", ctypes.c_int),
                 ("iters", ctypes.c_int), ("sigma_start", ctypes.c_double),
                 ("sigma_end", ctypes.c_double), ("w", ctypes.c_double),
-                ("renormalize_normals", ctypes.c_int), ("stop_twist", ctypes.c_double)]
+                ("renormalize_normals", ctypes.c_int), ("stop_twist", ctypes.c_double),
+                ("update_sigma", ctypes.c_int)]
 
 
 class _Report(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_int), ("degenerate_iters", ctypes.c_int),
                 ("last_inliers", ctypes.c_int64), ("last_sum_w", ctypes.c_double),
-                ("last_cost", ctypes.c_double), ("last_twist_norm", ctypes.c_double)]
+                ("last_cost", ctypes.c_double), ("last_twist_norm", ctypes.c_double),
+                ("sigma_next", ctypes.c_double), ("last_sigma", ctypes.c_double)]
 
 
 def _declare(L):
@@ -318,24 +320,28 @@ class Report:
     last_sum_w: float
     last_cost: float
     last_twist_norm: float
+    sigma_next: float = 0.0   # update_sigma: the next iteration's sigma before the floor
+    last_sigma: float = 0.0   # sigma of the last iteration run
 
 
 def register_rigid(X, Y, Yn=None, *, sigma=0.02, sigma_end=None, w=0.1, iters=30,
                    residual=PT2PT, backend=LATTICE, blur=False, renormalize_normals=False,
-                   stop_twist=0.0, T0=None):
-    """Rigid EM registration; returns (T (4,4) float64, Report)."""
+                   stop_twist=0.0, T0=None, update_sigma=False):
+    """Rigid EM registration; returns (T (4,4) float64, Report).  With
+    update_sigma, sigma starts at `sigma` and is re-estimated each iteration
+    (floor: sigma_end)."""
     X, Y = _pts(X), _pts(Y)
     Yn = _pts(Yn) if Yn is not None else None
     T = np.ascontiguousarray(np.eye(4) if T0 is None else T0, dtype=np.float64).copy()
     o = _Options(backend, residual, int(blur), int(iters), float(sigma),
                  float(sigma if sigma_end is None else sigma_end), float(w),
-                 int(renormalize_normals), float(stop_twist))
+                 int(renormalize_normals), float(stop_twist), int(bool(update_sigma)))
     rep = _Report()
     st = _L().or_register_rigid(_p(X, _f32p), X.shape[0], _p(Y, _f32p), _p(Yn, _f32p), Y.shape[0],
                                 ctypes.byref(o), _p(T, _f64p), ctypes.byref(rep))
     _check(st, "register_rigid")
     return T, Report(rep.iters_run, rep.degenerate_iters, rep.last_inliers, rep.last_sum_w,
-                     rep.last_cost, rep.last_twist_norm)
+                     rep.last_cost, rep.last_twist_norm, rep.sigma_next, rep.last_sigma)
 
 
 def align_error(X, T, Tgt) -> float:

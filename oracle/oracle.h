@@ -53,6 +53,9 @@ typedef struct {
     double w;                /* outlier ratio, 0 <= w < 1 (Section 3.1) */
     int renormalize_normals; /* pt2pl: 1 = unit-normalise N_x (Eq. 9 as written: 0) */
     double stop_twist;       /* stop once |delta zeta| < stop_twist (0 = never) */
+    int update_sigma;        /* 1 = sigma re-estimated every iteration (Section 3.3's
+                                sigma as a decision variable, point-to-point): sigma_start
+                                starts it, sigma_end is its floor; 0 = the schedule */
 } or_options;
 
 typedef struct {
@@ -62,6 +65,9 @@ typedef struct {
     double last_sum_w;       /* sum of outlier weights in the last iteration */
     double last_cost;        /* sum of squared weighted residuals in the last iteration */
     double last_twist_norm;  /* |delta zeta| of the last applied update */
+    double sigma_next;       /* update_sigma: the sigma the next iteration would use,
+                                before the floor (otherwise 0) */
+    double last_sigma;       /* sigma of the last iteration run */
 } or_report;
 
 /* ---- exact E step (Eq. 6, Eq. 9 numerator), unnormalised kernel ---------- */

@@ -29,6 +29,17 @@
  *   - A model point with M0 <= 0 has no defined target and is skipped.
  *   - One Gauss-Newton step per EM iteration; the lattice is rebuilt only when
  *     sigma changes (Section 3.2: the index is built once for a fixed sigma).
+ *   - sigma as a decision variable (Section 3.3; its closed form is in the
+ *     missing supplement), point-to-point: with the E step's posteriors
+ *     P_ij = K_ij / (M0_i + c), maximising the expected complete-data
+ *     log-likelihood sum_ij P_ij [-|x_i - y_j|^2 / (2 sigma^2) - 3 log sigma]
+ *     over sigma gives
+ *       sigma^2 = sum_i Q_i / (M0_i + c) / (3 sum_i W_i),
+ *       Q_i = sum_j K_ij |x_i - y_j|^2 = M0_i |x_i|^2 - 2 x_i . M1_i + M2_i,
+ *     M2_i = sum_j K_ij |y_j|^2 (one more splat channel, |y|^2), W_i as in
+ *     Eq. 7.  It is taken from the same E step as the Gauss-Newton step (a
+ *     conditional maximisation over sigma at the current pose), floored at
+ *     sigma_end, rounded to float and used from the next iteration on.
  */
 #include "oracle.h"
 
@@ -95,7 +106,7 @@ int or_point_terms(const double x[3], double M0, const double M1[3], const doubl
 /* Points per fixed summation chunk of the Gauss-Newton sums, and the values
  * each chunk carries. */
 #define GN_CHUNK 4096
-#define GN_VALS 45
+#define GN_VALS 46
 
 static void transform_point(const double T[16], const float *p, double x[3])
 {
@@ -148,6 +159,17 @@ static int estep_at(const float *X, int64_t M, const float *Y, const float *Yn, 
             if (vdim == 7)
                 for (int c = 0; c < 3; ++c)
                     out[i * vdim + 4 + c] = ns[c];
+            if (vdim == 5) { /* M2 = sum_k K |y_k|^2 */
+                const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+                double m2 = 0.0;
+                for (int64_t k = 0; k < N; ++k) {
+                    const double d0 = x[0] - Y[4 * k], d1 = x[1] - Y[4 * k + 1], d2 = x[2] - Y[4 * k + 2];
+                    const double yy = (double)Y[4 * k] * Y[4 * k] + (double)Y[4 * k + 1] * Y[4 * k + 1] +
+                                      (double)Y[4 * k + 2] * Y[4 * k + 2];
+                    m2 += exp(-(d0 * d0 + d1 * d1 + d2 * d2) * inv2s2) * yy;
+                }
+                out[i * vdim + 4] = m2;
+            }
         }
     }
     free(xs);
@@ -167,6 +189,9 @@ static double *observation_values(const float *Y, const float *Yn, int64_t N, in
         if (vdim == 7)
             for (int c = 0; c < 3; ++c)
                 V[k * vdim + 4 + c] = Yn[4 * k + c];
+        if (vdim == 5) /* |y|^2, for the sigma update */
+            V[k * vdim + 4] = (double)Y[4 * k] * Y[4 * k] + (double)Y[4 * k + 1] * Y[4 * k + 1] +
+                              (double)Y[4 * k + 2] * Y[4 * k + 2];
     }
     return V;
 }
@@ -205,7 +230,9 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
         return OR_EINVAL;
     if (opt->residual == OR_PT2PL && !Yn)
         return OR_EINVAL;
-    const int vdim = (opt->residual == OR_PT2PL) ? 7 : 4;
+    if (opt->update_sigma && (opt->residual != OR_PT2PT || opt->blur))
+        return OR_EINVAL; /* the sigma update is derived for point-to-point without blur */
+    const int vdim = (opt->residual == OR_PT2PL) ? 7 : (opt->update_sigma ? 5 : 4);
 
     float *sched = (float *)malloc((size_t)(opt->iters ? opt->iters : 1) * sizeof(float));
     double *V = observation_values(Y, Yn, N, vdim);
@@ -219,8 +246,10 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
     or_lattice *lat = NULL;
     float lat_sigma = 0.0f;
     int status = OR_OK;
+    float sig_upd = (float)opt->sigma_start; /* the updated sigma (update_sigma) */
     for (int it = 0; it < opt->iters; ++it) {
-        const float sigf = sched[it];
+        const float sigf = opt->update_sigma ? sig_upd : sched[it];
+        rep->last_sigma = sigf;
         const double sigma = (double)sigf;
         if (opt->backend == OR_LATTICE && (lat == NULL || sigf != lat_sigma)) {
             or_lattice_free(lat);
@@ -264,6 +293,11 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
                     continue;
                 q[44] += 1.0;
                 q[42] += Wt;
+                if (opt->update_sigma) { /* Q_i / (M0_i + c) */
+                    const double xx = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+                    const double xm = x[0] * e[1] + x[1] * e[2] + x[2] * e[3];
+                    q[45] += (e[0] * xx - 2.0 * xm + e[4]) / (e[0] + c_eff);
+                }
                 for (int a = 0; a < rows; ++a) {
                     q[43] += r[a] * r[a];
                     for (int p = 0; p < 6; ++p) {
@@ -274,7 +308,7 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
                 }
             }
         }
-        double A[36] = {0}, b[6] = {0}, sum_w = 0.0, cost = 0.0;
+        double A[36] = {0}, b[6] = {0}, sum_w = 0.0, cost = 0.0, sum_q = 0.0;
         int64_t inliers = 0;
         for (int64_t ch = 0; ch < nchunk; ++ch) {
             const double *q = part + ch * GN_VALS;
@@ -285,8 +319,15 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
             sum_w += q[42];
             cost += q[43];
             inliers += (int64_t)q[44];
+            sum_q += q[45];
         }
         free(part);
+        if (opt->update_sigma && sum_w > 0.0) {
+            const double s2 = sum_q / (3.0 * sum_w);
+            rep->sigma_next = sqrt(s2 > 0.0 ? s2 : 0.0);
+            const double fl = opt->sigma_end;
+            sig_upd = (float)(rep->sigma_next > fl ? rep->sigma_next : fl);
+        }
         rep->iters_run = it + 1;
         rep->last_inliers = inliers;
         rep->last_sum_w = sum_w;

@@ -35,7 +35,7 @@ EXPORTED = [
     "fr_lattice_vertices", "fr_lattice_info", "fr_lattice_destroy", "fr_estep",
     "fr_register_rigid", "fr_register_rigid_host", "fr_ctx_set_profiling", "fr_ctx_profile",
     "fr_ctx_set_workspace_limit", "fr_tune_get", "fr_tune_set", "fr_tune_save", "fr_tune_load",
-    "fr_autotune_batch",
+    "fr_autotune_batch", "fr_gauss_transform",
     "fr_ctx_transfer_bytes", "fr_estep_noalloc", "fr_register_rigid_batch",
     "fr_register_rigid_batch_host", "fr_register_articulated", "fr_estep_storage",
     "fr_server_create", "fr_server_submit", "fr_server_poll", "fr_server_wait", "fr_server_release",
@@ -168,6 +168,7 @@ def load(build_if_missing: bool = True):
     L.fr_register_rigid_host.argtypes = L.fr_register_rigid.argtypes
     L.fr_ctx_set_profiling.argtypes = [_vp, ctypes.c_int]
     L.fr_ctx_set_workspace_limit.argtypes = [_vp, ctypes.c_size_t]
+    L.fr_gauss_transform.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_float, _f64p, _vp]
     L.fr_tune_get.argtypes = [_vp, _i64, ctypes.POINTER(fr_tune_params)]
     L.fr_tune_set.argtypes = [_vp, _i64, ctypes.POINTER(fr_tune_params)]
     L.fr_tune_save.argtypes = [_vp, ctypes.c_char_p]
@@ -486,6 +487,20 @@ class Context:
         for b in range(n):
             T = np.array(items[b].T[:], dtype=np.float64).reshape(4, 4)
             out.append((T, _report(reps[b]), int(items[b].status)))
+        return out
+
+    def gauss_transform(self, X, Y, Yn=None, sigma=0.02, T=None):
+        """Exact E-step sums at T X (every observation, no lattice): (M, 4)
+        [M0, M1] or (M, 7) [M0, M1, Nsum] float32 CUDA tensor."""
+        import torch
+        L = load()
+        vd = 7 if Yn is not None else 4
+        out = torch.empty((X.shape[0], vd), dtype=torch.float32, device=X.device)
+        Tm = _pose(T)
+        st = L.fr_gauss_transform(self._h, _dev_ptr(X, "X"), X.shape[0], _dev_ptr(Y, "Y"),
+                                  _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None, Y.shape[0],
+                                  float(sigma), Tm.ctypes.data_as(_f64p), out.data_ptr())
+        self._check(st, "fr_gauss_transform")
         return out
 
     def estep(self, X, Y, Yn=None, sigma=0.02, blur=False, T=None, storage=FR_FP32):
