@@ -593,7 +593,7 @@ def run_ours(args):
         la_ms = ev_time(lambda: ctx.estep(X0, Y0, Yn0, sigma=sig, T=p0.T_gt))
         ex = ctx.gauss_transform(X0, Y0, Yn0, sigma=sig, T=p0.T_gt).double().cpu().numpy()
         la = ctx.estep(X0, Y0, Yn0, sigma=sig, T=p0.T_gt).double().cpu().numpy()
-        live = ex[:, 0] > 1e-3 * ex[:, 0].max()
+        live = (ex[:, 0] > 1e-3 * ex[:, 0].max()) & (la[:, 0] > 0)
         terr = np.linalg.norm(la[live, 1:4] / la[live, :1] - ex[live, 1:4] / ex[live, :1], axis=1) / sig
         npairs = float(p0.X.shape[0]) * float(p0.Y.shape[0])
         sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -603,7 +603,8 @@ def run_ours(args):
                  "ms_per_estep": round(ex_ms, 4), "pairs_per_s": round(achieved, 1),
                  "lattice_estep_ms": round(la_ms, 4),
                  "lattice_target_err_over_sigma": {"median": round(float(np.median(terr)), 5),
-                                                   "p99": round(float(np.percentile(terr, 99)), 5)},
+                                                   "p99": round(float(np.percentile(terr, 99)), 5),
+                                                   "points": int(live.sum())},
                  "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
                               "unit": "pairs/s", "frac": round(achieved / peak, 4),
                               "peak_source": f"{sms} SMs x 128 FP32 lanes x 2.07 GHz / 15 FP32 operations "

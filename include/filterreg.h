@@ -83,6 +83,14 @@ typedef struct {
     float stop_twist;           /* stop once |delta zeta| < stop_twist (Section 6.1's
                                    termination); 0 = run all iterations           [0]   */
     int32_t use_graph;          /* replay the EM loop as one CUDA graph           [1]   */
+    int32_t update_sigma;       /* 1 = sigma as a decision variable (Section 3.3):
+                                   re-estimated after every E step as
+                                   sigma^2 = sum_i Q_i / (M0_i + c) / (3 sum_i W_i),
+                                   Q_i = sum_j K_ij |x_i - y_j|^2, starting at
+                                   sigma_start and floored at sigma_end; the lattice
+                                   is rebuilt every iteration.  Point-to-point,
+                                   float32 storage, no blur, fr_register_rigid only
+                                   (FR_ENOTSUPPORTED otherwise)                    [0]   */
 } fr_options;
 
 /* Per-call diagnostics (all nullable where passed). */
@@ -97,6 +105,7 @@ typedef struct {
     int64_t lattice_vertices;   /* vertices of the last lattice built */
     int32_t lattice_builds;     /* lattices built during the call (1, or one per sigma) */
     int64_t lattice_vertices_sum; /* vertices summed over those builds */
+    double last_sigma;          /* sigma of the last iteration run */
 } fr_report;
 
 /* Kernel classes of the per-kernel profile. */

@@ -57,7 +57,7 @@ class fr_options(ctypes.Structure):
                 ("sigma_start", ctypes.c_float), ("sigma_end", ctypes.c_float), ("w", ctypes.c_float),
                 ("storage", ctypes.c_int32), ("kahan", ctypes.c_int32),
                 ("renormalize_normals", ctypes.c_int32), ("stop_twist", ctypes.c_float),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("update_sigma", ctypes.c_int32)]
 
 
 class fr_report(ctypes.Structure):
@@ -65,7 +65,7 @@ class fr_report(ctypes.Structure):
                 ("last_inliers", ctypes.c_int64), ("last_sum_w", ctypes.c_double),
                 ("last_cost", ctypes.c_double), ("last_twist_norm", ctypes.c_double),
                 ("lattice_vertices", ctypes.c_int64), ("lattice_builds", ctypes.c_int32),
-                ("lattice_vertices_sum", ctypes.c_int64)]
+                ("lattice_vertices_sum", ctypes.c_int64), ("last_sigma", ctypes.c_double)]
 
 
 class fr_request(ctypes.Structure):
@@ -228,11 +228,13 @@ class Report:
     lattice_vertices: int
     lattice_builds: int
     lattice_vertices_sum: int
+    last_sigma: float = 0.0
 
 
 def _report(r: fr_report) -> Report:
     return Report(r.iters_run, r.degenerate_iters, r.last_inliers, r.last_sum_w, r.last_cost,
-                  r.last_twist_norm, r.lattice_vertices, r.lattice_builds, r.lattice_vertices_sum)
+                  r.last_twist_norm, r.lattice_vertices, r.lattice_builds, r.lattice_vertices_sum,
+                  r.last_sigma)
 
 
 def _dev_ptr(t, name, rows=None, cols=4):

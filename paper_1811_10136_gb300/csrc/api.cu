@@ -163,6 +163,7 @@ constexpr size_t kGraphCache = 64;
 
 struct Plan {
     int iters, residual, blur, kahan, profile, annealed, storage;
+    int sig;  // sigma as a decision variable: step and build launches alternate
     int gs, gv, gb, gc, g_blur, g_final;  // block counts of the roles
 };
 
@@ -226,7 +227,56 @@ void issue_blur(fr_ctx *ctx, Issuer &k, const Plan &p, const Table &t, const int
 //   lead 2: build(0) -> [convert 0 | build 1] -> [step k | convert k+1 | build k+2 | clear k-1] ...
 // A fixed sigma builds (and converts) table 0 only.  Then the tables left
 // are cleared.
+// Sigma as a decision variable: the next sigma is known once a step has
+// finished, so each iteration is two launches on two alternating tables --
+//   build(0) -> [step k | clear the other table (build k-1)] -> [build k+1] ...
+// -> clear the last table.
+int issue_plan_sigma(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
+    Issuer k{ctx, s, p.profile};
+    Table *tab = ctx->tables;
+    IterLaunch base{};
+    base.job = ctx->d_job;
+    base.ip = ctx->d_ip;
+    base.partials = ctx->partials;
+    base.st = ctx->d_state;
+    base.check_done = 1;
+    auto build = [&](int b) {
+        IterLaunch L = base;
+        L.check_done = b > 0;
+        L.build = tab[b & 1];
+        L.build_list = ctx->lists[b & 1];
+        L.build_it = b;
+        L.gb = p.gb + (b == 0 ? p.gs : 0);
+        k(b == 0 ? FR_K_BUILD : FR_K_STEP, [&] { launch_em_iter_sigma(p.kahan, L, s); });
+    };
+    if (p.iters > 0) build(0);
+    for (int it = 0; it < p.iters; ++it) {
+        IterLaunch L = base;
+        L.it = it;
+        L.gs = p.gs;
+        L.step = tab[it & 1];
+        L.sig_next = it + 1 < p.iters;
+        if (it >= 1) {
+            L.clear = tab[(it - 1) & 1];
+            L.clear_list = ctx->lists[(it - 1) & 1];
+            L.clear_it = it - 1;
+            L.gc = p.gc;
+        }
+        k(FR_K_STEP, [&] { launch_em_iter_sigma(p.kahan, L, s); });
+        if (it + 1 < p.iters) build(it + 1);
+    }
+    if (p.iters > 0) {
+        const int last = p.iters - 1;
+        Table t[1] = {tab[last & 1]};
+        int *lists[1] = {ctx->lists[last & 1]};
+        const int *counts[1] = {&ctx->d_ip[last].nvert};
+        k(FR_K_CLEAR, [&] { launch_clear_lists(t, lists, counts, 1, p.g_final, s); });
+    }
+    return k.kernels;
+}
+
 int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
+    if (p.sig) return issue_plan_sigma(ctx, p, s);
     Issuer k{ctx, s, p.profile};
     Table *tab = ctx->tables;
     const int lead = p.storage != FR_FP32 ? 2 : 1;
@@ -292,6 +342,7 @@ int issue_plan(fr_ctx *ctx, const Plan &p, cudaStream_t s) {
 
 // Kernels of a plan (all are profiled).
 int plan_kernels(const Plan &p) {
+    if (p.sig) return p.iters > 0 ? 2 * p.iters + 1 : 0;  // build 0, (step, build) ..., step, clear
     int n = 0;
     const int lead = p.storage != FR_FP32 ? 2 : 1;
     if (p.iters > 0) n += 2 + (p.blur ? 5 : 0) + (lead - 1);  // prologue (+ blur, scratch clear), final clear
@@ -307,7 +358,7 @@ fr_status run_plan(fr_ctx *ctx, const Plan &p, bool use_graph) {
         return ctx->cuda(cudaGetLastError(), "kernel launch");
     }
     GraphKey key{{p.iters, p.residual, p.blur, p.kahan, p.profile, p.annealed, p.gs, p.gb, p.gc,
-                  p.g_blur, p.g_final, (int)ctx->tables[0].mask, p.storage, 0},
+                  p.g_blur, p.g_final, (int)ctx->tables[0].mask, p.storage, p.sig},
                  ctx->ws_gen};
     CachedGraph *hit = nullptr;
     for (auto &g : ctx->graphs)
@@ -366,6 +417,9 @@ fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
         return ctx->fail(FR_EINVAL, "storage must be FR_FP32, FR_BF16 or FR_FP16");
     if (o->storage != FR_FP32 && o->blur)
         return ctx->fail(FR_ENOTSUPPORTED, "16-bit lattice storage is implemented without blur");
+    if (o->update_sigma && (o->residual != FR_PT2PT || o->storage != FR_FP32 || o->blur))
+        return ctx->fail(FR_ENOTSUPPORTED, "the sigma update is point-to-point, float32 storage, no blur");
+    if (o->update_sigma != 0 && o->update_sigma != 1) return ctx->fail(FR_EINVAL, "update_sigma must be 0 or 1");
     return FR_OK;
 }
 }  // namespace fr
@@ -479,6 +533,7 @@ FR_API void fr_options_default(fr_options *o) {
     o->renormalize_normals = 0;
     o->stop_twist = 0.0f;
     o->use_graph = 1;
+    o->update_sigma = 0;
 }
 
 FR_API const char *fr_status_string(fr_status s) {
@@ -913,7 +968,16 @@ static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, c
     p.kahan = opt->kahan ? 1 : 0;
     p.storage = opt->storage;
     p.profile = ctx->profiling;
-    p.annealed = fill_iter_params(opt, M, N, ctx->h_ip) ? 1 : 0;
+    p.sig = opt->update_sigma ? 1 : 0;
+    if (p.sig) {
+        // iteration 0 at sigma_start; the steps set up the later ones
+        fr_options o0 = *opt;
+        o0.sigma_end = opt->sigma_start;
+        fill_iter_params(&o0, M, N, ctx->h_ip);
+        p.annealed = 1;
+    } else {
+        p.annealed = fill_iter_params(opt, M, N, ctx->h_ip) ? 1 : 0;
+    }
     plan_grids(ctx, p, M, N, cap);
     FR_TRY(ensure_small(ctx, opt->iters, p.gs));
     FR_TRY(ensure_tables(ctx, cap, p.blur != 0, p.storage != FR_FP32));
@@ -932,6 +996,10 @@ static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, c
     j->renormalize = opt->renormalize_normals ? 1 : 0;
     j->stop_twist = opt->stop_twist;
     for (int i = 0; i < 16; ++i) j->T0[i] = T_inout[i];
+    for (int i = 1; i <= 3; ++i) j->sig_alpha[i - 1] = kAlpha / std::sqrt((double)(i * (i + 1)));
+    j->sig_c = (double)opt->w / (1.0 - (double)opt->w) * ((double)N / (double)M);
+    j->sig_G = lattice_kernel_mass(0);
+    j->sig_floor = (double)opt->sigma_end;
     DeviceState *hs = ctx->h_state;
     *hs = DeviceState{};
     for (int i = 0; i < 16; ++i) hs->T[i] = T_inout[i];
@@ -961,6 +1029,7 @@ static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, c
         rep->lattice_vertices = opt->iters > 0 ? ctx->h_ip[last_build].nvert : 0;
         rep->lattice_builds = s.builds;
         rep->lattice_vertices_sum = s.nvert_total;
+        rep->last_sigma = (opt->iters > 0 && s.iters_run > 0) ? ctx->h_ip[s.iters_run - 1].sigma : 0.0;
     }
     return FR_OK;
 }

@@ -271,6 +271,7 @@ extern "C" FR_API fr_status fr_register_articulated(fr_ctx *ctx, const float *d_
                                                     double *q_inout, fr_report *report) {
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_options(ctx, opt));
+    if (opt->update_sigma) return ctx->fail(FR_ENOTSUPPORTED, "the sigma update is implemented for rigid registration");
     if (opt->blur || opt->kahan)
         return ctx->fail(FR_ENOTSUPPORTED, "articulated registration supports neither blur nor Kahan sums");
     FR_TRY(validate_tree(ctx, tree));

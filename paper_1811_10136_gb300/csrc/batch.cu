@@ -574,6 +574,7 @@ fr_status validate_batch(fr_ctx *ctx, const fr_batch_item *items, int n, const f
                          bool on_host) {
     FR_TRY(validate_options(ctx, opt));
     if (opt->blur) return ctx->fail(FR_ENOTSUPPORTED, "batched registration does not blur");
+    if (opt->update_sigma) return ctx->fail(FR_ENOTSUPPORTED, "batched registration runs a sigma schedule");
     // block -> segment maps hold 16-bit segment indices: at most 65536
     // segments per launch, 4 per item (5 with 16-bit storage)
     const int max_items = opt->storage != FR_FP32 ? 65536 / 5 : 65536 / 4;

@@ -9,8 +9,9 @@ namespace fr {
 
 // Number of values each rigid reduction carries: the 21 upper-triangular
 // entries of A = sum J^T J, the 6 of b = sum J^T r (Eq. 18), then
-// sum of outlier weights, sum of squared residuals and the inlier count.
-constexpr int kRigidVals = 30;
+// sum of outlier weights, sum of squared residuals, the inlier count and --
+// with the sigma update -- sum_i Q_i / (M0_i + c), Q_i = sum_j K_ij |x_i - y_j|^2.
+constexpr int kRigidVals = 31;
 // Points per thread of the step and build blocks of a batched launch: fewer,
 // fuller blocks amortise each step block's 30-value reduction and each build
 // block's list append, while the other registrations keep the GPU full.  (A
@@ -47,6 +48,12 @@ struct RigidJob {
     int renormalize;
     float stop_twist;
     double T0[16];         // initial pose
+    // sigma as a decision variable (point-to-point): the constants the last
+    // step block needs to set up the next iteration's parameters
+    double sig_alpha[3];   // alpha / sqrt(i (i+1)), i = 1..3
+    double sig_c;          // w / (1 - w) N / M
+    double sig_G;          // kernel mass of the lattice
+    double sig_floor;      // smallest sigma
 };
 
 // Device-resident state of one registration.
@@ -144,6 +151,7 @@ struct IterLaunch {
     DeviceState *st;
     int gs, gv, gb, gc;    // blocks of the roles, in this order
     int check_done;        // roles return at once once st->done is set
+    int sig_next;          // sigma update: the step sets up ip[it + 1] (it + 1 < iterations)
 };
 
 // ---- articulated model -------------------------------------------------------
@@ -291,6 +299,10 @@ void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,
                      int storage);
 void launch_art_iter(int pt2pl, const ArtLaunch &a, cudaStream_t s, int storage);
 void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s, int storage);
+// The same roles with sigma as a decision variable (point-to-point, float32):
+// builds splat the extra moment, steps add Q_i / (M0_i + c) and the last step
+// block writes the next iteration's parameters.
+void launch_em_iter_sigma(int kahan, const IterLaunch &a, cudaStream_t s);
 void launch_zero_values(Table t, int grid, cudaStream_t s);
 void launch_ng_points(int pt2pl, const NgPoints &a, int warp_only, cudaStream_t s, int storage = kStoreF32);
 void launch_ng_edges(const NgEdges &a, cudaStream_t s);

@@ -258,7 +258,8 @@ __device__ void warp_se3_update(double dz, double *T /* row-major 4x4, global */
 // values w, w + 8, ...; each lane keeps 4 independent loads in flight), then
 // the solve and the pose update in warp 0.
 __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *st,
-                                 float stop_twist) {
+                                 float stop_twist, const RigidJob *sig_job = nullptr,
+                                 const IterParams *ip_cur = nullptr, IterParams *ip_next = nullptr) {
     __shared__ DF tot_s[32];
     __shared__ double sm_e[24];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -303,6 +304,36 @@ __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *
     if (lane == 27) st->sum_w = t;
     if (lane == 28) st->cost = t;
     if (lane == 29) st->inliers = (long long)(t + 0.5);
+    if (ip_next) {
+        // sigma^2 = sum_i Q_i / (M0_i + c) / (3 sum_i W_i) (floored; kept when
+        // no point had observations), rounded to float, and the parameters of
+        // the next iteration from it, as the host derives them from a sigma.
+        const double sw = __shfl_sync(kFull, t, 27), sq = __shfl_sync(kFull, t, 30);
+        if (lane == 0) {
+            double sig = (double)ip_cur->sigma;
+            if (sw > 0.0) {
+                const double s2 = sq / (3.0 * sw);
+                const double sn = sqrt(s2 > 0.0 ? s2 : 0.0);
+                sig = sn > sig_job->sig_floor ? sn : sig_job->sig_floor;
+            }
+            const float sf = (float)sig;
+            const double sd = (double)sf;
+            IterParams n = *ip_next;
+            n.sigma = sf;
+            n.s1 = (float)(sig_job->sig_alpha[0] / sd);
+            n.s2 = (float)(sig_job->sig_alpha[1] / sd);
+            n.s3 = (float)(sig_job->sig_alpha[2] / sd);
+            n.c_eff = (float)(sig_job->sig_c * sd * sd * sd * sig_job->sig_G);
+            n.inv_sigma2 = (float)(1.0 / (sd * sd));
+            n.rebuild = 1;
+            n.vscale = 1.0f;
+            n.inv_vscale = 1.0f;
+            n.ws1 = 1.0f / (2.0f * n.s1);
+            n.ws2 = 1.0f / (6.0f * n.s2);
+            n.ws3 = 1.0f / (12.0f * n.s3);
+            *ip_next = n;
+        }
+    }
     const Solved r = warp_solve6(t);
     if (lane == 0) st->iters_run += 1;
     if (!r.ok) {
@@ -385,10 +416,12 @@ __device__ __forceinline__ void red_add4(float4 *p, float a, float b, float c, f
 // round claims are appended to `list` (one atomic per block and round on the
 // build's vertex counter) so that the table can later be freed without
 // scanning it.
-template <bool PT2PL, int ST>
+template <bool PT2PL, int ST, bool SIG = false>
 __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, IterParams *ipp,
                                            Table t, int *list, DeviceState *st, int blk, int nblk) {
-    constexpr int kCh = PT2PL ? 7 : 4;
+    // the sigma update (point-to-point) adds the moment b |y - p_v|^2 about
+    // each vertex's position p_v, stored in v1.x
+    constexpr int kCh = PT2PL ? 7 : (SIG ? 5 : 4);
     constexpr int kClaimCap = 1024;
     __shared__ int s_claim[kClaimCap];
     __shared__ int s_n, s_fit, s_base;
@@ -442,6 +475,10 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
                 v[4] = b * n.x;
                 v[5] = b * n.y;
                 v[6] = b * n.z;
+            } else if (SIG) {
+                const float3 pv = vertex_position(key, ip);
+                const float dx = y.x - pv.x, dy = y.y - pv.y, dz = y.z - pv.z;
+                v[kCh - 1] = b * (dx * dx + dy * dy + dz * dz);
             }
 #pragma unroll
             for (int o = 1; o < 8; o <<= 1) {
@@ -461,6 +498,7 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
                     mask |= c ? (1 << k) : 0;
                     red_add4(rec_v0(t.keys, sl[k]), v[0], v[1], v[2], v[3]);
                     if (PT2PL) red_add4(rec_v1(t.keys, sl[k]), v[4], v[5], v[6], 0.f);
+                    else if (SIG) atomicAdd(reinterpret_cast<float *>(rec_v1(t.keys, sl[k])), v[kCh - 1]);
                 }
             }
         }
@@ -544,13 +582,14 @@ __device__ __forceinline__ void clear_role(Table t, const int *list, int n, int 
 // E-step sums of one moved model point: M0, M1 and (pt2pl) the normal sum.
 struct Sums {
     float m0, m1x, m1y, m1z, nx, ny, nz;
+    float q;  // sigma update: sum_j K |x - y_j|^2
 };
 
-template <bool PT2PL, int ST>
+template <bool PT2PL, int ST, bool SIG = false>
 __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, float x2,
                                             const IterParams &ip, Sums &o, int &bad) {
     Simplex sx;
-    o = Sums{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    o = Sums{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (!embed(x0, x1, x2, ip.s1, ip.s2, ip.s3, sx)) {
         bad |= kFlagRange;
         return false;
@@ -566,7 +605,7 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
             a[k] = slot[k] >= 0 ? __ldg(rec_v0(t.keys, slot[k])) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (PT2PL) c[k] = slot[k] >= 0 ? __ldg(rec_v1(t.keys, slot[k])) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (PT2PL || SIG) c[k] = slot[k] >= 0 ? __ldg(rec_v1(t.keys, slot[k])) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
@@ -579,6 +618,16 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
                 o.nx += b * c[k].x;
                 o.ny += b * c[k].y;
                 o.nz += b * c[k].z;
+            }
+            if (SIG && slot[k] >= 0) {
+                // sum over the vertex's observations of b |x - y|^2, from its
+                // moments about the vertex position p (all of size ~sigma):
+                // W |x - p|^2 - 2 (x - p).(V - W p) + sum b |y - p|^2
+                const float3 p = vertex_position(sx.key[k], ip);
+                const float dx = x0 - p.x, dy = x1 - p.y, dz = x2 - p.z;
+                const float W = a[k].x;
+                const float rx = a[k].y - W * p.x, ry = a[k].z - W * p.y, rz = a[k].w - W * p.z;
+                o.q += b * (W * (dx * dx + dy * dy + dz * dz) - 2.0f * (dx * rx + dy * ry + dz * rz) + c[k].x);
             }
         }
         return true;
@@ -627,7 +676,7 @@ __device__ __forceinline__ bool slice_point(const Table &t, float x0, float x1, 
 // (upper triangle, 21 values), b = sum J^T r (6), the weight sum, the cost
 // and the inlier count (Eq. 17-18).  Returns false for a point without
 // observations nearby (M0 = 0).
-template <bool PT2PL, typename Add>
+template <bool PT2PL, bool SIG = false, typename Add>
 __device__ __forceinline__ bool point_terms(float x0, float x1, float x2, const Sums &e,
                                             const IterParams &ip, int renorm, Add &&add) {
     if (!(e.m0 > 0.0f)) return false;
@@ -683,6 +732,7 @@ __device__ __forceinline__ bool point_terms(float x0, float x1, float x2, const 
     }
     add(27, W);
     add(29, 1.0f);
+    if (SIG) add(30, e.q / (e.m0 + ip.c_eff));  // Q_i / (M0_i + c): the sigma update's numerator
     return true;
 }
 
@@ -704,9 +754,10 @@ __device__ __forceinline__ void load_pose(const double *T, float *P) {
 // Eq. 6 / Eq. 9), outlier weight M0/(M0+c) and residuals (Eq. 7 / Eq. 10),
 // twist Jacobian, reduction of A and b (Eq. 17-18); the last block to finish
 // solves and updates the pose.
-template <bool PT2PL, bool KAHAN, int ST>
+template <bool PT2PL, bool KAHAN, int ST, bool SIG = false>
 __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams *ipp, const Table t,
-                                          float2 *partials, DeviceState *st, int blk, int nblk) {
+                                          float2 *partials, DeviceState *st, int blk, int nblk,
+                                          int sig_next = 0) {
     __shared__ float P[12];
     __shared__ int last;
     load_pose(st->T, P);
@@ -721,8 +772,8 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
         const float4 r = __ldg(X + i);
         const float x0 = apply_row(P, 0, r), x1 = apply_row(P, 1, r), x2 = apply_row(P, 2, r);
         Sums e;
-        if (!slice_point<PT2PL, ST>(t, x0, x1, x2, ip, e, bad)) continue;
-        point_terms<PT2PL>(x0, x1, x2, e, ip, renorm, [&](int v, float x) { acc.add(v, x); });
+        if (!slice_point<PT2PL, ST, SIG>(t, x0, x1, x2, ip, e, bad)) continue;
+        point_terms<PT2PL, SIG>(x0, x1, x2, e, ip, renorm, [&](int v, float x) { acc.add(v, x); });
     }
     if (bad) atomicOr(&st->flags, bad);
     block_partial<KAHAN>(acc, partials, blk, nblk);
@@ -737,7 +788,10 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
     }
     __syncthreads();
     if (!last) return;
-    finish_iteration(partials, nblk, st, job->stop_twist);
+    if (SIG && sig_next)
+        finish_iteration(partials, nblk, st, job->stop_twist, job, ipp, const_cast<IterParams *>(ipp) + 1);
+    else
+        finish_iteration(partials, nblk, st, job->stop_twist);
     if (threadIdx.x == 0) st->ticket = 0;
 }
 
@@ -764,6 +818,29 @@ __global__ void __launch_bounds__(kBlock, 4) k_em_iter(IterLaunch L) {
     if (b < L.gb) {
         if (L.check_done && stopped(L.st)) return;
         build_role<PT2PL, ST>(L.job, L.ip + L.build_it, L.build, L.build_list, L.st, b, L.gb);
+        return;
+    }
+    b -= L.gb;
+    if (b < L.gc) clear_role(L.clear, L.clear_list, __ldcg(&L.ip[L.clear_it].nvert), b, L.gc);
+}
+
+// Sigma as a decision variable (point-to-point, float32 records): the step
+// of iteration `it` (whose last block also writes ip[it + 1]), or the build
+// of an iteration at the sigma the previous step chose, and a clear.  The
+// next sigma is known only once a step finishes, so steps and builds are
+// separate launches.
+template <bool KAHAN>
+__global__ void __launch_bounds__(kBlock, 4) k_em_iter_sigma(IterLaunch L) {
+    int b = blockIdx.x;
+    if (b < L.gs) {
+        if (L.check_done && stopped(L.st)) return;
+        step_role<false, KAHAN, kStoreF32, true>(L.job, L.ip + L.it, L.step, L.partials, L.st, b, L.gs, L.sig_next);
+        return;
+    }
+    b -= L.gs;
+    if (b < L.gb) {
+        if (L.check_done && stopped(L.st)) return;
+        build_role<false, kStoreF32, true>(L.job, L.ip + L.build_it, L.build, L.build_list, L.st, b, L.gb);
         return;
     }
     b -= L.gb;
@@ -2213,6 +2290,15 @@ void launch_em_iter(int pt2pl, int kahan, const IterLaunch &a, cudaStream_t s, i
 #define FR_CALL(P, K, S) k_em_iter<P, K, S><<<grid, kBlock, 0, s>>>(a)
     FR_VARIANTS(FR_CALL);
 #undef FR_CALL
+}
+
+void launch_em_iter_sigma(int kahan, const IterLaunch &a, cudaStream_t s) {
+    const int grid = a.gs + a.gb + a.gc;
+    if (grid <= 0) return;
+    if (kahan)
+        k_em_iter_sigma<true><<<grid, kBlock, 0, s>>>(a);
+    else
+        k_em_iter_sigma<false><<<grid, kBlock, 0, s>>>(a);
 }
 
 void launch_em_multi(int pt2pl, int kahan, const Slot *slots, const Seg *segs,

@@ -306,6 +306,7 @@ fr_status ng_validate(fr_ctx *ctx, const fr_nodegraph *g, const float *d_Y, cons
     if (!ctx || !g) return FR_EINVAL;
     if (g->ctx != ctx) return ctx->fail(FR_EINVAL, "the node graph belongs to another context");
     FR_TRY(validate_options(ctx, opt));
+    if (opt->update_sigma) return ctx->fail(FR_ENOTSUPPORTED, "the sigma update is implemented for rigid registration");
     FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));
     if (opt->residual == FR_PT2PL) FR_TRY(validate_cloud(ctx, d_Yn, N, "d_Yn"));
     if (opt->blur || opt->kahan || opt->stop_twist > 0.0f)

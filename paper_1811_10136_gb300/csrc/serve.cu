@@ -543,6 +543,7 @@ FR_API fr_status fr_server_create(fr_ctx *ctx, size_t budget, int max_live, cons
     if (!ctx || !out) return FR_EINVAL;
     *out = nullptr;
     FR_TRY(validate_options(ctx, opt));
+    if (opt->update_sigma) return ctx->fail(FR_ENOTSUPPORTED, "the sigma update is implemented for rigid registration");
     if (opt->blur) return ctx->fail(FR_ENOTSUPPORTED, "the server runs without blur");
     if (opt->iters < 1) return ctx->fail(FR_EINVAL, "the server needs iters >= 1");
     if (max_live < 1 || max_live > 4096) return ctx->fail(FR_EINVAL, "max_live must be in 1..4096");
