@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-nodegraph", action="store_true", help="skip the node-graph line")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact Gauss-transform line")
+    ap.add_argument("--no-sigma", action="store_true", help="skip the updated-sigma line")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct rendered frames behind the stream")
     return ap.parse_args()
@@ -611,6 +612,33 @@ def run_ours(args):
                                              "per pair (3 differences, squared distance 3, exponent scale 1, "
                                              "sums 7, exp2 argument 1)"}}
 
+    # ---- sigma as a decision variable vs a fixed sigma (bumpy sphere) --------
+    sigma_upd = None
+    if not args.no_sigma:
+        f32 = lambda x: float(np.float32(x))
+        rows = {"fixed_0.02": dict(sigma_start=f32(0.02), sigma_end=f32(0.02)),
+                "updated_0.08_floor_0.005": dict(sigma_start=f32(0.08), sigma_end=f32(0.005), update_sigma=1)}
+        sigma_upd = {"workload": "bumpy sphere 2000 x 2200 points (10% outliers), motion <= 5 deg / 3 cm, "
+                                 "point-to-point, w 0.1, stop at |dzeta| < 1e-5, at most 100 iterations, seeds 0-4"}
+        for name, kw in rows.items():
+            its, errs, ms = [], [], []
+            for seed in range(5):
+                sp = synth.sphere_bumps_pair(seed, max_angle_deg=5.0, max_trans=0.03)
+                Xs, Ys = dev(sp.X), dev(sp.Y)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                Ts, rs = ctx.register_rigid(Xs, Ys, None, residual=fr.FR_PT2PT, iters=100, w=f32(0.1),
+                                            stop_twist=1e-5, **kw)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+                its.append(rs.iters_run)
+                errs.append(synth.rotation_angle_deg(Ts, sp.T_gt))
+            sigma_upd[name] = {"em_iters_to_stop_mean": round(statistics.mean(its), 1), "iters": its,
+                               "ms_per_registration_mean": round(statistics.mean(ms), 4),
+                               "rot_err_deg_vs_truth_mean": round(statistics.mean(errs), 4)}
+
     # ---- serving: Poisson stream through fr_server vs the plain path ---------
     serving = None
     if not args.no_serving:
@@ -678,6 +706,7 @@ def run_ours(args):
             "serving": serving,
             "nodegraph": nodegraph,
             "exact": exact,
+            "sigma_update": sigma_upd,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
