@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-nodegraph", action="store_true", help="skip the node-graph line")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact Gauss-transform line")
     ap.add_argument("--no-sigma", action="store_true", help="skip the updated-sigma line")
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes (no autotuning)")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct rendered frames behind the stream")
     return ap.parse_args()
@@ -410,10 +411,13 @@ def run_ours(args):
         plain_step()
 
     # ---- launch-shape autotuning of the batched path (outside the timed region)
-    best, tuned_ms, default_ms = ctx.autotune_batch(dpairs, objective=fr.FR_TUNE_THROUGHPUT, reps=3, **opts)
-    tuning = {"params": best, "em_iters_per_s_tuned": round(ITERS * args.frames / (tuned_ms * 1e-3), 1),
-              "em_iters_per_s_default": round(ITERS * args.frames / (default_ms * 1e-3), 1),
-              "timing": "median of 3 whole batched calls (CUDA events) per candidate shape, L2 warm"}
+    tuning = None
+    if not args.no_tune:
+        best, tuned_ms, default_ms = ctx.autotune_batch(dpairs, objective=fr.FR_TUNE_THROUGHPUT, reps=3, **opts)
+    if not args.no_tune:
+        tuning = {"params": best, "em_iters_per_s_tuned": round(ITERS * args.frames / (tuned_ms * 1e-3), 1),
+                  "em_iters_per_s_default": round(ITERS * args.frames / (default_ms * 1e-3), 1),
+                  "timing": "median of 3 whole batched calls (CUDA events) per candidate shape, L2 warm"}
     for _ in range(2):
         batched_step()
 
