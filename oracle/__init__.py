@@ -22,7 +22,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["estep.c", "lattice.c", "se3.c", "rigid.c", "articulated.c", "nodegraph.c"]
+_SOURCES = ["estep.c", "lattice.c", "se3.c", "rigid.c", "articulated.c", "nodegraph.c", "lattice_d.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _OMP_LIB_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
@@ -143,6 +143,7 @@ def _declare(L):
     if hasattr(L, "or_register_articulated"):
         _declare_articulated(L)
         _declare_nodegraph(L)
+    _declare_features(L)
 
 
 def _pts(a) -> np.ndarray:
@@ -262,6 +263,131 @@ class Lattice:
 
 def kernel_mass(backend=LATTICE, blur=False) -> float:
     return float(_L().or_kernel_mass(backend, int(blur)))
+
+
+# ---- feature-space E step (d-dimensional lattice) ------------------------------
+
+FEATURE_DMAX = 7
+
+
+def _declare_features(L):
+    L.or_feature_scale.argtypes = [ctypes.c_int, _f32p, _f32p]
+    L.or_feature_scale.restype = None
+    L.or_feature_embed.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int, _f32p, _i32p, _f32p]
+    L.or_feature_embed.restype = ctypes.c_int
+    L.or_flattice_build.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int, _f32p, _f64p, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int)]
+    L.or_flattice_build.restype = ctypes.c_void_p
+    L.or_flattice_slice.argtypes = [ctypes.c_void_p, _f32p, ctypes.c_int64, _f64p]
+    L.or_flattice_slice.restype = ctypes.c_int
+    L.or_flattice_size.argtypes = [ctypes.c_void_p]
+    L.or_flattice_size.restype = ctypes.c_int64
+    L.or_flattice_vertices.argtypes = [ctypes.c_void_p, _i32p, _f64p]
+    L.or_flattice_vertices.restype = None
+    L.or_flattice_free.argtypes = [ctypes.c_void_p]
+    L.or_flattice_free.restype = None
+    L.or_estep_features.argtypes = [_f32p, ctypes.c_int64, _f32p, ctypes.c_int64, ctypes.c_int, _f32p,
+                                    _f32p, _f32p, ctypes.c_int, _f64p]
+    L.or_estep_features.restype = ctypes.c_int
+    L.or_feature_kernel_mass.argtypes = [ctypes.c_int]
+    L.or_feature_kernel_mass.restype = ctypes.c_double
+
+
+def _feats(F, d=None) -> np.ndarray:
+    F = np.ascontiguousarray(F, dtype=np.float32)
+    if F.ndim != 2 or not 1 <= F.shape[1] <= FEATURE_DMAX or (d is not None and F.shape[1] != d):
+        raise ValueError(f"features must have shape (n, d), 1 <= d <= {FEATURE_DMAX}")
+    return F
+
+
+def feature_scales(sigma_f) -> np.ndarray:
+    """Per-axis float scale alpha / sqrt(i (i+1)) / sigma_f[i-1] of the d-dimensional elevation."""
+    sf = np.ascontiguousarray(sigma_f, dtype=np.float32).reshape(-1)
+    s = np.zeros(sf.shape[0], np.float32)
+    _L().or_feature_scale(sf.shape[0], _p(sf, _f32p), _p(s, _f32p))
+    return s
+
+
+def feature_embed(F, sigma_f):
+    """Per feature row: keys (n, d+1, d+1) int32 [vertex k][coordinate j] and bary (n, d+1)."""
+    F = _feats(F)
+    n, d = F.shape
+    s = feature_scales(sigma_f)
+    keys = np.zeros((n, d + 1, d + 1), np.int32)
+    bary = np.zeros((n, d + 1), np.float32)
+    st = _L().or_feature_embed(_p(F, _f32p), n, d, _p(s, _f32p), _p(keys, _i32p), _p(bary, _f32p))
+    return keys, bary, st
+
+
+class FeatureLattice:
+    """The d-dimensional reference lattice: key-sorted vertices with double values."""
+
+    def __init__(self, F, V, sigma_f):
+        F = _feats(F)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        if V.ndim == 1:
+            V = V[:, None].copy()
+        self.d = F.shape[1]
+        self.vdim = V.shape[1]
+        s = feature_scales(sigma_f)
+        st = ctypes.c_int(0)
+        self._lib = _L()
+        self._h = self._lib.or_flattice_build(_p(F, _f32p), F.shape[0], self.d, _p(s, _f32p), _p(V, _f64p),
+                                              self.vdim, ctypes.byref(st))
+        if not self._h:
+            raise OracleError(f"feature lattice build failed ({st.value})")
+        self.status = st.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        lib = getattr(self, "_lib", None)
+        if h and lib is not None:
+            lib.or_flattice_free(h)
+            self._h = None
+
+    def __len__(self):
+        return int(self._lib.or_flattice_size(self._h))
+
+    def slice(self, Q):
+        Q = _feats(Q, self.d)
+        out = np.zeros((Q.shape[0], self.vdim), np.float64)
+        st = self._lib.or_flattice_slice(self._h, _p(Q, _f32p), Q.shape[0], _p(out, _f64p))
+        return out, st
+
+    def vertices(self):
+        nv = len(self)
+        keys = np.zeros((nv, self.d + 1), np.int32)
+        vals = np.zeros((nv, self.vdim), np.float64)
+        self._lib.or_flattice_vertices(self._h, _p(keys, _i32p), _p(vals, _f64p))
+        return keys, vals
+
+
+def estep_features(FX, FY, sigma_f, Y, Yn=None, backend=LATTICE):
+    """Feature-space E-step sums at the model features FX: (M, 4) [M0, M1] or (M, 7) with normals.
+
+    The kernel is exp(-sum_c (fx_c - fy_c)^2 / (2 sigma_c^2)) between feature rows; the values
+    splatted are the observation points Y (and normals Yn)."""
+    FX, FY = _feats(FX), _feats(FY)
+    if FX.shape[1] != FY.shape[1]:
+        raise ValueError("model and observation features differ in dimension")
+    d = FX.shape[1]
+    sf = np.ascontiguousarray(sigma_f, dtype=np.float32).reshape(-1)
+    if sf.shape[0] != d:
+        raise ValueError("sigma_f needs one entry per feature channel")
+    Y = _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    if Y.shape[0] != FY.shape[0] or (Yn is not None and Yn.shape[0] != FY.shape[0]):
+        raise ValueError("observation points and features differ in count")
+    vdim = 7 if Yn is not None else 4
+    out = np.zeros((FX.shape[0], vdim), np.float64)
+    _check(_L().or_estep_features(_p(FX, _f32p), FX.shape[0], _p(FY, _f32p), FY.shape[0], d, _p(sf, _f32p),
+                                  _p(Y, _f32p), _p(Yn, _f32p), backend, _p(out, _f64p)), "estep_features")
+    return out
+
+
+def feature_kernel_mass(d: int) -> float:
+    """Integral of the unnormalised splat+slice kernel over normalised feature space."""
+    return float(_L().or_feature_kernel_mass(int(d)))
 
 
 def sigma_schedule(s0, s1, iters) -> np.ndarray:

@@ -217,6 +217,29 @@ int or_register_nodegraph(const float *Xref, const int32_t *knn, const float *sk
 /* Alignment error of Eq. 22: mean |(T - T_gt) x_ref|. */
 double or_align_error(const float *X, int64_t M, const double T[16], const double Tgt[16]);
 
+/* ---- feature-space E step (Eq. feature_estep), d-dimensional lattice ------
+ * Features are rows of d floats (1 <= d <= OR_FEATURE_DMAX), the kernel a
+ * Gaussian with diagonal covariance diag(sigma_f^2) in feature space.        */
+#define OR_FEATURE_DMAX 7
+/* Per-axis scale alpha / sqrt(i (i+1)) / sigma_f[i-1], alpha = sqrt(2/3)(d+1). */
+void or_feature_scale(int d, const float *sigma_f, float *scale);
+/* Vertices (keys[i][k][j], j < d+1) and barycentric weights of n features.  */
+int or_feature_embed(const float *F, int64_t n, int d, const float *scale, int32_t *keys, float *bary);
+typedef struct or_flattice or_flattice;
+or_flattice *or_flattice_build(const float *F, int64_t n, int d, const float *scale, const double *V,
+                               int vdim, int *status);
+int or_flattice_slice(const or_flattice *lat, const float *Q, int64_t m, double *out);
+int64_t or_flattice_size(const or_flattice *lat);
+void or_flattice_vertices(const or_flattice *lat, int32_t *keys, double *vals);
+void or_flattice_free(or_flattice *lat);
+/* M0, M1 (and normal sums with Yn) at the model features FX, kernel over the
+ * observation features FY: exact sums (OR_EXACT) or splat + slice on the
+ * d-dimensional lattice (OR_LATTICE); out is M x 4 or M x 7.                 */
+int or_estep_features(const float *FX, int64_t M, const float *FY, int64_t N, int d, const float *sigma_f,
+                      const float *Y, const float *Yn, int backend, double *out);
+/* Integral of the unnormalised splat+slice kernel in normalised feature units. */
+double or_feature_kernel_mass(int d);
+
 /* Threads the OpenMP build uses (1 for the plain build); set them (n > 0). */
 int or_num_threads(void);
 void or_set_threads(int n);
