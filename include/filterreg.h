@@ -241,6 +241,54 @@ FR_API fr_status fr_estep_storage(fr_ctx *ctx, const float *d_X, int64_t M, cons
                                   const float *d_Yn, int64_t N, float sigma, int32_t storage,
                                   const double T[16], float *d_out);
 
+/* ---- feature-space E step (Section 3.3, Eq. feature_estep) -------------------
+ * The E step's Gaussian over d-dimensional per-point features (1 <= d <= 7)
+ * with diagonal covariance diag(sigma_f^2): K_ij = exp(-sum_c (fx_ic -
+ * fy_jc)^2 / (2 sigma_f[c]^2)), unnormalised as in Eq. 11.  Features are
+ * row-major float rows of d values (d_FX: M x d of the model, d_FY: N x d of
+ * the observation, 4-byte aligned; positions, normals, colours or any
+ * descriptor, already expressed in the frame the caller wants compared);
+ * sigma_f is a host array of d positive floats.  Filtering follows Section
+ * 4.2 on the (d+1)-dimensional permutohedral lattice: g = f / sigma_f is
+ * elevated with alpha = sqrt(2/3) (d+1), the enclosing simplex found, the
+ * observation splatted, the model sliced (no blur; queries insert nothing).
+ */
+
+/* fr_feature_embed: the d+1 vertex keys (int32, n x (d+1) x (d+1):
+ * [row][vertex k][coordinate j], vertex k's coordinates all congruent to k
+ * mod d+1) and barycentric weights (float, n x (d+1)) of n feature rows d_F.
+ * Either output may be NULL.  FR_EINVAL for d outside [1, 7], a sigma_f entry
+ * that is not finite and > 0, or a row with a non-finite value or an elevated
+ * coordinate of magnitude >= 1e6 (>= 131000 for d = 7, whose packed key
+ * fields are 18 bits); such rows' outputs are 0.  Synchronises the stream. */
+FR_API fr_status fr_feature_embed(fr_ctx *ctx, const float *d_F, int64_t n, int32_t d, const float *sigma_f,
+                                  int32_t *d_keys, float *d_bary);
+
+/* fr_estep_features: build the lattice over the observation features d_FY
+ * with values [1, y] (d_Yn == NULL) or [1, y, n_y] (d_Y, d_Yn: N x 4 float,
+ * 16-byte aligned) and slice it at the model features d_FX: d_out (float,
+ * M x 4, 16-byte aligned, or M x 7) = [M0, M1 (3) (, Nsum (3))], the
+ * feature-space counterparts of Eq. 6 / Eq. 9's numerators.  The number of
+ * lattice vertices goes to *n_vertices (host, nullable).  The context keeps
+ * the table (2 (d+1) N slots rounded up to a power of two, 32-byte records,
+ * 64-byte with normals) between calls and empties only the slots each call
+ * claimed.  FR_EINVAL as for fr_feature_embed (rows out of range contribute
+ * nothing and read 0) or for more than 2^27 table slots; FR_ECAPACITY if a
+ * probe sequence runs past 512 slots; FR_ENOMEM past the workspace limit.
+ * Synchronises the stream. */
+FR_API fr_status fr_estep_features(fr_ctx *ctx, const float *d_FX, int64_t M, const float *d_FY, int64_t N,
+                                   int32_t d, const float *sigma_f, const float *d_Y, const float *d_Yn,
+                                   float *d_out, int64_t *n_vertices);
+
+/* fr_gauss_transform_features: the same sums without the lattice, every
+ * model-observation pair in float32 (O(N M) work; observation tiles summed
+ * on their own before joining each model point's totals).  d_out as for
+ * fr_estep_features (4-byte aligned suffices).  FR_EINVAL for invalid
+ * arguments.  Synchronises the stream. */
+FR_API fr_status fr_gauss_transform_features(fr_ctx *ctx, const float *d_FX, int64_t M, const float *d_FY,
+                                             int64_t N, int32_t d, const float *sigma_f, const float *d_Y,
+                                             const float *d_Yn, float *d_out);
+
 /* ---- rigid registration (Sections 3.1, 3.3, 4, 5) ---------------------------
  * fr_register_rigid: run opt->iters EM iterations aligning the model d_X
  * (M x 4) to the observation d_Y (N x 4).  Each iteration: (re)build the

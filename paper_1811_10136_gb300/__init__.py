@@ -41,7 +41,9 @@ EXPORTED = [
     "fr_server_create", "fr_server_submit", "fr_server_poll", "fr_server_wait", "fr_server_release",
     "fr_server_stats", "fr_server_destroy", "fr_nodegraph_create", "fr_nodegraph_destroy",
     "fr_register_nodegraph", "fr_nodegraph_system", "fr_nodegraph_warp",
+    "fr_feature_embed", "fr_estep_features", "fr_gauss_transform_features",
 ]
+FR_FEATURE_DMAX = 7
 FR_NOALLOC_MAX_OBS = 8192
 KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert", "ng_assemble", "ng_solve")
 
@@ -126,6 +128,7 @@ class fr_profile(ctypes.Structure):
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _f64p = ctypes.POINTER(ctypes.c_double)
+_f32p = ctypes.POINTER(ctypes.c_float)
 _lib = None
 
 
@@ -200,6 +203,10 @@ def load(build_if_missing: bool = True):
     L.fr_nodegraph_system.argtypes = [_vp, _vp, _vp, _vp, _i64, ctypes.POINTER(fr_options), ctypes.c_double,
                                       _f64p, _f64p, _f64p, ctypes.POINTER(fr_report)]
     L.fr_nodegraph_warp.argtypes = [_vp, _vp, _f64p, _vp]
+    L.fr_feature_embed.argtypes = [_vp, _vp, _i64, ctypes.c_int32, _f32p, _vp, _vp]
+    L.fr_estep_features.argtypes = [_vp, _vp, _i64, _vp, _i64, ctypes.c_int32, _f32p, _vp, _vp, _vp,
+                                    ctypes.POINTER(_i64)]
+    L.fr_gauss_transform_features.argtypes = [_vp, _vp, _i64, _vp, _i64, ctypes.c_int32, _f32p, _vp, _vp, _vp]
     for name in EXPORTED:  # every entry point must resolve (ctypes restype defaults to int)
         getattr(L, name)
     _lib = L
@@ -526,6 +533,56 @@ class Context:
                                     out.data_ptr())
             self._check(st, "fr_estep_storage")
         return out
+
+    # ---- feature-space E step (d-dimensional features) ------------------
+    def _features(self, F, name, d=None):
+        import torch
+        if not isinstance(F, torch.Tensor) or not F.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if F.dtype != torch.float32 or F.dim() != 2 or not F.is_contiguous() or \
+                not 1 <= F.shape[1] <= FR_FEATURE_DMAX or (d is not None and F.shape[1] != d):
+            raise TypeError(f"{name} must be a contiguous float32 (n, d) tensor, 1 <= d <= {FR_FEATURE_DMAX}")
+        return F.data_ptr()
+
+    @staticmethod
+    def _sigma_f(sigma_f, d):
+        sf = np.ascontiguousarray(sigma_f, dtype=np.float32).reshape(-1)
+        if sf.shape[0] != d:
+            raise ValueError("sigma_f needs one entry per feature channel")
+        return sf
+
+    def feature_embed(self, F, sigma_f):
+        """Vertex keys (n, d+1, d+1) int32 and barycentric weights (n, d+1) of feature rows F."""
+        import torch
+        n, d = F.shape
+        keys = torch.empty((n, d + 1, d + 1), dtype=torch.int32, device=F.device)
+        bary = torch.empty((n, d + 1), dtype=torch.float32, device=F.device)
+        sf = self._sigma_f(sigma_f, d)
+        st = load().fr_feature_embed(self._h, self._features(F, "F"), n, d, sf.ctypes.data_as(_f32p),
+                                     keys.data_ptr(), bary.data_ptr())
+        self._check(st, "fr_feature_embed")
+        return keys, bary
+
+    def estep_features(self, FX, FY, sigma_f, Y, Yn=None, exact=False):
+        """Feature-space E-step sums at the model features FX over the observation
+        features FY (Eq. feature_estep): (M, 4) [M0, M1] or (M, 7) with normals,
+        float32 CUDA tensor; the lattice unless exact.  Returns (out, vertices)
+        (vertices None for the exact sums)."""
+        import torch
+        L = load()
+        M, d = FX.shape
+        N = FY.shape[0]
+        vd = 7 if Yn is not None else 4
+        sf = self._sigma_f(sigma_f, d)
+        out = torch.empty((M, vd), dtype=torch.float32, device=FX.device)
+        args = (self._features(FX, "FX"), M, self._features(FY, "FY", d), N, d, sf.ctypes.data_as(_f32p),
+                _dev_ptr(Y, "Y", rows=N), _dev_ptr(Yn, "Yn", rows=N) if Yn is not None else None, out.data_ptr())
+        if exact:
+            self._check(L.fr_gauss_transform_features(self._h, *args), "fr_gauss_transform_features")
+            return out, None
+        nv = _i64(0)
+        self._check(L.fr_estep_features(self._h, *args, ctypes.byref(nv)), "fr_estep_features")
+        return out, int(nv.value)
 
     # ---- lattice primitives ----------------------------------------------
     def lattice_embed(self, P, sigma):

@@ -579,6 +579,7 @@ FR_API fr_status fr_ctx_destroy(fr_ctx *ctx) {
     drop_graphs(ctx);
     free_batch_workspace(ctx);
     free_art_workspace(ctx);
+    free_feat_workspace(ctx);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     free_tables(ctx);
     cudaFree(ctx->partials);

@@ -19,6 +19,7 @@ namespace fr {
 struct BatchWorkspace;
 struct ArtWorkspace;
 struct ServerState;
+struct FeatWorkspace;
 }
 
 namespace fr {
@@ -142,6 +143,7 @@ struct fr_ctx {
                                              fr::tune_default(), fr::tune_default()};
     fr::BatchWorkspace *batch = nullptr;  // batched-registration workspace (batch.cu)
     fr::ArtWorkspace *art = nullptr;      // articulated-registration workspace (articulated.cu)
+    fr::FeatWorkspace *feat = nullptr;    // feature-space lattice table (features.cu)
 
     // per-kernel profiling: event pairs around each launch of a plan
     int profiling = 0;
@@ -193,6 +195,7 @@ int fused_blocks_per_sm(fr_ctx *ctx, int pt2pl, int kahan);
 void collect_profile(fr_ctx *ctx, int kernels);
 void free_batch_workspace(fr_ctx *ctx);   // batch.cu
 void free_art_workspace(fr_ctx *ctx);     // articulated.cu
+void free_feat_workspace(fr_ctx *ctx);    // features.cu
 fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur, bool compact = false);
 fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows);
 }  // namespace fr

@@ -523,3 +523,26 @@ def nodegraph_pair(seed: int, W: int = 640, H: int = 480, n_nodes: int = 1000, n
                          {"workload": "height_field_nodegraph", "seed": seed, "M": int(Pm.shape[0]),
                           "N": int(Yp.shape[0]), "K": n_nodes, "E": int(edges.shape[0]),
                           "skin_radius": r})
+
+
+@dataclass
+class FeaturePair:
+    FX: np.ndarray  # (M, d) float32 model features
+    FY: np.ndarray  # (N, d) float32 observation features
+    Y: np.ndarray   # (N, 4) observation points
+    Yn: np.ndarray  # (N, 4) observation normals
+    meta: dict
+
+
+def feature_frame_pair(seed: int, W: int = 320, H: int = 240, **kw) -> FeaturePair:
+    """A depth-frame pair (depth_frame_pair) with the 6-d per-point feature
+    [position, normal]: FX holds every model pixel's position and the normal
+    of its own depth image, FY the observation's (after dropout); Y and Yn are
+    the observation's points and normals."""
+    p = depth_frame_pair(seed, W=W, H=H, **kw)
+    Xn = depth_normals(p.X[:, :3].astype(np.float64).reshape(H, W, 3)).reshape(-1, 3)
+    FX = np.concatenate([p.X[:, :3], Xn], 1).astype(np.float32)
+    FY = np.concatenate([p.Y[:, :3], p.Yn[:, :3]], 1).astype(np.float32)
+    return FeaturePair(np.ascontiguousarray(FX), np.ascontiguousarray(FY), p.Y, p.Yn,
+                       {"workload": "depth_frames_xyz_normal", "seed": seed, "W": W, "H": H, "d": 6,
+                        "M": FX.shape[0], "N": FY.shape[0]})
