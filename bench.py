@@ -39,6 +39,7 @@ METRIC = "EM iters/s at 76.8k pts; batched regs/s + p99 latency vs plain, <=0.1 
 UNIT = "EM iters/s"
 ITERS = 20
 SIGMA0, SIGMA1, W_OUT = 0.04, 0.01, 0.1
+FEAT_SIGMA_P, FEAT_SIGMA_N = 0.02, 0.25   # feature E step: position (m) and normal bandwidths
 ART_ITERS, ART_SIGMA = 15, 0.01      # articulated workload: 15 EM iterations at sigma 1 cm
 NG_ITERS, NG_PCG, NG_SIGMA, NG_LAMBDA = 10, 20, 0.02, 10.0  # node-graph workload
 SERVE_RATE = 2000.0                   # serving stream: Poisson arrivals per second
@@ -61,6 +62,7 @@ def parse():
     ap.add_argument("--no-nodegraph", action="store_true", help="skip the node-graph line")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact Gauss-transform line")
     ap.add_argument("--no-sigma", action="store_true", help="skip the updated-sigma line")
+    ap.add_argument("--no-features", action="store_true", help="skip the feature-space E-step line")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes (no autotuning)")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct rendered frames behind the stream")
@@ -616,6 +618,68 @@ def run_ours(args):
                                              "per pair (3 differences, squared distance 3, exponent scale 1, "
                                              "sums 7, exp2 argument 1)"}}
 
+    # ---- feature-space E step: 6-d [position, normal] features ---------------
+    features = None
+    if not args.no_features:
+        fp = synth.feature_frame_pair(args.seed)
+        sf = np.array([FEAT_SIGMA_P] * 3 + [FEAT_SIGMA_N] * 3, np.float32)
+        FX, FY, FYp, FYn = dev(fp.FX), dev(fp.FY), dev(fp.Y), dev(fp.Yn)
+
+        def ev_ms(fn, reps=7):
+            fn()
+            ts = []
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            return statistics.median(ts)
+
+        la_out, nv = ctx.estep_features(FX, FY, sf, FYp, FYn)
+        l0 = ctx.kernel_launches
+        la_out, nv = ctx.estep_features(FX, FY, sf, FYp, FYn)
+        per_call = ctx.kernel_launches - l0
+        la_ms = ev_ms(lambda: ctx.estep_features(FX, FY, sf, FYp, FYn))
+        # per-kernel device times: event pairs around each launch
+        ctx.profile(reset=True)
+        ctx.set_profiling(True)
+        for _ in range(20):
+            ctx.estep_features(FX, FY, sf, FYp, FYn)
+        ctx.set_profiling(False)
+        kp = ctx.profile(reset=True)
+        k_us = {name: round(1000.0 * kp[name][1] / max(1, kp[name][0]), 3) for name in ("build", "slice", "clear")}
+        ex_ms = ev_ms(lambda: ctx.estep_features(FX, FY, sf, FYp, FYn, exact=True), reps=3)
+        la = la_out.double().cpu().numpy()
+        ex = ctx.estep_features(FX, FY, sf, FYp, FYn, exact=True)[0].double().cpu().numpy()
+        live = (ex[:, 0] > 1e-3 * ex[:, 0].max()) & (la[:, 0] > 0)
+        terr = np.linalg.norm(la[live, 1:4] / la[live, :1] - ex[live, 1:4] / ex[live, :1], axis=1) / FEAT_SIGMA_P
+        M, N = fp.FX.shape[0], fp.FY.shape[0]
+        # algorithmic bytes of the build (the dominant kernel): observation
+        # features, points and normals read once, every vertex record (64 B)
+        # written once
+        alg = N * (24 + 16 + 16) + nv * 64
+        hbm, hbm_src = measured_peaks()
+        ach = alg / (k_us["build"] * 1e-6) / 1e9
+        features = {"workload": f"one 320x240 pair, 6-d [position, normal] features, {M} x {N} points, "
+                                f"pt2pl values, sigma_f ({FEAT_SIGMA_P} m x 3, {FEAT_SIGMA_N} x 3)",
+                    "lattice_ms_per_estep": round(la_ms, 4), "estep_per_s": round(1000.0 / la_ms, 1),
+                    "kernel_us": k_us, "kernels_us_sum": round(sum(k_us.values()), 3),
+                    "lattice_vertices": nv, "launches_per_estep": per_call,
+                    "exact_ms_per_estep": round(ex_ms, 4),
+                    "lattice_over_exact_speedup": round(ex_ms / la_ms, 1),
+                    "lattice_target_err_over_sigma_p": {"median": round(float(np.median(terr)), 5),
+                                                        "p99": round(float(np.percentile(terr, 99)), 5),
+                                                        "points": int(live.sum())},
+                    "roofline": {"kernel": "k_feat_build", "bound": "hbm", "achieved": round(ach, 1),
+                                 "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                                 "peak_source": hbm_src, "algorithmic_bytes": int(alg),
+                                 "timing": "CUDA events around each build launch (20 calls); "
+                                           "lattice_ms_per_estep brackets the whole call (3 kernels, a "
+                                           "memset, the counter read-back and the synchronisation)"}}
+
     # ---- sigma as a decision variable vs a fixed sigma (bumpy sphere) --------
     sigma_upd = None
     if not args.no_sigma:
@@ -711,6 +775,7 @@ def run_ours(args):
             "nodegraph": nodegraph,
             "exact": exact,
             "sigma_update": sigma_upd,
+            "features": features,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -786,6 +851,15 @@ def cpu_baseline(pair, seed):
                          "cores": oracle.num_threads()}
         exact["depth_frame_estep"] = sub
         out["exact"] = exact
+        # one feature-space lattice E step (6-d [position, normal]) on the full frame
+        oracle.set_parallel(False)
+        fp = synth.feature_frame_pair(seed)
+        sf = np.array([FEAT_SIGMA_P] * 3 + [FEAT_SIGMA_N] * 3, np.float32)
+        t0 = time.perf_counter()
+        oracle.estep_features(fp.FX, fp.FY, sf, fp.Y, fp.Yn, backend=oracle.LATTICE)
+        el = time.perf_counter() - t0
+        out["features"] = {"sample": f"one 6-d lattice E step, {fp.FX.shape[0]} x {fp.FY.shape[0]} points",
+                           "s_per_estep": round(el, 3), "cores": 1}
     finally:
         oracle.set_parallel(False)
     return out

@@ -28,6 +28,11 @@
  *   - Handles (fr_ctx, fr_lattice) are owned by the library and released by
  *     the matching *_destroy call.  A context must be used by one host thread
  *     at a time.
+ *   - Registration calls take the method's scalar parameters -- the sigma
+ *     schedule, the outlier ratio w, the EM iteration count, the residual,
+ *     blur and storage -- in one fr_options struct (fr_options_default fills
+ *     it) rather than as separate arguments, so that one struct describes a
+ *     registration for the single, batched and served forms alike.
  */
 #ifndef FILTERREG_H
 #define FILTERREG_H
@@ -113,10 +118,11 @@ typedef struct {
  * step under 16-bit storage; later conversions run inside FR_K_STEP launches.
  * FR_K_NG_ASSEMBLE / FR_K_NG_SOLVE: a node-graph iteration's E step with the
  * assembly of A and g (point and edge kernels), and its PCG solve with the
- * node update (timed as spans of launches). */
+ * node update (timed as spans of launches).  FR_K_SLICE: the feature-space
+ * E step's slice (its build and clear count as FR_K_BUILD and FR_K_CLEAR). */
 enum {
     FR_K_CLEAR = 0, FR_K_BUILD = 1, FR_K_BLUR = 2, FR_K_STEP = 3, FR_K_CONVERT = 4,
-    FR_K_NG_ASSEMBLE = 5, FR_K_NG_SOLVE = 6, FR_K_CLASSES = 7
+    FR_K_NG_ASSEMBLE = 5, FR_K_NG_SOLVE = 6, FR_K_SLICE = 7, FR_K_CLASSES = 8
 };
 typedef struct {
     int64_t launches[FR_K_CLASSES]; /* kernels of each class timed since the last reset */

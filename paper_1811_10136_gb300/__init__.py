@@ -45,7 +45,7 @@ EXPORTED = [
 ]
 FR_FEATURE_DMAX = 7
 FR_NOALLOC_MAX_OBS = 8192
-KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert", "ng_assemble", "ng_solve")
+KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert", "ng_assemble", "ng_solve", "slice")
 
 
 class FilterRegError(RuntimeError):
@@ -122,7 +122,7 @@ FR_TUNE_THROUGHPUT, FR_TUNE_LATENCY = 0, 1
 
 
 class fr_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 7), ("total_ms", ctypes.c_double * 7)]
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("total_ms", ctypes.c_double * 8)]
 
 
 _vp = ctypes.c_void_p

@@ -203,23 +203,28 @@ __device__ __forceinline__ unsigned long long hi_of(uint4 v) {
     return (unsigned long long)v.z | ((unsigned long long)v.w << 32);
 }
 
-// Find or claim the slot of key (lo, hi); -1 when the probe limit is reached.
-// A packed key never has an all-ones half (every field stays below its
-// maximum), so a key read with an all-ones half is empty or being written and
-// is settled by the compare-and-swap; a key with two other halves is final.
+// Find or claim the slot of key (lo, hi), the first probe's key already read
+// (cur, at slot s0); -1 when the probe limit is reached.  A packed key never
+// has an all-ones half (every field stays below its maximum), so a key read
+// with an all-ones half is empty or being written and is settled by the
+// compare-and-swap; a key with two other halves is final.
 template <int STRIDE>
-__device__ int finsert(const FTable &t, unsigned long long lo, unsigned long long hi) {
-    uint32_t s = fslot(lo, hi, t.mask);
+__device__ __forceinline__ int finsert_from(const FTable &t, unsigned long long lo, unsigned long long hi,
+                                            uint32_t s0, uint4 cur, bool &claimed) {
+    claimed = false;
+    const unsigned long long clo = lo_of(cur), chi = hi_of(cur);
+    if (clo == lo && chi == hi) return (int)s0;
+    uint32_t s = s0;
     for (int p = 0; p < kFMaxProbe; ++p) {
         uint4 *r = t.rec + (size_t)s * STRIDE;
-        const uint4 cur = __ldcg(r);
-        const unsigned long long clo = lo_of(cur), chi = hi_of(cur);
-        if (clo == lo && chi == hi) return (int)s;
-        if (clo == kFEmpty || chi == kFEmpty) {
+        const uint4 c = p == 0 ? cur : __ldcg(r);
+        const unsigned long long a = lo_of(c), b = hi_of(c);
+        if (a == lo && b == hi) return (int)s;
+        if (a == kFEmpty || b == kFEmpty) {
             unsigned long long olo, ohi;
             fcas128(r, kFEmpty, kFEmpty, lo, hi, olo, ohi);
             if (olo == kFEmpty && ohi == kFEmpty) {
-                t.list[atomicAdd(t.count, 1)] = (int)s;
+                claimed = true;
                 return (int)s;
             }
             if (olo == lo && ohi == hi) return (int)s;
@@ -248,36 +253,104 @@ __device__ __forceinline__ int ffind(const FTable &t, unsigned long long lo, uns
 namespace {
 
 // Splat (Section 4.2) of the observation features with values [1, y] or
-// [1, y, n_y]: one thread per observation, grid-stride.
+// [1, y, n_y]: one thread per observation, block-strided rounds.  For each
+// vertex k in turn, runs of equal keys in neighbouring lanes (consecutive
+// observations -- pixels of a depth image in raster order -- mostly share
+// vertices) are merged by a segmented scan within 8-lane chunks, and only a
+// run's last lane inserts the key and issues the vector reductions.  The
+// slots a round claims are gathered in shared memory and appended to the
+// list with one global atomic per block and round.
 template <int d, bool PT2PL>
 __global__ void __launch_bounds__(kFThreads) k_feat_build(const float *__restrict__ F, int N, FScale S,
                                                           const float4 *__restrict__ Y,
                                                           const float4 *__restrict__ Yn, FTable t) {
     constexpr int STRIDE = PT2PL ? 4 : 2;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    constexpr int kCh = PT2PL ? 7 : 4;
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ int s_claim[kFThreads * (d + 1)];
+    __shared__ int s_n, s_base;
+    const int lane = threadIdx.x & 31;
+    int bad = 0;
+    for (int base = blockIdx.x * kFThreads; base < N; base += gridDim.x * kFThreads) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        const int i = base + threadIdx.x;
         FSimplex<d> sx;
-        if (!fembed<d>(F + (size_t)i * d, S, sx)) {
-            atomicOr(t.count + 1, kFlagRange);
-            continue;
+        bool valid = false;
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f), n = y;
+        if (i < N) {
+            valid = fembed<d>(F + (size_t)i * d, S, sx);
+            if (!valid) bad |= kFlagRange;
+            y = __ldg(Y + i);
+            if (PT2PL) n = __ldg(Yn + i);
         }
-        const float4 y = __ldg(Y + i);
-        float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (PT2PL) n = __ldg(Yn + i);
+        // pass 1: keys, run tails, and each tail's first probe in flight
+        unsigned long long lo[d + 1], hi[d + 1];
+        uint32_t s0[d + 1];
+        uint4 cur[d + 1];
+        unsigned tails = 0;
 #pragma unroll
         for (int k = 0; k <= d; ++k) {
-            unsigned long long lo, hi;
-            fpack<d>(sx, k, lo, hi);
-            const int s = finsert<STRIDE>(t, lo, hi);
-            if (s < 0) {
-                atomicOr(t.count + 1, kFlagCapacity);
-                continue;
-            }
-            const float b = sx.b[k];
-            uint4 *r = t.rec + (size_t)s * STRIDE;
-            fred_add4(r + 1, b, b * y.x, b * y.y, b * y.z);
-            if (PT2PL) fred_add4(r + 2, b * n.x, b * n.y, b * n.z, 0.f);
+            lo[k] = hi[k] = kFEmpty;
+            if (valid) fpack<d>(sx, k, lo[k], hi[k]);
+            const unsigned long long plo = __shfl_up_sync(kFull, lo[k], 1), phi = __shfl_up_sync(kFull, hi[k], 1);
+            const unsigned heads = __ballot_sync(kFull, (lane & 7) == 0 || plo != lo[k] || phi != hi[k]);
+            const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+            if (valid && tail) tails |= 1u << k;
+            s0[k] = fslot(lo[k], hi[k], t.mask);
+            if (valid && tail) cur[k] = __ldcg(t.rec + (size_t)s0[k] * STRIDE);
         }
+        // pass 2: settle each tail's slot (claiming new vertices)
+        int slot[d + 1];
+#pragma unroll
+        for (int k = 0; k <= d; ++k) {
+            slot[k] = -1;
+            if ((tails >> k) & 1u) {
+                bool claimed = false;
+                slot[k] = finsert_from<STRIDE>(t, lo[k], hi[k], s0[k], cur[k], claimed);
+                if (slot[k] < 0) bad |= kFlagCapacity;
+                else if (claimed) s_claim[atomicAdd(&s_n, 1)] = slot[k];
+            }
+        }
+        // pass 3: merge each run's values (segmented scan within 8-lane
+        // chunks, heads recomputed from the run tails) and reduce at its tail
+#pragma unroll
+        for (int k = 0; k <= d; ++k) {
+            const unsigned long long plo = __shfl_up_sync(kFull, lo[k], 1), phi = __shfl_up_sync(kFull, hi[k], 1);
+            const unsigned heads = __ballot_sync(kFull, (lane & 7) == 0 || plo != lo[k] || phi != hi[k]);
+            const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+            const float b = valid ? sx.b[k] : 0.0f;
+            float v[kCh];
+            v[0] = b;
+            v[1] = b * y.x;
+            v[2] = b * y.y;
+            v[3] = b * y.z;
+            if (PT2PL) {
+                v[4] = b * n.x;
+                v[5] = b * n.y;
+                v[6] = b * n.z;
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+#pragma unroll
+                for (int c = 0; c < kCh; ++c) {
+                    const float tv = __shfl_up_sync(kFull, v[c], o);
+                    if (lane - o >= head) v[c] += tv;
+                }
+            }
+            if (slot[k] >= 0) {
+                uint4 *r = t.rec + (size_t)slot[k] * STRIDE;
+                fred_add4(r + 1, v[0], v[1], v[2], v[3]);
+                if (PT2PL) fred_add4(r + 2, v[4], v[5], v[6], 0.f);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_base = s_n ? atomicAdd(t.count, s_n) : 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < s_n; j += kFThreads) t.list[s_base + j] = s_claim[j];
+        __syncthreads();  // s_n and s_claim are reused by the next round
     }
+    if (bad) atomicOr(t.count + 1, bad);
 }
 
 // Slice at the model features: out_i = sum_k b_k value(vertex k), absent
@@ -291,24 +364,48 @@ __global__ void __launch_bounds__(kFThreads) k_feat_slice(const float *__restric
         float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         FSimplex<d> sx;
         if (fembed<d>(F + (size_t)i * d, S, sx)) {
+            // first probe of every vertex, key and values, in flight at once
+            unsigned long long lo[d + 1], hi[d + 1];
+            uint32_t s0[d + 1];
+            uint4 key[d + 1];
+            float4 v0[d + 1], v1[d + 1];
 #pragma unroll
             for (int k = 0; k <= d; ++k) {
-                unsigned long long lo, hi;
-                fpack<d>(sx, k, lo, hi);
-                const int s = ffind<STRIDE>(t, lo, hi);
-                if (s < 0) continue;
+                fpack<d>(sx, k, lo[k], hi[k]);
+                s0[k] = fslot(lo[k], hi[k], t.mask);
+            }
+#pragma unroll
+            for (int k = 0; k <= d; ++k) {
+                const uint4 *r = t.rec + (size_t)s0[k] * STRIDE;
+                key[k] = __ldg(r);
+                v0[k] = __ldg(reinterpret_cast<const float4 *>(r + 1));
+                if (PT2PL) v1[k] = __ldg(reinterpret_cast<const float4 *>(r + 2));
+            }
+#pragma unroll
+            for (int k = 0; k <= d; ++k) {
+                const unsigned long long a = lo_of(key[k]), c = hi_of(key[k]);
+                if (!(a == lo[k] && c == hi[k])) {
+                    // absent, or the slot holds another key: probe on
+                    v0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (PT2PL) v1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!(a == kFEmpty && c == kFEmpty)) {
+                        const int s = ffind<STRIDE>(t, lo[k], hi[k]);
+                        if (s >= 0) {
+                            const uint4 *r = t.rec + (size_t)s * STRIDE;
+                            v0[k] = __ldg(reinterpret_cast<const float4 *>(r + 1));
+                            if (PT2PL) v1[k] = __ldg(reinterpret_cast<const float4 *>(r + 2));
+                        }
+                    }
+                }
                 const float b = sx.b[k];
-                const uint4 *r = t.rec + (size_t)s * STRIDE;
-                const float4 v0 = __ldg(reinterpret_cast<const float4 *>(r + 1));
-                acc[0] = fmaf(b, v0.x, acc[0]);
-                acc[1] = fmaf(b, v0.y, acc[1]);
-                acc[2] = fmaf(b, v0.z, acc[2]);
-                acc[3] = fmaf(b, v0.w, acc[3]);
+                acc[0] = fmaf(b, v0[k].x, acc[0]);
+                acc[1] = fmaf(b, v0[k].y, acc[1]);
+                acc[2] = fmaf(b, v0[k].z, acc[2]);
+                acc[3] = fmaf(b, v0[k].w, acc[3]);
                 if (PT2PL) {
-                    const float4 v1 = __ldg(reinterpret_cast<const float4 *>(r + 2));
-                    acc[4] = fmaf(b, v1.x, acc[4]);
-                    acc[5] = fmaf(b, v1.y, acc[5]);
-                    acc[6] = fmaf(b, v1.z, acc[6]);
+                    acc[4] = fmaf(b, v1[k].x, acc[4]);
+                    acc[5] = fmaf(b, v1[k].y, acc[5]);
+                    acc[6] = fmaf(b, v1[k].z, acc[6]);
                 }
             }
         } else {
@@ -541,21 +638,54 @@ fr_status feat_ensure(fr_ctx *ctx, uint32_t cap, int stride, long long list_len)
     return FR_OK;
 }
 
+// With profiling on, an event pair around each of the three launches
+// (classes FR_K_BUILD, FR_K_SLICE, FR_K_CLEAR), collected after the sync.
+struct FeatTimer {
+    fr_ctx *ctx;
+    int n = 0;
+    void begin(int cls) {
+        if (!ctx->profiling) return;
+        while (ctx->events.size() < 2 * (size_t)(n + 1)) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ctx->events.push_back(e);
+        }
+        if (ctx->event_class.size() < (size_t)(n + 1)) ctx->event_class.resize(n + 1);
+        ctx->event_class[n] = cls;
+        cudaEventRecord(ctx->events[2 * n], ctx->stream);
+    }
+    void end() {
+        if (!ctx->profiling) return;
+        cudaEventRecord(ctx->events[2 * n + 1], ctx->stream);
+        ++n;
+    }
+};
+
 template <int d>
-void launch_feat(bool pt2pl, const fr_ctx *ctx, const float *FX, int M, const float *FY, int N, const FScale &S,
-                 const float4 *Y, const float4 *Yn, FTable t, float *out) {
+void launch_feat(bool pt2pl, fr_ctx *ctx, FeatTimer &tm, const float *FX, int M, const float *FY, int N,
+                 const FScale &S, const float4 *Y, const float4 *Yn, FTable t, float *out) {
     const int gb = feat_grid(ctx, N), gs = feat_grid(ctx, M);
     // a list entry per claimed slot: at most (d+1) N
     const int limit = (int)std::min<long long>((long long)(d + 1) * N, (long long)t.mask + 1);
-    if (pt2pl) {
+    const int gc = feat_grid(ctx, limit);
+    tm.begin(FR_K_BUILD);
+    if (pt2pl)
         k_feat_build<d, true><<<gb, kFThreads, 0, ctx->stream>>>(FY, N, S, Y, Yn, t);
-        k_feat_slice<d, true><<<gs, kFThreads, 0, ctx->stream>>>(FX, M, S, t, out);
-        k_feat_clear<4><<<feat_grid(ctx, limit), kFThreads, 0, ctx->stream>>>(t, limit);
-    } else {
+    else
         k_feat_build<d, false><<<gb, kFThreads, 0, ctx->stream>>>(FY, N, S, Y, nullptr, t);
+    tm.end();
+    tm.begin(FR_K_SLICE);
+    if (pt2pl)
+        k_feat_slice<d, true><<<gs, kFThreads, 0, ctx->stream>>>(FX, M, S, t, out);
+    else
         k_feat_slice<d, false><<<gs, kFThreads, 0, ctx->stream>>>(FX, M, S, t, out);
-        k_feat_clear<2><<<feat_grid(ctx, limit), kFThreads, 0, ctx->stream>>>(t, limit);
-    }
+    tm.end();
+    tm.begin(FR_K_CLEAR);
+    if (pt2pl)
+        k_feat_clear<4><<<gc, kFThreads, 0, ctx->stream>>>(t, limit);
+    else
+        k_feat_clear<2><<<gc, kFThreads, 0, ctx->stream>>>(t, limit);
+    tm.end();
 }
 
 template <int d>
@@ -610,9 +740,10 @@ extern "C" FR_API fr_status fr_estep_features(fr_ctx *ctx, const float *d_FX, in
     FR_CUDA(ctx, cudaMemsetAsync(w->count, 0, 2 * sizeof(int), ctx->stream));
     FTable t{w->rec, w->list, w->count, cap - 1};
     const bool pt2pl = d_Yn != nullptr;
-#define FR_FEAT_CALL(DD)                                                                                      \
-    launch_feat<DD>(pt2pl, ctx, d_FX, (int)M, d_FY, (int)N, S, (const float4 *)d_Y, (const float4 *)d_Yn, t, \
-                    d_out)
+    FeatTimer tm{ctx};
+#define FR_FEAT_CALL(DD)                                                                                   \
+    launch_feat<DD>(pt2pl, ctx, tm, d_FX, (int)M, d_FY, (int)N, S, (const float4 *)d_Y, (const float4 *)d_Yn, \
+                    t, d_out)
     FR_FEATURE_DISPATCH(d, FR_FEAT_CALL)
 #undef FR_FEAT_CALL
     ctx->launches += 3;
@@ -627,6 +758,7 @@ extern "C" FR_API fr_status fr_estep_features(fr_ctx *ctx, const float *d_FX, in
         w->cap = 0;
         return ctx->cuda(se, "feature lattice");
     }
+    if (tm.n) collect_profile(ctx, tm.n);
     if (n_vertices) *n_vertices = w->h_count[0];
     return check_flags(ctx, w->h_count[1]);
 }

@@ -216,3 +216,19 @@ def test_exact_matches_oracle(ctx, orc, d, pt2pl):
     out, _ = ctx.estep_features(dev(FX), dev(FY), sf, dev(Y), dev(Yn) if pt2pl else None, exact=True)
     ref = orc.estep_features(FX, FY, sf, Y, Yn, backend=orc.EXACT)
     assert within(host(out), ref, Y) <= 1.0
+
+
+def test_profiling_times_the_three_kernels(ctx):
+    d, N = 6, 5000
+    FY = clustered(3, N, d)
+    Y = pad4(np.zeros((N, 3), np.float32))
+    sf = np.full(d, 0.3, np.float32)
+    ctx.profile(reset=True)
+    ctx.set_profiling(True)
+    try:
+        ctx.estep_features(dev(FY[:200]), dev(FY), sf, dev(Y))
+    finally:
+        ctx.set_profiling(False)
+    prof = ctx.profile(reset=True)
+    for name in ("build", "slice", "clear"):
+        assert prof[name][0] == 1 and prof[name][1] > 0.0
