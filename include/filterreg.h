@@ -247,6 +247,68 @@ FR_API fr_status fr_estep_storage(fr_ctx *ctx, const float *d_X, int64_t M, cons
                                   const float *d_Yn, int64_t N, float sigma, int32_t storage,
                                   const double T[16], float *d_out);
 
+/* ---- sharded single registration (model points split across ranks) -----------
+ * One rigid registration whose model X is partitioned across ranks (one
+ * process per GPU), every rank holding the whole observation Y: the E step's
+ * sums and the Gauss-Newton sums of Eq. 17-18 are sums over model points, so
+ * each rank forms its shard's normal equations, one all-reduce adds them, and
+ * every rank solves the same 6 x 6 system and makes the same update (Eq. 16,
+ * Eq. 18).  The collective is the caller's (NCCL, MPI, gloo, ...), passed as a
+ * callback; the library owns the EM loop.
+ *
+ * The FR_NE_VALS values of one shard's normal equations, in order: A's upper
+ * triangle row by row (21: A[0][0..5], A[1][1..5], ..., A[5][5]), b =
+ * sum J^T r (6), the sum of outlier weights M0/(M0+c), the cost sum r^2, and
+ * the number of model points with M0 > 0 -- all additive over shards. */
+#define FR_NE_VALS 30
+
+/* Normal-equation provider: at pose T (host double[16]) and scale sigma,
+ * write this rank's FR_NE_VALS values to ne; return 0 or an fr_status. */
+typedef int (*fr_ne_fn)(const double T[16], float sigma, double *ne, void *user);
+/* Sum of n doubles in place over the ranks of one registration; return 0 on
+ * success.  Every rank must call its collective the same number of times. */
+typedef int (*fr_allreduce_fn)(double *vals, int n, void *user);
+
+/* fr_rigid_normal_equations: one EM iteration's E step (lattice over d_Y at
+ * sigma = opt->sigma_start, sliced at T x) and the Gauss-Newton sums of the
+ * model points d_X (M x 4, one shard of a model of M_total points: Eq. 7's
+ * outlier constant c = w/(1-w) N / M_total) written to ne (host
+ * double[FR_NE_VALS]).  Options as for fr_register_rigid (iters, sigma_end and
+ * stop_twist ignored); FR_ENOTSUPPORTED with update_sigma; FR_EINVAL for
+ * M_total < M or a non-finite pose.  Synchronises the stream. */
+FR_API fr_status fr_rigid_normal_equations(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                           const float *d_Yn, int64_t N, const fr_options *opt, int64_t M_total,
+                                           const double T[16], double ne[FR_NE_VALS]);
+
+/* fr_rigid_solve_update: the M step from summed normal equations: delta zeta
+ * = -A^-1 b (float64 LDL^T; a pivot at or below 1e-12 of A's largest diagonal
+ * entry makes A count as singular), T_inout <- exp(delta zeta^) T_inout (Eq.
+ * 16, Eq. 18); |delta zeta| to *twist_norm (nullable).  FR_EINVAL if A is
+ * singular or not positive definite (T_inout unchanged).  Host only: needs
+ * no GPU and no context. */
+FR_API fr_status fr_rigid_solve_update(const double ne[FR_NE_VALS], double T_inout[16], double *twist_norm);
+
+/* fr_em_sharded: the EM loop of a sharded registration on the host: for each
+ * iteration k of opt's geometric sigma schedule (as fr_register_rigid), the
+ * provider's normal equations at the current pose, the all-reduce (NULL: a
+ * single rank), fr_rigid_solve_update (a singular system counts as a
+ * degenerate iteration and leaves the pose), and the stop test |delta zeta| <
+ * stop_twist.  report (nullable) gets iters_run, degenerate_iters,
+ * last_inliers, last_sum_w, last_cost, last_twist_norm and last_sigma.  A
+ * non-zero return of a callback ends the call with it (FR_ECUDA if it is not
+ * an fr_status).  FR_EINVAL for invalid options; FR_ENOTSUPPORTED with
+ * update_sigma. */
+FR_API fr_status fr_em_sharded(fr_ne_fn ne_fn, void *ne_user, fr_allreduce_fn allreduce, void *ar_user,
+                               const fr_options *opt, double T_inout[16], fr_report *report);
+
+/* fr_register_rigid_sharded: fr_em_sharded with this context's GPU as the
+ * provider (fr_rigid_normal_equations of this rank's shard d_X, M points of a
+ * model of M_total).  The lattice is rebuilt every iteration. */
+FR_API fr_status fr_register_rigid_sharded(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                           const float *d_Yn, int64_t N, const fr_options *opt, int64_t M_total,
+                                           fr_allreduce_fn allreduce, void *ar_user, double T_inout[16],
+                                           fr_report *report);
+
 /* ---- feature-space E step (Section 3.3, Eq. feature_estep) -------------------
  * The E step's Gaussian over d-dimensional per-point features (1 <= d <= 7)
  * with diagonal covariance diag(sigma_f^2): K_ij = exp(-sum_c (fx_ic -

@@ -470,6 +470,25 @@ def register_rigid(X, Y, Yn=None, *, sigma=0.02, sigma_end=None, w=0.1, iters=30
                      rep.last_cost, rep.last_twist_norm, rep.sigma_next, rep.last_sigma)
 
 
+def rigid_normal_equations(X, Y, Yn=None, *, sigma, M_total=None, T=None, w=0.1, residual=PT2PT,
+                           backend=LATTICE, blur=False, renormalize_normals=False) -> np.ndarray:
+    """One EM iteration's normal equations of the shard X of a model of M_total
+    points at pose T: (30,) = A's upper triangle row by row, b, sum_w, cost, inliers."""
+    X, Y = _pts(X), _pts(Y)
+    Yn = _pts(Yn) if Yn is not None else None
+    T = np.ascontiguousarray(np.eye(4) if T is None else T, dtype=np.float64)
+    o = _Options(backend, residual, int(blur), 1, float(sigma), float(sigma), float(w),
+                 int(renormalize_normals), 0.0, 0)
+    ne = np.zeros(30, np.float64)
+    L = _L()
+    L.or_rigid_normal_equations.argtypes = [_f32p, ctypes.c_int64, _f32p, _f32p, ctypes.c_int64,
+                                            ctypes.POINTER(_Options), ctypes.c_int64, _f64p, _f64p]
+    _check(L.or_rigid_normal_equations(_p(X, _f32p), X.shape[0], _p(Y, _f32p), _p(Yn, _f32p), Y.shape[0],
+                                       ctypes.byref(o), int(M_total or X.shape[0]), _p(T, _f64p),
+                                       _p(ne, _f64p)), "rigid_normal_equations")
+    return ne
+
+
 def align_error(X, T, Tgt) -> float:
     """Eq. 22: mean |(T - T_gt) x_ref|."""
     X = _pts(X)

@@ -135,6 +135,13 @@ double or_outlier_constant(double w, int64_t N, int64_t M, double sigma, int bac
 int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn,
                       int64_t N, const or_options *opt, double T[16], or_report *rep);
 
+/* One EM iteration's normal equations of a shard X (M points) of a model of
+ * M_total points at pose T and sigma = opt->sigma_start (Eq. 7's outlier
+ * constant from M_total): ne = A's upper triangle row by row (21),
+ * b = sum J^T r (6), sum of weights, cost, inliers -- additive over shards. */
+int or_rigid_normal_equations(const float *X, int64_t M, const float *Y, const float *Yn, int64_t N,
+                              const or_options *opt, int64_t M_total, const double T[16], double ne[30]);
+
 /* E-step sums at the model points moved by T (lattice or exact back end), for
  * parity of a single E step: out is M x (1 + 3 [+ 3]) = [M0, M1, Ns].        */
 int or_estep(const float *X, int64_t M, const float *Y, const float *Yn, int64_t N,

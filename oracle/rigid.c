@@ -218,6 +218,69 @@ int or_estep(const float *X, int64_t M, const float *Y, const float *Yn, int64_t
     return status != OR_OK ? status : s2;
 }
 
+/* The Gauss-Newton sums of Eq. 17-18 at pose T from the E-step sums es
+ * (M x vdim): out = A (36, row-major), b (6), sum of weights, cost, inliers,
+ * and the sigma moment sum_i Q_i / (M0_i + c) (update_sigma).  Each fixed
+ * chunk of GN_CHUNK points is summed in point order, then the chunk sums in
+ * chunk order -- the same result whatever the number of threads. */
+static int gn_sums(const float *X, int64_t M, const double *es, int vdim, const double T[16],
+                   double c_eff, double sigma, const or_options *opt, double out[GN_VALS])
+{
+    const int64_t nchunk = (M + GN_CHUNK - 1) / GN_CHUNK;
+    double *part = (double *)calloc((size_t)(nchunk ? nchunk : 1) * GN_VALS, sizeof(double));
+    if (!part)
+        return OR_ENOMEM;
+#pragma omp parallel for schedule(static)
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+        double *q = part + ch * GN_VALS; /* A (36), b (6), sum_w, cost, inliers, sum_q */
+        const int64_t i1 = (ch + 1) * GN_CHUNK < M ? (ch + 1) * GN_CHUNK : M;
+        for (int64_t i = ch * GN_CHUNK; i < i1; ++i) {
+            double x[3];
+            transform_point(T, X + 4 * i, x);
+            const double *e = es + i * vdim;
+            double Ns[3] = {0, 0, 0};
+            if (vdim == 7)
+                for (int c = 0; c < 3; ++c)
+                    Ns[c] = e[4 + c];
+            double Wt, r[3], J[18];
+            int rows = or_point_terms(x, e[0], e + 1, Ns, c_eff, sigma, opt->residual,
+                                      opt->renormalize_normals, &Wt, r, J);
+            if (rows == 0)
+                continue;
+            q[44] += 1.0;
+            q[42] += Wt;
+            if (opt->update_sigma) { /* Q_i / (M0_i + c) */
+                const double xx = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+                const double xm = x[0] * e[1] + x[1] * e[2] + x[2] * e[3];
+                q[45] += (e[0] * xx - 2.0 * xm + e[4]) / (e[0] + c_eff);
+            }
+            for (int a = 0; a < rows; ++a) {
+                q[43] += r[a] * r[a];
+                for (int p = 0; p < 6; ++p) {
+                    q[36 + p] += J[6 * a + p] * r[a];
+                    for (int qq = 0; qq < 6; ++qq)
+                        q[6 * p + qq] += J[6 * a + p] * J[6 * a + qq];
+                }
+            }
+        }
+    }
+    for (int v = 0; v < GN_VALS; ++v)
+        out[v] = 0.0;
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+        const double *q = part + ch * GN_VALS;
+        for (int v = 0; v < 36; ++v)
+            out[v] += q[v];
+        for (int p = 0; p < 6; ++p)
+            out[36 + p] += q[36 + p];
+        out[42] += q[42];
+        out[43] += q[43];
+        out[44] += q[44];
+        out[45] += q[45];
+    }
+    free(part);
+    return OR_OK;
+}
+
 int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn,
                       int64_t N, const or_options *opt, double T[16], or_report *rep)
 {
@@ -265,63 +328,15 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
             break;
 
         const double c_eff = or_outlier_constant(opt->w, N, M, sigma, opt->backend, opt->blur);
-        /* A = sum J^T J, b = sum J^T r (Eq. 17-18): each fixed chunk of
-         * GN_CHUNK points summed in point order, then the chunk sums in chunk
-         * order -- the same result whatever the number of threads. */
-        const int64_t nchunk = (M + GN_CHUNK - 1) / GN_CHUNK;
-        double *part = (double *)calloc((size_t)nchunk * GN_VALS, sizeof(double));
-        if (!part) {
-            status = OR_ENOMEM;
+        double g[GN_VALS];
+        status = gn_sums(X, M, es, vdim, T, c_eff, sigma, opt, g);
+        if (status != OR_OK)
             break;
-        }
-#pragma omp parallel for schedule(static)
-        for (int64_t ch = 0; ch < nchunk; ++ch) {
-            double *q = part + ch * GN_VALS; /* A (36), b (6), sum_w, cost, inliers */
-            const int64_t i1 = (ch + 1) * GN_CHUNK < M ? (ch + 1) * GN_CHUNK : M;
-            for (int64_t i = ch * GN_CHUNK; i < i1; ++i) {
-                double x[3];
-                transform_point(T, X + 4 * i, x);
-                const double *e = es + i * vdim;
-                double Ns[3] = {0, 0, 0};
-                if (vdim == 7)
-                    for (int c = 0; c < 3; ++c)
-                        Ns[c] = e[4 + c];
-                double Wt, r[3], J[18];
-                int rows = or_point_terms(x, e[0], e + 1, Ns, c_eff, sigma, opt->residual,
-                                          opt->renormalize_normals, &Wt, r, J);
-                if (rows == 0)
-                    continue;
-                q[44] += 1.0;
-                q[42] += Wt;
-                if (opt->update_sigma) { /* Q_i / (M0_i + c) */
-                    const double xx = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-                    const double xm = x[0] * e[1] + x[1] * e[2] + x[2] * e[3];
-                    q[45] += (e[0] * xx - 2.0 * xm + e[4]) / (e[0] + c_eff);
-                }
-                for (int a = 0; a < rows; ++a) {
-                    q[43] += r[a] * r[a];
-                    for (int p = 0; p < 6; ++p) {
-                        q[36 + p] += J[6 * a + p] * r[a];
-                        for (int qq = 0; qq < 6; ++qq)
-                            q[6 * p + qq] += J[6 * a + p] * J[6 * a + qq];
-                    }
-                }
-            }
-        }
-        double A[36] = {0}, b[6] = {0}, sum_w = 0.0, cost = 0.0, sum_q = 0.0;
-        int64_t inliers = 0;
-        for (int64_t ch = 0; ch < nchunk; ++ch) {
-            const double *q = part + ch * GN_VALS;
-            for (int v = 0; v < 36; ++v)
-                A[v] += q[v];
-            for (int p = 0; p < 6; ++p)
-                b[p] += q[36 + p];
-            sum_w += q[42];
-            cost += q[43];
-            inliers += (int64_t)q[44];
-            sum_q += q[45];
-        }
-        free(part);
+        double A[36], b[6];
+        memcpy(A, g, sizeof A);
+        memcpy(b, g + 36, sizeof b);
+        const double sum_w = g[42], cost = g[43], sum_q = g[45];
+        const int64_t inliers = (int64_t)g[44];
         if (opt->update_sigma && sum_w > 0.0) {
             const double s2 = sum_q / (3.0 * sum_w);
             rep->sigma_next = sqrt(s2 > 0.0 ? s2 : 0.0);
@@ -352,6 +367,60 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
     }
     or_lattice_free(lat);
     free(sched);
+    free(V);
+    free(es);
+    return status;
+}
+
+/* One EM iteration's normal equations for a shard of the model (X, M points
+ * of a model of M_total): the E step at sigma_start and pose T, the
+ * Gauss-Newton sums with Eq. 7's outlier constant from M_total.  ne = A's
+ * upper triangle row by row (21), b (6), sum of weights, cost, inliers. */
+int or_rigid_normal_equations(const float *X, int64_t M, const float *Y, const float *Yn, int64_t N,
+                              const or_options *opt, int64_t M_total, const double T[16], double ne[30])
+{
+    if (M <= 0 || N <= 0 || M_total < M || !(opt->sigma_start > 0.0) || !(opt->w >= 0.0 && opt->w < 1.0))
+        return OR_EINVAL;
+    if (opt->residual == OR_PT2PL && !Yn)
+        return OR_EINVAL;
+    if (opt->update_sigma)
+        return OR_EINVAL;
+    const int vdim = (opt->residual == OR_PT2PL) ? 7 : 4;
+    const float sigf = (float)opt->sigma_start;
+    const double sigma = (double)sigf;
+    double *V = observation_values(Y, opt->residual == OR_PT2PL ? Yn : NULL, N, vdim);
+    double *es = (double *)malloc((size_t)M * vdim * sizeof(double));
+    if (!V || !es) {
+        free(V);
+        free(es);
+        return OR_ENOMEM;
+    }
+    int status = OR_OK;
+    or_lattice *lat = NULL;
+    if (opt->backend == OR_LATTICE) {
+        lat = or_lattice_build(Y, V, N, vdim, sigf, &status);
+        if (lat && status == OR_OK && opt->blur)
+            or_lattice_blur(lat);
+    }
+    if (status == OR_OK && (lat || opt->backend != OR_LATTICE))
+        status = estep_at(X, M, Y, Yn, N, opt->backend, lat, sigma, T, vdim, es);
+    double g[GN_VALS];
+    if (status == OR_OK) {
+        const double c_eff = or_outlier_constant(opt->w, N, M_total, sigma, opt->backend, opt->blur);
+        status = gn_sums(X, M, es, vdim, T, c_eff, sigma, opt, g);
+    }
+    if (status == OR_OK) {
+        int t = 0;
+        for (int p = 0; p < 6; ++p)
+            for (int q = p; q < 6; ++q)
+                ne[t++] = g[6 * p + q];
+        for (int p = 0; p < 6; ++p)
+            ne[21 + p] = g[36 + p];
+        ne[27] = g[42];
+        ne[28] = g[43];
+        ne[29] = g[44];
+    }
+    or_lattice_free(lat);
     free(V);
     free(es);
     return status;

@@ -42,7 +42,13 @@ EXPORTED = [
     "fr_server_stats", "fr_server_destroy", "fr_nodegraph_create", "fr_nodegraph_destroy",
     "fr_register_nodegraph", "fr_nodegraph_system", "fr_nodegraph_warp",
     "fr_feature_embed", "fr_estep_features", "fr_gauss_transform_features",
+    "fr_rigid_normal_equations", "fr_rigid_solve_update", "fr_em_sharded", "fr_register_rigid_sharded",
 ]
+FR_NE_VALS = 30
+# fr_ne_fn and fr_allreduce_fn of include/filterreg.h
+NE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_float,
+                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p)
 FR_FEATURE_DMAX = 7
 FR_NOALLOC_MAX_OBS = 8192
 KERNEL_CLASSES = ("clear", "build", "blur", "em_iter", "convert", "ng_assemble", "ng_solve", "slice")
@@ -207,6 +213,13 @@ def load(build_if_missing: bool = True):
     L.fr_estep_features.argtypes = [_vp, _vp, _i64, _vp, _i64, ctypes.c_int32, _f32p, _vp, _vp, _vp,
                                     ctypes.POINTER(_i64)]
     L.fr_gauss_transform_features.argtypes = [_vp, _vp, _i64, _vp, _i64, ctypes.c_int32, _f32p, _vp, _vp, _vp]
+    L.fr_rigid_normal_equations.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.POINTER(fr_options), _i64,
+                                            _f64p, _f64p]
+    L.fr_rigid_solve_update.argtypes = [_f64p, _f64p, ctypes.POINTER(ctypes.c_double)]
+    L.fr_em_sharded.argtypes = [NE_FN, _vp, ALLREDUCE_FN, _vp, ctypes.POINTER(fr_options), _f64p,
+                                ctypes.POINTER(fr_report)]
+    L.fr_register_rigid_sharded.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.POINTER(fr_options), _i64,
+                                            ALLREDUCE_FN, _vp, _f64p, ctypes.POINTER(fr_report)]
     for name in EXPORTED:  # every entry point must resolve (ctypes restype defaults to int)
         getattr(L, name)
     _lib = L
@@ -253,6 +266,77 @@ def _dev_ptr(t, name, rows=None, cols=4):
     if rows is not None and t.shape[0] != rows:
         raise ValueError(f"{name} must have {rows} rows")
     return t.data_ptr()
+
+
+# ---- sharded single registration (host-side EM loop, caller's collective) ----
+
+class _Callbacks:
+    """ctypes callbacks around Python callables; the first exception raised
+    inside one is kept and re-raised after the library call returns."""
+
+    def __init__(self, provider=None, allreduce=None):
+        self.error = None
+        self.ne = NE_FN(self._ne) if provider is not None else NE_FN()
+        self.ar = ALLREDUCE_FN(self._ar) if allreduce is not None else ALLREDUCE_FN()
+        self._provider, self._allreduce = provider, allreduce
+
+    def _ne(self, T, sigma, ne, user):
+        try:
+            Tm = np.ctypeslib.as_array(T, shape=(16,)).reshape(4, 4).copy()
+            out = np.asarray(self._provider(Tm, float(sigma)), dtype=np.float64).reshape(-1)
+            if out.shape[0] != FR_NE_VALS:
+                raise ValueError(f"a provider returns {FR_NE_VALS} values")
+            np.ctypeslib.as_array(ne, shape=(FR_NE_VALS,))[:] = out
+            return 0
+        except BaseException as e:  # noqa: BLE001 -- re-raised after the call
+            self.error = self.error or e
+            return FR_EINVAL
+
+    def _ar(self, vals, n, user):
+        try:
+            v = np.ctypeslib.as_array(vals, shape=(n,))
+            v[:] = np.asarray(self._allreduce(v.copy()), dtype=np.float64)
+            return 0
+        except BaseException as e:  # noqa: BLE001
+            self.error = self.error or e
+            return FR_ECUDA
+
+
+def torch_allreduce(group=None, device="cpu"):
+    """An all-reduce for the sharded registration over torch.distributed
+    (gloo with device="cpu", NCCL with a CUDA device): values -> summed values."""
+    import torch
+    import torch.distributed as dist
+
+    def ar(v):
+        t = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(device)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        return t.cpu().numpy()
+    return ar
+
+
+def rigid_solve_update(ne, T):
+    """fr_rigid_solve_update: (T_new (4,4), |delta zeta|, ok) from summed normal equations."""
+    ne = np.ascontiguousarray(ne, dtype=np.float64).reshape(-1)
+    Tm = _pose(T)
+    tn = ctypes.c_double(0.0)
+    st = load().fr_rigid_solve_update(ne.ctypes.data_as(_f64p), Tm.ctypes.data_as(_f64p), ctypes.byref(tn))
+    return Tm, float(tn.value), st == FR_OK
+
+
+def em_sharded(provider, allreduce=None, T0=None, **opts):
+    """fr_em_sharded: the host EM loop with provider(T (4,4), sigma) -> 30
+    normal-equation values of this rank and allreduce(values) -> summed values
+    (None: one rank).  Returns (T, Report, status)."""
+    cb = _Callbacks(provider, allreduce)
+    o = options(**opts)
+    T = _pose(T0)
+    rep = fr_report()
+    st = load().fr_em_sharded(cb.ne, None, cb.ar, None, ctypes.byref(o), T.ctypes.data_as(_f64p),
+                              ctypes.byref(rep))
+    if cb.error is not None:
+        raise cb.error
+    return T, _report(rep), int(st)
 
 
 def _pose(T) -> np.ndarray:
@@ -397,6 +481,35 @@ class Context:
         st = L.fr_register_rigid(self._h, pX, X.shape[0], pY, pN, Y.shape[0], ctypes.byref(o),
                                  T.ctypes.data_as(_f64p), ctypes.byref(rep))
         self._check(st, "fr_register_rigid")
+        return T, _report(rep)
+
+    def rigid_normal_equations(self, X, Y, Yn=None, sigma=0.02, M_total=None, T=None, **opts):
+        """fr_rigid_normal_equations: (30,) float64 -- A's upper triangle, b, sum_w, cost, inliers."""
+        o = options(sigma_start=float(sigma), sigma_end=float(sigma), **opts)
+        Tm = _pose(T)
+        ne = np.zeros(FR_NE_VALS, np.float64)
+        pN = _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None
+        st = load().fr_rigid_normal_equations(self._h, _dev_ptr(X, "X"), X.shape[0], _dev_ptr(Y, "Y"), pN,
+                                              Y.shape[0], ctypes.byref(o), int(M_total or X.shape[0]),
+                                              Tm.ctypes.data_as(_f64p), ne.ctypes.data_as(_f64p))
+        self._check(st, "fr_rigid_normal_equations")
+        return ne
+
+    def register_rigid_sharded(self, X, Y, Yn=None, M_total=None, allreduce=None, T0=None, **opts):
+        """fr_register_rigid_sharded: this rank's shard X of a model of M_total
+        points; allreduce(values) -> summed values over the ranks (None: one
+        rank; see torch_allreduce).  Returns (T, Report)."""
+        cb = _Callbacks(None, allreduce)
+        o = options(**opts)
+        T = _pose(T0)
+        rep = fr_report()
+        pN = _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None
+        st = load().fr_register_rigid_sharded(self._h, _dev_ptr(X, "X"), X.shape[0], _dev_ptr(Y, "Y"), pN,
+                                              Y.shape[0], ctypes.byref(o), int(M_total or X.shape[0]), cb.ar,
+                                              None, T.ctypes.data_as(_f64p), ctypes.byref(rep))
+        if cb.error is not None:
+            raise cb.error
+        self._check(st, "fr_register_rigid_sharded")
         return T, _report(rep)
 
     def register_rigid_host(self, X, Y, Yn=None, T0=None, **opts):

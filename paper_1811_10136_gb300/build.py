@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfilterreg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kernels.cu", "api.cu", "batch.cu", "articulated.cu", "noalloc.cu", "serve.cu", "nodegraph.cu",
-           "exact.cu", "features.cu"]
+           "exact.cu", "features.cu", "sharded.cu"]
 
 
 def _nvcc() -> str:

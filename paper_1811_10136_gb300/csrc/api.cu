@@ -444,16 +444,11 @@ void collect_profile(fr_ctx *ctx, int kernels) {
 // c = w/(1-w) N/M (Eq. 7) in the lattice kernel's units (times sigma^3 G).
 // Returns true when sigma changes during the schedule (annealing).
 bool fill_iter_params(const fr_options *o, int64_t M, int64_t N, IterParams *ip) {
-    const double s0 = o->sigma_start, s1 = o->sigma_end;
     const double c = (double)o->w / (1.0 - (double)o->w) * ((double)N / (double)M);
     const double G = lattice_kernel_mass(o->blur);
     bool changes = false;
     for (int k = 0; k < o->iters; ++k) {
-        float sig;
-        if (o->iters == 1 || s0 == s1)
-            sig = (float)s0;
-        else
-            sig = (float)(s0 * std::pow(s1 / s0, (double)k / (double)(o->iters - 1)));
+        const float sig = schedule_sigma(o, k);
         IterParams &p = ip[k];
         p.sigma = sig;
         float s[3];
@@ -956,9 +951,12 @@ FR_API fr_status fr_estep_storage(fr_ctx *ctx, const float *d_X, int64_t M, cons
 
 // ---- rigid registration -----------------------------------------------------
 
+// m_outlier: the model point count in Eq. 7's outlier constant (the whole
+// model's when X is one shard of it; 0 = M).
 static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                                      const float *d_Yn, int64_t N, const fr_options *opt,
-                                     double T_inout[16], fr_report *rep, bool safe) {
+                                     double T_inout[16], fr_report *rep, bool safe, int64_t m_outlier = 0) {
+    const int64_t Mo = m_outlier > 0 ? m_outlier : M;
     const int pt2pl = opt->residual == FR_PT2PL;
     const uint32_t cap = table_slots(N, safe);
     FR_TRY(ensure_small(ctx, opt->iters, 1));
@@ -974,10 +972,10 @@ static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, c
         // iteration 0 at sigma_start; the steps set up the later ones
         fr_options o0 = *opt;
         o0.sigma_end = opt->sigma_start;
-        fill_iter_params(&o0, M, N, ctx->h_ip);
+        fill_iter_params(&o0, Mo, N, ctx->h_ip);
         p.annealed = 1;
     } else {
-        p.annealed = fill_iter_params(opt, M, N, ctx->h_ip) ? 1 : 0;
+        p.annealed = fill_iter_params(opt, Mo, N, ctx->h_ip) ? 1 : 0;
     }
     plan_grids(ctx, p, M, N, cap);
     FR_TRY(ensure_small(ctx, opt->iters, p.gs));
@@ -998,7 +996,7 @@ static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, c
     j->stop_twist = opt->stop_twist;
     for (int i = 0; i < 16; ++i) j->T0[i] = T_inout[i];
     for (int i = 1; i <= 3; ++i) j->sig_alpha[i - 1] = kAlpha / std::sqrt((double)(i * (i + 1)));
-    j->sig_c = (double)opt->w / (1.0 - (double)opt->w) * ((double)N / (double)M);
+    j->sig_c = (double)opt->w / (1.0 - (double)opt->w) * ((double)N / (double)Mo);
     j->sig_G = lattice_kernel_mass(0);
     j->sig_floor = (double)opt->sigma_end;
     DeviceState *hs = ctx->h_state;
@@ -1043,6 +1041,40 @@ static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, c
     const fr_status s = register_rigid_once(ctx, d_X, M, d_Y, d_Yn, N, opt, T_inout, rep, false);
     if (s != FR_ECAPACITY) return s;
     return register_rigid_once(ctx, d_X, M, d_Y, d_Yn, N, opt, T_inout, rep, true);
+}
+
+FR_API fr_status fr_rigid_normal_equations(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
+                                           const float *d_Yn, int64_t N, const fr_options *opt, int64_t M_total,
+                                           const double T[16], double ne[FR_NE_VALS]) {
+    if (!ctx) return FR_EINVAL;
+    FR_TRY(validate_options(ctx, opt));
+    FR_TRY(validate_cloud(ctx, d_X, M, "d_X"));
+    FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));
+    if (opt->residual == FR_PT2PL) FR_TRY(validate_cloud(ctx, d_Yn, N, "d_Yn (normals, required for FR_PT2PL)"));
+    if (opt->update_sigma) return ctx->fail(FR_ENOTSUPPORTED, "normal equations are taken at a given sigma");
+    if (M_total < M || M_total > (1ll << 40)) return ctx->fail(FR_EINVAL, "M_total must be >= M");
+    if (!T || !ne) return ctx->fail(FR_EINVAL, "T and ne must not be NULL");
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(T[i])) return ctx->fail(FR_EINVAL, "T is not finite");
+    cudaSetDevice(ctx->device);
+    // one EM iteration at sigma_start: its E step and reduced sums (the pose
+    // update it also makes is discarded)
+    fr_options o = *opt;
+    o.iters = 1;
+    o.sigma_end = o.sigma_start;
+    o.stop_twist = 0.0f;
+    double Tw[16];
+    for (int i = 0; i < 16; ++i) Tw[i] = T[i];
+    const float *yn = opt->residual == FR_PT2PL ? d_Yn : nullptr;
+    fr_status st = register_rigid_once(ctx, d_X, M, d_Y, yn, N, &o, Tw, nullptr, false, M_total);
+    if (st == FR_ECAPACITY) {
+        for (int i = 0; i < 16; ++i) Tw[i] = T[i];
+        st = register_rigid_once(ctx, d_X, M, d_Y, yn, N, &o, Tw, nullptr, true, M_total);
+    }
+    if (st != FR_OK) return st;
+    const double *v = ctx->h_state->sums;
+    for (int i = 0; i < FR_NE_VALS; ++i) ne[i] = v[i];
+    return FR_OK;
 }
 
 FR_API fr_status fr_register_rigid(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,

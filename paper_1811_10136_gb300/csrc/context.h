@@ -41,6 +41,14 @@ inline void feature_scales(float sigma, float s[3]) {
         s[i - 1] = (float)(kAlpha / std::sqrt((double)(i * (i + 1))) / (double)sigma);
 }
 
+// Sigma of iteration k of the geometric schedule from sigma_start to
+// sigma_end over o->iters iterations (Section 3.2's annealing), in float.
+inline float schedule_sigma(const fr_options *o, int k) {
+    const double s0 = o->sigma_start, s1 = o->sigma_end;
+    if (o->iters <= 1 || s0 == s1) return (float)s0;
+    return (float)(s0 * std::pow(s1 / s0, (double)k / (double)(o->iters - 1)));
+}
+
 inline uint32_t pow2_at_least(long long n) {
     uint32_t c = 1024;
     while ((long long)c < n && c < (1u << 30)) c <<= 1;

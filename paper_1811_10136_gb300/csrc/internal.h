@@ -68,6 +68,9 @@ struct DeviceState {
     int nvert;             // vertices created by the last build
     int builds;            // lattices built during this call
     long long nvert_total; // vertices summed over this call's builds
+    // the last iteration's reduced Gauss-Newton values: A's upper triangle row
+    // by row (21), b = sum J^T r (6), sum of weights, cost, inliers, sigma moment
+    double sums[32];
 };
 
 // A lattice hash table: a power-of-two array of 64-byte slot records, two

@@ -304,6 +304,7 @@ __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *
     if (lane == 27) st->sum_w = t;
     if (lane == 28) st->cost = t;
     if (lane == 29) st->inliers = (long long)(t + 0.5);
+    if (lane < kRigidVals) st->sums[lane] = t;
     if (ip_next) {
         // sigma^2 = sum_i Q_i / (M0_i + c) / (3 sum_i W_i) (floored; kept when
         // no point had observations), rounded to float, and the parameters of
