@@ -68,16 +68,18 @@ def _bumpy_sphere_points(rng, n, centres, amp, width):
 def sphere_bumps_pair(seed: int, n_model: int = 2000, n_obs: int = 2000, n_bumps: int = 8,
                       amp: float = 0.1, width: float = 0.2, max_angle_deg: float = 30.0,
                       max_trans: float = 0.1, noise: float = 0.005,
-                      outlier_frac: float = 0.1) -> RigidPair:
+                      outlier_frac: float = 0.1, exact_angle: bool = False) -> RigidPair:
     """Unit sphere with Gaussian bumps; the observation is an independent sample
-    of the same surface under a random rigid motion, with isotropic noise and
-    uniform outliers (outlier_frac * n_obs extra points) in its bounding box."""
+    of the same surface under a random rigid motion (rotation up to
+    max_angle_deg about a uniform axis, exactly max_angle_deg with
+    exact_angle), with isotropic noise and uniform outliers (outlier_frac *
+    n_obs extra points) in its bounding box."""
     rng = np.random.default_rng(seed)
     c = rng.normal(size=(n_bumps, 3))
     c /= np.linalg.norm(c, axis=1, keepdims=True)
     X = _bumpy_sphere_points(rng, n_model, c, amp, width)
     Ys = _bumpy_sphere_points(rng, n_obs, c, amp, width)
-    R = random_rotation(rng, math.radians(max_angle_deg))
+    R = random_rotation(rng, math.radians(max_angle_deg), exact=exact_angle)
     t = rng.uniform(-max_trans, max_trans, size=3)
     T = make_T(R, t)
     Y = Ys @ R.T + t + rng.normal(scale=noise, size=Ys.shape)
@@ -387,6 +389,19 @@ def articulated_pair(seed: int, n_points: int = 30000, max_joint_deg: float = 20
     return ArticulatedPair(tree, Xref, body, _pad4(Yw[perm]), _pad4(Nw[perm]), root_gt, q_gt,
                            {"workload": "kintree_capsules", "seed": seed, "M": n_points,
                             "N": Yw.shape[0], "dof": 6 + tree.nj})
+
+
+def posed_surface_error(pair: ArticulatedPair, root_T: np.ndarray, q: np.ndarray):
+    """Mean and 99th-percentile distance between the model points posed at
+    (root_T, q) and at the pair's true pose (an evaluation metric: joints that
+    barely move the surface do not count against an estimate)."""
+    Ta = pose_bodies(pair.tree, root_T, q)
+    Tg = pose_bodies(pair.tree, pair.root_gt, pair.q_gt)
+    X, B = pair.Xref[:, :3].astype(np.float64), pair.body
+    Pa = np.einsum("nij,nj->ni", Ta[B][:, :3, :3], X) + Ta[B][:, :3, 3]
+    Pg = np.einsum("nij,nj->ni", Tg[B][:, :3, :3], X) + Tg[B][:, :3, 3]
+    d = np.linalg.norm(Pa - Pg, axis=1)
+    return float(d.mean()), float(np.percentile(d, 99))
 
 
 # ---------------------------------------------------------------------------
