@@ -356,7 +356,6 @@ void ng_assemble(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Table t, int it
     Ed.stats = g->stats;
     launch_ng_edges(Ed, s);
     sp.end();
-    ctx->launches += 2;
 }
 
 void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Spans &sp, cudaStream_t s) {
@@ -388,13 +387,13 @@ void ng_solve_update(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, Spans &sp, 
     }
     launch_ng_update(g->K, g->x, g->node_T, g->node_dq, g->stats + 2, s);
     sp.end();
-    ctx->launches += 2 + 2 * run.pcg_iters;
 }
 
 // The registration's kernels after the uploads, on stream s: node dual
 // quaternions, the first lattice, then per iteration (a rebuild when sigma
 // changes,) the assembly and the solve with the node update; finally the
-// last table is freed.  Returns the number of kernels.
+// last table is freed.  Returns the number of kernels (the callers count
+// them: directly issued, or once per graph replay).
 int ng_issue(fr_ctx *ctx, fr_nodegraph *g, const NgRun &run, const Table tab[2], int iters, int64_t N,
              cudaStream_t s, Spans &sp) {
     int launches = 1;

@@ -160,3 +160,18 @@ def test_rejects_bad_models(ctx, small):
     with pytest.raises(fr.FilterRegError) as e:
         ng.register(dev(small.Y), None, blur=1, iters=2)
     assert e.value.status == fr.FR_ENOTSUPPORTED
+
+
+def test_launch_count_is_the_same_replayed_or_issued(ctx, small):
+    # every kernel counted once, whether the registration is issued directly
+    # or replayed from its captured graph
+    ng = model(ctx, small)
+    kw = dict(lam=10.0, pcg_iters=5, residual=1, iters=3, sigma_start=f32(0.02), sigma_end=f32(0.02), w=f32(0.1))
+    counts = []
+    for use_graph in (0, 1, 1):
+        n0 = ctx.kernel_launches
+        ng.register(dev(small.Y), dev(small.Yn), use_graph=use_graph, **kw)
+        counts.append(ctx.kernel_launches - n0)
+    assert counts[0] == counts[1] == counts[2], counts
+    # per iteration: points + edges, preconditioner set-up, 2 per PCG iteration, node update
+    assert counts[0] >= 3 * (2 + 1 + 2 * 5 + 1)
