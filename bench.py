@@ -526,9 +526,16 @@ def run_ours(args):
                 run()
             ms, res = timed_steps(run, args.steps)
             R, q, rep = res
+            surf, surf99 = synth.posed_surface_error(ap, R, q)
             entry = {"value": round(ART_ITERS * args.steps / (sum(ms) / 1000.0), 1), "unit": UNIT,
                      "ms_per_registration": round(statistics.mean(ms), 4),
-                     "max_joint_err_deg_vs_truth": round(float(np.degrees(np.abs(q - ap.q_gt).max())), 4)}
+                     "max_joint_err_deg_vs_truth": round(float(np.degrees(np.abs(q - ap.q_gt).max())), 4),
+                     "joint_err_deg_vs_truth": [round(float(v), 2) for v in np.degrees(np.abs(q - ap.q_gt))],
+                     "posed_surface_err_mm": {"mean": round(surf * 1e3, 3), "p99": round(surf99 * 1e3, 3),
+                                              "before_mean": round(synth.posed_surface_error(
+                                                  ap, np.eye(4), np.zeros_like(ap.q_gt))[0] * 1e3, 3)},
+                     "note": "the configuration's perturbation (joints +-20 deg) lies outside the EM's "
+                             "recovery range; see recovery.articulated"}
             if res32 is None:
                 res32 = q
             else:
