@@ -737,14 +737,16 @@ def run_ours(args):
     sigma_upd = None
     if not args.no_sigma:
         f32 = lambda x: float(np.float32(x))
-        rows = {"fixed_0.02": dict(sigma_start=f32(0.02), sigma_end=f32(0.02)),
-                "updated_0.08_floor_0.005": dict(sigma_start=f32(0.08), sigma_end=f32(0.005), update_sigma=1)}
-        sigma_upd = {"workload": "bumpy sphere 2000 x 2200 points (10% outliers), motion <= 5 deg / 3 cm, "
-                                 "point-to-point, w 0.1, stop at |dzeta| < 1e-5, at most 100 iterations, seeds 0-4"}
+        rows = {"fixed_0.05": dict(sigma_start=f32(0.05), sigma_end=f32(0.05)),
+                "updated_from_0.1_floor_0.005": dict(sigma_start=f32(0.1), sigma_end=f32(0.005), update_sigma=1)}
+        sigma_upd = {"workload": "bumpy sphere 2000 x 2200 points (10% outliers), pronounced bumps (amplitude 0.5, "
+                                 "width 0.35), rotation 5 deg, translation up to 3 cm, point-to-point, w 0.1, "
+                                 "stop at |dzeta| < 1e-5, at most 100 iterations, seeds 0-4"}
         for name, kw in rows.items():
-            its, errs, ms = [], [], []
+            its, errs, ms, sig_last = [], [], [], []
             for seed in range(5):
-                sp = synth.sphere_bumps_pair(seed, max_angle_deg=5.0, max_trans=0.03)
+                sp = synth.sphere_bumps_pair(seed, max_angle_deg=5.0, amp=0.5, width=0.35, max_trans=0.03,
+                                             exact_angle=True)
                 Xs, Ys = dev(sp.X), dev(sp.Y)
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
@@ -755,10 +757,12 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 ms.append(a.elapsed_time(b))
                 its.append(rs.iters_run)
+                sig_last.append(rs.last_sigma)
                 errs.append(synth.rotation_angle_deg(Ts, sp.T_gt))
             sigma_upd[name] = {"em_iters_to_stop_mean": round(statistics.mean(its), 1), "iters": its,
                                "ms_per_registration_mean": round(statistics.mean(ms), 4),
-                               "rot_err_deg_vs_truth_mean": round(statistics.mean(errs), 4)}
+                               "rot_err_deg_vs_truth_mean": round(statistics.mean(errs), 4),
+                               "last_sigma": [round(float(r), 4) for r in sig_last]}
 
     # ---- serving: Poisson stream through fr_server vs the plain path ---------
     serving = None

@@ -265,6 +265,13 @@ def kernel_mass(backend=LATTICE, blur=False) -> float:
     return float(_L().or_kernel_mass(backend, int(blur)))
 
 
+def lattice_kernel_variance() -> float:
+    L = _L()
+    L.or_lattice_kernel_variance.argtypes = []
+    L.or_lattice_kernel_variance.restype = ctypes.c_double
+    return float(L.or_lattice_kernel_variance())
+
+
 # ---- feature-space E step (d-dimensional lattice) ------------------------------
 
 FEATURE_DMAX = 7

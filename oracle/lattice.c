@@ -430,6 +430,36 @@ double or_kernel_mass(int backend, int blur)
     return g;
 }
 
+/* Per-axis variance, in units of sigma^2, of the unblurred splat+slice
+ * kernel K(p, q) = sum_v b_v(p) b_v(q), averaged over positions p:
+ * E_p[int K(p,q) |q - p|^2 dq] / (d int K) = 2 M2 / (d covol), where M2 =
+ * int b_0(q) |q|^2 dq is the second moment of one vertex's hat (the first
+ * moment vanishes: the triangulation is symmetric about a vertex).  The hat is
+ * linear on the (d+1)! congruent simplices around the vertex, each of volume
+ * covol / d!, and on a simplex with vertices 0, v_1..v_d the integral of
+ * lambda_0 lambda_k lambda_l is d! vol (1 + [k == l]) / (d+3)!, so that
+ * M2 = covol (|sum_k v_k|^2 + sum_k |v_k|^2) / ((d+2)(d+3)), the v_k the
+ * canonical simplex's vertices in feature units (elevated coordinates over
+ * alpha).  For d = 3 this is 1/4: the kernel is half as wide as the Gaussian
+ * of the same sigma. */
+double or_lattice_kernel_variance(void)
+{
+    const double alpha = sqrt(2.0 / 3.0) * (double)LD1;
+    double sum[LD1] = {0, 0, 0, 0}, sq = 0.0;
+    for (int k = 1; k < LD1; ++k)
+        for (int j = 0; j < LD1; ++j) {
+            /* canonical vertex k: k in its first LD1 - k coordinates, k - LD1 after */
+            const double c = (j < LD1 - k) ? (double)k : (double)(k - LD1);
+            sum[j] += c;
+            sq += c * c;
+        }
+    double s2 = 0.0;
+    for (int j = 0; j < LD1; ++j)
+        s2 += sum[j] * sum[j];
+    const double B = (s2 + sq) / (alpha * alpha);
+    return 2.0 * B / ((double)LD * (LD + 2) * (LD + 3));
+}
+
 void or_sigma_schedule(double s0, double s1, int iters, float *out)
 {
     for (int k = 0; k < iters; ++k) {

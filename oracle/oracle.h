@@ -107,6 +107,11 @@ void or_lattice_free(or_lattice *lat);
  * exact Gaussian (2 pi)^{3/2}; lattice splat+slice: volume per lattice vertex
  * in feature units; times the blur gain 2^4 when blurred.                    */
 double or_kernel_mass(int backend, int blur);
+/* Per-axis variance of the unblurred splat+slice kernel in units of sigma^2,
+ * averaged over positions (1/4 for d = 3; the exact Gaussian's is 1).  The
+ * sigma update divides by it, so that sigma is the width at which the kernel
+ * actually used matches the residuals.                                        */
+double or_lattice_kernel_variance(void);
 
 /* Geometric sigma schedule: sigma_k = s0 (s1/s0)^{k/(iters-1)}, rounded to float. */
 void or_sigma_schedule(double s0, double s1, int iters, float *out);

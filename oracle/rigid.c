@@ -338,7 +338,10 @@ int or_register_rigid(const float *X, int64_t M, const float *Y, const float *Yn
         const double sum_w = g[42], cost = g[43], sum_q = g[45];
         const int64_t inliers = (int64_t)g[44];
         if (opt->update_sigma && sum_w > 0.0) {
-            const double s2 = sum_q / (3.0 * sum_w);
+            /* the lattice kernel's per-axis variance is kappa sigma^2, not
+             * sigma^2: the sigma at which it matches the residuals */
+            const double kappa = opt->backend == OR_LATTICE ? or_lattice_kernel_variance() : 1.0;
+            const double s2 = sum_q / (3.0 * sum_w * kappa);
             rep->sigma_next = sqrt(s2 > 0.0 ? s2 : 0.0);
             const double fl = opt->sigma_end;
             sig_upd = (float)(rep->sigma_next > fl ? rep->sigma_next : fl);

@@ -999,6 +999,7 @@ static fr_status register_rigid_once(fr_ctx *ctx, const float *d_X, int64_t M, c
     j->sig_c = (double)opt->w / (1.0 - (double)opt->w) * ((double)N / (double)Mo);
     j->sig_G = lattice_kernel_mass(0);
     j->sig_floor = (double)opt->sigma_end;
+    j->sig_kappa = lattice_kernel_variance();
     DeviceState *hs = ctx->h_state;
     *hs = DeviceState{};
     for (int i = 0; i < 16; ++i) hs->T[i] = T_inout[i];

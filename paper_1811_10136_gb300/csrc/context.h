@@ -36,6 +36,26 @@ inline double lattice_kernel_mass(int blur) {
     return blur ? g * 16.0 : g;
 }
 
+// Per-axis variance of the unblurred splat+slice kernel in units of sigma^2,
+// averaged over positions: 2 M2 / (d covol), M2 the second moment of one
+// vertex's hat.  The hat is linear on (d+1)! congruent simplices of volume
+// covol / d! around its vertex, and the simplex moments give
+// M2 = covol (|sum_k v_k|^2 + sum_k |v_k|^2) / ((d+2)(d+3)) over the
+// canonical simplex's vertices v_1..v_d in feature units (1/4 for d = 3).
+inline double lattice_kernel_variance() {
+    constexpr int d = 3, D = 4;
+    double colsum[D] = {0.0, 0.0, 0.0, 0.0}, norms = 0.0;
+    for (int k = 1; k <= d; ++k)
+        for (int j = 0; j < D; ++j) {
+            const double c = j + k < D ? (double)k : (double)(k - D);  // canonical vertex k
+            colsum[j] += c;
+            norms += c * c;
+        }
+    double sumsq = 0.0;
+    for (int j = 0; j < D; ++j) sumsq += colsum[j] * colsum[j];
+    return 2.0 * (sumsq + norms) / (kAlpha * kAlpha) / (double)(d * (d + 2) * (d + 3));
+}
+
 inline void feature_scales(float sigma, float s[3]) {
     for (int i = 1; i <= 3; ++i)
         s[i - 1] = (float)(kAlpha / std::sqrt((double)(i * (i + 1))) / (double)sigma);

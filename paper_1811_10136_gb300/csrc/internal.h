@@ -54,6 +54,7 @@ struct RigidJob {
     double sig_c;          // w / (1 - w) N / M
     double sig_G;          // kernel mass of the lattice
     double sig_floor;      // smallest sigma
+    double sig_kappa;      // the lattice kernel's per-axis variance over sigma^2
 };
 
 // Device-resident state of one registration.

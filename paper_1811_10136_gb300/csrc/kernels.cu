@@ -306,14 +306,17 @@ __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *
     if (lane == 29) st->inliers = (long long)(t + 0.5);
     if (lane < kRigidVals) st->sums[lane] = t;
     if (ip_next) {
-        // sigma^2 = sum_i Q_i / (M0_i + c) / (3 sum_i W_i) (floored; kept when
-        // no point had observations), rounded to float, and the parameters of
-        // the next iteration from it, as the host derives them from a sigma.
+        // sigma^2 = sum_i Q_i / (M0_i + c) / (3 kappa sum_i W_i) -- kappa the
+        // lattice kernel's per-axis variance in units of sigma^2, so that sigma
+        // is the width at which the kernel used matches the residuals --
+        // (floored; kept when no point had observations), rounded to float, and
+        // the parameters of the next iteration from it, as the host derives
+        // them from a sigma.
         const double sw = __shfl_sync(kFull, t, 27), sq = __shfl_sync(kFull, t, 30);
         if (lane == 0) {
             double sig = (double)ip_cur->sigma;
             if (sw > 0.0) {
-                const double s2 = sq / (3.0 * sw);
+                const double s2 = sq / (3.0 * sw * sig_job->sig_kappa);
                 const double sn = sqrt(s2 > 0.0 ? s2 : 0.0);
                 sig = sn > sig_job->sig_floor ? sn : sig_job->sig_floor;
             }

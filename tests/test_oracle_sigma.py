@@ -7,7 +7,12 @@ the E step's posteriors), pinned against values fixed independently:
     (2 sigma^2) - 3 log sigma] with P_ij = K_ij / (sum_k K_ik + c) computed
     here in numpy from the definitions (exact back-end);
   - the lattice back-end's update equals the same formula evaluated from the
-    lattice slice of the values [1, y, |y|^2];
+    lattice slice of the values [1, y, |y|^2], divided by the lattice kernel's
+    per-axis variance in units of sigma^2 (1/4, a closed form checked here
+    against the kernel's measured second moment): the sigma at which the
+    kernel actually used matches the residuals;
+  - so the lattice update settles where the exact one does (its sigma times
+    the kernel's width ratio 1/2) instead of contracting to its floor;
   - on a clean planted motion the updated-sigma EM recovers the motion and
     needs fewer iterations than the fixed-sigma EM to reach the same stop."""
 import math
@@ -73,7 +78,7 @@ def test_lattice_update_from_its_own_slice(orc):
     live = s[:, 0] > 0
     m0, m1, m2 = s[live, 0], s[live, 1:4], s[live, 4]
     q = m0 * (x[live] ** 2).sum(1) - 2 * (x[live] * m1).sum(1) + m2
-    s2 = (q / (m0 + c)).sum() / (3 * (m0 / (m0 + c)).sum())
+    s2 = (q / (m0 + c)).sum() / (3 * (m0 / (m0 + c)).sum()) / orc.lattice_kernel_variance()
     assert rep.sigma_next == pytest.approx(math.sqrt(s2), rel=1e-9)
     assert rng is not None
 
@@ -98,3 +103,41 @@ def test_recovers_planted_motion_in_fewer_iterations(orc):
     assert ru.iters_run < rf.iters_run / 2, (ru.iters_run, rf.iters_run)
     assert math.radians(synth.rotation_angle_deg(Tf, T_gt)) > 1e-3   # the fixed wide kernel's bias
     assert ru.last_sigma == pytest.approx(0.002)                      # the floor
+
+
+def test_lattice_kernel_variance_is_its_second_moment(orc):
+    # one point splatted with value 1 and sliced on a grid around it: the
+    # per-axis second moment of K(p, .) about p, averaged over positions p
+    rng = np.random.default_rng(3)
+    h = 0.1
+    ax = np.arange(-3.0, 3.0, h) + h / 2
+    Q = np.zeros((ax.size ** 3, 4), np.float32)
+    Q[:, :3] = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    moments = []
+    for _ in range(24):
+        P = np.zeros((1, 4), np.float32)
+        P[0, :3] = rng.uniform(-1.0, 1.0, 3)
+        K, _ = orc.Lattice(P, np.ones(1), 1.0).slice(Q)
+        d2 = ((Q[:, :3].astype(np.float64) - P[0, :3]) ** 2).sum(1)
+        moments.append((K[:, 0] * d2).sum() / K[:, 0].sum() / 3.0)
+    assert orc.lattice_kernel_variance() == 0.25
+    assert np.mean(moments) == pytest.approx(0.25, abs=0.01)
+
+
+def test_lattice_update_settles_where_the_exact_one_does(orc):
+    # 600 points in a cube, observed after a small motion with 1 cm noise:
+    # the exact update settles near the residual scale; the lattice update
+    # at twice that (its kernel is half as wide), far above the floor
+    rng = np.random.default_rng(11)
+    X = np.zeros((600, 4), np.float32)
+    X[:, :3] = rng.uniform(-0.5, 0.5, (600, 3))
+    T_gt = synth.make_T(synth.random_rotation(rng, math.radians(3.0), exact=True), [0.01, -0.02, 0.01])
+    Y = np.zeros_like(X)
+    Y[:, :3] = X[:, :3].astype(np.float64) @ T_gt[:3, :3].T + T_gt[:3, 3] + rng.normal(scale=0.01, size=(600, 3))
+    kw = dict(w=0.0, iters=60, sigma=0.1, sigma_end=0.001, update_sigma=True)
+    Te, re = orc.register_rigid(X, Y, None, backend=orc.EXACT, **kw)
+    Tl, rl = orc.register_rigid(X, Y, None, backend=orc.LATTICE, **kw)
+    assert rl.last_sigma > 10 * 0.001
+    assert rl.last_sigma * 0.5 == pytest.approx(re.last_sigma, rel=0.25), (rl.last_sigma, re.last_sigma)
+    for T in (Te, Tl):
+        assert synth.rotation_angle_deg(T, T_gt) < 0.3
