@@ -940,12 +940,14 @@ static fr_status estep_impl(fr_ctx *ctx, const float *d_X, int64_t M, const floa
 FR_API fr_status fr_estep(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                           const float *d_Yn, int64_t N, float sigma, int blur, const double T[16],
                           float *d_out) {
+    fr::NvtxRange nvtx_("fr_estep");
     return estep_impl(ctx, d_X, M, d_Y, d_Yn, N, sigma, blur, FR_FP32, T, d_out);
 }
 
 FR_API fr_status fr_estep_storage(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                                   const float *d_Yn, int64_t N, float sigma, int32_t storage,
                                   const double T[16], float *d_out) {
+    fr::NvtxRange nvtx_("fr_estep_storage");
     return estep_impl(ctx, d_X, M, d_Y, d_Yn, N, sigma, 0, storage, T, d_out);
 }
 
@@ -1047,6 +1049,7 @@ static fr_status register_rigid_impl(fr_ctx *ctx, const float *d_X, int64_t M, c
 FR_API fr_status fr_rigid_normal_equations(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                                            const float *d_Yn, int64_t N, const fr_options *opt, int64_t M_total,
                                            const double T[16], double ne[FR_NE_VALS]) {
+    fr::NvtxRange nvtx_("fr_rigid_normal_equations");
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_options(ctx, opt));
     FR_TRY(validate_cloud(ctx, d_X, M, "d_X"));
@@ -1081,6 +1084,7 @@ FR_API fr_status fr_rigid_normal_equations(fr_ctx *ctx, const float *d_X, int64_
 FR_API fr_status fr_register_rigid(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                                    const float *d_Yn, int64_t N, const fr_options *opt,
                                    double T_inout[16], fr_report *report) {
+    fr::NvtxRange nvtx_("fr_register_rigid");
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_options(ctx, opt));
     FR_TRY(validate_cloud(ctx, d_X, M, "d_X"));
@@ -1098,6 +1102,7 @@ FR_API fr_status fr_register_rigid_host(fr_ctx *ctx, const float *h_X, int64_t M
                                         const float *h_Y, const float *h_Yn, int64_t N,
                                         const fr_options *opt, double T_inout[16],
                                         fr_report *report) {
+    fr::NvtxRange nvtx_("fr_register_rigid_host");
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_options(ctx, opt));
     if (!h_X || !h_Y || M < 1 || N < 1 || M > (1ll << 30) || N > (1ll << 30))

@@ -269,6 +269,7 @@ extern "C" FR_API fr_status fr_register_articulated(fr_ctx *ctx, const float *d_
                                                     const float *d_Yn, int64_t N,
                                                     const fr_options *opt, double root_T_inout[16],
                                                     double *q_inout, fr_report *report) {
+    fr::NvtxRange nvtx_("fr_register_articulated");
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_options(ctx, opt));
     if (opt->update_sigma) return ctx->fail(FR_ENOTSUPPORTED, "the sigma update is implemented for rigid registration");

@@ -603,6 +603,7 @@ extern "C" {
 
 FR_API fr_status fr_register_rigid_batch(fr_ctx *ctx, fr_batch_item *items, int n_items,
                                          const fr_options *opt, fr_report *reports) {
+    fr::NvtxRange nvtx_("fr_register_rigid_batch");
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_batch(ctx, items, n_items, opt, false));
     cudaSetDevice(ctx->device);
@@ -611,6 +612,7 @@ FR_API fr_status fr_register_rigid_batch(fr_ctx *ctx, fr_batch_item *items, int 
 
 FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items, int n_items,
                                               const fr_options *opt, fr_report *reports) {
+    fr::NvtxRange nvtx_("fr_register_rigid_batch_host");
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_batch(ctx, items, n_items, opt, true));
     cudaSetDevice(ctx->device);
@@ -686,6 +688,7 @@ FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items,
 FR_API fr_status fr_autotune_batch(fr_ctx *ctx, const fr_batch_item *items, int n_items, const fr_options *opt,
                                    int objective, int reps, fr_tune_params *best, double *best_ms,
                                    double *default_ms) {
+    fr::NvtxRange nvtx_("fr_autotune_batch");
     if (!ctx || !best) return FR_EINVAL;
     if (objective != FR_TUNE_THROUGHPUT && objective != FR_TUNE_LATENCY)
         return ctx->fail(FR_EINVAL, "objective must be FR_TUNE_THROUGHPUT or FR_TUNE_LATENCY");

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "filterreg.h"
 #include "internal.h"
 
@@ -76,6 +78,16 @@ inline uint32_t pow2_at_least(long long n) {
 }
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// A named NVTX range over one C-ABI call: what profilers show and filter on
+// (ncu --nvtx --nvtx-include "<name>/"); without an attached tool a push and
+// a pop are a few instructions.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Everything a captured graph bakes in besides the job descriptor.
 struct GraphKey {

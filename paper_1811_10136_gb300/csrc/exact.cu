@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kExThreads) k_gauss_exact(const float4 *__rest
 extern "C" FR_API fr_status fr_gauss_transform(fr_ctx *ctx, const float *d_X, int64_t M, const float *d_Y,
                                                const float *d_Yn, int64_t N, float sigma, const double T[16],
                                                float *d_out) {
+    fr::NvtxRange nvtx_("fr_gauss_transform");
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_cloud(ctx, d_X, M, "d_X"));
     FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));

@@ -718,6 +718,7 @@ void launch_exact(bool pt2pl, const float *FX, int M, const float *FY, const flo
 extern "C" FR_API fr_status fr_estep_features(fr_ctx *ctx, const float *d_FX, int64_t M, const float *d_FY,
                                               int64_t N, int32_t d, const float *sigma_f, const float *d_Y,
                                               const float *d_Yn, float *d_out, int64_t *n_vertices) {
+    fr::NvtxRange nvtx_("fr_estep_features");
     if (!ctx) return FR_EINVAL;
     FScale S;
     FR_TRY(feat_scales(ctx, d, sigma_f, &S, nullptr));
@@ -765,6 +766,7 @@ extern "C" FR_API fr_status fr_estep_features(fr_ctx *ctx, const float *d_FX, in
 
 extern "C" FR_API fr_status fr_feature_embed(fr_ctx *ctx, const float *d_F, int64_t n, int32_t d,
                                              const float *sigma_f, int32_t *d_keys, float *d_bary) {
+    fr::NvtxRange nvtx_("fr_feature_embed");
     if (!ctx) return FR_EINVAL;
     FScale S;
     FR_TRY(feat_scales(ctx, d, sigma_f, &S, nullptr));
@@ -788,6 +790,7 @@ extern "C" FR_API fr_status fr_gauss_transform_features(fr_ctx *ctx, const float
                                                         const float *d_FY, int64_t N, int32_t d,
                                                         const float *sigma_f, const float *d_Y,
                                                         const float *d_Yn, float *d_out) {
+    fr::NvtxRange nvtx_("fr_gauss_transform_features");
     if (!ctx) return FR_EINVAL;
     FScale S, inv;
     FR_TRY(feat_scales(ctx, d, sigma_f, &S, &inv));

@@ -87,6 +87,7 @@ constexpr int kPairJ[kNgPairs] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
 FR_API fr_status fr_nodegraph_create(fr_ctx *ctx, const float *d_Xref, const int32_t *d_knn,
                                      const float *d_skw, int64_t M, const double *node_pos, int K,
                                      const int32_t *edges, int E, fr_nodegraph **out) {
+    fr::NvtxRange nvtx_("fr_nodegraph_create");
     if (!ctx || !out) return FR_EINVAL;
     *out = nullptr;
     FR_TRY(validate_cloud(ctx, d_Xref, M, "d_Xref"));
@@ -597,6 +598,7 @@ fr_status ng_run(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_
 FR_API fr_status fr_register_nodegraph(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_Yn,
                                        int64_t N, const fr_options *opt, double lambda, int pcg_iters,
                                        double *node_T, fr_report *rep) {
+    fr::NvtxRange nvtx_("fr_register_nodegraph");
     FR_TRY(ng_validate(ctx, g, d_Y, d_Yn, N, opt, lambda, pcg_iters));
     if (!node_T) return ctx->fail(FR_EINVAL, "node_T must not be NULL");
     for (int64_t i = 0; i < 16 * (int64_t)g->K; ++i)
@@ -620,6 +622,7 @@ FR_API fr_status fr_register_nodegraph(fr_ctx *ctx, fr_nodegraph *g, const float
 FR_API fr_status fr_nodegraph_system(fr_ctx *ctx, fr_nodegraph *g, const float *d_Y, const float *d_Yn,
                                      int64_t N, const fr_options *opt, double lambda,
                                      const double *node_T, double *A_out, double *g_out, fr_report *rep) {
+    fr::NvtxRange nvtx_("fr_nodegraph_system");
     FR_TRY(ng_validate(ctx, g, d_Y, d_Yn, N, opt, lambda, 0));
     if (!node_T) return ctx->fail(FR_EINVAL, "node_T must not be NULL");
     cudaSetDevice(ctx->device);
@@ -635,6 +638,7 @@ FR_API fr_status fr_nodegraph_system(fr_ctx *ctx, fr_nodegraph *g, const float *
 }
 
 FR_API fr_status fr_nodegraph_warp(fr_ctx *ctx, fr_nodegraph *g, const double *node_T, float *d_out) {
+    fr::NvtxRange nvtx_("fr_nodegraph_warp");
     if (!ctx || !g || !node_T || !d_out) return FR_EINVAL;
     if (g->ctx != ctx) return ctx->fail(FR_EINVAL, "the node graph belongs to another context");
     if (!aligned16(d_out)) return ctx->fail(FR_EINVAL, "d_out must be 16-byte aligned (M x 4 floats)");

@@ -287,6 +287,7 @@ struct fr_server {
     int tab_of(const Request &r, int build) const { return r.annealed ? build % r.ntab : 0; }
 
     fr_status launch_tick() {
+        NvtxRange nvtx_("fr_server_tick");
         std::vector<Seg> segs;
         segs.reserve(live.size() * 3);
         int blk = 0;

@@ -183,6 +183,7 @@ extern "C" FR_API fr_status fr_register_rigid_sharded(fr_ctx *ctx, const float *
                                                       const float *d_Yn, int64_t N, const fr_options *opt,
                                                       int64_t M_total, fr_allreduce_fn allreduce, void *ar_user,
                                                       double T_inout[16], fr_report *report) {
+    fr::NvtxRange nvtx_("fr_register_rigid_sharded");
     if (!ctx) return FR_EINVAL;
     FR_TRY(validate_options(ctx, opt));
     FR_TRY(validate_cloud(ctx, d_X, M, "d_X"));
