@@ -130,12 +130,12 @@ __device__ __forceinline__ void block_partial(const Acc<KAHAN> &acc, float2 *par
 // tri_index(p, q) (p <= q) holds A[p][q], then D[p] (p == q) or L[q][p].
 // ---------------------------------------------------------------------------
 
-// 1/d in float64 from the float reciprocal refined by two Newton steps
-// (error squared at each step: ~1e-7 -> 1e-14 -> below float64 rounding),
-// a handful of float64 operations instead of a full division sequence.
+// 1/d in float64 from the float reciprocal refined by one Newton step (the
+// relative error squares: ~1e-7 -> ~1e-14, far below what the solve's pivot
+// floor of 1e-12 and the float32 sums it is fed need), two dependent float64
+// operations instead of a full division sequence on the narrow float64 pipe.
 __device__ __forceinline__ double rcp64(double d) {
     double r = (double)(1.0f / (float)d);
-    r = fma(r, fma(-d, r, 1.0), r);
     r = fma(r, fma(-d, r, 1.0), r);
     return r;
 }
@@ -199,8 +199,23 @@ __device__ Solved warp_solve6(double t /* lane v: reduced value v */) {
 // warp: R = I + A W + B W^2 and V = I + B W + C W^2 with W = [omega]_x,
 // W^2 = omega omega^T - th^2 I; A, B, C by their series for th < 0.25 (each
 // term below 2e-17 at the cut-off), else from sin and cos.
+__device__ void warp_se3_update_cols(double dz, double *T /* row-major 4x4, global */,
+                                     double *smem /* 24 doubles */, double c0, double c1, double c2);
 __device__ void warp_se3_update(double dz, double *T /* row-major 4x4, global */,
                                 double *smem /* 24 doubles */) {
+    const int lane = threadIdx.x & 31, j = lane & 3;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    if (lane < 12) {
+        c0 = T[j];
+        c1 = T[4 + j];
+        c2 = T[8 + j];
+    }
+    warp_se3_update_cols(dz, T, smem, c0, c1, c2);
+}
+// The same with lane l < 12's column entries T[j], T[4 + j], T[8 + j]
+// (j = l mod 4) already loaded.
+__device__ void warp_se3_update_cols(double dz, double *T /* row-major 4x4, global */,
+                                     double *smem /* 24 doubles */, double c0, double c1, double c2) {
     const int lane = threadIdx.x & 31;
     double w[3], v[3];
 #pragma unroll
@@ -247,7 +262,7 @@ __device__ void warp_se3_update(double dz, double *T /* row-major 4x4, global */
     double tn = 0.0;
     if (lane < 12) {
         const int i = lane / 4, j = lane % 4;
-        tn = smem[3 * i] * T[j] + smem[3 * i + 1] * T[4 + j] + smem[3 * i + 2] * T[8 + j];
+        tn = smem[3 * i] * c0 + smem[3 * i + 1] * c1 + smem[3 * i + 2] * c2;
         if (j == 3) tn += smem[18 + i];
     }
     __syncwarp();
@@ -263,6 +278,14 @@ __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *
     __shared__ DF tot_s[32];
     __shared__ double sm_e[24];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the pose entries the update multiplies, loaded while the partials are summed
+    double tc0 = 0.0, tc1 = 0.0, tc2 = 0.0;
+    if (warp == 0 && lane < 12) {
+        const int j = lane & 3;
+        tc0 = st->T[j];
+        tc1 = st->T[4 + j];
+        tc2 = st->T[8 + j];
+    }
     // Warp w reduces values w, w + 8, w + 16, w + 24: all of its loads are
     // issued before any of them is consumed.
     constexpr int kPer = 4;      // values per warp
@@ -344,7 +367,7 @@ __device__ void finish_iteration(const float2 *partials, int rows, DeviceState *
         if (lane == 0) st->degenerate += 1;
         return;
     }
-    warp_se3_update(r.dz, st->T, sm_e);
+    warp_se3_update_cols(r.dz, st->T, sm_e, tc0, tc1, tc2);
     // |delta zeta| (a diagnostic and the stop test) in float
     float n2 = lane < 6 ? (float)r.dz * (float)r.dz : 0.0f;
 #pragma unroll
