@@ -156,6 +156,13 @@ FR_API int64_t fr_ctx_kernel_launches(const fr_ctx *ctx);
  * duration; fr_ctx_profile copies the totals to *out and, if reset, zeroes
  * them.  Off by default. */
 FR_API fr_status fr_ctx_set_profiling(fr_ctx *ctx, int on);
+/* fr_debug_fail_allocations: host-side fault injection for testing error
+ * paths -- of the library's next device allocations (any context, any
+ * thread) the first `after` proceed and the `n` after them fail as on a full
+ * device, so that the call making them returns FR_ENOMEM with whatever it had
+ * allocated before; n = 0 clears.  Nothing faults on the GPU.  FR_EINVAL for
+ * a negative argument. */
+FR_API fr_status fr_debug_fail_allocations(int32_t after, int32_t n);
 /* Bytes this context has copied host->device and device->host (all calls). */
 FR_API fr_status fr_ctx_transfer_bytes(const fr_ctx *ctx, int64_t *h2d, int64_t *d2h);
 FR_API fr_status fr_ctx_profile(fr_ctx *ctx, fr_profile *out, int reset);

@@ -43,6 +43,7 @@ EXPORTED = [
     "fr_register_nodegraph", "fr_nodegraph_system", "fr_nodegraph_warp",
     "fr_feature_embed", "fr_estep_features", "fr_gauss_transform_features",
     "fr_rigid_normal_equations", "fr_rigid_solve_update", "fr_em_sharded", "fr_register_rigid_sharded",
+    "fr_debug_fail_allocations",
 ]
 FR_NE_VALS = 30
 # fr_ne_fn and fr_allreduce_fn of include/filterreg.h
@@ -213,6 +214,7 @@ def load(build_if_missing: bool = True):
     L.fr_estep_features.argtypes = [_vp, _vp, _i64, _vp, _i64, ctypes.c_int32, _f32p, _vp, _vp, _vp,
                                     ctypes.POINTER(_i64)]
     L.fr_gauss_transform_features.argtypes = [_vp, _vp, _i64, _vp, _i64, ctypes.c_int32, _f32p, _vp, _vp, _vp]
+    L.fr_debug_fail_allocations.argtypes = [ctypes.c_int32, ctypes.c_int32]
     L.fr_rigid_normal_equations.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.POINTER(fr_options), _i64,
                                             _f64p, _f64p]
     L.fr_rigid_solve_update.argtypes = [_f64p, _f64p, ctypes.POINTER(ctypes.c_double)]
@@ -322,6 +324,14 @@ def rigid_solve_update(ne, T):
     tn = ctypes.c_double(0.0)
     st = load().fr_rigid_solve_update(ne.ctypes.data_as(_f64p), Tm.ctypes.data_as(_f64p), ctypes.byref(tn))
     return Tm, float(tn.value), st == FR_OK
+
+
+def debug_fail_allocations(after: int = 0, n: int = 0) -> None:
+    """fr_debug_fail_allocations: of the library's next device allocations the
+    first `after` proceed and the `n` after them fail (testing; n = 0 clears)."""
+    st = load().fr_debug_fail_allocations(int(after), int(n))
+    if st != FR_OK:
+        raise FilterRegError(st, "fr_debug_fail_allocations: arguments must be >= 0")
 
 
 def em_sharded(provider, allreduce=None, T0=None, **opts):

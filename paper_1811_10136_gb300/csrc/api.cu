@@ -43,6 +43,8 @@ void free_tables(fr_ctx *ctx) {
 
 fr_status alloc_table(fr_ctx *ctx, int i, uint32_t cap) {
     Table &t = ctx->tables[i];
+    cudaFree(ctx->lists[i]);  // left by an earlier attempt that failed part way
+    ctx->lists[i] = nullptr;
     FR_CUDA(ctx, dev_alloc(&ctx->lists[i], cap));
     FR_CUDA(ctx, dev_alloc(&t.keys, (size_t)cap * kRecWords));
     FR_CUDA(ctx, cudaMemsetAsync(t.keys, 0, table_bytes(cap), ctx->stream));
@@ -59,25 +61,28 @@ fr_status alloc_table(fr_ctx *ctx, int i, uint32_t cap) {
 namespace fr {
 fr_status ensure_tables(fr_ctx *ctx, uint32_t cap, bool blur, bool compact) {
     if (cap > ctx->table_cap) {
+        // Captured graphs go with the buffers they name, before any new
+        // allocation can fail; a failed one leaves table_cap at 0, so the
+        // next call allocates all again.
         cudaStreamSynchronize(ctx->stream);
+        ctx->ws_gen++;
+        drop_graphs(ctx);
         free_tables(ctx);
         for (int i = 0; i < 3; ++i) FR_TRY(alloc_table(ctx, i, cap));
         ctx->table_cap = cap;
-        ctx->ws_gen++;
-        drop_graphs(ctx);
     }
     if (compact && !ctx->tables[3].keys) {  // 16-bit storage: a fourth table in rotation
-        FR_TRY(alloc_table(ctx, 3, ctx->table_cap));
         ctx->ws_gen++;
         drop_graphs(ctx);
+        FR_TRY(alloc_table(ctx, 3, ctx->table_cap));
     }
     if (blur && !ctx->blur) {
+        ctx->ws_gen++;
+        drop_graphs(ctx);
         FR_CUDA(ctx, dev_alloc(&ctx->blur, (size_t)ctx->table_cap * kRecWords));
         // Blur passes write only the slots their lattice holds and free them
         // afterwards: the scratch table starts empty and stays so.
         FR_CUDA(ctx, cudaMemsetAsync(ctx->blur, 0, table_bytes(ctx->table_cap), ctx->stream));
-        ctx->ws_gen++;
-        drop_graphs(ctx);
     }
     return FR_OK;
 }
@@ -89,16 +94,20 @@ namespace {
 
 namespace fr {
 fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows) {
+    // each buffer on its own test: an attempt that failed part way leaves
+    // the ones it made, and the next call makes the rest
     if (!ctx->d_state) {
         FR_CUDA(ctx, dev_alloc(&ctx->d_state, 1));
-        FR_CUDA(ctx, dev_alloc(&ctx->d_job, 1));
-        FR_CUDA(ctx, cudaMallocHost((void **)&ctx->h_job, sizeof(RigidJob)));
-        FR_CUDA(ctx, cudaMallocHost((void **)&ctx->h_state, sizeof(DeviceState)));
         FR_CUDA(ctx, cudaMemsetAsync(ctx->d_state, 0, sizeof(DeviceState), ctx->stream));
     }
+    if (!ctx->d_job) FR_CUDA(ctx, dev_alloc(&ctx->d_job, 1));
+    if (!ctx->h_job) FR_CUDA(ctx, cudaMallocHost((void **)&ctx->h_job, sizeof(RigidJob)));
+    if (!ctx->h_state) FR_CUDA(ctx, cudaMallocHost((void **)&ctx->h_state, sizeof(DeviceState)));
     int need = iters > 1 ? iters : 1;
     if (need > ctx->ip_cap) {
         cudaStreamSynchronize(ctx->stream);
+        ctx->ws_gen++;
+        drop_graphs(ctx);
         cudaFree(ctx->d_ip);
         cudaFreeHost(ctx->h_ip);
         ctx->d_ip = nullptr;
@@ -109,18 +118,16 @@ fr_status ensure_small(fr_ctx *ctx, int iters, int grid_rows) {
         FR_CUDA(ctx, dev_alloc(&ctx->d_ip, cap));
         FR_CUDA(ctx, cudaMallocHost((void **)&ctx->h_ip, cap * sizeof(IterParams)));
         ctx->ip_cap = cap;
-        ctx->ws_gen++;
-        drop_graphs(ctx);
     }
     if (grid_rows > ctx->partial_rows) {
         cudaStreamSynchronize(ctx->stream);
+        ctx->ws_gen++;
+        drop_graphs(ctx);
         cudaFree(ctx->partials);
         ctx->partials = nullptr;
         ctx->partial_rows = 0;
         FR_CUDA(ctx, dev_alloc(&ctx->partials, (size_t)grid_rows * kRigidVals));
         ctx->partial_rows = grid_rows;
-        ctx->ws_gen++;
-        drop_graphs(ctx);
     }
     return FR_OK;
 }
@@ -426,6 +433,15 @@ fr_status validate_options(fr_ctx *ctx, const fr_options *o) {
 
 namespace fr {
 
+std::atomic<int> &alloc_skip() {
+    static std::atomic<int> n{0};
+    return n;
+}
+std::atomic<int> &alloc_fail() {
+    static std::atomic<int> n{0};
+    return n;
+}
+
 // After the stream is synchronised: add the event-pair durations of the last
 // launches to the per-class totals.
 void collect_profile(fr_ctx *ctx, int kernels) {
@@ -660,6 +676,14 @@ FR_API fr_status fr_ctx_transfer_bytes(const fr_ctx *ctx, int64_t *h2d, int64_t 
     if (!ctx) return FR_EINVAL;
     if (h2d) *h2d = ctx->h2d_bytes;
     if (d2h) *d2h = ctx->d2h_bytes;
+    return FR_OK;
+}
+
+FR_API fr_status fr_debug_fail_allocations(int32_t after, int32_t n) {
+    if (after < 0 || n < 0) return FR_EINVAL;
+    fr::alloc_fail().store(0);
+    fr::alloc_skip().store(n > 0 ? after : 0);
+    fr::alloc_fail().store(n);
     return FR_OK;
 }
 

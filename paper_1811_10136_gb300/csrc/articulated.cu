@@ -107,12 +107,11 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
     const int pt2pl = opt->residual == FR_PT2PL;
     if (!ctx->art) ctx->art = new ArtWorkspace();
     ArtWorkspace *w = ctx->art;
-    if (!w->d_job) {
-        FR_CUDA(ctx, dev_alloc(&w->d_job, 1));
-        FR_CUDA(ctx, dev_alloc(&w->d_state, 1));
-        FR_CUDA(ctx, cudaMallocHost((void **)&w->h_job, sizeof(ArtJob)));
-        FR_CUDA(ctx, cudaMallocHost((void **)&w->h_state, sizeof(ArtState)));
-    }
+    // each on its own test: a failed attempt may have made some of them
+    if (!w->d_job) FR_CUDA(ctx, dev_alloc(&w->d_job, 1));
+    if (!w->d_state) FR_CUDA(ctx, dev_alloc(&w->d_state, 1));
+    if (!w->h_job) FR_CUDA(ctx, cudaMallocHost((void **)&w->h_job, sizeof(ArtJob)));
+    if (!w->h_state) FR_CUDA(ctx, cudaMallocHost((void **)&w->h_state, sizeof(ArtState)));
     const uint32_t cap = table_slots(N, safe);
     FR_TRY(ensure_small(ctx, opt->iters, 1));
     FR_TRY(ensure_tables(ctx, cap, false, opt->storage != FR_FP32));

@@ -663,7 +663,7 @@ FR_API fr_status fr_register_rigid_batch_host(fr_ctx *ctx, fr_batch_item *items,
             w->d_chunks = w->h_chunks = nullptr;
             w->chunks_cap = 0;
             const size_t cap = std::max(bytes * 2, (size_t)4096);
-            FR_CUDA(ctx, cudaMalloc(&w->d_chunks, cap));
+            FR_CUDA(ctx, fr::dev_malloc(&w->d_chunks, cap));
             FR_CUDA(ctx, cudaMallocHost(&w->h_chunks, cap));
             w->chunks_cap = cap;
         }

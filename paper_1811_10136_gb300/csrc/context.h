@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -124,9 +125,28 @@ struct CachedGraph {
     uint64_t last_use = 0;
 };
 
+// Host-side fault injection (fr_debug_fail_allocations): the library's next
+// `skip` device allocations proceed, the `fail` after them fail as a full
+// device's would.
+std::atomic<int> &alloc_skip();   // api.cu
+std::atomic<int> &alloc_fail();   // api.cu
+inline bool take_one(std::atomic<int> &c) {
+    int n = c.load();
+    while (n > 0 && !c.compare_exchange_weak(n, n - 1)) {
+    }
+    return n > 0;
+}
+inline cudaError_t dev_malloc(void **p, size_t bytes) {
+    if (!take_one(alloc_skip()) && take_one(alloc_fail())) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 inline cudaError_t dev_alloc(T **p, size_t count) {
-    return cudaMalloc((void **)p, count * sizeof(T) + 16);
+    return dev_malloc((void **)p, count * sizeof(T) + 16);
 }
 
 }  // namespace fr

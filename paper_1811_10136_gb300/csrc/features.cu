@@ -598,7 +598,7 @@ fr_status feat_ensure_counts(fr_ctx *ctx) {
     if (!ctx->feat) ctx->feat = new FeatWorkspace();
     FeatWorkspace *w = ctx->feat;
     if (!w->count) {
-        FR_CUDA(ctx, cudaMalloc((void **)&w->count, 4 * sizeof(int)));
+        FR_CUDA(ctx, fr::dev_malloc((void **)&w->count, 4 * sizeof(int)));
         FR_CUDA(ctx, cudaMemsetAsync(w->count, 0, 4 * sizeof(int), ctx->stream));
     }
     if (!w->h_count) FR_CUDA(ctx, cudaMallocHost((void **)&w->h_count, 4 * sizeof(int)));
@@ -616,7 +616,7 @@ fr_status feat_ensure(fr_ctx *ctx, uint32_t cap, int stride, long long list_len)
         cudaFree(w->list);
         w->list = nullptr;
         w->list_cap = 0;
-        FR_CUDA(ctx, cudaMalloc((void **)&w->list, (size_t)list_len * sizeof(int)));
+        FR_CUDA(ctx, fr::dev_malloc((void **)&w->list, (size_t)list_len * sizeof(int)));
         w->list_cap = (size_t)list_len;
     }
     if (bytes > w->rec_bytes) {
@@ -624,7 +624,7 @@ fr_status feat_ensure(fr_ctx *ctx, uint32_t cap, int stride, long long list_len)
         w->rec = nullptr;
         w->rec_bytes = 0;
         w->cap = 0;
-        FR_CUDA(ctx, cudaMalloc((void **)&w->rec, bytes));
+        FR_CUDA(ctx, fr::dev_malloc((void **)&w->rec, bytes));
         w->rec_bytes = bytes;
     }
     if (w->cap != cap || w->stride != stride) {

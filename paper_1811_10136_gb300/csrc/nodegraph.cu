@@ -64,7 +64,7 @@ namespace {
 
 template <typename T>
 cudaError_t up(T **d, const std::vector<T> &h) {
-    cudaError_t e = cudaMalloc((void **)d, std::max<size_t>(1, h.size()) * sizeof(T));
+    cudaError_t e = fr::dev_malloc((void **)d, std::max<size_t>(1, h.size()) * sizeof(T));
     if (e != cudaSuccess || h.empty()) return e;
     return cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
@@ -238,19 +238,19 @@ FR_API fr_status fr_nodegraph_create(fr_ctx *ctx, const float *d_Xref, const int
     chk(up(&g->diag_blk, diag));
     chk(up(&g->ent, ent));
     const size_t n6 = 6 * (size_t)K;
-    chk(cudaMalloc((void **)&g->blocks, (size_t)nnzb * 36 * sizeof(float)));
-    chk(cudaMalloc((void **)&g->blocks_d, (size_t)nnzb * 36 * sizeof(double)));
-    chk(cudaMalloc((void **)&g->g, n6 * sizeof(float)));
-    chk(cudaMalloc((void **)&g->node_dq, (size_t)K * 8 * sizeof(float)));
-    chk(cudaMalloc((void **)&g->stats, 4 * sizeof(double)));
-    chk(cudaMalloc((void **)&g->inliers, sizeof(unsigned long long)));
-    chk(cudaMalloc((void **)&g->node_T, (size_t)K * 16 * sizeof(double)));
-    chk(cudaMalloc((void **)&g->P, (size_t)K * 36 * sizeof(double)));
+    chk(fr::dev_malloc((void **)&g->blocks, (size_t)nnzb * 36 * sizeof(float)));
+    chk(fr::dev_malloc((void **)&g->blocks_d, (size_t)nnzb * 36 * sizeof(double)));
+    chk(fr::dev_malloc((void **)&g->g, n6 * sizeof(float)));
+    chk(fr::dev_malloc((void **)&g->node_dq, (size_t)K * 8 * sizeof(float)));
+    chk(fr::dev_malloc((void **)&g->stats, 4 * sizeof(double)));
+    chk(fr::dev_malloc((void **)&g->inliers, sizeof(unsigned long long)));
+    chk(fr::dev_malloc((void **)&g->node_T, (size_t)K * 16 * sizeof(double)));
+    chk(fr::dev_malloc((void **)&g->P, (size_t)K * 36 * sizeof(double)));
     for (double **v : {&g->x, &g->r, &g->z, &g->Ap, &g->p[0], &g->p[1]})
-        chk(cudaMalloc((void **)v, n6 * sizeof(double)));
-    chk(cudaMalloc((void **)&g->scal, 4 * sizeof(double)));
-    chk(cudaMalloc((void **)&g->partial, (size_t)g->grid_max * sizeof(double)));
-    chk(cudaMalloc((void **)&g->ticket, sizeof(int)));
+        chk(fr::dev_malloc((void **)v, n6 * sizeof(double)));
+    chk(fr::dev_malloc((void **)&g->scal, 4 * sizeof(double)));
+    chk(fr::dev_malloc((void **)&g->partial, (size_t)g->grid_max * sizeof(double)));
+    chk(fr::dev_malloc((void **)&g->ticket, sizeof(int)));
     if (e == cudaSuccess) e = cudaMemset(g->ticket, 0, sizeof(int));
     if (e != cudaSuccess) {
         free_model(g);

@@ -338,8 +338,8 @@ struct fr_server {
             map_cap = cap / sizeof(unsigned short);
             if (cudaMallocHost((void **)&h_tick[0], cap) != cudaSuccess ||
                 cudaMallocHost((void **)&h_tick[1], cap) != cudaSuccess ||
-                cudaMalloc((void **)&d_segs, map_cap * sizeof(Seg)) != cudaSuccess ||
-                cudaMalloc((void **)&d_map, cap) != cudaSuccess) {
+                fr::dev_malloc((void **)&d_segs, map_cap * sizeof(Seg)) != cudaSuccess ||
+                fr::dev_malloc((void **)&d_map, cap) != cudaSuccess) {
                 map_cap = 0;
                 h_tick_cap = 0;
                 return FR_ENOMEM;
@@ -571,7 +571,7 @@ FR_API fr_status fr_server_create(fr_ctx *ctx, size_t budget, int max_live, cons
     s->table_slots_total = (size_t)1 << top;
     s->tab_buddy.init(top);
     const size_t S = s->table_slots_total;
-    if (cudaMalloc((void **)&s->keys, table_bytes(S)) != cudaSuccess)
+    if (fr::dev_malloc((void **)&s->keys, table_bytes(S)) != cudaSuccess)
         return bail(FR_ENOMEM, "table arena");
     cudaMemsetAsync(s->keys, 0, table_bytes(S), s->stream);
     // byte arena
@@ -579,8 +579,8 @@ FR_API fr_status fr_server_create(fr_ctx *ctx, size_t budget, int max_live, cons
     while (((size_t)2 << btop) * kByteUnit <= budget - S * per_slot && btop < 40) ++btop;
     s->bytes_total = ((size_t)1 << btop) * kByteUnit;
     s->byte_buddy.init(btop);
-    if (cudaMalloc((void **)&s->bytes, s->bytes_total) != cudaSuccess) return bail(FR_ENOMEM, "byte arena");
-    if (cudaMalloc((void **)&s->d_slots, (size_t)max_live * sizeof(Slot)) != cudaSuccess)
+    if (fr::dev_malloc((void **)&s->bytes, s->bytes_total) != cudaSuccess) return bail(FR_ENOMEM, "byte arena");
+    if (fr::dev_malloc((void **)&s->d_slots, (size_t)max_live * sizeof(Slot)) != cudaSuccess)
         return bail(FR_ENOMEM, "slot table");
     // pinned per-slot staging
     s->stage_up = align256(sizeof(RigidJob)) + align256(sizeof(DeviceState)) +

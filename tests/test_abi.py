@@ -58,6 +58,16 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.fr_ctx_kernel_launches(None) == 0
 
 
+def test_fault_injection_arguments(lib):
+    import paper_1811_10136_gb300 as fr
+    assert lib.fr_debug_fail_allocations(-1, 1) == 1      # FR_EINVAL
+    assert lib.fr_debug_fail_allocations(0, -1) == 1
+    with pytest.raises(fr.FilterRegError):
+        fr.debug_fail_allocations(-1, 1)
+    fr.debug_fail_allocations(3, 2)
+    fr.debug_fail_allocations(0, 0)                        # clears
+
+
 def test_no_device_reports_cuda_error(lib):
     import torch
     if torch.cuda.is_available():
