@@ -117,6 +117,17 @@ class fr_batch_item(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+# fr_batch_item as a numpy record (same offsets): the items of a call are
+# filled and read field by field for all items at once.
+_BATCH_ITEM_DTYPE = np.dtype({
+    "names": ["d_X", "M", "d_Y", "d_Yn", "N", "sigma_start", "sigma_end", "w", "T", "status"],
+    "formats": ["u8", "i8", "u8", "u8", "i8", "f4", "f4", "f4", ("f8", (16,)), "i4"],
+    "offsets": [getattr(fr_batch_item, f).offset for f in
+                ("d_X", "M", "d_Y", "d_Yn", "N", "sigma_start", "sigma_end", "w", "T", "status")],
+    "itemsize": ctypes.sizeof(fr_batch_item)})
+_EYE16 = np.eye(4).ravel()
+
+
 class fr_tune_params(ctypes.Structure):
     _fields_ = [("step_points_per_thread", ctypes.c_int32), ("build_points_per_thread", ctypes.c_int32),
                 ("table_slots_x2", ctypes.c_int32), ("serve_points_per_thread", ctypes.c_int32)]
@@ -578,25 +589,32 @@ class Context:
     def _batch_items(self, pairs, sigmas, ws, T0s, host, o):
         n = len(pairs)
         items = (fr_batch_item * n)()
+        a = np.frombuffer(items, dtype=_BATCH_ITEM_DTYPE)   # the same memory, by field
         keep = []
+        ptr = np.zeros((n, 3), np.uint64)
+        rows = np.zeros((n, 2), np.int64)
         for b, (X, Y, Yn) in enumerate(pairs):
-            it = items[b]
             if host:
-                arrs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None for a in (X, Y, Yn)]
+                arrs = [np.ascontiguousarray(a_, dtype=np.float32) if a_ is not None else None for a_ in (X, Y, Yn)]
                 keep.append(arrs)
-                it.d_X, it.d_Y = arrs[0].ctypes.data, arrs[1].ctypes.data
-                it.d_Yn = arrs[2].ctypes.data if arrs[2] is not None else None
-                it.M, it.N = arrs[0].shape[0], arrs[1].shape[0]
+                ptr[b] = (arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data if arrs[2] is not None else 0)
+                rows[b] = (arrs[0].shape[0], arrs[1].shape[0])
             else:
-                it.d_X, it.d_Y = _dev_ptr(X, "X"), _dev_ptr(Y, "Y")
-                it.d_Yn = _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None
-                it.M, it.N = X.shape[0], Y.shape[0]
-            s0, s1 = sigmas[b] if sigmas is not None else (o.sigma_start, o.sigma_end)
-            it.sigma_start, it.sigma_end = float(s0), float(s1)
-            it.w = float(ws[b]) if ws is not None else o.w
-            T = _pose(T0s[b] if T0s is not None else None)
-            for i in range(16):
-                it.T[i] = T.ravel()[i]
+                ptr[b] = (_dev_ptr(X, "X"), _dev_ptr(Y, "Y"),
+                          _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else 0)
+                rows[b] = (X.shape[0], Y.shape[0])
+        a["d_X"], a["d_Y"], a["d_Yn"] = ptr[:, 0], ptr[:, 1], ptr[:, 2]
+        a["M"], a["N"] = rows[:, 0], rows[:, 1]
+        if sigmas is not None:
+            sg = np.asarray(sigmas, dtype=np.float64).reshape(n, 2)
+            a["sigma_start"], a["sigma_end"] = sg[:, 0], sg[:, 1]
+        else:
+            a["sigma_start"], a["sigma_end"] = o.sigma_start, o.sigma_end
+        a["w"] = np.asarray(ws, dtype=np.float64).reshape(n) if ws is not None else o.w
+        if T0s is None:
+            a["T"] = _EYE16
+        else:
+            a["T"] = np.stack([_pose(T) for T in T0s]).reshape(n, 16)
         return items, keep
 
     def register_rigid_batch(self, pairs, sigmas=None, ws=None, T0s=None, host=False, **opts):
@@ -615,11 +633,10 @@ class Context:
         st = f(self._h, items, n, ctypes.byref(o), reps)
         if st != FR_OK and not any(items[b].status != FR_OK for b in range(n)):
             self._check(st, "fr_register_rigid_batch")   # the call itself failed
-        out = []
-        for b in range(n):
-            T = np.array(items[b].T[:], dtype=np.float64).reshape(4, 4)
-            out.append((T, _report(reps[b]), int(items[b].status)))
-        return out
+        a = np.frombuffer(items, dtype=_BATCH_ITEM_DTYPE)
+        T = a["T"].reshape(n, 4, 4).copy()
+        status = a["status"].tolist()
+        return [(T[b], _report(reps[b]), status[b]) for b in range(n)]
 
     def gauss_transform(self, X, Y, Yn=None, sigma=0.02, T=None):
         """Exact E-step sums at T X (every observation, no lattice): (M, 4)

@@ -480,18 +480,35 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
         // Merge runs of equal keys across neighbouring lanes: a segmented
         // inclusive scan within 8-lane chunks (three shuffle steps, lane
         // order) leaves each run's sum at its last lane, which alone inserts
-        // the key and issues the atomics.  One vertex at a time: only its
-        // seven sums are live (holding all four vertices' sums for a joint
-        // four-probe insert spilled more than the overlapped probes saved).
+        // the key and issues the atomics.  First the runs of all four
+        // vertices (head bits by ballot) and the inserts of this lane's run
+        // tails, their probes and claims in flight together (insert4); then
+        // the sums one vertex at a time, so that only its seven sums are live
+        // (holding all four vertices' sums spilled more than overlapping
+        // their probes saved).
         int sl[kD];
         int mask = 0;
+        unsigned hd[kD];
+        unsigned want = 0;
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
             const unsigned long long key = valid ? sx.key[k] : kEmpty;
             const unsigned long long prev = __shfl_up_sync(kFull, key, 1);
-            const unsigned heads = __ballot_sync(kFull, (lane & 7) == 0 || prev != key);
+            hd[k] = __ballot_sync(kFull, (lane & 7) == 0 || prev != key);
+            const bool tail = lane == 31 || ((hd[k] >> (lane + 1)) & 1u);
+            want |= (valid && tail) ? 1u << k : 0u;
+        }
+        {
+            unsigned cl;
+            insert4(t.keys, t.mask, sx, want, t.max_probe, sl, cl);
+            mask = (int)cl;
+        }
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            const unsigned heads = hd[k];
             const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-            const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+            const bool tail = (want >> k) & 1u;
+            const unsigned long long key = valid ? sx.key[k] : kEmpty;
             const float b = valid ? sx.b[k] : 0.0f;
             float v[kCh];
             v[0] = b;
@@ -515,14 +532,10 @@ __device__ __forceinline__ void build_role(const RigidJob *__restrict__ job, Ite
                     if (lane - o >= head) v[c] += tv;
                 }
             }
-            sl[k] = -1;
-            if (valid && tail) {
-                bool c;
-                sl[k] = insert_key(t.keys, t.mask, key, t.max_probe, c);
+            if (tail) {
                 if (sl[k] < 0) {
                     bad |= kFlagCapacity;
                 } else {
-                    mask |= c ? (1 << k) : 0;
                     red_add4(rec_v0(t.keys, sl[k]), v[0], v[1], v[2], v[3]);
                     if (PT2PL) red_add4(rec_v1(t.keys, sl[k]), v[4], v[5], v[6], 0.f);
                     else if (SIG) atomicAdd(reinterpret_cast<float *>(rec_v1(t.keys, sl[k])), v[kCh - 1]);
@@ -787,8 +800,13 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
                                           int sig_next = 0) {
     __shared__ float P[12];
     __shared__ int last;
+    // The iteration's constants stay in shared memory and are re-read where
+    // used (volatile: not hoisted), instead of being held in registers
+    // across the slice, where the step runs short of them.
+    __shared__ IterParams s_ip;
+    if (threadIdx.x == 0) s_ip = *ipp;
+    const volatile IterParams *vip = &s_ip;
     load_pose(st->T, P);
-    const IterParams ip = *ipp;
     const int M = job->M;
     const int renorm = job->renormalize;
     const float4 *__restrict__ X = job->X;
@@ -799,7 +817,22 @@ __device__ __forceinline__ void step_role(const RigidJob *job, const IterParams 
         const float4 r = __ldg(X + i);
         const float x0 = apply_row(P, 0, r), x1 = apply_row(P, 1, r), x2 = apply_row(P, 2, r);
         Sums e;
+        IterParams ip;
+        ip.s1 = vip->s1;
+        ip.s2 = vip->s2;
+        ip.s3 = vip->s3;
+        if constexpr (ST != kStoreF32) {
+            ip.vscale = vip->vscale;
+            ip.inv_vscale = vip->inv_vscale;
+        }
+        if constexpr (ST != kStoreF32 || SIG) {
+            ip.ws1 = vip->ws1;
+            ip.ws2 = vip->ws2;
+            ip.ws3 = vip->ws3;
+        }
         if (!slice_point<PT2PL, ST, SIG>(t, x0, x1, x2, ip, e, bad)) continue;
+        ip.c_eff = vip->c_eff;
+        ip.inv_sigma2 = vip->inv_sigma2;
         point_terms<PT2PL, SIG>(x0, x1, x2, e, ip, renorm, [&](int v, float x) { acc.add(v, x); });
     }
     if (bad) atomicOr(&st->flags, bad);

@@ -151,6 +151,44 @@ __device__ __forceinline__ int insert_key(unsigned long long *keys, uint32_t mas
     return -1;
 }
 
+// insert_key for the four vertices of one point, those in `want`: the four
+// home-slot loads are in flight together, then the compare-and-swaps of the
+// empty ones together; only a collision walks on (insert_key from the next
+// slot, the remaining max_probe - 1 probes).  slot[k] = -1 for a vertex not
+// wanted or not placed; bit k of *claimed set where this call created it.
+__device__ __forceinline__ void insert4(unsigned long long *keys, uint32_t mask, const Simplex &sx,
+                                        unsigned want, uint32_t max_probe, int slot[kD],
+                                        unsigned &claimed) {
+    uint32_t s[kD];
+    unsigned long long cur[kD];
+    claimed = 0;
+#pragma unroll
+    for (int k = 0; k < kD; ++k) s[k] = slot_of(sx.key[k], mask);
+#pragma unroll
+    for (int k = 0; k < kD; ++k) cur[k] = ((want >> k) & 1u) ? __ldcg(rec_key(keys, s[k])) : 0ull;
+#pragma unroll
+    for (int k = 0; k < kD; ++k)
+        if (((want >> k) & 1u) && cur[k] == kEmpty) {
+            cur[k] = atomicCAS(rec_key(keys, s[k]), kEmpty, sx.key[k]);
+            if (cur[k] == kEmpty) {
+                claimed |= 1u << k;
+                cur[k] = sx.key[k];
+            }
+        }
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        slot[k] = -1;
+        if (!((want >> k) & 1u)) continue;
+        if (cur[k] == sx.key[k]) {
+            slot[k] = (int)s[k];
+        } else if (max_probe > 1) {
+            bool c;
+            slot[k] = insert_key(keys, mask, sx.key[k], max_probe - 1, c, (int)((s[k] + 1) & mask));
+            claimed |= c ? 1u << k : 0u;
+        }
+    }
+}
+
 // Slot of `key`, or -1 if absent.  The table must not change during the call
 // (read through the read-only path).  An insert never places a key more than
 // max_probe slots past its home, so a lookup stops there too: a full table
