@@ -417,9 +417,9 @@ typedef struct {
  * (int32, M) names each point's body (points sorted by body run faster);
  * the observation d_Y (N x 4, + normals d_Yn for FR_PT2PL).  Each iteration
  * slices the lattice over Y at x_i = T_b(i) x_i_ref, sums J^T J and J^T r
- * per body over the body twists (Algorithm 1, lines 1-4), assembles the
+ * per body over the body twists (Algorithm 1), assembles the
  * (6 + n_joints)^2 normal equations with the spatial velocity Jacobians
- * (lines 5-9: world-frame twists about the origin; identity for the root,
+ * (world-frame twists about the origin; identity for the root,
  * (a; p x a) for a joint of world axis a through world point p, on every
  * body under the joint), solves them in float64 and updates the root pose
  * and the joint angles (clamped).  root_T_inout (host double[16]) and

@@ -21,8 +21,8 @@
  *     moves x by dq a_w x (x - p_w));
  *   - zero otherwise.
  * The normal equations follow Algorithm 1: per-body J^T J and J^T r sums over
- * the body's points (lines 1-4), then A = sum_b J_sp^T (J^T J)_b J_sp and
- * g = sum_b J_sp^T (J^T r)_b (lines 5-9).  One Gauss-Newton step per EM
+ * the body's points first, then A = sum_b J_sp^T (J^T J)_b J_sp and
+ * g = sum_b J_sp^T (J^T r)_b.  One Gauss-Newton step per EM
  * iteration, solved by Cholesky; the root is updated by the exponential, the
  * joints additively and clamped to their limits.
  */
@@ -139,7 +139,7 @@ static double *obs_values(const float *Y, const float *Yn, int64_t N, int vdim)
     return V;
 }
 
-/* Per-body sums (Algorithm 1, lines 1-4) at the current pose, then the
+/* Per-body sums (Algorithm 1, first part) at the current pose, then the
  * assembled A (nd x nd) and g (nd).  Returns the number of inliers via
  * *inliers and the weighted cost via *cost. */
 static int normal_equations(const float *Xref, const int32_t *body, int64_t M, const or_kintree *t,

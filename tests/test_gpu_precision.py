@@ -178,7 +178,7 @@ def test_kahan_sums_with_16bit_storage(ctx, depth_oracle, storage):
 
 @pytest.mark.parametrize("storage", [1, 2])
 def test_nodegraph_16bit_storage(ctx, storage):
-    # The height-field node graph (configs[3] shape: ~250k points, 1,000
+    # The height-field node graph (the benchmark's shape: ~250k points, 1,000
     # nodes, sigma 2 cm, 10 EM x 20 PCG, lambda 10) with 16-bit lattice
     # records against the float32 records.  Each target moves by at most
     # e = 6 u R; the regularised least-squares fit of the node poses to the
