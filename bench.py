@@ -541,6 +541,24 @@ def run_ours(args):
             else:
                 entry["max_joint_diff_deg_vs_f32"] = round(float(np.degrees(np.abs(q - res32).max())), 5)
             articulated[name] = entry
+        # the same model and workload, 16 registrations per call
+        # (fr_register_articulated_batch: concurrent streams)
+        bpairs = [ap] + [synth.articulated_pair(args.seed + 1 + s, tree=ap.tree) for s in range(15)]
+        bitems = [(dev(p.Xref), torch.from_numpy(p.body.astype(np.int32)).cuda(), dev(p.Y), None, None, None)
+                  for p in bpairs]
+        bopts = dict(iters=ART_ITERS, sigma_start=ART_SIGMA, sigma_end=ART_SIGMA, w=W_OUT)
+        brun = lambda: ctx.register_articulated_batch(bitems, ap.tree, **bopts)
+        for _ in range(max(1, args.warmup)):
+            brun()
+        ms, bres = timed_steps(brun, args.steps)
+        R, q, _ = ctx.register_articulated(aX, abody, ap.tree, aY, None, **bopts)
+        articulated["batched"] = {
+            "registrations_per_call": len(bpairs),
+            "value": round(ART_ITERS * len(bpairs) * args.steps / (sum(ms) / 1000.0), 1), "unit": UNIT,
+            "ms_per_call": round(statistics.mean(ms), 4),
+            "failed": sum(1 for r in bres if r[3] != 0),
+            "max_joint_diff_deg_vs_single": round(float(np.degrees(np.abs(bres[0][1] - q).max())), 5),
+            "note": "fr_register_articulated_batch, up to 16 registrations in flight on their own streams"}
 
     # ---- node-graph registration (Section 5.2): ~250k points, 1,000 nodes ---
     nodegraph = None

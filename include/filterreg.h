@@ -433,6 +433,44 @@ FR_API fr_status fr_register_articulated(fr_ctx *ctx, const float *d_Xref, const
                                          double root_T_inout[16], double *q_inout,
                                          fr_report *report);
 
+/* ---- batched articulated registration ----------------------------------------
+ * One registration of a batched articulated call: clouds as for
+ * fr_register_articulated (device pointers), the initial root pose in
+ * root_T (row-major, replaced by the result) and the joint angles in the
+ * caller's host array q (double[n_joints], replaced by the result); status
+ * is written by the call. */
+typedef struct fr_articulated_item {
+    const float *d_Xref;    /* M x 4, in the bodies' frames */
+    const int32_t *d_body;  /* M, body of each point */
+    int64_t M;
+    const float *d_Y;       /* N x 4 */
+    const float *d_Yn;      /* N x 4 normals (FR_PT2PL) or NULL */
+    int64_t N;
+    double root_T[16];      /* in: initial root pose; out: result */
+    double *q;              /* host double[n_joints]: in initial, out result */
+    int32_t status;         /* out: FR_OK or this item's failure */
+} fr_articulated_item;
+
+#define FR_ART_BATCH_MAX 4096 /* items per call */
+#define FR_ART_CONCURRENT 16  /* registrations in flight together */
+
+/* fr_register_articulated_batch: n_items articulated registrations of one
+ * kinematic tree (Section 5.1, Algorithm 1) with the same options, each
+ * exactly as fr_register_articulated would run it, up to FR_ART_CONCURRENT
+ * of them at once, each on a stream of its own owned by ctx (created on
+ * first use, destroyed with ctx), so that one registration's serial solve
+ * overlaps the others' point work.  The items' streams start after the work
+ * queued on ctx's stream when the call is made.  An item whose table
+ * overflows is rerun alone at the safe size.  Returns FR_OK when every item
+ * succeeded, else the first failing item's status (its pose and angles are
+ * left as given; items[b].status tells each); reports (n_items, may be NULL)
+ * receive each item's report.  FR_EINVAL for invalid arguments (checked
+ * before any work), FR_ENOTSUPPORTED as fr_register_articulated.
+ * Synchronises the items' streams. */
+FR_API fr_status fr_register_articulated_batch(fr_ctx *ctx, const fr_kintree *tree,
+                                               fr_articulated_item *items, int32_t n_items,
+                                               const fr_options *opt, fr_report *reports);
+
 /* ---- batched rigid registration ---------------------------------------------
  * One registration of a batch.  Clouds as for fr_register_rigid (device
  * pointers for fr_register_rigid_batch, host pointers for

@@ -43,8 +43,10 @@ EXPORTED = [
     "fr_register_nodegraph", "fr_nodegraph_system", "fr_nodegraph_warp",
     "fr_feature_embed", "fr_estep_features", "fr_gauss_transform_features",
     "fr_rigid_normal_equations", "fr_rigid_solve_update", "fr_em_sharded", "fr_register_rigid_sharded",
-    "fr_debug_fail_allocations",
+    "fr_debug_fail_allocations", "fr_register_articulated_batch",
 ]
+FR_ART_BATCH_MAX = 4096
+FR_ART_CONCURRENT = 16
 FR_NE_VALS = 30
 # fr_ne_fn and fr_allreduce_fn of include/filterreg.h
 NE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_float,
@@ -128,6 +130,13 @@ _BATCH_ITEM_DTYPE = np.dtype({
 _EYE16 = np.eye(4).ravel()
 
 
+class fr_articulated_item(ctypes.Structure):
+    _fields_ = [("d_Xref", ctypes.c_void_p), ("d_body", ctypes.c_void_p), ("M", ctypes.c_int64),
+                ("d_Y", ctypes.c_void_p), ("d_Yn", ctypes.c_void_p), ("N", ctypes.c_int64),
+                ("root_T", ctypes.c_double * 16), ("q", ctypes.POINTER(ctypes.c_double)),
+                ("status", ctypes.c_int32)]
+
+
 class fr_tune_params(ctypes.Structure):
     _fields_ = [("step_points_per_thread", ctypes.c_int32), ("build_points_per_thread", ctypes.c_int32),
                 ("table_slots_x2", ctypes.c_int32), ("serve_points_per_thread", ctypes.c_int32)]
@@ -204,6 +213,8 @@ def load(build_if_missing: bool = True):
     L.fr_register_rigid_batch_host.argtypes = L.fr_register_rigid_batch.argtypes
     L.fr_register_articulated.argtypes = [_vp, _vp, _vp, _i64, ctypes.POINTER(fr_kintree), _vp, _vp, _i64,
                                           ctypes.POINTER(fr_options), _f64p, _f64p, ctypes.POINTER(fr_report)]
+    L.fr_register_articulated_batch.argtypes = [_vp, ctypes.POINTER(fr_kintree), ctypes.POINTER(fr_articulated_item),
+                                                ctypes.c_int32, ctypes.POINTER(fr_options), ctypes.POINTER(fr_report)]
     L.fr_estep_noalloc.argtypes = [_vp, _i64, _vp, _vp, _i64, ctypes.c_float, _f64p, _vp, _vp]
     L.fr_server_create.argtypes = [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(fr_options),
                                    ctypes.POINTER(_vp)]
@@ -585,6 +596,39 @@ class Context:
         del keep
         self._check(r, "fr_register_articulated")
         return R, q, _report(rep)
+
+    def register_articulated_batch(self, items, tree, **opts):
+        """fr_register_articulated_batch: several articulated registrations of
+        one tree, run concurrently.  items: list of (Xref, body, Y, Yn,
+        root_T0, q0) -- CUDA tensors as for register_articulated, Yn, root_T0
+        and q0 may be None.  Returns a list of (root_T (4,4), q (nj,), Report,
+        status) per item; raises if a call-level argument is invalid."""
+        import torch
+        L = load()
+        o = options(**opts)
+        st, keep = kintree(tree)
+        n = len(items)
+        arr = (fr_articulated_item * n)()
+        qs = []
+        reps = (fr_report * n)()
+        for b, (Xref, body, Y, Yn, R0, q0) in enumerate(items):
+            if not (isinstance(body, torch.Tensor) and body.is_cuda and body.dtype == torch.int32
+                    and body.is_contiguous() and body.shape[0] == Xref.shape[0]):
+                raise TypeError("body must be a contiguous int32 CUDA tensor with one entry per model point")
+            it = arr[b]
+            it.d_Xref, it.d_body, it.M = _dev_ptr(Xref, "Xref"), body.data_ptr(), Xref.shape[0]
+            it.d_Y, it.N = _dev_ptr(Y, "Y"), Y.shape[0]
+            it.d_Yn = _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else None
+            it.root_T[:] = _pose(R0).ravel().tolist()
+            q = np.ascontiguousarray(np.zeros(st.n_joints) if q0 is None else q0, dtype=np.float64).copy()
+            qs.append(q)
+            it.q = q.ctypes.data_as(_f64p) if q.size else None
+        r = L.fr_register_articulated_batch(self._h, ctypes.byref(st), arr, n, ctypes.byref(o), reps)
+        del keep
+        if r != FR_OK and all(arr[b].status == FR_OK for b in range(n)):
+            self._check(r, "fr_register_articulated_batch")   # the call itself failed
+        return [(np.array(arr[b].root_T[:], dtype=np.float64).reshape(4, 4), qs[b], _report(reps[b]),
+                 int(arr[b].status)) for b in range(n)]
 
     def _batch_items(self, pairs, sigmas, ws, T0s, host, o):
         n = len(pairs)

@@ -601,6 +601,8 @@ FR_API fr_status fr_ctx_destroy(fr_ctx *ctx) {
     cudaFreeHost(ctx->h_job);
     cudaFreeHost(ctx->h_ip);
     cudaFreeHost(ctx->h_state);
+    for (fr_ctx *sub : ctx->subs) fr_ctx_destroy(sub);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return FR_OK;
 }

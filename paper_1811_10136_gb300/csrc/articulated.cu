@@ -21,6 +21,7 @@ struct ArtWorkspace {
     ArtState *d_state = nullptr;
     ArtJob *h_job = nullptr;
     ArtState *h_state = nullptr;
+    bool annealed = false;  // of the registration last enqueued
 };
 
 void free_art_workspace(fr_ctx *ctx) {
@@ -100,10 +101,12 @@ void host_fk(const ArtTree &t, const double *root_T, const double *q, ArtState &
     }
 }
 
-fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_body, int64_t M,
-                          const fr_kintree *tree, const float *d_Y, const float *d_Yn, int64_t N,
-                          const fr_options *opt, double root_T[16], double *q, fr_report *rep,
-                          bool safe) {
+// Everything of one registration on ctx's stream up to the final wait: the
+// job, the launches and the copies of the result to the pinned mirrors.
+// art_finish waits for them and hands the result out.
+fr_status art_enqueue(fr_ctx *ctx, const float *d_Xref, const int32_t *d_body, int64_t M,
+                      const fr_kintree *tree, const float *d_Y, const float *d_Yn, int64_t N,
+                      const fr_options *opt, const double root_T[16], const double *q, bool safe) {
     const int pt2pl = opt->residual == FR_PT2PL;
     if (!ctx->art) ctx->art = new ArtWorkspace();
     ArtWorkspace *w = ctx->art;
@@ -122,6 +125,7 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
         tab[i].max_probe = table_probe_limit(cap, safe);
     }
     const bool annealed = fill_iter_params(opt, M, N, ctx->h_ip);
+    w->annealed = annealed;
 
     // ---- job and initial state ---------------------------------------------
     ArtJob &J = *w->h_job;
@@ -240,7 +244,15 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
     if (opt->iters > 0)
         FR_CUDA(ctx, copy_async(ctx, ctx->h_ip, ctx->d_ip, opt->iters * sizeof(IterParams),
                                 cudaMemcpyDeviceToHost));
+    return FR_OK;
+}
+
+fr_status art_finish(fr_ctx *ctx, const fr_options *opt, double root_T[16], double *q, fr_report *rep) {
+    ArtWorkspace *w = ctx->art;
     FR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const ArtState &S = *w->h_state;
+    const ArtTree &T = w->h_job->tree;
+    const bool annealed = w->annealed;
     const DeviceState &ds = S.ds;
     FR_TRY(check_flags(ctx, ds.flags));
     for (int k = 0; k < 16; ++k) root_T[k] = S.root_T[k];
@@ -260,6 +272,49 @@ fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_bod
     return FR_OK;
 }
 
+fr_status run_articulated(fr_ctx *ctx, const float *d_Xref, const int32_t *d_body, int64_t M,
+                          const fr_kintree *tree, const float *d_Y, const float *d_Yn, int64_t N,
+                          const fr_options *opt, double root_T[16], double *q, fr_report *rep,
+                          bool safe) {
+    FR_TRY(art_enqueue(ctx, d_Xref, d_body, M, tree, d_Y, d_Yn, N, opt, root_T, q, safe));
+    return art_finish(ctx, opt, root_T, q, rep);
+}
+
+fr_status validate_articulated(fr_ctx *ctx, const fr_options *opt, const fr_kintree *tree) {
+    FR_TRY(validate_options(ctx, opt));
+    if (opt->update_sigma) return ctx->fail(FR_ENOTSUPPORTED, "the sigma update is implemented for rigid registration");
+    if (opt->blur || opt->kahan)
+        return ctx->fail(FR_ENOTSUPPORTED, "articulated registration supports neither blur nor Kahan sums");
+    return validate_tree(ctx, tree);
+}
+
+fr_status validate_articulated_clouds(fr_ctx *ctx, const fr_options *opt, const float *d_Xref,
+                                      const int32_t *d_body, int64_t M, const float *d_Y, const float *d_Yn,
+                                      int64_t N) {
+    FR_TRY(validate_cloud(ctx, d_Xref, M, "d_Xref"));
+    FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));
+    if (!d_body) return ctx->fail(FR_EINVAL, "d_body is NULL");
+    if (opt->residual == FR_PT2PL) FR_TRY(validate_cloud(ctx, d_Yn, N, "d_Yn (normals, required for FR_PT2PL)"));
+    return FR_OK;
+}
+
+// A context of ctx's device with a non-blocking stream of its own, sharing
+// ctx's launch-shape table and workspace limit.
+fr_status make_sub(fr_ctx *ctx, fr_ctx **out) {
+    fr_ctx *sub = new fr_ctx();
+    sub->device = ctx->device;
+    sub->num_sms = ctx->num_sms;
+    sub->ws_limit = ctx->ws_limit;
+    for (int c = 0; c < kTuneClasses; ++c) sub->tune[c] = ctx->tune[c];
+    if (cudaStreamCreateWithFlags(&sub->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete sub;
+        return ctx->cuda(cudaGetLastError(), "stream of a concurrent registration");
+    }
+    sub->own_stream = true;
+    *out = sub;
+    return FR_OK;
+}
+
 }  // namespace
 
 extern "C" FR_API fr_status fr_register_articulated(fr_ctx *ctx, const float *d_Xref,
@@ -270,15 +325,8 @@ extern "C" FR_API fr_status fr_register_articulated(fr_ctx *ctx, const float *d_
                                                     double *q_inout, fr_report *report) {
     fr::NvtxRange nvtx_("fr_register_articulated");
     if (!ctx) return FR_EINVAL;
-    FR_TRY(validate_options(ctx, opt));
-    if (opt->update_sigma) return ctx->fail(FR_ENOTSUPPORTED, "the sigma update is implemented for rigid registration");
-    if (opt->blur || opt->kahan)
-        return ctx->fail(FR_ENOTSUPPORTED, "articulated registration supports neither blur nor Kahan sums");
-    FR_TRY(validate_tree(ctx, tree));
-    FR_TRY(validate_cloud(ctx, d_Xref, M, "d_Xref"));
-    FR_TRY(validate_cloud(ctx, d_Y, N, "d_Y"));
-    if (!d_body) return ctx->fail(FR_EINVAL, "d_body is NULL");
-    if (opt->residual == FR_PT2PL) FR_TRY(validate_cloud(ctx, d_Yn, N, "d_Yn (normals, required for FR_PT2PL)"));
+    FR_TRY(validate_articulated(ctx, opt, tree));
+    FR_TRY(validate_articulated_clouds(ctx, opt, d_Xref, d_body, M, d_Y, d_Yn, N));
     if (!root_T_inout || (tree->n_joints && !q_inout)) return ctx->fail(FR_EINVAL, "pose outputs are NULL");
     for (int k = 0; k < 16; ++k)
         if (!std::isfinite(root_T_inout[k])) return ctx->fail(FR_EINVAL, "root pose is not finite");
@@ -293,4 +341,84 @@ extern "C" FR_API fr_status fr_register_articulated(fr_ctx *ctx, const float *d_
     std::copy(q0.begin(), q0.end(), q_inout);
     return run_articulated(ctx, d_Xref, d_body, M, tree, d_Y, d_Yn, N, opt, root_T_inout, q_inout,
                            report, true);
+}
+
+extern "C" FR_API fr_status fr_register_articulated_batch(fr_ctx *ctx, const fr_kintree *tree,
+                                                          fr_articulated_item *items, int32_t n_items,
+                                                          const fr_options *opt, fr_report *reports) {
+    fr::NvtxRange nvtx_("fr_register_articulated_batch");
+    if (!ctx) return FR_EINVAL;
+    FR_TRY(validate_articulated(ctx, opt, tree));
+    if (!items || n_items < 1 || n_items > FR_ART_BATCH_MAX)
+        return ctx->fail(FR_EINVAL, "need 1..%d items", FR_ART_BATCH_MAX);
+    for (int b = 0; b < n_items; ++b) {
+        const fr_articulated_item &it = items[b];
+        FR_TRY(validate_articulated_clouds(ctx, opt, it.d_Xref, it.d_body, it.M, it.d_Y, it.d_Yn, it.N));
+        if (tree->n_joints && !it.q) return ctx->fail(FR_EINVAL, "item %d: q is NULL", b);
+        for (int k = 0; k < 16; ++k)
+            if (!std::isfinite(it.root_T[k])) return ctx->fail(FR_EINVAL, "item %d: root pose is not finite", b);
+    }
+    cudaSetDevice(ctx->device);
+    while ((int)ctx->subs.size() < std::min<int>(n_items, FR_ART_CONCURRENT)) {
+        fr_ctx *sub = nullptr;
+        FR_TRY(make_sub(ctx, &sub));
+        ctx->subs.push_back(sub);
+    }
+    // the items' clouds were written in ctx's stream order: every item's
+    // stream starts after what ctx's stream holds now
+    cudaEvent_t ready;
+    FR_CUDA(ctx, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ready, ctx->stream);
+    fr_status first = FR_OK;
+    const int nj = tree->n_joints;
+    for (int w0 = 0; w0 < n_items && e == cudaSuccess; w0 += FR_ART_CONCURRENT) {
+        const int w1 = std::min(n_items, w0 + FR_ART_CONCURRENT);
+        std::vector<fr_status> st(w1 - w0, FR_OK);
+        std::vector<int64_t> l0(w1 - w0), h0(w1 - w0), d0(w1 - w0);
+        for (int b = w0; b < w1; ++b) {
+            fr_ctx *sub = ctx->subs[b - w0];
+            l0[b - w0] = sub->launches;
+            h0[b - w0] = sub->h2d_bytes;
+            d0[b - w0] = sub->d2h_bytes;
+            if (cudaStreamWaitEvent(sub->stream, ready, 0) != cudaSuccess) {
+                st[b - w0] = sub->cuda(cudaGetLastError(), "stream wait");
+                continue;
+            }
+            const fr_articulated_item &it = items[b];
+            st[b - w0] = art_enqueue(sub, it.d_Xref, it.d_body, it.M, tree, it.d_Y, it.d_Yn, it.N, opt,
+                                     it.root_T, it.q, false);
+        }
+        for (int b = w0; b < w1; ++b) {
+            fr_ctx *sub = ctx->subs[b - w0];
+            fr_articulated_item &it = items[b];
+            fr_report *rep = reports ? reports + b : nullptr;
+            double R0[16];
+            std::vector<double> q0(it.q, it.q + nj);
+            std::memcpy(R0, it.root_T, sizeof R0);
+            fr_status s = st[b - w0];
+            if (s == FR_OK) s = art_finish(sub, opt, it.root_T, it.q, rep);
+            if (s == FR_ECAPACITY) {  // this item alone again, at the safe table size
+                std::memcpy(it.root_T, R0, sizeof R0);
+                std::copy(q0.begin(), q0.end(), it.q);
+                s = run_articulated(sub, it.d_Xref, it.d_body, it.M, tree, it.d_Y, it.d_Yn, it.N, opt,
+                                    it.root_T, it.q, rep, true);
+            }
+            if (s != FR_OK) {
+                cudaStreamSynchronize(sub->stream);
+                std::memcpy(it.root_T, R0, sizeof R0);
+                std::copy(q0.begin(), q0.end(), it.q);
+                if (first == FR_OK) {
+                    first = s;
+                    ctx->err = "item " + std::to_string(b) + ": " + sub->err;
+                }
+            }
+            it.status = s;
+            ctx->launches += sub->launches - l0[b - w0];
+            ctx->h2d_bytes += sub->h2d_bytes - h0[b - w0];
+            ctx->d2h_bytes += sub->d2h_bytes - d0[b - w0];
+        }
+    }
+    cudaEventDestroy(ready);
+    if (e != cudaSuccess) return ctx->cuda(e, "event record");
+    return first;
 }

@@ -204,6 +204,11 @@ struct fr_ctx {
     fr::BatchWorkspace *batch = nullptr;  // batched-registration workspace (batch.cu)
     fr::ArtWorkspace *art = nullptr;      // articulated-registration workspace (articulated.cu)
     fr::FeatWorkspace *feat = nullptr;    // feature-space lattice table (features.cu)
+    // Contexts of the concurrent registrations of a batched articulated call,
+    // each with a stream of its own (made on first use, destroyed with this
+    // context); own_stream marks a context that created its stream.
+    std::vector<fr_ctx *> subs;
+    bool own_stream = false;
 
     // per-kernel profiling: event pairs around each launch of a plan
     int profiling = 0;

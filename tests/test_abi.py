@@ -56,6 +56,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.fr_ctx_create(0, None, None) == 1          # FR_EINVAL
     assert lib.fr_register_rigid(None, None, 0, None, None, 0, None, None, None) == 1
     assert lib.fr_ctx_kernel_launches(None) == 0
+    assert lib.fr_register_articulated_batch(None, None, None, 1, None, None) == 1
 
 
 def test_fault_injection_arguments(lib):

@@ -152,3 +152,69 @@ def test_joint_limits_clamp_alike(ctx, orc):
     assert (np.abs(qg) <= lim).all() and (np.abs(qo) <= lim).all()
     dr, dt, dq = diffs(Rg, qg, Ro, qo)
     assert dr < 1e-3 and dt < 1e-4 and dq < 1e-3, (dr, dt, dq)
+
+
+# ---- batched articulated registration (concurrent streams) ------------------
+
+def batch_items(pairs, residual, poses=None):
+    return [(dev(p.Xref), dev(p.body, np.int32), dev(p.Y), dev(p.Yn) if residual else None,
+             None if poses is None else poses[b][0], None if poses is None else poses[b][1])
+            for b, p in enumerate(pairs)]
+
+
+@pytest.mark.parametrize("residual", [0, 1])
+def test_batch_equals_single_registrations(ctx, orc, residual):
+    # Five registrations of one tree in one call: each equals the same
+    # registration run alone, and the first matches the oracle.
+    tree = synth.random_kintree(20)
+    pairs = [synth.articulated_pair(30 + s, n_points=6000, max_joint_deg=5, tree=tree) for s in range(5)]
+    kw = dict(residual=residual, iters=6, sigma_start=f32(0.03), sigma_end=f32(0.01), w=f32(0.1))
+    items = batch_items(pairs, residual)
+    out = ctx.register_articulated_batch(items, tree, **kw)
+    for (Rb, qb, rb, st), it in zip(out, items):
+        assert st == 0
+        Rs, qs, rs = ctx.register_articulated(it[0], it[1], tree, it[2], it[3], **kw)
+        dr, dt, dq = diffs(Rb, qb, Rs, qs)
+        assert dr < 1e-3 and dt < 1e-4 and dq < 1e-3, (dr, dt, dq)
+        assert rb.iters_run == rs.iters_run == 6 and rb.lattice_builds == rs.lattice_builds
+    p = pairs[0]
+    Ro, qo, ro = orc.register_articulated(p.Xref, p.body, tree, p.Y, p.Yn if residual else None,
+                                          sigma=f32(0.03), sigma_end=f32(0.01), w=f32(0.1), iters=6,
+                                          residual=residual)
+    dr, dt, dq = diffs(out[0][0], out[0][1], Ro, qo)
+    assert dr < 1e-3 and dt < 1e-4 and dq < 1e-3, (dr, dt, dq)
+
+
+def test_batch_more_items_than_streams(ctx):
+    # More items than registrations in flight (waves), with given initial
+    # poses and angles: each item as run alone from the same start.
+    import paper_1811_10136_gb300 as fr
+    tree = synth.random_kintree(21)
+    n = fr.FR_ART_CONCURRENT + 3
+    pairs = [synth.articulated_pair(50 + s, n_points=1500, max_joint_deg=5, tree=tree) for s in range(n)]
+    rng = np.random.default_rng(5)
+    poses = [(synth.make_T(synth.random_rotation(rng, np.radians(1.0)), rng.uniform(-0.002, 0.002, 3)),
+              rng.uniform(-0.02, 0.02, tree.nj)) for _ in range(n)]
+    kw = dict(residual=0, iters=3, sigma_start=f32(0.02), sigma_end=f32(0.02), w=f32(0.1))
+    items = batch_items(pairs, 0, poses)
+    launches0 = ctx.kernel_launches
+    out = ctx.register_articulated_batch(items, tree, **kw)
+    assert ctx.kernel_launches - launches0 == n * (3 + 2)   # first build, 3 iterations, final clear
+    for (Rb, qb, rb, st), it in zip(out, items):
+        assert st == 0
+        Rs, qs, rs = ctx.register_articulated(it[0], it[1], tree, it[2], None, root_T0=it[4], q0=it[5], **kw)
+        dr, dt, dq = diffs(Rb, qb, Rs, qs)
+        assert dr < 1e-3 and dt < 1e-4 and dq < 1e-3, (dr, dt, dq)
+
+
+def test_batch_rejects_bad_items_before_work(ctx):
+    import paper_1811_10136_gb300 as fr
+    tree = synth.random_kintree(22)
+    p = synth.articulated_pair(60, n_points=1000, tree=tree)
+    good = batch_items([p], 0)[0]
+    bad = good[:4] + (np.full((4, 4), np.nan), None)
+    launches0 = ctx.kernel_launches
+    with pytest.raises(fr.FilterRegError) as e:
+        ctx.register_articulated_batch([good, bad], tree, iters=2)
+    assert e.value.status == fr.FR_EINVAL
+    assert ctx.kernel_launches == launches0
