@@ -281,6 +281,15 @@ def _report(r: fr_report) -> Report:
                   r.last_sigma)
 
 
+def _host_ptr(a: np.ndarray) -> int:
+    """Address of a contiguous host array's data (the buffer protocol's
+    address is cheaper to take than ndarray.ctypes for a writable array)."""
+    try:
+        return ctypes.addressof(ctypes.c_char.from_buffer(a))
+    except (TypeError, ValueError, BufferError):
+        return a.ctypes.data
+
+
 def _dev_ptr(t, name, rows=None, cols=4):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
@@ -635,20 +644,24 @@ class Context:
         items = (fr_batch_item * n)()
         a = np.frombuffer(items, dtype=_BATCH_ITEM_DTYPE)   # the same memory, by field
         keep = []
-        ptr = np.zeros((n, 3), np.uint64)
-        rows = np.zeros((n, 2), np.int64)
-        for b, (X, Y, Yn) in enumerate(pairs):
+        px, py, pn, rm, rn = [], [], [], [], []
+        for X, Y, Yn in pairs:
             if host:
                 arrs = [np.ascontiguousarray(a_, dtype=np.float32) if a_ is not None else None for a_ in (X, Y, Yn)]
                 keep.append(arrs)
-                ptr[b] = (arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data if arrs[2] is not None else 0)
-                rows[b] = (arrs[0].shape[0], arrs[1].shape[0])
+                px.append(_host_ptr(arrs[0]))
+                py.append(_host_ptr(arrs[1]))
+                pn.append(_host_ptr(arrs[2]) if arrs[2] is not None else 0)
+                rm.append(arrs[0].shape[0])
+                rn.append(arrs[1].shape[0])
             else:
-                ptr[b] = (_dev_ptr(X, "X"), _dev_ptr(Y, "Y"),
-                          _dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else 0)
-                rows[b] = (X.shape[0], Y.shape[0])
-        a["d_X"], a["d_Y"], a["d_Yn"] = ptr[:, 0], ptr[:, 1], ptr[:, 2]
-        a["M"], a["N"] = rows[:, 0], rows[:, 1]
+                px.append(_dev_ptr(X, "X"))
+                py.append(_dev_ptr(Y, "Y"))
+                pn.append(_dev_ptr(Yn, "Yn", rows=Y.shape[0]) if Yn is not None else 0)
+                rm.append(X.shape[0])
+                rn.append(Y.shape[0])
+        a["d_X"], a["d_Y"], a["d_Yn"] = px, py, pn
+        a["M"], a["N"] = rm, rn
         if sigmas is not None:
             sg = np.asarray(sigmas, dtype=np.float64).reshape(n, 2)
             a["sigma_start"], a["sigma_end"] = sg[:, 0], sg[:, 1]
