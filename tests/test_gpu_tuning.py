@@ -124,6 +124,56 @@ def test_pinned_host_gather_equals_device(ctx):
         assert ra.last_inliers == rb.last_inliers
 
 
+def pinned(arrays):
+    import torch
+    ts = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory() if a is not None else None
+          for a in arrays]
+    return ts, tuple(t.numpy() if t is not None else None for t in ts)
+
+
+@pytest.mark.parametrize("storage,annealed", [(0, False), (1, True), (2, False)])
+def test_pinned_host_gather_storage_and_schedule(ctx, storage, annealed):
+    # Page-locked clouds gathered into the staging area, then registered with
+    # a fixed sigma (one build) and with 16-bit storage (two builds ahead).
+    pairs = views()[:3]
+    keep, hp = [], []
+    for p in pairs:
+        k, h = pinned((p.X, p.Y, p.Yn))
+        keep.append(k)
+        hp.append(h)
+    s1 = 0.02 if annealed else 0.04
+    opts = dict(residual=1, iters=5, sigma_start=0.04, sigma_end=s1, storage=storage)
+    a = ctx.register_rigid_batch([(dev(p.X), dev(p.Y), dev(p.Yn)) for p in pairs], **opts)
+    b = ctx.register_rigid_batch(hp, host=True, **opts)
+    for (Ta, ra, sa), (Tb, rb, sb) in zip(a, b):
+        assert sa == sb == 0
+        dr, dt = pose_diff(Ta, Tb)
+        assert dr < SAME_ROT and dt < SAME_TRANS, (dr, dt)
+        assert ra.lattice_builds == rb.lattice_builds
+
+
+def test_pinned_host_overflowing_item_reruns(ctx):
+    # An item of a page-locked batch whose table overflows is rerun from the
+    # staged clouds.
+    rng = np.random.default_rng(78)
+    X = np.zeros((3000, 4), np.float32)
+    X[:, :3] = rng.uniform(-1, 1, size=(3000, 3))
+    Y = X.copy()
+    Y[:, 0] += 0.001
+    good = synth.depth_frame_pair(310, W=96, H=72)
+    k1, h1 = pinned((good.X, good.Y))
+    k2, h2 = pinned((X, Y))
+    opts = dict(residual=0, iters=3, sigma_start=0.01, sigma_end=0.01)
+    out = ctx.register_rigid_batch([h1 + (None,), h2 + (None,)], host=True, **opts)
+    for (Xh, Yh), (T, rep, st) in zip([(good.X, good.Y), (X, Y)], out):
+        assert st == 0
+        Ts, rs = ctx.register_rigid(dev(Xh), dev(Yh), **opts)
+        assert rep.lattice_vertices == rs.lattice_vertices
+        dr, dt = pose_diff(T, Ts)
+        assert dr < SAME_ROT and dt < SAME_TRANS
+    assert out[1][1].lattice_vertices > 1.5 * 3000
+
+
 def test_autotune_installs_a_valid_shape():
     import paper_1811_10136_gb300 as fr
     c = fr.Context(0)
