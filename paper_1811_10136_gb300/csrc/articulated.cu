@@ -419,6 +419,9 @@ extern "C" FR_API fr_status fr_register_articulated_batch(fr_ctx *ctx, const fr_
         }
     }
     cudaEventDestroy(ready);
-    if (e != cudaSuccess) return ctx->cuda(e, "event record");
+    if (e != cudaSuccess) {
+        for (int b = 0; b < n_items; ++b) items[b].status = FR_ECUDA;
+        return ctx->cuda(e, "event record");
+    }
     return first;
 }
