@@ -192,3 +192,26 @@ def test_degenerate_when_nothing_overlaps(orc):
     T, rep = orc.register_rigid(p.X, Y, sigma=0.02, iters=3)
     np.testing.assert_array_equal(T, np.eye(4))
     assert rep.degenerate_iters == 3 and rep.last_inliers == 0
+
+
+def test_align_error_closed_forms():
+    # Eq. 22's mean distance between the estimated and the true placement of
+    # the model: a pure translation t moves every point by |t|; a rotation by
+    # theta about z moves a point at radius rho by 2 rho sin(theta / 2); equal
+    # poses give 0 and the empty model 0.
+    import math
+    import numpy as np
+    import oracle as orc
+    rng = np.random.default_rng(3)
+    X = np.zeros((500, 4), np.float32)
+    X[:, :3] = rng.normal(size=(500, 3))
+    Tt = np.eye(4)
+    Tt[:3, 3] = [0.3, -0.4, 1.2]
+    assert abs(orc.align_error(X, np.eye(4), Tt) - 1.3) < 1e-12
+    th = 0.7
+    Rz = np.eye(4)
+    Rz[:2, :2] = [[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]]
+    rho = np.hypot(X[:, 0].astype(np.float64), X[:, 1].astype(np.float64))
+    assert abs(orc.align_error(X, Rz, np.eye(4)) - np.mean(2 * rho * math.sin(th / 2))) < 1e-12
+    assert orc.align_error(X, Rz, Rz) == 0.0
+    assert orc.align_error(X[:0], Rz, np.eye(4)) == 0.0
