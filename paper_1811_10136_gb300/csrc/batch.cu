@@ -324,10 +324,11 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     unsigned short *bs_pro2 = (unsigned short *)(U + o_bs_pro2);
     unsigned short *bs_epi = (unsigned short *)(U + o_bs_epi);
     auto tab_of = [&](int b, int build) { return ip[b].annealed ? build % ntab : 0; };
-    // iteration k: every item's step k first, then the builds k+lead (annealed
-    // items), conversions k+1 (lead 2) and clears k-1: blocks are dispatched in
-    // index order, so the steps -- and their float64 tails -- start before the
-    // builds rather than the last items' steps ending the launch.
+    // iteration k: every item's step k first, then the clears k-1 and the
+    // builds k+lead (annealed items) and conversions k+1 (lead 2): blocks are
+    // dispatched in index order, so the steps -- and their float64 tails --
+    // start before the builds rather than the last items' steps ending the
+    // launch.
     // Phase q: 0 step, 1 build, 2 convert, 3 clear.
     auto seg_blocks = [&](int b, int q) {
         if (q == 0) return ip[b].gs;
@@ -336,11 +337,15 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
         if (q == 2) return lead == 2 ? ip[b].gv : -1;
         return ip[b].gc;
     };
+    // Dispatch order of the phases, measured on the batched depth-frame step:
+    // steps, clears, builds, conversions 98.0 us per launch; steps, builds,
+    // conversions, clears 99.8; builds first 103.9.
+    const int qord[4] = {0, 3, 1, 2};
     for (int k = 0; k < iters; ++k) {
         Seg *S = segs + (size_t)k * seg_per_iter;
         int si = 0, blk = 0;
-        for (int q = 0; q < 4; ++q)
-            for (int b = 0; b < n; ++b) {
+        for (int qi = 0; qi < 4; ++qi)
+            for (int b = 0, q = qord[qi]; b < n; ++b) {
                 const int nb = seg_blocks(b, q);
                 if (nb < 0) continue;
                 Seg sg{b, kRoleNone, 0, 0, blk, nb};
@@ -367,8 +372,8 @@ fr_status run_batch(fr_ctx *ctx, fr_batch_item *items, int n, const fr_options *
     }
     {
         int si = 0, blk = 0;
-        for (int q = 0; q < 4; ++q)
-            for (int b = 0; b < n; ++b) {
+        for (int qi = 0; qi < 4; ++qi)
+            for (int b = 0, q = qord[qi]; b < n; ++b) {
                 const int nb = seg_blocks(b, q);
                 if (nb < 0) continue;
                 for (int r = 0; r < nb; ++r) bs_iter[blk++] = (unsigned short)si;
