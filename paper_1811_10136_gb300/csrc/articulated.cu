@@ -364,6 +364,10 @@ extern "C" FR_API fr_status fr_register_articulated_batch(fr_ctx *ctx, const fr_
         FR_TRY(make_sub(ctx, &sub));
         ctx->subs.push_back(sub);
     }
+    for (fr_ctx *sub : ctx->subs) {  // the context's current shapes and limit
+        sub->ws_limit = ctx->ws_limit;
+        for (int c = 0; c < kTuneClasses; ++c) sub->tune[c] = ctx->tune[c];
+    }
     // the items' clouds were written in ctx's stream order: every item's
     // stream starts after what ctx's stream holds now
     cudaEvent_t ready;
